@@ -1,0 +1,183 @@
+/*
+ * findpts_gb.h -- C ABI of the GB300 point-location / interpolation library.
+ *
+ * The library finds, for query points x* in R^3, the computational
+ * coordinates q* = (subdomain, element e, r, s, t) on a set of overlapping
+ * hexahedral spectral-element meshes, and interpolates nodal fields there
+ * (arXiv 1811.04891, Sec. 2.1: findpts_setup / findpts / findpts_eval with a
+ * session discriminator and the distance-to-boundary owner rule).
+ *
+ * Conventions shared by every entry point
+ *  - N is the polynomial order, n = N + 1 GLL points per direction,
+ *    n3 = n^3 nodes per element, 1 <= N <= 15.
+ *  - Node (i,j,k) of an element sits at local index i + n*(j + n*k), i fastest.
+ *  - All array arguments are DEVICE pointers (cudaMalloc'd or from a device
+ *    allocator such as PyTorch's) on the current CUDA device unless stated.
+ *    The caller owns every pointer it passes; the library never frees them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Every call only enqueues work on that stream; outputs are valid once the
+ *    stream has been synchronised.  No call synchronises the device, except
+ *    fp_setup and workspace growth (see fp_reserve), which allocate.
+ *  - No C++ exception crosses this boundary.  Every call returns an
+ *    fp_status; the text of the last failure is kept in the handle and
+ *    returned by fp_last_error().
+ *  - A handle is not thread-safe: calls on one handle must be serialised by
+ *    the caller (they may use different streams, but one at a time; find
+ *    calls share the handle's workspace).
+ */
+#ifndef FINDPTS_GB_H
+#define FINDPTS_GB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fp_handle fp_handle;   /* opaque; owns all resident device state */
+
+typedef enum {
+    FP_OK = 0,
+    FP_ERR_INVALID_ARG = 1,   /* bad sizes, null required pointer, non-finite mesh  */
+    FP_ERR_OOM = 2,           /* device allocation failed                            */
+    FP_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed         */
+    FP_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up                  */
+    FP_ERR_NOT_SETUP = 5      /* null handle or handle without a mesh                */
+} fp_status;
+
+/* Per-point result codes (Sec. 2.1: found inside an element, on a border, or
+   not found within the mesh). */
+enum { FP_CODE_INSIDE = 0, FP_CODE_BORDER = 1, FP_CODE_NOT_FOUND = 2 };
+
+/* Arithmetic forms of fp_find. */
+enum {
+    FP_PREC_FP64 = 0,         /* every step in FP64                                      */
+    FP_PREC_MIXED = 1         /* FP32 seed and early Newton steps on element-local
+                                 coordinates, FP64 final Newton step(s), residual,
+                                 classification, owner comparison and eval          */
+};
+
+typedef struct {
+    int precision;              /* FP_PREC_FP64 (default) or FP_PREC_MIXED               */
+    double tol_accept;          /* INSIDE if ||x^e(r)-x*|| <= tol_accept*h_e (1e-12)     */
+    double tol_border;          /* BORDER if residual <= tol_border*h_e (1e-6)           */
+    int max_newton;             /* Newton iteration cap per candidate (40)               */
+    double hash_cells_per_elem; /* hash-grid cells per element (1.0); result-invariant   */
+    double tie_band;            /* owner and border ties within tie_band*L (1e-10)       */
+    int points_per_block;       /* threads per block of the Newton kernel: 0 (= 128) or a
+                                   multiple of 32 up to 256; result-invariant          */
+} fp_opts;
+/* h_e = diagonal of the axis-aligned box spanned by element e's nodes;
+   L = diagonal of the box spanned by all nodes. */
+
+/* Fill *o with the defaults above. */
+void fp_default_opts(fp_opts *o);
+
+/* fp_setup -- post the meshes (Sec. 2.1, findpts_setup with a per-element
+ * session discriminator) and build the resident search structures: per
+ * element bounding boxes from the Bernstein form of the element map (an axis
+ * box and a box in the element's own affine frame) and a uniform hash grid
+ * over the global box with a cell -> element list.
+ *   h      out: new handle (set to NULL on failure)
+ *   coords [3][E][n3] FP64 node coordinates x, y, z of every element
+ *   E      number of elements (>= 1, < 2^31)
+ *   N      polynomial order (1..15)
+ *   sub    [E] int32 subdomain (session) id per element, 0 <= sub < 65536;
+ *          NULL = all elements in subdomain 0
+ *   dist   [E][n3] FP64 nodal distance-to-own-boundary field D^k used by the
+ *          owner rule, or NULL.  When NULL and the mesh has more than one
+ *          subdomain, the library computes D (distance from each node to the
+ *          nearest boundary-face GLL node of its own subdomain); that
+ *          brute-force pass is limited to meshes with at most 2^37
+ *          node x boundary-node pairs, beyond which FP_ERR_INVALID_ARG is
+ *          returned and D must be supplied.
+ *   opts   NULL = defaults
+ * The library copies everything it keeps; the caller may free its buffers
+ * once `stream` has been synchronised.  Synchronises `stream` before return.
+ * Errors: FP_ERR_INVALID_ARG (E, N, sub or opts out of range, null coords,
+ * non-finite coordinates), FP_ERR_OOM, FP_ERR_CUDA. */
+fp_status fp_setup(fp_handle **h, const double *coords, int64_t E, int N,
+                   const int32_t *sub, const double *dist, const fp_opts *opts,
+                   void *stream);
+
+/* fp_reserve -- pre-size the find workspace for up to P points, so that
+ * later fp_find calls with at most P points allocate nothing (required before
+ * capturing fp_find into a CUDA graph).  Synchronises the device. */
+fp_status fp_reserve(fp_handle *h, int64_t P);
+
+/* fp_find -- locate P points (Sec. 2.1, findpts).
+ *   pts    [3][P] FP64 query coordinates
+ *   qsess  [P] int32 session tag per point: a point tagged j searches only
+ *          elements with sub != j; -1 searches all.  NULL = all -1.
+ * Outputs (all [P] unless stated):
+ *   code   int32 FP_CODE_*;  non-finite points give FP_CODE_NOT_FOUND
+ *   sub    int32 owning subdomain (-1 when not found)
+ *   elem   int32 element index in [0,E) (-1 when not found)
+ *   rst    [3][P] FP64 reference coordinates in [-1,1]^3 (0 when not found)
+ *   dist2  FP64 squared residual ||x^e(r)-x*||^2 (+inf when not found)
+ * Rules: INSIDE elements within a subdomain -> lowest element id; between
+ * subdomains -> largest interpolated D^k(x*), ties within tie_band*L to the
+ * lower subdomain id; no INSIDE element but a constrained residual within
+ * tol_border*h_e -> BORDER at the element of smallest residual (lowest id
+ * within tie_band*L).  P = 0 is a no-op.  May grow the workspace (allocates
+ * and synchronises) when P exceeds what fp_reserve or an earlier call sized.
+ * Errors: FP_ERR_NOT_SETUP, FP_ERR_INVALID_ARG (P < 0, null pointers),
+ * FP_ERR_OOM, FP_ERR_CUDA. */
+fp_status fp_find(fp_handle *h, int64_t P, const double *pts, const int32_t *qsess,
+                  int32_t *code, int32_t *sub, int32_t *elem, double *rst,
+                  double *dist2, void *stream);
+
+/* fp_eval -- interpolate F nodal fields at located points (Sec. 2.1,
+ * findpts_eval): out[f][p] = sum_ijk fields[f][elem[p]][ijk] h_i(r) h_j(s) h_k(t)
+ * evaluated by sum factorisation in FP64.
+ *   code, elem, rst  as written by fp_find (rst is [3][P])
+ *   fields  [F][E][n3] FP64 nodal values on the handle's mesh
+ *   out     [F][P] FP64; quiet NaN where code is FP_CODE_NOT_FOUND
+ * `fields` must be 16-byte aligned when n is even (rows are read as 16-byte
+ * vectors).  Allocates nothing.  Errors: FP_ERR_NOT_SETUP,
+ * FP_ERR_INVALID_ARG (P < 0, F < 1, null pointers, misaligned fields),
+ * FP_ERR_CUDA. */
+fp_status fp_eval(fp_handle *h, int64_t P, const int32_t *code, const int32_t *elem,
+                  const double *rst, int F, const double *fields, double *out,
+                  void *stream);
+
+/* Release every device resource of the handle (synchronises it first).
+   NULL is a no-op. */
+void fp_free(fp_handle *h);
+
+/* Static text for a status code. */
+const char *fp_error_string(fp_status s);
+
+/* Text of the handle's most recent failure ("" if none); valid until the next
+   call on the handle. */
+const char *fp_last_error(const fp_handle *h);
+
+/* Measurement support.  With fp_profile(h, 1) the library brackets its own
+ * kernels with CUDA events recorded on the launching stream; fp_profile_read
+ * waits for the recorded events of one kernel class and returns the summed
+ * device time (ms) and number of timed launches since the previous read.
+ * kind: 0 screen (hash + boxes + pair emission, with the offset scan),
+ * 1 pair sort by element, 2 Newton, 3 classification / ownership, 4 eval. */
+fp_status fp_profile(fp_handle *h, int enable);
+fp_status fp_profile_read(fp_handle *h, int kind, double *total_ms, int64_t *launches);
+
+/* Number of kernels the library has launched in this process. */
+int64_t fp_launch_count(void);
+
+/* Introspection for tests: E, N, number of hash cells, number of
+   cell -> element entries, number of subdomains. */
+fp_status fp_info(const fp_handle *h, int64_t *E, int *N, int64_t *ncell, int64_t *nnz,
+                  int *nsub);
+
+/* Introspection for tests: copy the per-element axis boxes [E][6]
+   (xmin,ymin,zmin,xmax,ymax,zmax, padded) and the hash grid to DEVICE
+   buffers.  grid[9] = origin xyz, inverse cell size xyz, dims xyz (as
+   doubles); cell_start [ncell+1] and cell_elems [nnz] int32.  Any output may
+   be NULL.  Enqueued on `stream`. */
+fp_status fp_debug_boxes(const fp_handle *h, double *aabb, double *grid,
+                         int32_t *cell_start, int32_t *cell_elems, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FINDPTS_GB_H */

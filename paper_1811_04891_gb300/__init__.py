@@ -1,0 +1,228 @@
+"""GB300-native findpts / findpts_eval (arXiv 1811.04891, Sec. 2.1).
+
+Thin ctypes binding over the C ABI in ``include/findpts_gb.h``: every function
+here only marshals torch CUDA tensors into device pointers and calls the
+library of the same name, whose CUDA kernels do all the work.  There is no CPU
+fallback: importing the package fails loudly when the shared library cannot
+be built or loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import torch
+
+from . import build as _build
+
+FP_OK, FP_ERR_INVALID_ARG, FP_ERR_OOM, FP_ERR_CUDA, FP_ERR_TIMEOUT, FP_ERR_NOT_SETUP = range(6)
+INSIDE, BORDER, NOT_FOUND = 0, 1, 2
+PREC_FP64, PREC_MIXED = 0, 1
+
+
+class FindptsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+class fp_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("tol_accept", ctypes.c_double),
+                ("tol_border", ctypes.c_double), ("max_newton", ctypes.c_int),
+                ("hash_cells_per_elem", ctypes.c_double), ("tie_band", ctypes.c_double),
+                ("points_per_block", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        path = _build.build()
+    L = ctypes.CDLL(path)
+    vp, i64, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.fp_default_opts.argtypes = [ctypes.POINTER(fp_opts)]
+    L.fp_default_opts.restype = None
+    L.fp_setup.argtypes = [ctypes.POINTER(vp), vp, i64, ci, vp, vp, ctypes.POINTER(fp_opts), vp]
+    L.fp_setup.restype = ci
+    L.fp_reserve.argtypes = [vp, i64]
+    L.fp_reserve.restype = ci
+    L.fp_find.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.fp_find.restype = ci
+    L.fp_eval.argtypes = [vp, i64, vp, vp, vp, ci, vp, vp, vp]
+    L.fp_eval.restype = ci
+    L.fp_free.argtypes = [vp]
+    L.fp_free.restype = None
+    L.fp_error_string.argtypes = [ci]
+    L.fp_error_string.restype = ctypes.c_char_p
+    L.fp_last_error.argtypes = [vp]
+    L.fp_last_error.restype = ctypes.c_char_p
+    L.fp_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ci), ctypes.POINTER(i64),
+                          ctypes.POINTER(i64), ctypes.POINTER(ci)]
+    L.fp_info.restype = ci
+    L.fp_debug_boxes.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.fp_debug_boxes.restype = ci
+    L.fp_profile.argtypes = [vp, ci]
+    L.fp_profile.restype = ci
+    L.fp_profile_read.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+    L.fp_profile_read.restype = ci
+    L.fp_launch_count.argtypes = []
+    L.fp_launch_count.restype = i64
+    _lib = L
+    return L
+
+
+def lib():
+    return _load()
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(st: int, h=None):
+    if st != FP_OK:
+        L = lib()
+        msg = L.fp_last_error(h).decode() if h is not None else L.fp_last_error(None).decode()
+        raise FindptsError(st, msg or L.fp_error_string(st).decode())
+
+
+def _dev(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name}: expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    return t.contiguous()
+
+
+def default_opts(**kw) -> fp_opts:
+    o = fp_opts()
+    lib().fp_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class Handle:
+    ptr: ctypes.c_void_p
+    E: int
+    N: int
+
+    def __del__(self):
+        if getattr(self, "ptr", None) is not None and self.ptr.value:
+            try:
+                lib().fp_free(self.ptr)
+            except Exception:
+                pass
+            self.ptr = ctypes.c_void_p(None)
+
+    def info(self):
+        E, N, nc, nnz, ns = (ctypes.c_int64(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int())
+        _check(lib().fp_info(self.ptr, ctypes.byref(E), ctypes.byref(N), ctypes.byref(nc),
+                             ctypes.byref(nnz), ctypes.byref(ns)), self.ptr)
+        return {"E": E.value, "N": N.value, "ncell": nc.value, "nnz": nnz.value, "nsub": ns.value}
+
+
+def fp_setup(coords: torch.Tensor, N: int, sub: Optional[torch.Tensor] = None,
+             dist: Optional[torch.Tensor] = None, opts: Optional[fp_opts] = None,
+             stream=None) -> Handle:
+    """Post a mesh: coords [3][E][(N+1)^3] float64 CUDA tensor, sub [E] int32,
+    dist [E][(N+1)^3] float64 or None."""
+    coords = _dev(coords, torch.float64, "coords")
+    E = coords.shape[1]
+    if coords.ndim != 3 or coords.shape[0] != 3 or coords.shape[2] != (N + 1) ** 3:
+        raise ValueError("coords must be [3][E][(N+1)^3]")
+    sub = None if sub is None else _dev(sub, torch.int32, "sub")
+    dist = None if dist is None else _dev(dist, torch.float64, "dist")
+    h = ctypes.c_void_p()
+    st = lib().fp_setup(ctypes.byref(h), _ptr(coords), E, N, _ptr(sub), _ptr(dist),
+                        None if opts is None else ctypes.byref(opts), _stream(stream))
+    _check(st, None)
+    return Handle(ptr=h, E=E, N=N)
+
+
+def fp_reserve(h: Handle, P: int):
+    _check(lib().fp_reserve(h.ptr, int(P)), h.ptr)
+
+
+def fp_find(h: Handle, pts: torch.Tensor, qsess: Optional[torch.Tensor] = None, out=None, stream=None):
+    """Locate points pts [3][P] float64.  Returns (code, sub, elem, rst [3][P], dist2)."""
+    pts = _dev(pts, torch.float64, "pts")
+    P = pts.shape[1]
+    qsess = None if qsess is None else _dev(qsess, torch.int32, "qsess")
+    dev = pts.device
+    if out is None:
+        out = (torch.empty(P, dtype=torch.int32, device=dev), torch.empty(P, dtype=torch.int32, device=dev),
+               torch.empty(P, dtype=torch.int32, device=dev), torch.empty((3, P), dtype=torch.float64, device=dev),
+               torch.empty(P, dtype=torch.float64, device=dev))
+    code, sub, elem, rst, dist2 = out
+    st = lib().fp_find(h.ptr, P, _ptr(pts), _ptr(qsess), _ptr(code), _ptr(sub), _ptr(elem), _ptr(rst),
+                       _ptr(dist2), _stream(stream))
+    _check(st, h.ptr)
+    return code, sub, elem, rst, dist2
+
+
+def fp_eval(h: Handle, code: torch.Tensor, elem: torch.Tensor, rst: torch.Tensor, fields: torch.Tensor,
+            out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Interpolate fields [F][E][(N+1)^3] (or [E][(N+1)^3]) at located points -> [F][P]."""
+    fields = _dev(fields, torch.float64, "fields")
+    if fields.ndim == 2:
+        fields = fields.unsqueeze(0)
+    F = fields.shape[0]
+    P = code.shape[0]
+    if out is None:
+        out = torch.empty((F, P), dtype=torch.float64, device=fields.device)
+    st = lib().fp_eval(h.ptr, P, _ptr(code), _ptr(elem), _ptr(rst), F, _ptr(fields), _ptr(out),
+                       _stream(stream))
+    _check(st, h.ptr)
+    return out
+
+
+PROF_KINDS = {"screen": 0, "sort": 1, "newton": 2, "rank": 3, "eval": 4}
+
+
+def fp_profile(h: Handle, enable: bool = True):
+    _check(lib().fp_profile(h.ptr, int(bool(enable))), h.ptr)
+
+
+def fp_profile_read(h: Handle, kind: str):
+    """(total device ms, launches) of one kernel class since the last read."""
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(lib().fp_profile_read(h.ptr, PROF_KINDS[kind], ctypes.byref(ms), ctypes.byref(n)), h.ptr)
+    return ms.value, n.value
+
+
+def fp_launch_count() -> int:
+    return int(lib().fp_launch_count())
+
+
+def fp_debug_boxes(h: Handle):
+    """Per-element padded axis boxes and the hash grid (for tests)."""
+    inf = h.info()
+    dev = torch.device("cuda")
+    aabb = torch.empty((h.E, 6), dtype=torch.float64, device=dev)
+    grid = torch.empty(9, dtype=torch.float64, device=dev)
+    cs = torch.empty(inf["ncell"] + 1, dtype=torch.int32, device=dev)
+    ce = torch.empty(max(inf["nnz"], 1), dtype=torch.int32, device=dev)
+    _check(lib().fp_debug_boxes(h.ptr, _ptr(aabb), _ptr(grid), _ptr(cs), _ptr(ce), _stream(None)), h.ptr)
+    torch.cuda.synchronize()
+    return aabb, grid, cs, ce

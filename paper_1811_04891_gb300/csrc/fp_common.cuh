@@ -1,0 +1,228 @@
+// fp_common.cuh -- internal types and device building blocks shared by the
+// library's translation units (never by the CPU oracle).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/findpts_gb.h"
+
+namespace fpg {
+
+constexpr int NMAX = 16;   // GLL points per direction, N <= 15
+
+// Lagrange data on the GLL points of one order: abscissae xi and the
+// normalisers ci = 1 / prod_{m != i} (xi_i - xi_m).  Passed by value as a
+// kernel argument, so every read is a uniform constant-bank load.
+struct BasisTab {
+    double xi[NMAX];
+    double ci[NMAX];
+    float xif[NMAX];
+    float cif[NMAX];
+};
+
+// Per-element search data (FP64), built once by the hull kernel.
+struct ElemBox {
+    double c[3];        // frame origin (mean of the 8 vertices)
+    double Ai[9];       // y = Ai (x - c): inverse of the vertex-averaged affine frame
+    double olo[3];      // bounds of y over the element (Bernstein hull) minus pad
+    double ohi[3];      //   ... plus pad
+    double blo[3];      // axis-aligned Bernstein-hull bounds minus pad
+    double bhi[3];      //   ... plus pad
+    double he;          // diagonal of the axis box spanned by the element's nodes
+    double spare;
+};
+
+struct HashGrid {
+    double org[3];
+    double inv[3];      // 1 / cell size
+    int dim[3];
+    int pad_;
+    int64_t ncell;
+};
+
+struct FindParams {
+    double tol_accept;  // relative to h_e
+    double tol_border;  // relative to h_e
+    double band;        // absolute tie band = tie_band * L
+    int max_newton;
+    int mixed;
+};
+
+// ---------------------------------------------------------------------------
+// Lagrange basis on the GLL points by prefix / suffix products:
+//   h_i(r) = ci_i * prod_{m<i} (r - xi_m) * prod_{m>i} (r - xi_m)
+// and its derivative by the product rule applied to the running products.
+// ---------------------------------------------------------------------------
+template <int n, typename T>
+__device__ __forceinline__ void lagrange_hd(const T* __restrict__ xi, const T* __restrict__ ci,
+                                            T r, T (&h)[n], T (&d)[n])
+{
+    T dm[n];
+#pragma unroll
+    for (int m = 0; m < n; ++m) dm[m] = r - xi[m];
+    T pre[n], dpre[n];
+    pre[0] = T(1);
+    dpre[0] = T(0);
+#pragma unroll
+    for (int i = 1; i < n; ++i) {
+        dpre[i] = dpre[i - 1] * dm[i - 1] + pre[i - 1];
+        pre[i] = pre[i - 1] * dm[i - 1];
+    }
+    T suf = T(1), dsuf = T(0);
+#pragma unroll
+    for (int i = n - 1; i >= 0; --i) {
+        h[i] = ci[i] * (pre[i] * suf);
+        d[i] = ci[i] * (dpre[i] * suf + pre[i] * dsuf);
+        dsuf = dsuf * dm[i] + suf;
+        suf = suf * dm[i];
+    }
+}
+
+template <int n, typename T>
+__device__ __forceinline__ void lagrange_h(const T* __restrict__ xi, const T* __restrict__ ci,
+                                           T r, T (&h)[n])
+{
+    T dm[n];
+#pragma unroll
+    for (int m = 0; m < n; ++m) dm[m] = r - xi[m];
+    T pre[n];
+    pre[0] = T(1);
+#pragma unroll
+    for (int i = 1; i < n; ++i) pre[i] = pre[i - 1] * dm[i - 1];
+    T suf = T(1);
+#pragma unroll
+    for (int i = n - 1; i >= 0; --i) {
+        h[i] = ci[i] * (pre[i] * suf);
+        suf = suf * dm[i];
+    }
+}
+
+template <typename T> struct Tab;
+template <> struct Tab<double> {
+    static __device__ __forceinline__ const double* xi(const BasisTab& b) { return b.xi; }
+    static __device__ __forceinline__ const double* ci(const BasisTab& b) { return b.ci; }
+};
+template <> struct Tab<float> {
+    static __device__ __forceinline__ const float* xi(const BasisTab& b) { return b.xif; }
+    static __device__ __forceinline__ const float* ci(const BasisTab& b) { return b.cif; }
+};
+
+// Load one row of n contiguous values (vectorised when n is even and the row
+// is 16-byte aligned, which holds for every row when n is even).
+template <int n>
+__device__ __forceinline__ void load_row(const double* __restrict__ p, double (&v)[n])
+{
+    if constexpr (n % 2 == 0) {
+        const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i) {
+            double2 t = __ldg(q + i);
+            v[2 * i] = t.x;
+            v[2 * i + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < n; ++i) v[i] = __ldg(p + i);
+    }
+}
+
+template <int n>
+__device__ __forceinline__ void load_row(const float* __restrict__ p, float (&v)[n])
+{
+    if constexpr (n % 4 == 0) {
+        const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+        for (int i = 0; i < n / 4; ++i) {
+            float4 t = __ldg(q + i);
+            v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+        }
+    } else if constexpr (n % 2 == 0) {
+        const float2* q = reinterpret_cast<const float2*>(p);
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i) {
+            float2 t = __ldg(q + i);
+            v[2 * i] = t.x; v[2 * i + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < n; ++i) v[i] = __ldg(p + i);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Element map x(r) and Jacobian by sum factorisation (Sec. 2: O(N^{d+1})
+// tensor-product work).  X[a] points at coordinate a's n^3 nodes of one
+// element.  Contract i (contiguous rows) with h_r and h_r', then j with h_s
+// and h_s', then k with h_t and h_t'.
+// ---------------------------------------------------------------------------
+template <int n, typename T>
+__device__ __forceinline__ void map_jac(const T* __restrict__ X0, const T* __restrict__ X1,
+                                        const T* __restrict__ X2, const T (&hr)[n],
+                                        const T (&dr)[n], const T (&hs)[n], const T (&ds)[n],
+                                        const T* ht, const T* dt, T (&x)[3], T (&J)[9])
+{
+    T xa[3] = {0, 0, 0}, xr[3] = {0, 0, 0}, xs[3] = {0, 0, 0}, xt[3] = {0, 0, 0};
+#pragma unroll 1
+    for (int k = 0; k < n; ++k) {
+        T c[3] = {0, 0, 0}, cs[3] = {0, 0, 0}, cr[3] = {0, 0, 0};
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+            const int off = n * (j + n * k);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const T* row = (a == 0 ? X0 : (a == 1 ? X1 : X2)) + off;
+                T v[n];
+                load_row<n>(row, v);
+                T u = 0, w = 0;
+#pragma unroll
+                for (int i = 0; i < n; ++i) {
+                    u = fma(hr[i], v[i], u);
+                    w = fma(dr[i], v[i], w);
+                }
+                c[a] = fma(hs[j], u, c[a]);
+                cs[a] = fma(ds[j], u, cs[a]);
+                cr[a] = fma(hs[j], w, cr[a]);
+            }
+        }
+        const T tk = ht[k], dk = dt[k];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            xa[a] = fma(tk, c[a], xa[a]);
+            xt[a] = fma(dk, c[a], xt[a]);
+            xs[a] = fma(tk, cs[a], xs[a]);
+            xr[a] = fma(tk, cr[a], xr[a]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        x[a] = xa[a];
+        J[3 * a + 0] = xr[a];
+        J[3 * a + 1] = xs[a];
+        J[3 * a + 2] = xt[a];
+    }
+}
+
+// Value-only contraction of one nodal array F (n^3) at a point.
+template <int n, typename T>
+__device__ __forceinline__ T contract(const T* __restrict__ F, const T (&hr)[n], const T (&hs)[n],
+                                      const T* ht)
+{
+    T acc = 0;
+#pragma unroll 1
+    for (int k = 0; k < n; ++k) {
+        T c = 0;
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+            T v[n];
+            load_row<n>(F + n * (j + n * k), v);
+            T u = 0;
+#pragma unroll
+            for (int i = 0; i < n; ++i) u = fma(hr[i], v[i], u);
+            c = fma(hs[j], u, c);
+        }
+        acc = fma(ht[k], c, acc);
+    }
+    return acc;
+}
+
+}  // namespace fpg

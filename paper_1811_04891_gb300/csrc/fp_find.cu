@@ -1,0 +1,654 @@
+// fp_find.cu -- point location (Sec. 2.1, findpts) as a pair stream.
+//
+//  1. k_screen<false>  per point: hash cell -> candidate list, session
+//                      filter (sub != tag), axis box, box in the element's
+//                      affine frame; count the survivors.
+//  2. scan             per-point pair offsets.
+//  3. k_screen<true>   write the (point, element) pairs in point order.
+//  4. k_ehist / scan / k_escatter   counting sort of the pairs by element, so
+//                      neighbouring threads work on the same element and its
+//                      geometry is served by broadcast loads from L1.
+//  5. k_newton<n,MIXED>  per pair: seed at the nearest mapped GLL node, then
+//                      box-constrained trust-region Newton on
+//                      ||x^e(r) - x*||^2; MIXED runs the seed and the early
+//                      iterations in FP32 on element-local coordinates and the
+//                      last step(s), the residual and the chord check in FP64.
+//  6. k_rank<n>        per point: classify its pairs (INSIDE / BORDER), lowest
+//                      element id within a subdomain, owner = argmax of the
+//                      interpolated distance field D^k with lower-id tie band.
+#include "fp_common.cuh"
+#include "fp_internal.h"
+
+namespace fpg {
+
+// ---------------------------------------------------------------------------
+// screening
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool inside_boxes(const ElemBox* __restrict__ bp, double x, double y, double z)
+{
+    const double* b = reinterpret_cast<const double*>(bp);
+    // ElemBox layout: c[0..2], Ai[3..11], olo[12..14], ohi[15..17], blo[18..20], bhi[21..23]
+    if (x < __ldg(b + 18) || x > __ldg(b + 21) || y < __ldg(b + 19) || y > __ldg(b + 22) ||
+        z < __ldg(b + 20) || z > __ldg(b + 23))
+        return false;
+    const double dx = x - __ldg(b + 0), dy = y - __ldg(b + 1), dz = z - __ldg(b + 2);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double v = __ldg(b + 3 + 3 * a) * dx + __ldg(b + 4 + 3 * a) * dy + __ldg(b + 5 + 3 * a) * dz;
+        if (v < __ldg(b + 12 + a) || v > __ldg(b + 15 + a)) return false;
+    }
+    return true;
+}
+
+struct ScreenArgs {
+    int64_t P;
+    const double* pts;
+    const int32_t* qsess;
+    const int32_t* sub;
+    const ElemBox* boxes;
+    HashGrid g;
+    const int32_t* cell_start;
+    const int32_t* cell_elems;
+    int32_t* cnt;
+    const int32_t* off;
+    int32_t* pair_elem;
+    int32_t* pair_pt;
+};
+
+template <bool EMIT>
+__global__ void __launch_bounds__(256) k_screen(ScreenArgs A)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= A.P) return;
+    const double x = A.pts[p], y = A.pts[A.P + p], z = A.pts[2 * A.P + p];
+    const int tag = A.qsess ? A.qsess[p] : -1;
+    int c = 0;
+    int base = EMIT ? A.off[p] : 0;
+    if (isfinite(x) && isfinite(y) && isfinite(z)) {
+        const double u0 = (x - A.g.org[0]) * A.g.inv[0];
+        const double u1 = (y - A.g.org[1]) * A.g.inv[1];
+        const double u2 = (z - A.g.org[2]) * A.g.inv[2];
+        if (u0 >= 0.0 && u1 >= 0.0 && u2 >= 0.0 && u0 <= (double)A.g.dim[0] && u1 <= (double)A.g.dim[1] &&
+            u2 <= (double)A.g.dim[2]) {
+            const int i = min((int)u0, A.g.dim[0] - 1);
+            const int j = min((int)u1, A.g.dim[1] - 1);
+            const int k = min((int)u2, A.g.dim[2] - 1);
+            const int64_t cell = i + (int64_t)A.g.dim[0] * (j + (int64_t)A.g.dim[1] * k);
+            const int b = __ldg(A.cell_start + cell), en = __ldg(A.cell_start + cell + 1);
+            for (int q = b; q < en; ++q) {
+                const int e = __ldg(A.cell_elems + q);
+                if (tag >= 0 && __ldg(A.sub + e) == tag) continue;
+                if (!inside_boxes(A.boxes + e, x, y, z)) continue;
+                if (EMIT) {
+                    A.pair_elem[base + c] = e;
+                    A.pair_pt[base + c] = (int32_t)p;
+                }
+                ++c;
+            }
+        }
+    }
+    if (!EMIT) A.cnt[p] = c;
+}
+
+__global__ void k_ehist(int64_t npairs, const int32_t* __restrict__ pair_elem, int32_t* __restrict__ ecount)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < npairs) atomicAdd(ecount + pair_elem[q], 1);
+}
+
+__global__ void k_escatter(int64_t npairs, const int32_t* __restrict__ pair_elem, const int32_t* __restrict__ estart,
+                           int32_t* __restrict__ cursor, int32_t* __restrict__ order)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= npairs) return;
+    int e = pair_elem[q];
+    int pos = estart[e] + atomicAdd(cursor + e, 1);
+    order[pos] = (int32_t)q;
+}
+
+// ---------------------------------------------------------------------------
+// Newton machinery
+// ---------------------------------------------------------------------------
+template <typename T>
+struct ElemPtr {
+    const T* X0;
+    const T* X1;
+    const T* X2;
+};
+
+template <int n, typename T>
+__device__ __forceinline__ void eval_fJ(const ElemPtr<T>& el, const BasisTab& tab, const T (&r)[3],
+                                        const T (&xs)[3], T (&f)[3], T (&J)[9])
+{
+    T hr[n], dr[n], hs[n], ds[n], ht[n], dt[n];
+    lagrange_hd<n, T>(Tab<T>::xi(tab), Tab<T>::ci(tab), r[0], hr, dr);
+    lagrange_hd<n, T>(Tab<T>::xi(tab), Tab<T>::ci(tab), r[1], hs, ds);
+    lagrange_hd<n, T>(Tab<T>::xi(tab), Tab<T>::ci(tab), r[2], ht, dt);
+    T x[3];
+    map_jac<n, T>(el.X0, el.X1, el.X2, hr, dr, hs, ds, ht, dt, x, J);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) f[a] = x[a] - xs[a];
+}
+
+template <int n, typename T>
+__device__ __forceinline__ void eval_f(const ElemPtr<T>& el, const BasisTab& tab, const T (&r)[3],
+                                       const T (&xs)[3], T (&f)[3])
+{
+    T hr[n], hs[n], ht[n];
+    lagrange_h<n, T>(Tab<T>::xi(tab), Tab<T>::ci(tab), r[0], hr);
+    lagrange_h<n, T>(Tab<T>::xi(tab), Tab<T>::ci(tab), r[1], hs);
+    lagrange_h<n, T>(Tab<T>::xi(tab), Tab<T>::ci(tab), r[2], ht);
+    f[0] = contract<n, T>(el.X0, hr, hs, ht) - xs[0];
+    f[1] = contract<n, T>(el.X1, hr, hs, ht) - xs[1];
+    f[2] = contract<n, T>(el.X2, hr, hs, ht) - xs[2];
+}
+
+// J d = -f by cofactors; returns false when J is singular.
+template <typename T>
+__device__ __forceinline__ bool newton_solve3(const T (&J)[9], const T (&f)[3], T (&d)[3])
+{
+    const T C00 = J[4] * J[8] - J[5] * J[7], C01 = J[5] * J[6] - J[3] * J[8], C02 = J[3] * J[7] - J[4] * J[6];
+    const T det = J[0] * C00 + J[1] * C01 + J[2] * C02;
+    if (det == T(0) || !isfinite(det)) return false;
+    const T C10 = J[2] * J[7] - J[1] * J[8], C11 = J[0] * J[8] - J[2] * J[6], C12 = J[1] * J[6] - J[0] * J[7];
+    const T C20 = J[1] * J[5] - J[2] * J[4], C21 = J[2] * J[3] - J[0] * J[5], C22 = J[0] * J[4] - J[1] * J[3];
+    const T id = T(1) / det;
+    d[0] = -(C00 * f[0] + C10 * f[1] + C20 * f[2]) * id;
+    d[1] = -(C01 * f[0] + C11 * f[1] + C21 * f[2]) * id;
+    d[2] = -(C02 * f[0] + C12 * f[1] + C22 * f[2]) * id;
+    return true;
+}
+
+// Gauss-Newton step with an active set: coordinates on a bound whose
+// descent direction leaves the box are frozen; the remaining ones solve the
+// reduced normal equations (the plain Newton step when all three are free).
+// Returns the number of free coordinates.
+template <typename T>
+__device__ __forceinline__ int gn_step(const T (&J)[9], const T (&f)[3], const T (&r)[3], T (&d)[3])
+{
+    T g[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) g[b] = J[b] * f[0] + J[3 + b] * f[1] + J[6 + b] * f[2];
+    bool act[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) act[b] = (r[b] <= T(-1) && g[b] > T(0)) || (r[b] >= T(1) && g[b] < T(0));
+    int nfree = 0;
+    for (int pass = 0; pass < 4; ++pass) {
+        d[0] = d[1] = d[2] = T(0);
+        int fi[3];
+        nfree = 0;
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            if (!act[b]) fi[nfree++] = b;
+        if (nfree == 0) break;
+        bool ok = false;
+        if (nfree == 3) {
+            ok = newton_solve3<T>(J, f, d);
+        } else if (nfree == 2) {
+            const int p = fi[0], q = fi[1];
+            const T a00 = J[p] * J[p] + J[3 + p] * J[3 + p] + J[6 + p] * J[6 + p];
+            const T a11 = J[q] * J[q] + J[3 + q] * J[3 + q] + J[6 + q] * J[6 + q];
+            const T a01 = J[p] * J[q] + J[3 + p] * J[3 + q] + J[6 + p] * J[6 + q];
+            const T det = a00 * a11 - a01 * a01;
+            if (det > T(0)) {
+                d[p] = (-a11 * g[p] + a01 * g[q]) / det;
+                d[q] = (-a00 * g[q] + a01 * g[p]) / det;
+                ok = true;
+            }
+        } else {
+            const int p = fi[0];
+            const T a00 = J[p] * J[p] + J[3 + p] * J[3 + p] + J[6 + p] * J[6 + p];
+            if (a00 > T(0)) {
+                d[p] = -g[p] / a00;
+                ok = true;
+            }
+        }
+        if (!ok) {                                   // singular: steepest descent
+            for (int t = 0; t < nfree; ++t) d[fi[t]] = -g[fi[t]];
+        }
+        bool grew = false;
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            if (!act[b] && ((r[b] <= T(-1) && d[b] < T(0)) || (r[b] >= T(1) && d[b] > T(0)))) {
+                act[b] = true;
+                grew = true;
+            }
+        if (!grew) break;
+    }
+    return nfree;
+}
+
+template <typename T> struct Lim;
+template <> struct Lim<double> {
+    static constexpr double quick = 1e-6;     // full Newton step size that ends the loop
+    static constexpr double chord = 1e-13;    // chord correction that confirms convergence
+    static constexpr double stop = 1e-13;     // accepted step that ends a constrained solve
+    static constexpr double rho_min = 1e-15;
+};
+template <> struct Lim<float> {
+    static constexpr float quick = 2e-5f;
+    static constexpr float chord = 0.0f;      // unused: the FP64 phase follows
+    static constexpr float stop = 1e-6f;
+    static constexpr float rho_min = 1e-7f;
+};
+
+// Box-constrained trust-region Newton (Sec. 2.1) from r (in/out).
+// Returns the residual norm ||x(r) - x*|| at the returned r.  With FINAL
+// (the FP64 phase) a small full Newton step is confirmed by a value-only
+// residual and a chord correction with the current Jacobian; without it
+// (FP32 phase) the loop simply stops after such a step.
+template <int n, typename T, bool FINAL>
+__device__ T newton(const ElemPtr<T>& el, const BasisTab& tab, const T (&xs)[3], T (&r)[3], int max_it)
+{
+    T f[3], J[9];
+    eval_fJ<n, T>(el, tab, r, xs, f, J);
+    T phi = T(0.5) * (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    T rho = T(1);
+    for (int it = 0; it < max_it; ++it) {
+        if (!(phi > T(0))) break;
+        T d[3];
+        if (gn_step<T>(J, f, r, d) == 0) break;
+        const T dn = fmax(fabs(d[0]), fmax(fabs(d[1]), fabs(d[2])));
+        if (!(dn > T(0))) break;
+        bool full = true;
+        if (dn > rho) {
+            const T sc = rho / dn;
+            d[0] *= sc; d[1] *= sc; d[2] *= sc;
+            full = false;
+        }
+        T t = T(1);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if (d[b] > T(0) && r[b] + d[b] > T(1)) t = fmin(t, (T(1) - r[b]) / d[b]);
+            if (d[b] < T(0) && r[b] + d[b] < T(-1)) t = fmin(t, (T(-1) - r[b]) / d[b]);
+        }
+        if (t < T(1)) full = false;
+        T rn[3], s[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            T v = r[b] + t * d[b];
+            if (t < T(1)) {
+                if (d[b] > T(0) && (T(1) - r[b]) / d[b] == t) v = T(1);
+                if (d[b] < T(0) && (T(-1) - r[b]) / d[b] == t) v = T(-1);
+            }
+            rn[b] = fmin(T(1), fmax(T(-1), v));
+            s[b] = rn[b] - r[b];
+        }
+        const T sn = fmax(fabs(s[0]), fmax(fabs(s[1]), fabs(s[2])));
+        if (!(sn > T(0))) break;
+        if (full && dn <= Lim<T>::quick) {
+            r[0] = rn[0]; r[1] = rn[1]; r[2] = rn[2];
+            if (!FINAL) return sqrt(T(2) * phi);
+            T fn[3];
+            eval_f<n, T>(el, tab, r, xs, fn);
+            T d2[3];
+            const bool ok = newton_solve3<T>(J, fn, d2);
+            f[0] = fn[0]; f[1] = fn[1]; f[2] = fn[2];
+            phi = T(0.5) * (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+            if (ok && fmax(fabs(d2[0]), fmax(fabs(d2[1]), fabs(d2[2]))) <= Lim<T>::chord) break;
+            eval_fJ<n, T>(el, tab, r, xs, f, J);      // not yet converged: refresh J
+            phi = T(0.5) * (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+            continue;
+        }
+        T mf[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) mf[a] = f[a] + J[3 * a] * s[0] + J[3 * a + 1] * s[1] + J[3 * a + 2] * s[2];
+        const T pred = phi - T(0.5) * (mf[0] * mf[0] + mf[1] * mf[1] + mf[2] * mf[2]);
+        T fn[3], Jn[9];
+        eval_fJ<n, T>(el, tab, rn, xs, fn, Jn);
+        const T phin = T(0.5) * (fn[0] * fn[0] + fn[1] * fn[1] + fn[2] * fn[2]);
+        if (sn <= Lim<T>::stop) {
+            if (phin <= phi) {
+                r[0] = rn[0]; r[1] = rn[1]; r[2] = rn[2];
+                phi = phin;
+            }
+            break;
+        }
+        if (phin < phi) {
+            const T ratio = pred > T(0) ? (phi - phin) / pred : T(0);
+            r[0] = rn[0]; r[1] = rn[1]; r[2] = rn[2];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) J[q] = Jn[q];
+            f[0] = fn[0]; f[1] = fn[1]; f[2] = fn[2];
+            phi = phin;
+            if (ratio > T(0.75) && sn >= T(0.99) * rho) rho = fmin(T(2) * rho, T(2));
+            else if (ratio < T(0.25)) rho = T(0.25) * sn;
+        } else {
+            rho = T(0.25) * sn;
+            if (rho < Lim<T>::rho_min) break;
+        }
+    }
+    return sqrt(T(2) * phi);
+}
+
+// nearest mapped GLL node (ties: lowest node index) -> its reference coordinates
+template <int n, typename T>
+__device__ __forceinline__ void seed_nearest(const ElemPtr<T>& el, const BasisTab& tab, const T (&xs)[3], T (&r)[3])
+{
+    constexpr int n3 = n * n * n;
+    T best = T(INFINITY);
+    int bq = 0;
+#pragma unroll 4
+    for (int q = 0; q < n3; ++q) {
+        const T dx = __ldg(el.X0 + q) - xs[0];
+        const T dy = __ldg(el.X1 + q) - xs[1];
+        const T dz = __ldg(el.X2 + q) - xs[2];
+        const T d2 = dx * dx + dy * dy + dz * dz;
+        if (d2 < best) {
+            best = d2;
+            bq = q;
+        }
+    }
+    const int i = bq % n, j = (bq / n) % n, k = bq / (n * n);
+    r[0] = Tab<T>::xi(tab)[i];
+    r[1] = Tab<T>::xi(tab)[j];
+    r[2] = Tab<T>::xi(tab)[k];
+}
+
+struct NewtonArgs {
+    int64_t npairs;
+    int64_t E;
+    const int32_t* order;
+    const int32_t* pair_elem;
+    const int32_t* pair_pt;
+    int64_t P;
+    const double* pts;
+    const double* coords;
+    const float* coords32;
+    const ElemBox* boxes;
+    double* pres;
+    double* prst;
+    int64_t cap;
+    double reject32;      // mixed: reject after FP32 when residual > reject32 * h_e
+    int max_newton;
+};
+
+template <int n, bool MIXED>
+__global__ void __launch_bounds__(256) k_newton(NewtonArgs A, BasisTab tab)
+{
+    constexpr int n3 = n * n * n;
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= A.npairs) return;
+    const int32_t q = A.order[s];
+    const int e = A.pair_elem[q];
+    const int64_t p = A.pair_pt[q];
+    const double xs[3] = {A.pts[p], A.pts[A.P + p], A.pts[2 * A.P + p]};
+    const ElemPtr<double> el64 = {A.coords + (int64_t)e * n3, A.coords + (A.E + e) * n3,
+                                  A.coords + (2 * A.E + e) * n3};
+    double r[3];
+    double res;
+    if (MIXED) {
+        const double* c = A.boxes[e].c;
+        const float xl[3] = {(float)(xs[0] - c[0]), (float)(xs[1] - c[1]), (float)(xs[2] - c[2])};
+        const ElemPtr<float> el32 = {A.coords32 + (int64_t)e * n3, A.coords32 + (A.E + e) * n3,
+                                     A.coords32 + (2 * A.E + e) * n3};
+        float r32[3];
+        seed_nearest<n, float>(el32, tab, xl, r32);
+        const float res32 = newton<n, float, false>(el32, tab, xl, r32, A.max_newton);
+        r[0] = r32[0]; r[1] = r32[1]; r[2] = r32[2];
+        if ((double)res32 > A.reject32 * A.boxes[e].he) {
+            res = (double)res32;                   // clearly not this element
+        } else {
+            res = newton<n, double, true>(el64, tab, xs, r, A.max_newton);
+        }
+    } else {
+        seed_nearest<n, double>(el64, tab, xs, r);
+        res = newton<n, double, true>(el64, tab, xs, r, A.max_newton);
+    }
+    A.pres[q] = res;
+    A.prst[q] = r[0];
+    A.prst[A.cap + q] = r[1];
+    A.prst[2 * A.cap + q] = r[2];
+}
+
+// ---------------------------------------------------------------------------
+// classification and ownership
+// ---------------------------------------------------------------------------
+struct RankArgs {
+    int64_t P;
+    int64_t E;
+    const int32_t* off;
+    const int32_t* pair_elem;
+    const double* pres;
+    const double* prst;
+    int64_t cap;
+    const int32_t* sub;
+    const ElemBox* boxes;
+    const double* dist;
+    int32_t* code;
+    int32_t* osub;
+    int32_t* oelem;
+    double* rst;
+    double* dist2;
+};
+
+template <int n>
+__device__ __forceinline__ double interp_delta(const double* __restrict__ D, const BasisTab& tab, double r0, double r1,
+                                               double r2)
+{
+    double hr[n], hs[n], ht[n];
+    lagrange_h<n, double>(tab.xi, tab.ci, r0, hr);
+    lagrange_h<n, double>(tab.xi, tab.ci, r1, hs);
+    lagrange_h<n, double>(tab.xi, tab.ci, r2, ht);
+    return contract<n, double>(D, hr, hs, ht);
+}
+
+template <int n>
+__global__ void __launch_bounds__(128) k_rank(RankArgs A, FindParams fp, BasisTab tab)
+{
+    constexpr int n3 = n * n * n;
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= A.P) return;
+    const int b = A.off[p], en = A.off[p + 1];
+    // INSIDE winners: lowest element id per subdomain
+    int best_q = -1, nwin = 0;
+    double bmin = INFINITY;
+    for (int q = b; q < en; ++q) {
+        const int e = A.pair_elem[q];
+        const double he = A.boxes[e].he;
+        const double res = A.pres[q];
+        if (res <= fp.tol_accept * he) {
+            const int s = A.sub[e];
+            bool winner = true;
+            for (int q2 = b; q2 < en && winner; ++q2) {
+                const int e2 = A.pair_elem[q2];
+                if (q2 != q && A.sub[e2] == s && e2 < e && A.pres[q2] <= fp.tol_accept * A.boxes[e2].he) winner = false;
+            }
+            if (winner) {
+                ++nwin;
+                if (best_q < 0) best_q = q;
+            }
+        } else if (res <= fp.tol_border * he) {
+            bmin = fmin(bmin, res);
+        }
+    }
+    int pick = -1;
+    int code = 2;
+    if (nwin == 1) {
+        pick = best_q;
+        code = 0;
+    } else if (nwin > 1) {
+        // owner = argmax delta^k(x*), ties within the band -> lower subdomain id
+        double dmax = -INFINITY;
+        for (int pass = 0; pass < 2; ++pass) {
+            int bs = 0x7fffffff;
+            for (int q = b; q < en; ++q) {
+                const int e = A.pair_elem[q];
+                if (!(A.pres[q] <= fp.tol_accept * A.boxes[e].he)) continue;
+                const int s = A.sub[e];
+                bool winner = true;
+                for (int q2 = b; q2 < en && winner; ++q2) {
+                    const int e2 = A.pair_elem[q2];
+                    if (q2 != q && A.sub[e2] == s && e2 < e && A.pres[q2] <= fp.tol_accept * A.boxes[e2].he)
+                        winner = false;
+                }
+                if (!winner) continue;
+                const double dl = A.dist ? interp_delta<n>(A.dist + (int64_t)e * n3, tab, A.prst[q], A.prst[A.cap + q],
+                                                           A.prst[2 * A.cap + q])
+                                         : 0.0;
+                if (pass == 0) {
+                    dmax = fmax(dmax, dl);
+                } else if (dl >= dmax - fp.band && s < bs) {
+                    bs = s;
+                    pick = q;
+                }
+            }
+        }
+        code = 0;
+    } else if (bmin < INFINITY) {
+        int be = 0x7fffffff;
+        for (int q = b; q < en; ++q) {
+            const int e = A.pair_elem[q];
+            const double he = A.boxes[e].he;
+            const double res = A.pres[q];
+            if (res > fp.tol_accept * he && res <= fp.tol_border * he && res <= bmin + fp.band && e < be) {
+                be = e;
+                pick = q;
+            }
+        }
+        code = 1;
+    }
+    if (pick >= 0) {
+        const int e = A.pair_elem[pick];
+        A.code[p] = code;
+        A.osub[p] = A.sub[e];
+        A.oelem[p] = e;
+        A.rst[p] = A.prst[pick];
+        A.rst[A.P + p] = A.prst[A.cap + pick];
+        A.rst[2 * A.P + p] = A.prst[2 * A.cap + pick];
+        const double res = A.pres[pick];
+        A.dist2[p] = res * res;
+    } else {
+        A.code[p] = 2;
+        A.osub[p] = -1;
+        A.oelem[p] = -1;
+        A.rst[p] = 0.0;
+        A.rst[A.P + p] = 0.0;
+        A.rst[2 * A.P + p] = 0.0;
+        A.dist2[p] = INFINITY;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static ScreenArgs screen_args(const FindArgs& a)
+{
+    ScreenArgs s;
+    s.P = a.P;
+    s.pts = a.pts;
+    s.qsess = a.qsess;
+    s.sub = a.sub;
+    s.boxes = a.boxes;
+    s.g = *a.grid;
+    s.cell_start = a.cell_start;
+    s.cell_elems = a.cell_elems;
+    s.cnt = a.cnt;
+    s.off = a.off;
+    s.pair_elem = a.pair_elem;
+    s.pair_pt = a.pair_pt;
+    return s;
+}
+
+cudaError_t find_count(const FindArgs& a, const BasisTab&, const FindParams&, cudaStream_t s)
+{
+    ScreenArgs sa = screen_args(a);
+    k_screen<false><<<(unsigned)((a.P + 255) / 256), 256, 0, s>>>(sa);
+    count_launch();
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    return scan_exclusive(a.cnt, a.off, a.P, a.scan_tmp, s);
+}
+
+cudaError_t find_emit(const FindArgs& a, cudaStream_t s)
+{
+    ScreenArgs sa = screen_args(a);
+    k_screen<true><<<(unsigned)((a.P + 255) / 256), 256, 0, s>>>(sa);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int n>
+static cudaError_t solve_n(const FindArgs& a, int64_t npairs, const BasisTab& tab, const FindParams& fp, int block,
+                           cudaStream_t s)
+{
+    if (npairs > 0) {
+        NewtonArgs na;
+        na.npairs = npairs;
+        na.E = a.E;
+        na.order = a.order;
+        na.pair_elem = a.pair_elem;
+        na.pair_pt = a.pair_pt;
+        na.P = a.P;
+        na.pts = a.pts;
+        na.coords = a.coords;
+        na.coords32 = a.coords32;
+        na.boxes = a.boxes;
+        na.pres = a.pres;
+        na.prst = a.prst;
+        na.cap = a.cap;
+        na.reject32 = 1e-3;
+        na.max_newton = fp.max_newton;
+        const unsigned grid = (unsigned)((npairs + block - 1) / block);
+        if (a.ev[2]) cudaEventRecord(a.ev[2], s);
+        if (fp.mixed)
+            k_newton<n, true><<<grid, block, 0, s>>>(na, tab);
+        else
+            k_newton<n, false><<<grid, block, 0, s>>>(na, tab);
+        count_launch();
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+        if (a.ev[3]) cudaEventRecord(a.ev[3], s);
+    }
+    RankArgs ra;
+    ra.P = a.P;
+    ra.E = a.E;
+    ra.off = a.off;
+    ra.pair_elem = a.pair_elem;
+    ra.pres = a.pres;
+    ra.prst = a.prst;
+    ra.cap = a.cap;
+    ra.sub = a.sub;
+    ra.boxes = a.boxes;
+    ra.dist = a.dist;
+    ra.code = a.code;
+    ra.osub = a.osub;
+    ra.oelem = a.oelem;
+    ra.rst = a.rst;
+    ra.dist2 = a.dist2;
+    if (a.ev[4]) cudaEventRecord(a.ev[4], s);
+    k_rank<n><<<(unsigned)((a.P + 127) / 128), 128, 0, s>>>(ra, fp, tab);
+    count_launch();
+    if (a.ev[5]) cudaEventRecord(a.ev[5], s);
+    return cudaGetLastError();
+}
+
+cudaError_t find_solve(const FindArgs& a, int64_t npairs, const BasisTab& tab, const FindParams& fp, int block,
+                       cudaStream_t s)
+{
+    cudaError_t err;
+    if (npairs > 0) {
+        if (a.ev[0]) cudaEventRecord(a.ev[0], s);
+        err = cudaMemsetAsync(a.ecount, 0, sizeof(int32_t) * a.E, s);
+        if (err != cudaSuccess) return err;
+        k_ehist<<<(unsigned)((npairs + 255) / 256), 256, 0, s>>>(npairs, a.pair_elem, a.ecount);
+        count_launch();
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        if ((err = scan_exclusive(a.ecount, a.estart, a.E, a.scan_tmp, s)) != cudaSuccess) return err;
+        if ((err = cudaMemsetAsync(a.ecount, 0, sizeof(int32_t) * a.E, s)) != cudaSuccess) return err;
+        k_escatter<<<(unsigned)((npairs + 255) / 256), 256, 0, s>>>(npairs, a.pair_elem, a.estart, a.ecount, a.order);
+        count_launch();
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        if (a.ev[1]) cudaEventRecord(a.ev[1], s);
+    }
+    switch (a.n) {
+#define FP_CASE(NN) \
+    case NN: return solve_n<NN>(a, npairs, tab, fp, block, s);
+        FP_CASE(2) FP_CASE(3) FP_CASE(4) FP_CASE(5) FP_CASE(6) FP_CASE(7) FP_CASE(8) FP_CASE(9)
+        FP_CASE(10) FP_CASE(11) FP_CASE(12) FP_CASE(13) FP_CASE(14) FP_CASE(15) FP_CASE(16)
+#undef FP_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace fpg

@@ -1,0 +1,683 @@
+// fp_host.cu -- the C ABI (include/findpts_gb.h): handle, validation,
+// resident mesh state, workspace, and the orchestration of the setup, find
+// and eval kernels.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "fp_common.cuh"
+#include "fp_internal.h"
+
+using namespace fpg;
+
+namespace fpg {
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace fpg
+
+enum { PROF_SCREEN = 0, PROF_SORT = 1, PROF_NEWTON = 2, PROF_RANK = 3, PROF_EVAL = 4, PROF_KINDS = 5 };
+
+struct fp_handle {
+    int N = 0, n = 0;
+    int64_t E = 0;
+    int nsub = 0;
+    fp_opts opts{};
+    BasisTab tab{};
+    HashGrid grid{};
+    int64_t nnz = 0;
+    double L = 0.0;
+    // resident device state
+    double* coords = nullptr;      // [3][E][n3]
+    float* coords32 = nullptr;     // [3][E][n3] element-local FP32 (mixed form)
+    int32_t* sub = nullptr;        // [E]
+    double* dist = nullptr;        // [E][n3] or null
+    ElemBox* boxes = nullptr;      // [E]
+    int32_t* cell_start = nullptr; // [ncell+1]
+    int32_t* cell_elems = nullptr; // [nnz]
+    int32_t* ecount = nullptr;     // [E]
+    int32_t* estart = nullptr;     // [E+1]
+    int32_t* escan_tmp = nullptr;
+    // find workspace
+    int64_t cap_pts = 0, cap_pairs = 0;
+    int32_t* cnt = nullptr;
+    int32_t* off = nullptr;
+    int32_t* scan_tmp = nullptr;
+    int32_t* pair_elem = nullptr;
+    int32_t* pair_pt = nullptr;
+    int32_t* order = nullptr;
+    double* pres = nullptr;
+    double* prst = nullptr;
+    int32_t* h_total = nullptr;    // pinned host word for the pair count
+    std::string err;
+    // optional per-kernel timing with CUDA events on the launching stream
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pend[PROF_KINDS];
+};
+
+static thread_local std::string g_setup_err;
+
+namespace {
+
+fp_status fail(fp_handle* h, fp_status s, const std::string& msg)
+{
+    if (h) h->err = msg;
+    else g_setup_err = msg;
+    return s;
+}
+
+fp_status cuda_fail(fp_handle* h, cudaError_t e, const char* where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(h, e == cudaErrorMemoryAllocation ? FP_ERR_OOM : FP_ERR_CUDA, m);
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, sizeof(T) * count);
+}
+
+template <typename T>
+void dfree(T*& p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+// ---- GLL points: -1, +1 and the interior roots of P_{N+1} - P_{N-1}, which
+// vanish exactly where (1 - x^2) P_N' does; Newton with the derivative
+// identity (P_{N+1} - P_{N-1})' = (2N+1) P_N.
+void legendre3(int N, double x, double* pm1, double* p0, double* pp1)
+{
+    double a = 1.0, b = x;          // P_0, P_1
+    if (N == 0) { *pm1 = 0.0; *p0 = 1.0; *pp1 = x; return; }
+    for (int k = 1; k < N; ++k) {
+        double c = ((2 * k + 1) * x * b - k * a) / (k + 1);
+        a = b;
+        b = c;
+    }
+    *pm1 = a;   // P_{N-1}
+    *p0 = b;    // P_N
+    *pp1 = ((2 * N + 1) * x * b - N * a) / (N + 1);
+}
+
+void gll_points(int N, double* xi)
+{
+    xi[0] = -1.0;
+    xi[N] = 1.0;
+    for (int i = 1; i < N; ++i) {
+        double x = -cos(M_PI * i / N);
+        for (int it = 0; it < 200; ++it) {
+            double pm1, p0, pp1;
+            legendre3(N, x, &pm1, &p0, &pp1);
+            double dx = (pp1 - pm1) / ((2 * N + 1) * p0);
+            x -= dx;
+            if (fabs(dx) <= 1e-16) break;
+        }
+        xi[i] = x;
+    }
+    for (int i = 0; i < (N + 1) / 2; ++i) {
+        double a = 0.5 * (xi[N - i] - xi[i]);
+        xi[i] = -a;
+        xi[N - i] = a;
+    }
+    if (N % 2 == 0) xi[N / 2] = 0.0;
+}
+
+// inverse of the Bernstein collocation matrix V[i][k] = C(N,k) u_i^k (1-u_i)^(N-k),
+// u_i = (xi_i + 1)/2, by Gauss-Jordan elimination with partial pivoting
+bool bernstein_inverse(int N, const double* xi, std::vector<double>& inv, double* norm_inf)
+{
+    const int n = N + 1;
+    std::vector<double> M((size_t)n * 2 * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double u = 0.5 * (xi[i] + 1.0);
+        double binom = 1.0;
+        for (int k = 0; k < n; ++k) {
+            if (k > 0) binom = binom * (N - k + 1) / k;
+            M[(size_t)i * 2 * n + k] = binom * pow(u, k) * pow(1.0 - u, N - k);
+        }
+        M[(size_t)i * 2 * n + n + i] = 1.0;
+    }
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(M[(size_t)r * 2 * n + c]) > fabs(M[(size_t)piv * 2 * n + c])) piv = r;
+        if (M[(size_t)piv * 2 * n + c] == 0.0) return false;
+        if (piv != c)
+            for (int k = 0; k < 2 * n; ++k) std::swap(M[(size_t)c * 2 * n + k], M[(size_t)piv * 2 * n + k]);
+        double d = M[(size_t)c * 2 * n + c];
+        for (int k = 0; k < 2 * n; ++k) M[(size_t)c * 2 * n + k] /= d;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            double f = M[(size_t)r * 2 * n + c];
+            if (f == 0.0) continue;
+            for (int k = 0; k < 2 * n; ++k) M[(size_t)r * 2 * n + k] -= f * M[(size_t)c * 2 * n + k];
+        }
+    }
+    inv.assign((size_t)n * n, 0.0);
+    double nm = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double row = 0.0;
+        for (int k = 0; k < n; ++k) {
+            inv[(size_t)i * n + k] = M[(size_t)i * 2 * n + n + k];
+            row += fabs(inv[(size_t)i * n + k]);
+        }
+        nm = std::max(nm, row);
+    }
+    *norm_inf = nm;
+    return true;
+}
+
+void make_tab(int N, BasisTab* t)
+{
+    memset(t, 0, sizeof(*t));
+    double xi[NMAX];
+    gll_points(N, xi);
+    for (int i = 0; i <= N; ++i) {
+        double p = 1.0;
+        for (int m = 0; m <= N; ++m)
+            if (m != i) p *= (xi[i] - xi[m]);
+        t->xi[i] = xi[i];
+        t->ci[i] = 1.0 / p;
+        t->xif[i] = (float)xi[i];
+        t->cif[i] = (float)(1.0 / p);
+    }
+}
+
+cudaEvent_t ev_get(fp_handle* h)
+{
+    if (!h->ev_free.empty()) {
+        cudaEvent_t e = h->ev_free.back();
+        h->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+void release(fp_handle* h)
+{
+    for (int k = 0; k < PROF_KINDS; ++k) {
+        for (auto& pr : h->ev_pend[k]) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        h->ev_pend[k].clear();
+    }
+    for (auto e : h->ev_free) cudaEventDestroy(e);
+    h->ev_free.clear();
+    dfree(h->coords); dfree(h->coords32); dfree(h->sub); dfree(h->dist); dfree(h->boxes);
+    dfree(h->cell_start); dfree(h->cell_elems); dfree(h->ecount); dfree(h->estart); dfree(h->escan_tmp);
+    dfree(h->cnt); dfree(h->off); dfree(h->scan_tmp); dfree(h->pair_elem); dfree(h->pair_pt);
+    dfree(h->order); dfree(h->pres); dfree(h->prst);
+    if (h->h_total) cudaFreeHost(h->h_total);
+    h->h_total = nullptr;
+}
+
+fp_status grow_points(fp_handle* h, int64_t P)
+{
+    if (P <= h->cap_pts) return FP_OK;
+    int64_t cap = std::max<int64_t>(P, 1024);
+    cudaDeviceSynchronize();
+    dfree(h->cnt); dfree(h->off); dfree(h->scan_tmp);
+    cudaError_t e;
+    if ((e = dalloc(&h->cnt, cap)) != cudaSuccess ||
+        (e = dalloc(&h->off, cap + 1)) != cudaSuccess ||
+        (e = dalloc(&h->scan_tmp, std::max(scan_tmp_elems(cap), scan_tmp_elems(h->E)))) != cudaSuccess) {
+        h->cap_pts = 0;
+        return cuda_fail(h, e, "workspace (points)");
+    }
+    h->cap_pts = cap;
+    return FP_OK;
+}
+
+fp_status grow_pairs(fp_handle* h, int64_t np)
+{
+    if (np <= h->cap_pairs) return FP_OK;
+    int64_t cap = std::max<int64_t>(np + np / 4, 2048);
+    cudaDeviceSynchronize();
+    dfree(h->pair_elem); dfree(h->pair_pt); dfree(h->order); dfree(h->pres); dfree(h->prst);
+    cudaError_t e;
+    if ((e = dalloc(&h->pair_elem, cap)) != cudaSuccess || (e = dalloc(&h->pair_pt, cap)) != cudaSuccess ||
+        (e = dalloc(&h->order, cap)) != cudaSuccess || (e = dalloc(&h->pres, cap)) != cudaSuccess ||
+        (e = dalloc(&h->prst, 3 * cap)) != cudaSuccess) {
+        h->cap_pairs = 0;
+        return cuda_fail(h, e, "workspace (pairs)");
+    }
+    h->cap_pairs = cap;
+    return FP_OK;
+}
+
+}  // namespace
+
+namespace fpg {
+cudaError_t launch_count_nonfinite(int64_t n, const double* x, int32_t* out, cudaStream_t s);
+}
+
+extern "C" {
+
+void fp_default_opts(fp_opts* o)
+{
+    if (!o) return;
+    o->precision = FP_PREC_FP64;
+    o->tol_accept = 1e-12;
+    o->tol_border = 1e-6;
+    o->max_newton = 40;
+    o->hash_cells_per_elem = 1.0;
+    o->tie_band = 1e-10;
+    o->points_per_block = 0;
+}
+
+const char* fp_error_string(fp_status s)
+{
+    switch (s) {
+        case FP_OK: return "ok";
+        case FP_ERR_INVALID_ARG: return "invalid argument";
+        case FP_ERR_OOM: return "device out of memory";
+        case FP_ERR_CUDA: return "CUDA error";
+        case FP_ERR_TIMEOUT: return "device-side wait timed out";
+        case FP_ERR_NOT_SETUP: return "handle not set up";
+    }
+    return "unknown status";
+}
+
+const char* fp_last_error(const fp_handle* h)
+{
+    return h ? h->err.c_str() : g_setup_err.c_str();
+}
+
+fp_status fp_setup(fp_handle** hout, const double* coords, int64_t E, int N, const int32_t* sub,
+                   const double* dist, const fp_opts* opts_in, void* stream)
+{
+    if (!hout) return fail(nullptr, FP_ERR_INVALID_ARG, "fp_setup: null handle pointer");
+    *hout = nullptr;
+    g_setup_err.clear();
+    if (!coords) return fail(nullptr, FP_ERR_INVALID_ARG, "fp_setup: null coords");
+    if (E < 1 || E >= (int64_t(1) << 31)) return fail(nullptr, FP_ERR_INVALID_ARG, "fp_setup: E out of range");
+    if (N < 1 || N >= NMAX) return fail(nullptr, FP_ERR_INVALID_ARG, "fp_setup: N must be in [1,15]");
+    fp_opts o;
+    fp_default_opts(&o);
+    if (opts_in) o = *opts_in;
+    if ((o.precision != FP_PREC_FP64 && o.precision != FP_PREC_MIXED) || !(o.tol_accept > 0) ||
+        !(o.tol_border >= o.tol_accept) || o.max_newton < 1 || o.max_newton > 1000 ||
+        !(o.hash_cells_per_elem > 0) || !(o.tie_band >= 0) || o.points_per_block < 0 ||
+        o.points_per_block > 256 || (o.points_per_block % 32) != 0)
+        return fail(nullptr, FP_ERR_INVALID_ARG, "fp_setup: options out of range");
+    const int n = N + 1, n3 = n * n * n;
+    if ((int64_t)E * n3 * 3 >= (int64_t(1) << 40)) return fail(nullptr, FP_ERR_INVALID_ARG, "fp_setup: mesh too large");
+    cudaStream_t s = (cudaStream_t)stream;
+
+    fp_handle* h = new fp_handle();
+    h->N = N; h->n = n; h->E = E; h->opts = o;
+    make_tab(N, &h->tab);
+    cudaError_t err;
+    const size_t ncoord = (size_t)3 * E * n3;
+#define CK(call, where) do { if ((err = (call)) != cudaSuccess) { fp_status st = cuda_fail(nullptr, err, where); release(h); delete h; return st; } } while (0)
+#define BAD(msg) do { fail(nullptr, FP_ERR_INVALID_ARG, msg); release(h); delete h; return FP_ERR_INVALID_ARG; } while (0)
+
+    CK(dalloc(&h->coords, ncoord), "alloc coords");
+    CK(cudaMemcpyAsync(h->coords, coords, sizeof(double) * ncoord, cudaMemcpyDefault, s), "copy coords");
+    CK(dalloc(&h->sub, E), "alloc sub");
+    if (sub) CK(cudaMemcpyAsync(h->sub, sub, sizeof(int32_t) * E, cudaMemcpyDefault, s), "copy sub");
+    else CK(cudaMemsetAsync(h->sub, 0, sizeof(int32_t) * E, s), "zero sub");
+    CK(cudaMallocHost((void**)&h->h_total, sizeof(int32_t) * 4), "alloc pinned");
+
+    // validation: finite coordinates, subdomain ids in range
+    {
+        int32_t* d_bad;
+        CK(dalloc(&d_bad, 1), "alloc flag");
+        cudaMemsetAsync(d_bad, 0, sizeof(int32_t), s);
+        err = launch_count_nonfinite((int64_t)ncoord, h->coords, d_bad, s);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(h->h_total, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+        cudaFree(d_bad);
+        CK(err, "check coords");
+        if (h->h_total[0] != 0) BAD("fp_setup: non-finite coordinates");
+        std::vector<int32_t> hs(E);
+        CK(cudaMemcpy(hs.data(), h->sub, sizeof(int32_t) * E, cudaMemcpyDeviceToHost), "read sub");
+        std::vector<char> seen(65536, 0);
+        int ns = 0;
+        for (int64_t e = 0; e < E; ++e) {
+            if (hs[e] < 0 || hs[e] >= 65536) BAD("fp_setup: subdomain id out of [0,65536)");
+            if (!seen[hs[e]]) { seen[hs[e]] = 1; ++ns; }
+        }
+        h->nsub = ns;
+    }
+
+    // A1: hulls
+    std::vector<double> binv;
+    double binv_norm = 1.0;
+    {
+        double xi[NMAX];
+        for (int i = 0; i < n; ++i) xi[i] = h->tab.xi[i];
+        if (!bernstein_inverse(N, xi, binv, &binv_norm)) BAD("fp_setup: Bernstein matrix singular");
+    }
+    double* d_binv = nullptr;
+    double* d_nodebox = nullptr;
+    CK(dalloc(&d_binv, binv.size()), "alloc binv");
+    CK(cudaMemcpyAsync(d_binv, binv.data(), sizeof(double) * binv.size(), cudaMemcpyHostToDevice, s), "copy binv");
+    CK(dalloc(&h->boxes, E), "alloc boxes");
+    CK(dalloc(&d_nodebox, 6 * E), "alloc nodebox");
+    const double pad_conv = 64.0 * 2.220446049250313e-16 * binv_norm * n;
+    CK(launch_hull(n, E, h->coords, d_binv, o.tol_border, pad_conv, h->boxes, d_nodebox, s), "hull");
+    const int nred = (int)std::min<int64_t>(1024, (E + 255) / 256);
+    double* d_red = nullptr;
+    CK(dalloc(&d_red, 12 * nred), "alloc red");
+    CK(launch_reduce_boxes(E, h->boxes, d_nodebox, d_red, nred, s), "reduce boxes");
+    std::vector<double> red(12 * nred);
+    CK(cudaMemcpyAsync(red.data(), d_red, sizeof(double) * 12 * nred, cudaMemcpyDeviceToHost, s), "read red");
+    CK(cudaStreamSynchronize(s), "sync hull");
+    cudaFree(d_red);
+    cudaFree(d_binv);
+    cudaFree(d_nodebox);
+    double glo[3], ghi[3], nlo[3], nhi[3];
+    for (int a = 0; a < 3; ++a) {
+        glo[a] = INFINITY; ghi[a] = -INFINITY; nlo[a] = INFINITY; nhi[a] = -INFINITY;
+        for (int b = 0; b < nred; ++b) {
+            glo[a] = std::min(glo[a], red[12 * b + a]);
+            ghi[a] = std::max(ghi[a], red[12 * b + 3 + a]);
+            nlo[a] = std::min(nlo[a], red[12 * b + 6 + a]);
+            nhi[a] = std::max(nhi[a], red[12 * b + 9 + a]);
+        }
+    }
+    {
+        double dx = nhi[0] - nlo[0], dy = nhi[1] - nlo[1], dz = nhi[2] - nlo[2];
+        double sq = dx * dx;
+        sq = sq + dy * dy;
+        sq = sq + dz * dz;
+        h->L = sqrt(sq);
+    }
+
+    // A2: hash grid over the global padded box
+    {
+        double ext[3], vol = 1.0;
+        int nd = 0;
+        for (int a = 0; a < 3; ++a) {
+            ext[a] = ghi[a] - glo[a];
+            if (ext[a] > 0) { vol *= ext[a]; ++nd; }
+        }
+        double target = std::max(1.0, o.hash_cells_per_elem * (double)E);
+        double hc = nd > 0 ? pow(vol / target, 1.0 / nd) : 1.0;
+        int64_t dims[3];
+        for (int it = 0; it < 64; ++it) {
+            int64_t tot = 1;
+            for (int a = 0; a < 3; ++a) {
+                dims[a] = ext[a] > 0 ? std::max<int64_t>(1, (int64_t)ceil(ext[a] / hc)) : 1;
+                dims[a] = std::min<int64_t>(dims[a], 1 << 20);
+                tot *= dims[a];
+            }
+            if (tot <= (int64_t(1) << 26)) break;
+            hc *= 1.25;
+        }
+        for (int a = 0; a < 3; ++a) {
+            h->grid.org[a] = glo[a];
+            h->grid.dim[a] = (int)dims[a];
+            h->grid.inv[a] = ext[a] > 0 ? (double)dims[a] / ext[a] : 0.0;
+        }
+        h->grid.ncell = dims[0] * dims[1] * dims[2];
+    }
+    const int64_t ncell = h->grid.ncell;
+    int32_t *d_cnt = nullptr, *d_tmp = nullptr;
+    CK(dalloc(&d_cnt, ncell), "alloc hash count");
+    CK(dalloc(&h->cell_start, ncell + 1), "alloc cell start");
+    CK(dalloc(&d_tmp, scan_tmp_elems(ncell)), "alloc scan tmp");
+    CK(cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * ncell, s), "zero hash count");
+    CK(launch_hash_count(E, h->boxes, h->grid, d_cnt, s), "hash count");
+    CK(scan_exclusive(d_cnt, h->cell_start, ncell, d_tmp, s), "hash scan");
+    CK(cudaMemcpyAsync(h->h_total, h->cell_start + ncell, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read nnz");
+    CK(cudaStreamSynchronize(s), "sync hash");
+    h->nnz = h->h_total[0];
+    if (h->nnz < 0) BAD("fp_setup: hash grid overflow");
+    CK(dalloc(&h->cell_elems, h->nnz), "alloc cell elems");
+    CK(cudaMemcpyAsync(d_cnt, h->cell_start, sizeof(int32_t) * ncell, cudaMemcpyDeviceToDevice, s), "copy cursor");
+    CK(launch_hash_fill(E, h->boxes, h->grid, d_cnt, h->cell_elems, s), "hash fill");
+    CK(launch_hash_sort(ncell, h->cell_start, h->cell_elems, s), "hash sort");
+    CK(cudaStreamSynchronize(s), "sync hash fill");
+    cudaFree(d_cnt);
+    cudaFree(d_tmp);
+
+    // distance field for the owner rule
+    if (dist) {
+        CK(dalloc(&h->dist, (size_t)E * n3), "alloc dist");
+        CK(cudaMemcpyAsync(h->dist, dist, sizeof(double) * E * n3, cudaMemcpyDefault, s), "copy dist");
+    } else if (h->nsub > 1) {
+        double* fc = nullptr;
+        int32_t *nb = nullptr, *nboff = nullptr, *tmp2 = nullptr;
+        CK(dalloc(&fc, 72 * E), "alloc face corners");
+        CK(dalloc(&nb, 6 * E), "alloc face flags");
+        CK(dalloc(&nboff, 6 * E + 1), "alloc face offsets");
+        CK(dalloc(&tmp2, scan_tmp_elems(6 * E)), "alloc face scan");
+        CK(launch_face_corners(n, E, h->coords, fc, s), "face corners");
+        CK(launch_face_boundary(E, fc, h->sub, h->grid, h->cell_start, h->cell_elems, nb, s), "face boundary");
+        CK(scan_exclusive(nb, nboff, 6 * E, tmp2, s), "face scan");
+        CK(cudaMemcpyAsync(h->h_total, nboff + 6 * E, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read nbnd");
+        CK(cudaStreamSynchronize(s), "sync faces");
+        const int64_t nbf = h->h_total[0];
+        const int64_t nbn = nbf * n * n;
+        if ((double)E * n3 * (double)nbn > 137438953472.0) {   // 2^37 node x boundary-node pairs
+            cudaFree(fc); cudaFree(nb); cudaFree(nboff); cudaFree(tmp2);
+            BAD("fp_setup: mesh too large for the default distance field; pass dist");
+        }
+        double* bx = nullptr;
+        int32_t* bs = nullptr;
+        CK(dalloc(&bx, 3 * std::max<int64_t>(nbn, 1)), "alloc boundary nodes");
+        CK(dalloc(&bs, std::max<int64_t>(nbn, 1)), "alloc boundary subs");
+        CK(dalloc(&h->dist, (size_t)E * n3), "alloc dist");
+        CK(launch_face_gather(n, E, h->coords, h->sub, nboff, bx, bs, nbn, s), "face gather");
+        CK(launch_dist_default(n, E, h->coords, h->sub, bx, bs, nbn, h->dist, s), "dist default");
+        CK(cudaStreamSynchronize(s), "sync dist");
+        cudaFree(fc); cudaFree(nb); cudaFree(nboff); cudaFree(tmp2); cudaFree(bx); cudaFree(bs);
+    }
+
+    // mixed form: element-local FP32 geometry
+    if (o.precision == FP_PREC_MIXED) {
+        CK(dalloc(&h->coords32, ncoord), "alloc coords32");
+        CK(launch_local32(n, E, h->coords, h->boxes, h->coords32, s), "local32");
+    }
+    CK(dalloc(&h->ecount, E), "alloc ecount");
+    CK(dalloc(&h->estart, E + 1), "alloc estart");
+    CK(cudaStreamSynchronize(s), "sync setup");
+#undef CK
+#undef BAD
+    *hout = h;
+    return FP_OK;
+}
+
+fp_status fp_reserve(fp_handle* h, int64_t P)
+{
+    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (P < 0) return fail(h, FP_ERR_INVALID_ARG, "fp_reserve: P < 0");
+    fp_status st = grow_points(h, P);
+    if (st != FP_OK) return st;
+    return grow_pairs(h, 2 * P);
+}
+
+fp_status fp_find(fp_handle* h, int64_t P, const double* pts, const int32_t* qsess, int32_t* code, int32_t* sub,
+                  int32_t* elem, double* rst, double* dist2, void* stream)
+{
+    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    h->err.clear();
+    if (P < 0 || P >= (int64_t(1) << 31)) return fail(h, FP_ERR_INVALID_ARG, "fp_find: P out of range");
+    if (P == 0) return FP_OK;
+    if (!pts || !code || !sub || !elem || !rst || !dist2)
+        return fail(h, FP_ERR_INVALID_ARG, "fp_find: null pointer argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    fp_status st = grow_points(h, P);
+    if (st != FP_OK) return st;
+    FindArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = h->n; a.E = h->E; a.P = P; a.pts = pts; a.qsess = qsess;
+    a.coords = h->coords; a.coords32 = h->coords32; a.sub = h->sub;
+    a.dist = h->nsub > 1 ? h->dist : nullptr;
+    a.boxes = h->boxes; a.grid = &h->grid; a.cell_start = h->cell_start; a.cell_elems = h->cell_elems;
+    a.cnt = h->cnt; a.off = h->off; a.ecount = h->ecount; a.estart = h->estart; a.scan_tmp = h->scan_tmp;
+    a.code = code; a.osub = sub; a.oelem = elem; a.rst = rst; a.dist2 = dist2;
+    cudaEvent_t scr0 = nullptr, scr1 = nullptr;
+    if (h->prof) {
+        for (int q = 0; q < 6; ++q) a.ev[q] = ev_get(h);
+        scr0 = ev_get(h);
+        scr1 = ev_get(h);
+        cudaEventRecord(scr0, s);
+    }
+    FindParams fp;
+    fp.tol_accept = h->opts.tol_accept;
+    fp.tol_border = h->opts.tol_border;
+    fp.band = h->opts.tie_band * h->L;
+    fp.max_newton = h->opts.max_newton;
+    fp.mixed = h->opts.precision == FP_PREC_MIXED;
+    cudaError_t err = find_count(a, h->tab, fp, s);
+    if (err != cudaSuccess) return cuda_fail(h, err, "fp_find count");
+    err = cudaMemcpyAsync(h->h_total, h->off + P, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) return cuda_fail(h, err, "fp_find pair count");
+    const int64_t npairs = h->h_total[0];
+    if (npairs < 0) return fail(h, FP_ERR_INVALID_ARG, "fp_find: candidate pairs overflow int32");
+    st = grow_pairs(h, npairs);
+    if (st != FP_OK) return st;
+    a.pair_elem = h->pair_elem; a.pair_pt = h->pair_pt; a.order = h->order;
+    a.pres = h->pres; a.prst = h->prst; a.cap = h->cap_pairs;
+    if (npairs > 0) {
+        err = find_emit(a, s);
+        if (err != cudaSuccess) return cuda_fail(h, err, "fp_find emit");
+    }
+    if (h->prof) {
+        cudaEventRecord(scr1, s);
+        h->ev_pend[PROF_SCREEN].push_back({scr0, scr1});
+    }
+    const int block = h->opts.points_per_block > 0 ? h->opts.points_per_block : 128;
+    err = find_solve(a, npairs, h->tab, fp, block, s);
+    if (h->prof) {
+        if (npairs > 0) {
+            h->ev_pend[PROF_SORT].push_back({a.ev[0], a.ev[1]});
+            h->ev_pend[PROF_NEWTON].push_back({a.ev[2], a.ev[3]});
+        } else {
+            for (int q = 0; q < 4; ++q) h->ev_free.push_back(a.ev[q]);
+        }
+        h->ev_pend[PROF_RANK].push_back({a.ev[4], a.ev[5]});
+    }
+    if (err != cudaSuccess) return cuda_fail(h, err, "fp_find solve");
+    return FP_OK;
+}
+
+fp_status fp_eval(fp_handle* h, int64_t P, const int32_t* code, const int32_t* elem, const double* rst, int F,
+                  const double* fields, double* out, void* stream)
+{
+    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    h->err.clear();
+    if (P < 0 || F < 1) return fail(h, FP_ERR_INVALID_ARG, "fp_eval: P < 0 or F < 1");
+    if (P == 0) return FP_OK;
+    if (!code || !elem || !rst || !fields || !out) return fail(h, FP_ERR_INVALID_ARG, "fp_eval: null pointer");
+    if ((h->n % 2 == 0) && ((uintptr_t)fields % 16) != 0)
+        return fail(h, FP_ERR_INVALID_ARG, "fp_eval: fields must be 16-byte aligned for even n");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->prof) {
+        e0 = ev_get(h);
+        e1 = ev_get(h);
+        cudaEventRecord(e0, (cudaStream_t)stream);
+    }
+    cudaError_t err = launch_eval(h->n, h->E, P, code, elem, rst, F, fields, out, h->tab, (cudaStream_t)stream);
+    if (h->prof) {
+        cudaEventRecord(e1, (cudaStream_t)stream);
+        h->ev_pend[PROF_EVAL].push_back({e0, e1});
+    }
+    if (err != cudaSuccess) return cuda_fail(h, err, "fp_eval");
+    return FP_OK;
+}
+
+void fp_free(fp_handle* h)
+{
+    if (!h) return;
+    cudaDeviceSynchronize();
+    release(h);
+    delete h;
+}
+
+fp_status fp_profile(fp_handle* h, int enable)
+{
+    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    h->prof = enable != 0;
+    return FP_OK;
+}
+
+fp_status fp_profile_read(fp_handle* h, int kind, double* total_ms, int64_t* launches)
+{
+    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (kind < 0 || kind >= PROF_KINDS) return fail(h, FP_ERR_INVALID_ARG, "fp_profile_read: kind out of range");
+    double tot = 0.0;
+    int64_t cnt = 0;
+    for (auto& pr : h->ev_pend[kind]) {
+        float ms = 0.0f;
+        cudaError_t e = cudaEventSynchronize(pr.second);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+        if (e != cudaSuccess) return cuda_fail(h, e, "fp_profile_read");
+        tot += ms;
+        ++cnt;
+        h->ev_free.push_back(pr.first);
+        h->ev_free.push_back(pr.second);
+    }
+    h->ev_pend[kind].clear();
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = cnt;
+    return FP_OK;
+}
+
+int64_t fp_launch_count(void) { return fpg::g_launches.load(); }
+
+fp_status fp_info(const fp_handle* h, int64_t* E, int* N, int64_t* ncell, int64_t* nnz, int* nsub)
+{
+    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (E) *E = h->E;
+    if (N) *N = h->N;
+    if (ncell) *ncell = h->grid.ncell;
+    if (nnz) *nnz = h->nnz;
+    if (nsub) *nsub = h->nsub;
+    return FP_OK;
+}
+
+fp_status fp_debug_boxes(const fp_handle* h, double* aabb, double* grid, int32_t* cell_start, int32_t* cell_elems,
+                         void* stream)
+{
+    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t err = cudaSuccess;
+    if (aabb) {
+        for (int a = 0; a < 3 && err == cudaSuccess; ++a) {
+            err = cudaMemcpy2DAsync(aabb + a, 6 * sizeof(double), (const char*)h->boxes + offsetof(ElemBox, blo) + a * sizeof(double),
+                                    sizeof(ElemBox), sizeof(double), h->E, cudaMemcpyDeviceToDevice, s);
+            if (err == cudaSuccess)
+                err = cudaMemcpy2DAsync(aabb + 3 + a, 6 * sizeof(double),
+                                        (const char*)h->boxes + offsetof(ElemBox, bhi) + a * sizeof(double),
+                                        sizeof(ElemBox), sizeof(double), h->E, cudaMemcpyDeviceToDevice, s);
+        }
+    }
+    if (grid && err == cudaSuccess) {
+        double g[9];
+        for (int a = 0; a < 3; ++a) {
+            g[a] = h->grid.org[a];
+            g[3 + a] = h->grid.inv[a];
+            g[6 + a] = (double)h->grid.dim[a];
+        }
+        err = cudaMemcpyAsync(grid, g, sizeof(g), cudaMemcpyHostToDevice, s);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    }
+    if (cell_start && err == cudaSuccess)
+        err = cudaMemcpyAsync(cell_start, h->cell_start, sizeof(int32_t) * (h->grid.ncell + 1), cudaMemcpyDeviceToDevice, s);
+    if (cell_elems && err == cudaSuccess)
+        err = cudaMemcpyAsync(cell_elems, h->cell_elems, sizeof(int32_t) * std::max<int64_t>(h->nnz, 0),
+                              cudaMemcpyDeviceToDevice, s);
+    if (err != cudaSuccess) return FP_ERR_CUDA;
+    return FP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// fp_internal.h -- launcher declarations shared between the library's
+// translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fpg {
+
+// number of kernels this library has launched (process-wide, for reporting)
+void count_launch(int k = 1);
+
+struct ElemBox;
+struct HashGrid;
+struct BasisTab;
+struct FindParams;
+
+// setup (fp_setup.cu)
+cudaError_t launch_hull(int n, int64_t E, const double* coords, const double* binv, double pad_border,
+                        double pad_conv, ElemBox* boxes, double* nodebox, cudaStream_t s);
+cudaError_t launch_reduce_boxes(int64_t E, const ElemBox* boxes, const double* nodebox, double* out,
+                                int nblocks, cudaStream_t s);
+cudaError_t launch_hash_count(int64_t E, const ElemBox* boxes, const HashGrid& g, int32_t* cnt, cudaStream_t s);
+cudaError_t launch_hash_fill(int64_t E, const ElemBox* boxes, const HashGrid& g, int32_t* cur, int32_t* elems,
+                             cudaStream_t s);
+cudaError_t launch_hash_sort(int64_t ncell, const int32_t* start, int32_t* elems, cudaStream_t s);
+cudaError_t launch_face_corners(int n, int64_t E, const double* coords, double* fc, cudaStream_t s);
+cudaError_t launch_face_boundary(int64_t E, const double* fc, const int32_t* sub, const HashGrid& g,
+                                 const int32_t* cstart, const int32_t* celems, int32_t* nbnd, cudaStream_t s);
+cudaError_t launch_face_gather(int n, int64_t E, const double* coords, const int32_t* sub, const int32_t* bnd_off,
+                               double* bx, int32_t* bs, int64_t nb, cudaStream_t s);
+cudaError_t launch_dist_default(int n, int64_t E, const double* coords, const int32_t* sub, const double* bx,
+                                const int32_t* bs, int64_t nb, double* D, cudaStream_t s);
+cudaError_t launch_local32(int n, int64_t E, const double* coords, const ElemBox* boxes, float* c32,
+                           cudaStream_t s);
+
+// scans (fp_scan.cu): out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
+// tmp must hold scan_tmp_elems(n) int32 entries.
+int64_t scan_tmp_elems(int64_t n);
+cudaError_t scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, cudaStream_t s);
+
+// find (fp_find.cu)
+struct FindArgs {
+    int n;
+    int64_t E;
+    int64_t P;
+    const double* pts;
+    const int32_t* qsess;
+    const double* coords;
+    const float* coords32;
+    const int32_t* sub;
+    const double* dist;
+    const ElemBox* boxes;
+    const HashGrid* grid;         // host copy
+    const int32_t* cell_start;
+    const int32_t* cell_elems;
+    // scratch
+    int32_t* cnt;                 // [P]
+    int32_t* off;                 // [P+1]
+    int32_t* pair_elem;           // [cap]
+    int32_t* pair_pt;             // [cap]
+    int32_t* ecount;              // [E]  (zeroed by the launcher)
+    int32_t* estart;              // [E+1]
+    int32_t* order;               // [cap]
+    double* pres;                 // [cap]
+    double* prst;                 // [3][cap]
+    int32_t* scan_tmp;
+    int64_t cap;
+    // optional timing events (null = off): [0,1] sort, [2,3] newton, [4,5] rank
+    cudaEvent_t ev[6];
+    // outputs
+    int32_t* code;
+    int32_t* osub;
+    int32_t* oelem;
+    double* rst;
+    double* dist2;
+};
+cudaError_t find_count(const FindArgs& a, const BasisTab& tab, const FindParams& fp, cudaStream_t s);
+cudaError_t find_emit(const FindArgs& a, cudaStream_t s);
+cudaError_t find_solve(const FindArgs& a, int64_t npairs, const BasisTab& tab, const FindParams& fp,
+                       int block, cudaStream_t s);
+
+// eval (fp_eval.cu)
+cudaError_t launch_eval(int n, int64_t E, int64_t P, const int32_t* code, const int32_t* elem, const double* rst,
+                        int F, const double* fields, double* out, const BasisTab& tab, cudaStream_t s);
+
+}  // namespace fpg

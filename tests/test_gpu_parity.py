@@ -1,0 +1,216 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.  Codes, subdomains and elements must match bit for bit;
+|delta r| <= 1e-12 in the FP64 form and <= 1e-10 in the mixed form; eval
+within 1e-12 of the field's max nodal magnitude."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import assert_parity, gpu_find, oracle_find
+
+pytestmark = pytest.mark.gpu
+PRECS = [0, 1]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1811_04891_gb300 as fg
+    fg.lib()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_config0_full(prec):
+    mesh, q = synth.config0()
+    g = gpu_find(mesh, q.pts, prec=prec, fields=q.fields)
+    r = oracle_find(mesh, q.pts, fields=q.fields)
+    assert (r["code"] == oracle.INSIDE).all()
+    assert_parity(g, r, prec, fields=q.fields)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_config1_interface_points(prec):
+    mesh, q = synth.config1()
+    g = gpu_find(mesh, q.pts, q.qsess, prec=prec, fields=q.fields)
+    r = oracle_find(mesh, q.pts, q.qsess, fields=q.fields)
+    assert_parity(g, r, prec, fields=q.fields)
+    # session exclusion: a tagged point never comes back from its own session
+    found = r["code"] != oracle.NOT_FOUND
+    assert np.all(g["sub"][found] != q.qsess[found])
+    assert found.mean() > 0.99
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_config1_untagged_owner_rule(prec):
+    """Untagged points in the box/cylinder overlap: owner = argmax delta^k."""
+    mesh, _ = synth.config1()
+    rng = np.random.default_rng(11)
+    th = rng.uniform(0, 2 * np.pi, 4000)
+    rho = rng.uniform(0.14, 0.36, 4000)
+    pts = np.stack([1 + rho * np.cos(th), 0.5 + rho * np.sin(th), rng.uniform(0.0, 1.0, 4000)])
+    g = gpu_find(mesh, pts, prec=prec)
+    r = oracle_find(mesh, pts)
+    assert_parity(g, r, prec)
+    assert set(np.unique(r["sub"][r["code"] == 0])) == {0, 1}
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_config2_reduced_with_near_face(prec):
+    mesh, q = synth.config2(ne=8, P_uniform=30011, P_face=5003)
+    g = gpu_find(mesh, q.pts, prec=prec, fields=q.fields)
+    r = oracle_find(mesh, q.pts, fields=q.fields)
+    assert_parity(g, r, prec, fields=q.fields)
+    assert (r["code"] == oracle.INSIDE).all()
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 5, 9, 12, 15])
+@pytest.mark.parametrize("prec", PRECS)
+def test_forward_recovery_all_orders(N, prec):
+    coords = synth.box_mesh((3, 2, 3), N, amp_frac=0.1)
+    mesh = synth.Mesh(coords=coords, N=N, sub=np.zeros(coords.shape[1], np.int32))
+    rng = np.random.default_rng(100 + N)
+    E = coords.shape[1]
+    P = 257
+    els = rng.integers(0, E, P)
+    r = rng.uniform(-0.97, 0.97, (3, P))
+    pts = np.empty((3, P))
+    for e in np.unique(els):
+        sel = els == e
+        x, _ = oracle.map_points(coords, N, int(e), r[:, sel])
+        pts[:, sel] = x
+    fields = synth.field_u(coords)[None]
+    g = gpu_find(mesh, pts, prec=prec, fields=fields)
+    ref = oracle_find(mesh, pts, fields=fields)
+    assert_parity(g, ref, prec, fields=fields)
+    np.testing.assert_array_equal(g["elem"], els)
+    assert np.abs(g["rst"] - r).max() <= 1e-11
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_edge_cases(prec):
+    import paper_1811_04891_gb300 as fg
+    N = 4
+    coords = synth.box_mesh((2, 2, 2), N)
+    mesh = synth.Mesh(coords=coords, N=N, sub=np.zeros(8, np.int32))
+    h_e = np.sqrt(3) * 0.5
+    xi = oracle.gll(N)[0]
+    pts = np.array([
+        [0.3, 0.3, 1.0 + 0.2e-6 * h_e],        # border
+        [0.3, 0.3, 1.0 + 10e-6 * h_e],         # not found
+        [-5.0, 0.0, 0.0],
+        [np.nan, 0.5, 0.5],
+        [0.5, np.inf, 0.5],
+        [1.0, 1.0, 1.0],                       # mesh corner
+        [0.5, 0.5, 0.5],                       # vertex shared by 8 elements
+        [0.25 * (1 + xi[1]), 0.5, 0.75],       # GLL node on a shared face
+        [1.0 + 0.5e-6 * h_e, 1.0 + 0.5e-6 * h_e, 0.5],   # border near an edge
+    ]).T
+    g = gpu_find(mesh, pts, prec=prec)
+    r = oracle_find(mesh, pts)
+    assert_parity(g, r, prec)
+    np.testing.assert_array_equal(g["code"], [1, 2, 2, 2, 2, 0, 0, 0, 1])
+    # empty query
+    h = g["handle"]
+    dev = torch.device("cuda:0")
+    out = fg.fp_find(h, torch.zeros((3, 0), dtype=torch.float64, device=dev))
+    assert out[0].numel() == 0
+    ev = fg.fp_eval(h, out[0], out[2], out[3], torch.zeros((1, 8, 125), dtype=torch.float64, device=dev))
+    assert ev.shape == (1, 0)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_tiny_overlap_owner_rule_all_tags(prec):
+    mesh = synth.tiny_overlap(N=4)
+    rng = np.random.default_rng(12)
+    xs = np.concatenate([rng.uniform(-0.05, 2.05, 600), [0.8, 0.8, 0.6, 1.0, 1.6]])
+    P = xs.size
+    pts = np.stack([xs, rng.uniform(0.02, 0.98, P), rng.uniform(0.02, 0.98, P)])
+    for tag in (-1, 0, 1, 2):
+        qs = np.full(P, tag, np.int32)
+        g = gpu_find(mesh, pts, qs, prec=prec)
+        r = oracle_find(mesh, pts, qs)
+        assert_parity(g, r, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_default_distance_field(prec):
+    """No D supplied: both sides compute the nodal distance to boundary-face
+    nodes of each subdomain (oracle brute force, device hash-accelerated)."""
+    N = 3
+    a = synth.box_mesh((3, 2, 2), N, lo=(0, 0, 0), hi=(1.2, 1, 1), amp_frac=0.05)
+    b = synth.box_mesh((2, 2, 2), N, lo=(0.7, 0.1, 0.2), hi=(1.9, 0.9, 1.1), amp_frac=0.05)
+    c = synth.box_mesh((2, 2, 1), N, lo=(0.9, -0.2, 0.3), hi=(1.5, 1.2, 0.8))
+    mesh = synth.concat_meshes([a, b, c], N, [0, 1, 2])
+    D = oracle.dist_default(mesh.coords, N, mesh.sub)
+    pts = synth.uniform_points(3000, 13, lo=(0, -0.2, 0), hi=(1.9, 1.2, 1.1))
+    g = gpu_find(mesh, pts, prec=prec, dist=None)
+    r = oracle_find(mesh, pts, dist=D)
+    assert_parity(g, r, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_spiral_element_N15(prec):
+    N = 15
+    coords, amap = synth.spiral_element(N)
+    mesh = synth.Mesh(coords=coords, N=N, sub=np.zeros(1, np.int32))
+    rng = np.random.default_rng(8)
+    r = rng.uniform(-0.98, 0.98, (3, 1000))
+    pts = amap(r[0], r[1], r[2])
+    g = gpu_find(mesh, pts, prec=prec, tol_accept=1e-10)
+    ref = oracle_find(mesh, pts, params=oracle.Params(tol_accept=1e-10, prefilter=False, n_restarts=8))
+    assert_parity(g, ref, prec)
+    assert (g["code"] == 0).all()
+
+
+def test_invariance_hash_and_block():
+    mesh, q = synth.config2(ne=6, P_uniform=20000, P_face=2000)
+    base = gpu_find(mesh, q.pts, prec=0)
+    for kw in ({"hash_cells_per_elem": 0.2}, {"hash_cells_per_elem": 4.0}, {"points_per_block": 64},
+               {"points_per_block": 256}):
+        g = gpu_find(mesh, q.pts, prec=0, **kw)
+        for k in ("code", "sub", "elem", "rst", "dist2"):
+            np.testing.assert_array_equal(g[k], base[k], err_msg=str(kw))
+
+
+def test_hull_and_hash_contain_elements():
+    import paper_1811_04891_gb300 as fg
+    N = 7
+    coords = synth.box_mesh((3, 3, 2), N, amp_frac=0.3)
+    coords[0] += 0.02 * np.sin(7 * coords[1])
+    E = coords.shape[1]
+    dev = torch.device("cuda:0")
+    h = fg.fp_setup(torch.from_numpy(coords).to(dev), N, torch.zeros(E, dtype=torch.int32, device=dev))
+    aabb, grid, cs, ce = [t.cpu().numpy() for t in fg.fp_debug_boxes(h)]
+    rng = np.random.default_rng(3)
+    for e in range(E):
+        r = rng.uniform(-1, 1, (3, 2000))
+        r[:, :8] = np.array(np.meshgrid([-1, 1], [-1, 1], [-1, 1])).reshape(3, 8)
+        x, _ = oracle.map_points(coords, N, e, r)
+        assert np.all(x >= aabb[e, :3, None]) and np.all(x <= aabb[e, 3:, None])
+    # brute-force overlap: every cell an element's box touches lists it
+    org, inv, dims = grid[:3], grid[3:6], grid[6:].astype(int)
+    lists = [set(ce[cs[c]:cs[c + 1]]) for c in range(len(cs) - 1)]
+    for e in range(E):
+        lo = np.clip(np.floor((aabb[e, :3] - org) * inv).astype(int), 0, dims - 1)
+        hi = np.clip(np.floor((aabb[e, 3:] - org) * inv).astype(int), 0, dims - 1)
+        for k in range(lo[2], hi[2] + 1):
+            for j in range(lo[1], hi[1] + 1):
+                for i in range(lo[0], hi[0] + 1):
+                    assert e in lists[i + dims[0] * (j + dims[1] * k)]
+    assert sum(len(s) for s in lists) == h.info()["nnz"]
+
+
+def test_errors_are_reported():
+    import paper_1811_04891_gb300 as fg
+    dev = torch.device("cuda:0")
+    bad = torch.zeros((3, 2, 8), dtype=torch.float64, device=dev)
+    bad[0, 0, 0] = float("nan")
+    with pytest.raises(fg.FindptsError) as ei:
+        fg.fp_setup(bad, 1)
+    assert ei.value.status == fg.FP_ERR_INVALID_ARG
+    with pytest.raises(fg.FindptsError):
+        fg.fp_setup(torch.zeros((3, 2, 8), dtype=torch.float64, device=dev), 1,
+                    torch.tensor([0, 70000], dtype=torch.int32, device=dev))
