@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Throughput of the findpts + findpts_eval hot path on GB300.
+
+Workload: the precision-form-at-scale configuration -- a 32^3 = 32768-element
+deformed hex cube at N=7 (interior nodes displaced by 0.1 h sin sin sin),
+1e7 uniform query points plus 1e5 points within 1e-9 of element faces, five
+FP64 fields.  One step = fp_find over all 10,100,000 points followed by
+fp_eval of the five fields, with the mesh, hash grid and inputs resident in
+HBM (setup is timed separately).  Metric: located+interpolated points/s.
+
+The headline `value` is the mixed form (FP32 seed and early Newton steps,
+FP64 final step, residual, classification and eval); the FP64 form is timed
+in the same run under `forms`.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (brute force, FP64, OpenMP on the
+host cores) on bounded samples of the same workload.  Under torchrun each
+rank processes its own copy of the workload (weak scaling, no collective on
+the data path); `value` is all ranks' points / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "located+interpolated points/s (mixed vs FP64 form, N=7); serving p50/p99 ms"
+UNIT = "points/s"
+# Peaks for the ALU-bound Newton kernel, from the nominal GB300 figures: FP64
+# 1.25 TFLOP/s; FP32 = 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s.
+P64_NOMINAL = 1.25e12
+P32_NOMINAL = 152 * 128 * 2 * 2.07e9
+# Algorithmic work per located point at N=7 (n = 8): nearest-node seed 4.1 kflop,
+# one Newton iteration with Jacobian 8.4 kflop, a value-only residual 3.5 kflop,
+# one field evaluation 1.17 kflop.  FP64 form: seed + 4 iterations in FP64.
+# Mixed form: seed + 4 iterations in FP32, then 1 iteration + 1 residual in FP64.
+SEED, ITER, RESID, EVAL1 = 4.1e3, 8.4e3, 3.5e3, 1.17e3
+WORK = {"fp64": {"f64": SEED + 4 * ITER, "f32": 0.0},
+        "mixed": {"f64": ITER + RESID, "f32": SEED + 4 * ITER}}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--forms", default="mixed,fp64")
+    ap.add_argument("--ne", type=int, default=32)
+    ap.add_argument("--points", type=int, default=10 ** 7)
+    ap.add_argument("--face-points", type=int, default=10 ** 5)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(args):
+    import synth
+    mesh, q = synth.config2(ne=args.ne, P_uniform=args.points, P_face=args.face_points)
+    return mesh, q
+
+
+def config_dict(args, mesh, q, form_note=""):
+    return {"workload": f"deformed cube {args.ne}^3 hex N=7 (amp 0.1h), {args.points} uniform + "
+                        f"{args.face_points} near-face points, 5 FP64 fields; find + eval per step",
+            "E": int(mesh.E), "N": int(mesh.N), "points_per_step": int(q.P), "fields": 5,
+            "l2_flush": "inputs larger than L2 (points 242 MB, coords 403 MB, fields 671 MB)",
+            "setup": "mesh, boxes and hash grid resident; setup timed separately"}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[4 + i] and "Not" not in r[4 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_rate(mesh, q, seconds: float, stride_seed: int = 0):
+    """Time the oracle's find + eval on a strided sample of the workload
+    sized to take about `seconds`; returns (points/s, sample size, cores, s)."""
+    import oracle
+    P = q.P
+
+    def run(idx):
+        pts = np.ascontiguousarray(q.pts[:, idx])
+        t0 = time.perf_counter()
+        r = oracle.find(mesh.coords, mesh.N, mesh.sub, pts)
+        oracle.evaluate(mesh.N, r["code"], r["elem"], r["rst"], q.fields)
+        return time.perf_counter() - t0
+
+    m0 = min(P, 2000)
+    idx0 = np.arange(stride_seed % max(1, P // m0), P, max(1, P // m0))[:m0]
+    dt0 = run(idx0)
+    rate0 = len(idx0) / max(dt0, 1e-9)
+    m = int(min(P, max(len(idx0), rate0 * seconds)))
+    idx = np.arange(0, P, max(1, P // m))[:m]
+    dt = run(idx)
+    return len(idx) / dt, len(idx), oracle.num_threads(), dt
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    mesh, q = workload(args)
+    vals = []
+    per_step = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    for s in range(args.warmup):
+        oracle_rate(mesh, q, per_step, stride_seed=s)
+    samples = []
+    for s in range(args.steps):
+        rate, m, cores, dt = oracle_rate(mesh, q, per_step, stride_seed=args.warmup + s)
+        vals.append(rate)
+        samples.append(m)
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * q.P / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(args, mesh, q),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"strided samples of {min(samples)}-{max(samples)} of the {q.P} points per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    import paper_1811_04891_gb300 as fg
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    mesh, q = workload(args)
+    P = q.P
+    coords = torch.from_numpy(mesh.coords).to(dev)
+    sub = torch.from_numpy(mesh.sub).to(dev)
+    fields = torch.from_numpy(q.fields).to(dev)
+    pts = torch.from_numpy(q.pts).to(dev)
+    F = fields.shape[0]
+    stream = torch.cuda.current_stream(dev)
+    code = torch.empty(P, dtype=torch.int32, device=dev)
+    osub = torch.empty_like(code)
+    elem = torch.empty_like(code)
+    rst = torch.empty((3, P), dtype=torch.float64, device=dev)
+    d2 = torch.empty(P, dtype=torch.float64, device=dev)
+    out = torch.empty((F, P), dtype=torch.float64, device=dev)
+    outs = (code, osub, elem, rst, d2)
+
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+
+    forms = [f.strip() for f in args.forms.split(",") if f.strip()]
+    results = {}
+    handles = {}
+    for form in forms:
+        prec = fg.PREC_MIXED if form == "mixed" else fg.PREC_FP64
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = fg.fp_setup(coords, mesh.N, sub, opts=fg.default_opts(precision=prec))
+        torch.cuda.synchronize()
+        setup_ms = 1e3 * (time.perf_counter() - t0)
+        fg.fp_reserve(h, P)
+        handles[form] = h
+
+        def step():
+            fg.fp_find(h, pts, None, out=outs)
+            fg.fp_eval(h, code, elem, rst, fields, out=out)
+
+        for _ in range(max(args.warmup, 1)):
+            step()
+        torch.cuda.synchronize()
+        fg.fp_profile(h, True)
+        for k in fg.PROF_KINDS:
+            fg.fp_profile_read(h, k)
+        clocks = ClockSampler(uuid)
+        clocks.start()
+        time.sleep(0.3)
+        barrier()
+        torch.cuda.synchronize()
+        l0 = fg.fp_launch_count()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        launches = fg.fp_launch_count() - l0
+        ms = ev0.elapsed_time(ev1)
+        clk = clocks.stop()
+        fg.fp_profile(h, False)
+        kt = {k: fg.fp_profile_read(h, k) for k in fg.PROF_KINDS}
+        ms_max = max_over_ranks(ms)
+        counts = torch.bincount(code.long(), minlength=3).tolist()
+        npairs = fg.fp_last_find_stats(h)
+        results[form] = {"ms_per_step": ms_max / args.steps, "value": world * P * args.steps / (ms_max / 1e3),
+                         "setup_ms": setup_ms, "gpu_launches": launches, "clocks": clk,
+                         "kernel_ms": {k: (v[0] / max(v[1], 1)) for k, v in kt.items()},
+                         "codes": {"inside": counts[0], "border": counts[1], "not_found": counts[2]},
+                         "pairs_per_point": npairs / P}
+
+    head = "mixed" if "mixed" in results else forms[0]
+    R = results[head]
+    # roofline of the dominant kernel (Newton), algorithmic flops per launch
+    kn = R["kernel_ms"]["newton"] / 1e3
+    w = WORK[head]
+    f64, f32 = w["f64"] * P, w["f32"] * P
+    t_roof = f64 / P64_NOMINAL + f32 / P32_NOMINAL
+    achieved = (f64 + f32 * P64_NOMINAL / P32_NOMINAL) / kn
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": P64_NOMINAL / 1e12,
+            "unit": "TFLOP/s (FP64-equivalent: FP64 flops + FP32 flops x P64/P32)",
+            "frac": t_roof / kn, "traffic": None, "kernel": f"k_newton<8,{str(head == 'mixed').lower()}>",
+            "peak_source": "nominal GB300 FP64 1.25 TFLOP/s; FP32 152 SMs x 128 x 2 x 2.07 GHz"}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h = handles[head]
+        pts_h = torch.from_numpy(q.pts).pin_memory()
+        out_h = torch.empty((F, P), dtype=torch.float64).pin_memory()
+        code_h = torch.empty(P, dtype=torch.int32).pin_memory()
+        pts_d = torch.empty_like(pts)
+
+        def e2e_step():
+            pts_d.copy_(pts_h, non_blocking=True)
+            fg.fp_find(h, pts_d, None, out=outs)
+            fg.fp_eval(h, code, elem, rst, fields, out=out)
+            out_h.copy_(out, non_blocking=True)
+            code_h.copy_(code, non_blocking=True)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": world * P * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(pts_h.numel() * 8),
+               "d2h_bytes_per_step": int(out_h.numel() * 8 + code_h.numel() * 4)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, m, cores, dt = oracle_rate(mesh, q, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{m} of the {P} points (strided), find + eval, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": R["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": R["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32" if head == "mixed" else "f64",
+                "data": "synthetic", "config": config_dict(args, mesh, q), "form": head,
+                "forms": {k: {"value": v["value"], "ms_per_step": v["ms_per_step"], "setup_ms": v["setup_ms"],
+                              "kernel_ms": v["kernel_ms"], "codes": v["codes"],
+                              "pairs_per_point": v["pairs_per_point"]} for k, v in results.items()},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": R["gpu_launches"],
+                "clocks": R["clocks"]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

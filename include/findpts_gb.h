@@ -164,6 +164,10 @@ fp_status fp_profile_read(fp_handle *h, int kind, double *total_ms, int64_t *lau
 /* Number of kernels the library has launched in this process. */
 int64_t fp_launch_count(void);
 
+/* Number of (point, candidate element) pairs that survived the box screen in
+   the handle's most recent fp_find (each pair gets one Newton solve). */
+fp_status fp_last_find_stats(const fp_handle *h, int64_t *npairs);
+
 /* Introspection for tests: E, N, number of hash cells, number of
    cell -> element entries, number of subdomains. */
 fp_status fp_info(const fp_handle *h, int64_t *E, int *N, int64_t *ncell, int64_t *nnz,

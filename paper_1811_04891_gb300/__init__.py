@@ -78,6 +78,8 @@ def _load():
     L.fp_profile_read.restype = ci
     L.fp_launch_count.argtypes = []
     L.fp_launch_count.restype = i64
+    L.fp_last_find_stats.argtypes = [vp, ctypes.POINTER(i64)]
+    L.fp_last_find_stats.restype = ci
     _lib = L
     return L
 
@@ -209,6 +211,13 @@ def fp_profile_read(h: Handle, kind: str):
     ms, n = ctypes.c_double(), ctypes.c_int64()
     _check(lib().fp_profile_read(h.ptr, PROF_KINDS[kind], ctypes.byref(ms), ctypes.byref(n)), h.ptr)
     return ms.value, n.value
+
+
+def fp_last_find_stats(h: Handle) -> int:
+    """Candidate pairs of the handle's last fp_find."""
+    n = ctypes.c_int64()
+    _check(lib().fp_last_find_stats(h.ptr, ctypes.byref(n)), h.ptr)
+    return n.value
 
 
 def fp_launch_count() -> int:

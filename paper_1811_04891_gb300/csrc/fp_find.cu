@@ -220,7 +220,7 @@ __device__ __forceinline__ int gn_step(const T (&J)[9], const T (&f)[3], const T
 
 template <typename T> struct Lim;
 template <> struct Lim<double> {
-    static constexpr double quick = 1e-6;     // full Newton step size that ends the loop
+    static constexpr double quick = 1e-4;     // full Newton step size that hands over to chord steps
     static constexpr double chord = 1e-13;    // chord correction that confirms convergence
     static constexpr double stop = 1e-13;     // accepted step that ends a constrained solve
     static constexpr double rho_min = 1e-15;
@@ -232,63 +232,104 @@ template <> struct Lim<float> {
     static constexpr float rho_min = 1e-7f;
 };
 
-// Box-constrained trust-region Newton (Sec. 2.1) from r (in/out).
-// Returns the residual norm ||x(r) - x*|| at the returned r.  With FINAL
-// (the FP64 phase) a small full Newton step is confirmed by a value-only
-// residual and a chord correction with the current Jacobian; without it
-// (FP32 phase) the loop simply stops after such a step.
-template <int n, typename T, bool FINAL>
-__device__ T newton(const ElemPtr<T>& el, const BasisTab& tab, const T (&xs)[3], T (&r)[3], int max_it)
+// Box truncation of a step d at r: largest t <= 1 with r + t d in the box;
+// the new point lands exactly on the bound it was cut at.
+template <typename T>
+__device__ __forceinline__ T box_step(const T (&r)[3], const T (&d)[3], T (&rn)[3])
 {
-    T f[3], J[9];
+    T t = T(1);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        if (d[b] > T(0) && r[b] + d[b] > T(1)) t = fmin(t, (T(1) - r[b]) / d[b]);
+        if (d[b] < T(0) && r[b] + d[b] < T(-1)) t = fmin(t, (T(-1) - r[b]) / d[b]);
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        T v = r[b] + t * d[b];
+        if (t < T(1)) {
+            if (d[b] > T(0) && (T(1) - r[b]) / d[b] == t) v = T(1);
+            if (d[b] < T(0) && (T(-1) - r[b]) / d[b] == t) v = T(-1);
+        }
+        rn[b] = fmin(T(1), fmax(T(-1), v));
+    }
+    return t;
+}
+
+// Chord iterations in FP64: value-only residuals with a fixed Jacobian J and
+// the active-set step.  Converged when the next step is <= 1e-13 in every
+// coordinate (r is then kept with its own residual).  Returns true on
+// convergence; `res` is the residual norm at the returned r.
+template <int n>
+__device__ bool chord64(const ElemPtr<double>& el, const BasisTab& tab, const double (&xs)[3], double (&r)[3],
+                        const double (&J)[9], double& res, int max_chord)
+{
+    for (int it = 0; it < max_chord; ++it) {
+        double f[3];
+        eval_f<n, double>(el, tab, r, xs, f);
+        res = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+        if (!(res > 0.0)) return true;
+        double d[3];
+        if (gn_step<double>(J, f, r, d) == 0) return true;         // KKT point at a vertex
+        double rn[3];
+        box_step<double>(r, d, rn);
+        const double sn = fmax(fabs(rn[0] - r[0]), fmax(fabs(rn[1] - r[1]), fabs(rn[2] - r[2])));
+        if (sn <= Lim<double>::chord) return true;
+        r[0] = rn[0]; r[1] = rn[1]; r[2] = rn[2];
+    }
+    return false;
+}
+
+// Box-constrained trust-region Newton (Sec. 2.1) from r (in/out); J returns
+// the Jacobian at (or one small step before) the returned r.  Returns the
+// residual norm ||x(r) - x*|| at the returned r.  With FINAL (FP64) a small
+// full Newton step hands over to chord iterations with the current Jacobian;
+// without it (FP32 phase of the mixed form) the loop stops after such a step.
+template <int n, typename T, bool FINAL>
+__device__ T newton(const ElemPtr<T>& el, const BasisTab& tab, const T (&xs)[3], T (&r)[3], T (&J)[9], int max_it,
+                    bool& converged)
+{
+    T f[3];
     eval_fJ<n, T>(el, tab, r, xs, f, J);
     T phi = T(0.5) * (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
     T rho = T(1);
+    converged = true;
     for (int it = 0; it < max_it; ++it) {
-        if (!(phi > T(0))) break;
+        if (!(phi > T(0))) return T(0);
         T d[3];
-        if (gn_step<T>(J, f, r, d) == 0) break;
+        const int nfree = gn_step<T>(J, f, r, d);
+        if (nfree == 0) return sqrt(T(2) * phi);          // KKT point at a vertex
         const T dn = fmax(fabs(d[0]), fmax(fabs(d[1]), fabs(d[2])));
-        if (!(dn > T(0))) break;
+        if (!(dn > T(0))) return sqrt(T(2) * phi);
         bool full = true;
         if (dn > rho) {
             const T sc = rho / dn;
             d[0] *= sc; d[1] *= sc; d[2] *= sc;
             full = false;
         }
-        T t = T(1);
+        T rn[3];
+        if (box_step<T>(r, d, rn) < T(1)) full = false;
+        T s[3];
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            if (d[b] > T(0) && r[b] + d[b] > T(1)) t = fmin(t, (T(1) - r[b]) / d[b]);
-            if (d[b] < T(0) && r[b] + d[b] < T(-1)) t = fmin(t, (T(-1) - r[b]) / d[b]);
-        }
-        if (t < T(1)) full = false;
-        T rn[3], s[3];
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            T v = r[b] + t * d[b];
-            if (t < T(1)) {
-                if (d[b] > T(0) && (T(1) - r[b]) / d[b] == t) v = T(1);
-                if (d[b] < T(0) && (T(-1) - r[b]) / d[b] == t) v = T(-1);
-            }
-            rn[b] = fmin(T(1), fmax(T(-1), v));
-            s[b] = rn[b] - r[b];
-        }
+        for (int b = 0; b < 3; ++b) s[b] = rn[b] - r[b];
         const T sn = fmax(fabs(s[0]), fmax(fabs(s[1]), fabs(s[2])));
-        if (!(sn > T(0))) break;
-        if (full && dn <= Lim<T>::quick) {
-            r[0] = rn[0]; r[1] = rn[1]; r[2] = rn[2];
-            if (!FINAL) return sqrt(T(2) * phi);
-            T fn[3];
-            eval_f<n, T>(el, tab, r, xs, fn);
-            T d2[3];
-            const bool ok = newton_solve3<T>(J, fn, d2);
-            f[0] = fn[0]; f[1] = fn[1]; f[2] = fn[2];
-            phi = T(0.5) * (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
-            if (ok && fmax(fabs(d2[0]), fmax(fabs(d2[1]), fabs(d2[2]))) <= Lim<T>::chord) break;
-            eval_fJ<n, T>(el, tab, r, xs, f, J);      // not yet converged: refresh J
-            phi = T(0.5) * (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
-            continue;
+        if (!(sn > T(0))) return sqrt(T(2) * phi);
+        // a small unconstrained Newton step: quadratic convergence from here
+        if (full && nfree == 3 && dn <= Lim<T>::quick) {
+            if constexpr (!FINAL) {
+                r[0] = rn[0]; r[1] = rn[1]; r[2] = rn[2];
+                return sqrt(T(2) * phi);
+            } else {
+                T rc[3] = {rn[0], rn[1], rn[2]};
+                T res;
+                if (chord64<n>(el, tab, xs, rc, J, res, 3)) {
+                    r[0] = rc[0]; r[1] = rc[1]; r[2] = rc[2];
+                    return res;
+                }
+                r[0] = rc[0]; r[1] = rc[1]; r[2] = rc[2];   // not yet converged: refresh J
+                eval_fJ<n, T>(el, tab, r, xs, f, J);
+                phi = T(0.5) * (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+                continue;
+            }
         }
         T mf[3];
 #pragma unroll
@@ -300,9 +341,11 @@ __device__ T newton(const ElemPtr<T>& el, const BasisTab& tab, const T (&xs)[3],
         if (sn <= Lim<T>::stop) {
             if (phin <= phi) {
                 r[0] = rn[0]; r[1] = rn[1]; r[2] = rn[2];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) J[q] = Jn[q];
                 phi = phin;
             }
-            break;
+            return sqrt(T(2) * phi);
         }
         if (phin < phi) {
             const T ratio = pred > T(0) ? (phi - phin) / pred : T(0);
@@ -318,6 +361,7 @@ __device__ T newton(const ElemPtr<T>& el, const BasisTab& tab, const T (&xs)[3],
             if (rho < Lim<T>::rho_min) break;
         }
     }
+    converged = false;                                     // iteration cap or collapsed radius
     return sqrt(T(2) * phi);
 }
 
@@ -375,25 +419,35 @@ __global__ void __launch_bounds__(256) k_newton(NewtonArgs A, BasisTab tab)
     const double xs[3] = {A.pts[p], A.pts[A.P + p], A.pts[2 * A.P + p]};
     const ElemPtr<double> el64 = {A.coords + (int64_t)e * n3, A.coords + (A.E + e) * n3,
                                   A.coords + (2 * A.E + e) * n3};
-    double r[3];
+    double r[3], J[9];
     double res;
     if (MIXED) {
         const double* c = A.boxes[e].c;
         const float xl[3] = {(float)(xs[0] - c[0]), (float)(xs[1] - c[1]), (float)(xs[2] - c[2])};
         const ElemPtr<float> el32 = {A.coords32 + (int64_t)e * n3, A.coords32 + (A.E + e) * n3,
                                      A.coords32 + (2 * A.E + e) * n3};
-        float r32[3];
+        float r32[3], J32[9];
         seed_nearest<n, float>(el32, tab, xl, r32);
-        const float res32 = newton<n, float, false>(el32, tab, xl, r32, A.max_newton);
+        bool conv32;
+        const float res32 = newton<n, float, false>(el32, tab, xl, r32, J32, A.max_newton, conv32);
         r[0] = r32[0]; r[1] = r32[1]; r[2] = r32[2];
-        if ((double)res32 > A.reject32 * A.boxes[e].he) {
-            res = (double)res32;                   // clearly not this element
+        bool conv64;
+        if (conv32 && (double)res32 > A.reject32 * A.boxes[e].he) {
+            res = (double)res32;                   // converged well away from the element
+        } else if (!conv32) {
+            res = newton<n, double, true>(el64, tab, xs, r, J, A.max_newton, conv64);
         } else {
-            res = newton<n, double, true>(el64, tab, xs, r, A.max_newton);
+            // FP64 final steps: FP64 residuals and 3x3 solves, Jacobian from
+            // the FP32 phase (chord); full FP64 Newton if that stalls
+#pragma unroll
+            for (int q = 0; q < 9; ++q) J[q] = (double)J32[q];
+            if (!chord64<n>(el64, tab, xs, r, J, res, 4))
+                res = newton<n, double, true>(el64, tab, xs, r, J, A.max_newton, conv64);
         }
     } else {
         seed_nearest<n, double>(el64, tab, xs, r);
-        res = newton<n, double, true>(el64, tab, xs, r, A.max_newton);
+        bool conv64;
+        res = newton<n, double, true>(el64, tab, xs, r, J, A.max_newton, conv64);
     }
     A.pres[q] = res;
     A.prst[q] = r[0];
@@ -587,7 +641,7 @@ static cudaError_t solve_n(const FindArgs& a, int64_t npairs, const BasisTab& ta
         na.pres = a.pres;
         na.prst = a.prst;
         na.cap = a.cap;
-        na.reject32 = 1e-3;
+        na.reject32 = 1e-4;
         na.max_newton = fp.max_newton;
         const unsigned grid = (unsigned)((npairs + block - 1) / block);
         if (a.ev[2]) cudaEventRecord(a.ev[2], s);

@@ -54,6 +54,7 @@ struct fp_handle {
     double* pres = nullptr;
     double* prst = nullptr;
     int32_t* h_total = nullptr;    // pinned host word for the pair count
+    int64_t last_pairs = 0;
     std::string err;
     // optional per-kernel timing with CUDA events on the launching stream
     bool prof = false;
@@ -543,6 +544,7 @@ fp_status fp_find(fp_handle* h, int64_t P, const double* pts, const int32_t* qse
     if (err != cudaSuccess) return cuda_fail(h, err, "fp_find pair count");
     const int64_t npairs = h->h_total[0];
     if (npairs < 0) return fail(h, FP_ERR_INVALID_ARG, "fp_find: candidate pairs overflow int32");
+    h->last_pairs = npairs;
     st = grow_pairs(h, npairs);
     if (st != FP_OK) return st;
     a.pair_elem = h->pair_elem; a.pair_pt = h->pair_pt; a.order = h->order;
@@ -633,6 +635,13 @@ fp_status fp_profile_read(fp_handle* h, int kind, double* total_ms, int64_t* lau
 }
 
 int64_t fp_launch_count(void) { return fpg::g_launches.load(); }
+
+fp_status fp_last_find_stats(const fp_handle* h, int64_t* npairs)
+{
+    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (npairs) *npairs = h->last_pairs;
+    return FP_OK;
+}
 
 fp_status fp_info(const fp_handle* h, int64_t* E, int* N, int64_t* ncell, int64_t* nnz, int* nsub)
 {
