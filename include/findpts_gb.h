@@ -141,6 +141,30 @@ fp_status fp_eval(fp_handle *h, int64_t P, const int32_t *code, const int32_t *e
                   const double *rst, int F, const double *fields, double *out,
                   void *stream);
 
+/* fp_find_static -- fp_find for callers that cannot allocate device memory
+ * at call time: a solver whose device memory is all handed to its own pool
+ * allocator, code running under CUDA stream capture (where cudaMalloc and
+ * cudaFree are not permitted), or a latency-bound loop that cannot afford
+ * their implicit device synchronisation.  The paper has no counterpart; this
+ * is a deployment variant of fp_find.
+ * Same arguments, outputs, rules and results as fp_find, for at most
+ * FP_STATIC_MAX_POINTS points and FP_STATIC_MAX_PAIRS candidate pairs per
+ * call (larger requests return FP_ERR_INVALID_ARG before any device work).
+ * All per-call scratch lives in one file-scope device array of about 2.8 MB
+ * that every GPU loading the library holds until exit; the call makes no
+ * cudaMalloc / cudaFree or other allocating call.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * should come before any stream capture.  All calls share the array and it
+ * keeps the last call's contents (no part of it needs to start at zero);
+ * calls that overlap on the GPU race on it and must be serialised.  Like
+ * fp_find it waits for `stream` once, to read the number of pairs.
+ * Errors: FP_ERR_NOT_SETUP, FP_ERR_INVALID_ARG, FP_ERR_CUDA. */
+#define FP_STATIC_MAX_POINTS 16384
+#define FP_STATIC_MAX_PAIRS 65536
+fp_status fp_find_static(fp_handle *h, int64_t P, const double *pts, const int32_t *qsess,
+                         int32_t *code, int32_t *sub, int32_t *elem, double *rst,
+                         double *dist2, void *stream);
+
 /* Release every device resource of the handle (synchronises it first).
    NULL is a no-op. */
 void fp_free(fp_handle *h);

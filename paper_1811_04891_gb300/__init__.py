@@ -59,6 +59,8 @@ def _load():
     L.fp_reserve.restype = ci
     L.fp_find.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     L.fp_find.restype = ci
+    L.fp_find_static.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.fp_find_static.restype = ci
     L.fp_eval.argtypes = [vp, i64, vp, vp, vp, ci, vp, vp, vp]
     L.fp_eval.restype = ci
     L.fp_free.argtypes = [vp]
@@ -179,6 +181,28 @@ def fp_find(h: Handle, pts: torch.Tensor, qsess: Optional[torch.Tensor] = None, 
     code, sub, elem, rst, dist2 = out
     st = lib().fp_find(h.ptr, P, _ptr(pts), _ptr(qsess), _ptr(code), _ptr(sub), _ptr(elem), _ptr(rst),
                        _ptr(dist2), _stream(stream))
+    _check(st, h.ptr)
+    return code, sub, elem, rst, dist2
+
+
+STATIC_MAX_POINTS = 16384
+
+
+def fp_find_static(h: Handle, pts: torch.Tensor, qsess: Optional[torch.Tensor] = None, out=None, stream=None):
+    """fp_find without any device allocation in the call (scratch in a fixed
+    device array; at most STATIC_MAX_POINTS points).  Pass preallocated
+    `out` tensors to keep the whole call allocation-free."""
+    pts = _dev(pts, torch.float64, "pts")
+    P = pts.shape[1]
+    qsess = None if qsess is None else _dev(qsess, torch.int32, "qsess")
+    dev = pts.device
+    if out is None:
+        out = (torch.empty(P, dtype=torch.int32, device=dev), torch.empty(P, dtype=torch.int32, device=dev),
+               torch.empty(P, dtype=torch.int32, device=dev), torch.empty((3, P), dtype=torch.float64, device=dev),
+               torch.empty(P, dtype=torch.float64, device=dev))
+    code, sub, elem, rst, dist2 = out
+    st = lib().fp_find_static(h.ptr, P, _ptr(pts), _ptr(qsess), _ptr(code), _ptr(sub), _ptr(elem), _ptr(rst),
+                              _ptr(dist2), _stream(stream))
     _check(st, h.ptr)
     return code, sub, elem, rst, dist2
 

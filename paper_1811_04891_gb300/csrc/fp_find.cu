@@ -705,4 +705,18 @@ cudaError_t find_solve(const FindArgs& a, int64_t npairs, const BasisTab& tab, c
     }
 }
 
+// Newton + classification on pairs already in `a.order` (no pair sort).
+cudaError_t find_solve_unsorted(const FindArgs& a, int64_t npairs, const BasisTab& tab, const FindParams& fp,
+                                int block, cudaStream_t s)
+{
+    switch (a.n) {
+#define FP_CASE(NN) \
+    case NN: return solve_n<NN>(a, npairs, tab, fp, block, s);
+        FP_CASE(2) FP_CASE(3) FP_CASE(4) FP_CASE(5) FP_CASE(6) FP_CASE(7) FP_CASE(8) FP_CASE(9)
+        FP_CASE(10) FP_CASE(11) FP_CASE(12) FP_CASE(13) FP_CASE(14) FP_CASE(15) FP_CASE(16)
+#undef FP_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace fpg

@@ -1,0 +1,52 @@
+// fp_handle.h -- the opaque handle behind the C ABI (shared by the
+// translation units that implement entry points).
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "fp_common.cuh"
+
+enum { PROF_SCREEN = 0, PROF_SORT = 1, PROF_NEWTON = 2, PROF_RANK = 3, PROF_EVAL = 4, PROF_KINDS = 5 };
+
+struct fp_handle {
+    int N = 0, n = 0;
+    int64_t E = 0;
+    int nsub = 0;
+    fp_opts opts{};
+    fpg::BasisTab tab{};
+    fpg::HashGrid grid{};
+    int64_t nnz = 0;
+    double L = 0.0;
+    // resident device state
+    double* coords = nullptr;      // [3][E][n3]
+    float* coords32 = nullptr;     // [3][E][n3] element-local FP32 (mixed form)
+    int32_t* sub = nullptr;        // [E]
+    double* dist = nullptr;        // [E][n3] or null
+    fpg::ElemBox* boxes = nullptr;      // [E]
+    int32_t* cell_start = nullptr; // [ncell+1]
+    int32_t* cell_elems = nullptr; // [nnz]
+    int32_t* ecount = nullptr;     // [E]
+    int32_t* estart = nullptr;     // [E+1]
+    int32_t* escan_tmp = nullptr;
+    // find workspace
+    int64_t cap_pts = 0, cap_pairs = 0;
+    int32_t* cnt = nullptr;
+    int32_t* off = nullptr;
+    int32_t* scan_tmp = nullptr;
+    int32_t* pair_elem = nullptr;
+    int32_t* pair_pt = nullptr;
+    int32_t* order = nullptr;
+    double* pres = nullptr;
+    double* prst = nullptr;
+    int32_t* h_total = nullptr;    // pinned host word for the pair count
+    int64_t last_pairs = 0;
+    std::string err;
+    // optional per-kernel timing with CUDA events on the launching stream
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pend[PROF_KINDS];
+};
+

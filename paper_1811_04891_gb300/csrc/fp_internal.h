@@ -78,6 +78,8 @@ cudaError_t find_count(const FindArgs& a, const BasisTab& tab, const FindParams&
 cudaError_t find_emit(const FindArgs& a, cudaStream_t s);
 cudaError_t find_solve(const FindArgs& a, int64_t npairs, const BasisTab& tab, const FindParams& fp,
                        int block, cudaStream_t s);
+cudaError_t find_solve_unsorted(const FindArgs& a, int64_t npairs, const BasisTab& tab, const FindParams& fp,
+                                int block, cudaStream_t s);
 
 // eval (fp_eval.cu)
 cudaError_t launch_eval(int n, int64_t E, int64_t P, const int32_t* code, const int32_t* elem, const double* rst,
