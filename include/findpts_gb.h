@@ -46,8 +46,10 @@ typedef enum {
 } fp_status;
 
 /* Per-point result codes (Sec. 2.1: found inside an element, on a border, or
-   not found within the mesh). */
-enum { FP_CODE_INSIDE = 0, FP_CODE_BORDER = 1, FP_CODE_NOT_FOUND = 2 };
+   not found within the mesh).  FP_CODE_RETRY only comes from fp_find_ws: the
+   workspace ran out of candidate-pair capacity before this point's pairs, so
+   the point was not searched (sub = elem = -1, r = 0, dist2 = +inf). */
+enum { FP_CODE_INSIDE = 0, FP_CODE_BORDER = 1, FP_CODE_NOT_FOUND = 2, FP_CODE_RETRY = 3 };
 
 /* Arithmetic forms of fp_find. */
 enum {
@@ -164,6 +166,32 @@ fp_status fp_eval(fp_handle *h, int64_t P, const int32_t *code, const int32_t *e
 fp_status fp_find_static(fp_handle *h, int64_t P, const double *pts, const int32_t *qsess,
                          int32_t *code, int32_t *sub, int32_t *elem, double *rst,
                          double *dist2, void *stream);
+
+/* Workspaces for asynchronous finds.  A workspace holds all per-call scratch
+ * of fp_find_ws for up to max_points points and max_pairs candidate pairs on
+ * one handle's mesh; several workspaces let several finds run at once on
+ * different streams (each workspace must be used by one call at a time).
+ * fp_workspace_create allocates (max_pairs <= 0 picks 2 * max_points). */
+typedef struct fp_workspace fp_workspace;
+fp_status fp_workspace_create(const fp_handle *h, int64_t max_points, int64_t max_pairs,
+                              fp_workspace **ws);
+void fp_workspace_free(fp_workspace *ws);
+
+/* fp_find_ws -- fp_find with its scratch in `ws`.  Never waits on the host
+ * and never allocates, so a sequence of fp_find_ws / fp_eval calls can be
+ * captured into a CUDA graph and replayed.  The number of candidate pairs
+ * stays on the device; if it exceeds the workspace's max_pairs, the points
+ * whose pairs did not fit come back as FP_CODE_RETRY (all others are
+ * complete and identical to fp_find).  Errors: FP_ERR_NOT_SETUP,
+ * FP_ERR_INVALID_ARG (P outside [0, max_points], null pointers, a workspace
+ * made for another handle), FP_ERR_CUDA. */
+fp_status fp_find_ws(fp_handle *h, fp_workspace *ws, int64_t P, const double *pts,
+                     const int32_t *qsess, int32_t *code, int32_t *sub, int32_t *elem,
+                     double *rst, double *dist2, void *stream);
+
+/* Number of candidate pairs of the workspace's most recent fp_find_ws
+ * (synchronises the device; for diagnostics). */
+fp_status fp_workspace_last_pairs(fp_workspace *ws, int64_t *npairs);
 
 /* Release every device resource of the handle (synchronises it first).
    NULL is a no-op. */

@@ -18,7 +18,7 @@ import torch
 from . import build as _build
 
 FP_OK, FP_ERR_INVALID_ARG, FP_ERR_OOM, FP_ERR_CUDA, FP_ERR_TIMEOUT, FP_ERR_NOT_SETUP = range(6)
-INSIDE, BORDER, NOT_FOUND = 0, 1, 2
+INSIDE, BORDER, NOT_FOUND, RETRY = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED = 0, 1
 
 
@@ -61,6 +61,14 @@ def _load():
     L.fp_find.restype = ci
     L.fp_find_static.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     L.fp_find_static.restype = ci
+    L.fp_workspace_create.argtypes = [vp, i64, i64, ctypes.POINTER(vp)]
+    L.fp_workspace_create.restype = ci
+    L.fp_workspace_free.argtypes = [vp]
+    L.fp_workspace_free.restype = None
+    L.fp_find_ws.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.fp_find_ws.restype = ci
+    L.fp_workspace_last_pairs.argtypes = [vp, ctypes.POINTER(i64)]
+    L.fp_workspace_last_pairs.restype = ci
     L.fp_eval.argtypes = [vp, i64, vp, vp, vp, ci, vp, vp, vp]
     L.fp_eval.restype = ci
     L.fp_free.argtypes = [vp]
@@ -181,6 +189,47 @@ def fp_find(h: Handle, pts: torch.Tensor, qsess: Optional[torch.Tensor] = None, 
     code, sub, elem, rst, dist2 = out
     st = lib().fp_find(h.ptr, P, _ptr(pts), _ptr(qsess), _ptr(code), _ptr(sub), _ptr(elem), _ptr(rst),
                        _ptr(dist2), _stream(stream))
+    _check(st, h.ptr)
+    return code, sub, elem, rst, dist2
+
+
+class Workspace:
+    """Scratch for asynchronous finds (fp_workspace_create); one call at a time."""
+
+    def __init__(self, h: Handle, max_points: int, max_pairs: int = 0):
+        self.ptr = ctypes.c_void_p()
+        self.handle = h
+        self.max_points = int(max_points)
+        _check(lib().fp_workspace_create(h.ptr, int(max_points), int(max_pairs), ctypes.byref(self.ptr)), h.ptr)
+
+    def __del__(self):
+        if getattr(self, "ptr", None) is not None and self.ptr.value:
+            try:
+                lib().fp_workspace_free(self.ptr)
+            except Exception:
+                pass
+            self.ptr = ctypes.c_void_p(None)
+
+    def last_pairs(self) -> int:
+        n = ctypes.c_int64()
+        _check(lib().fp_workspace_last_pairs(self.ptr, ctypes.byref(n)))
+        return n.value
+
+
+def fp_find_ws(h: Handle, ws: Workspace, pts: torch.Tensor, qsess: Optional[torch.Tensor] = None, out=None,
+               stream=None):
+    """Asynchronous find (no host wait, no allocation in the library call)."""
+    pts = _dev(pts, torch.float64, "pts")
+    P = pts.shape[1]
+    qsess = None if qsess is None else _dev(qsess, torch.int32, "qsess")
+    dev = pts.device
+    if out is None:
+        out = (torch.empty(P, dtype=torch.int32, device=dev), torch.empty(P, dtype=torch.int32, device=dev),
+               torch.empty(P, dtype=torch.int32, device=dev), torch.empty((3, P), dtype=torch.float64, device=dev),
+               torch.empty(P, dtype=torch.float64, device=dev))
+    code, sub, elem, rst, dist2 = out
+    st = lib().fp_find_ws(h.ptr, ws.ptr, P, _ptr(pts), _ptr(qsess), _ptr(code), _ptr(sub), _ptr(elem), _ptr(rst),
+                          _ptr(dist2), _stream(stream))
     _check(st, h.ptr)
     return code, sub, elem, rst, dist2
 

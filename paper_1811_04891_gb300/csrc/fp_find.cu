@@ -53,6 +53,7 @@ struct ScreenArgs {
     const int32_t* off;
     int32_t* pair_elem;
     int32_t* pair_pt;
+    int64_t cap;          // pair capacity: pairs at positions >= cap are not written
 };
 
 template <bool EMIT>
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs A)
                 const int e = __ldg(A.cell_elems + q);
                 if (tag >= 0 && __ldg(A.sub + e) == tag) continue;
                 if (!inside_boxes(A.boxes + e, x, y, z)) continue;
-                if (EMIT) {
+                if (EMIT && base + c < A.cap) {
                     A.pair_elem[base + c] = e;
                     A.pair_pt[base + c] = (int32_t)p;
                 }
@@ -90,20 +91,30 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs A)
     if (!EMIT) A.cnt[p] = c;
 }
 
-__global__ void k_ehist(int64_t npairs, const int32_t* __restrict__ pair_elem, int32_t* __restrict__ ecount)
+// number of pairs to process: the device-side total, capped by the capacity
+__device__ __forceinline__ int64_t live_pairs(const int32_t* __restrict__ dcount, int64_t cap)
 {
-    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q < npairs) atomicAdd(ecount + pair_elem[q], 1);
+    const int64_t t = *dcount;
+    return t < cap ? t : cap;
 }
 
-__global__ void k_escatter(int64_t npairs, const int32_t* __restrict__ pair_elem, const int32_t* __restrict__ estart,
-                           int32_t* __restrict__ cursor, int32_t* __restrict__ order)
+__global__ void k_ehist(const int32_t* __restrict__ dcount, int64_t cap, const int32_t* __restrict__ pair_elem,
+                        int32_t* __restrict__ ecount)
 {
-    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= npairs) return;
-    int e = pair_elem[q];
-    int pos = estart[e] + atomicAdd(cursor + e, 1);
-    order[pos] = (int32_t)q;
+    const int64_t npairs = live_pairs(dcount, cap);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npairs; q += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(ecount + pair_elem[q], 1);
+}
+
+__global__ void k_escatter(const int32_t* __restrict__ dcount, int64_t cap, const int32_t* __restrict__ pair_elem,
+                           const int32_t* __restrict__ estart, int32_t* __restrict__ cursor, int32_t* __restrict__ order)
+{
+    const int64_t npairs = live_pairs(dcount, cap);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npairs; q += (int64_t)gridDim.x * blockDim.x) {
+        const int e = pair_elem[q];
+        const int pos = estart[e] + atomicAdd(cursor + e, 1);
+        order[pos] = (int32_t)q;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -390,7 +401,7 @@ __device__ __forceinline__ void seed_nearest(const ElemPtr<T>& el, const BasisTa
 }
 
 struct NewtonArgs {
-    int64_t npairs;
+    const int32_t* dcount;  // device-side pair total (capped by cap)
     int64_t E;
     const int32_t* order;
     const int32_t* pair_elem;
@@ -408,11 +419,9 @@ struct NewtonArgs {
 };
 
 template <int n, bool MIXED>
-__global__ void __launch_bounds__(256) k_newton(NewtonArgs A, BasisTab tab)
+__device__ __forceinline__ void solve_pair(const NewtonArgs& A, const BasisTab& tab, int64_t s)
 {
     constexpr int n3 = n * n * n;
-    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= A.npairs) return;
     const int32_t q = A.order[s];
     const int e = A.pair_elem[q];
     const int64_t p = A.pair_pt[q];
@@ -455,6 +464,14 @@ __global__ void __launch_bounds__(256) k_newton(NewtonArgs A, BasisTab tab)
     A.prst[2 * A.cap + q] = r[2];
 }
 
+template <int n, bool MIXED>
+__global__ void __launch_bounds__(256) k_newton(NewtonArgs A, BasisTab tab)
+{
+    const int64_t npairs = live_pairs(A.dcount, A.cap);
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < npairs; s += (int64_t)gridDim.x * blockDim.x)
+        solve_pair<n, MIXED>(A, tab, s);
+}
+
 // ---------------------------------------------------------------------------
 // classification and ownership
 // ---------------------------------------------------------------------------
@@ -494,6 +511,16 @@ __global__ void __launch_bounds__(128) k_rank(RankArgs A, FindParams fp, BasisTa
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= A.P) return;
     const int b = A.off[p], en = A.off[p + 1];
+    if (en > A.cap) {                                  // pairs dropped: not searched
+        A.code[p] = FP_CODE_RETRY;
+        A.osub[p] = -1;
+        A.oelem[p] = -1;
+        A.rst[p] = 0.0;
+        A.rst[A.P + p] = 0.0;
+        A.rst[2 * A.P + p] = 0.0;
+        A.dist2[p] = INFINITY;
+        return;
+    }
     // INSIDE winners: lowest element id per subdomain
     int best_q = -1, nwin = 0;
     double bmin = INFINITY;
@@ -601,7 +628,17 @@ static ScreenArgs screen_args(const FindArgs& a)
     s.off = a.off;
     s.pair_elem = a.pair_elem;
     s.pair_pt = a.pair_pt;
+    s.cap = a.cap;
     return s;
+}
+
+// grid for `work` items; with a persistent block count the kernels loop
+// grid-stride over a count that only the device knows
+static unsigned grid_for(int64_t work, int block, int persistent)
+{
+    int64_t g = (work + block - 1) / block;
+    if (persistent > 0 && g > persistent) g = persistent;
+    return (unsigned)(g < 1 ? 1 : g);
 }
 
 cudaError_t find_count(const FindArgs& a, const BasisTab&, const FindParams&, cudaStream_t s)
@@ -628,7 +665,7 @@ static cudaError_t solve_n(const FindArgs& a, int64_t npairs, const BasisTab& ta
 {
     if (npairs > 0) {
         NewtonArgs na;
-        na.npairs = npairs;
+        na.dcount = a.off + a.P;
         na.E = a.E;
         na.order = a.order;
         na.pair_elem = a.pair_elem;
@@ -643,7 +680,7 @@ static cudaError_t solve_n(const FindArgs& a, int64_t npairs, const BasisTab& ta
         na.cap = a.cap;
         na.reject32 = 1e-4;
         na.max_newton = fp.max_newton;
-        const unsigned grid = (unsigned)((npairs + block - 1) / block);
+        const unsigned grid = grid_for(npairs, block, a.persistent_blocks);
         if (a.ev[2]) cudaEventRecord(a.ev[2], s);
         if (fp.mixed)
             k_newton<n, true><<<grid, block, 0, s>>>(na, tab);
@@ -685,12 +722,13 @@ cudaError_t find_solve(const FindArgs& a, int64_t npairs, const BasisTab& tab, c
         if (a.ev[0]) cudaEventRecord(a.ev[0], s);
         err = cudaMemsetAsync(a.ecount, 0, sizeof(int32_t) * a.E, s);
         if (err != cudaSuccess) return err;
-        k_ehist<<<(unsigned)((npairs + 255) / 256), 256, 0, s>>>(npairs, a.pair_elem, a.ecount);
+        const unsigned g256 = grid_for(npairs, 256, a.persistent_blocks ? 4 * a.persistent_blocks : 0);
+        k_ehist<<<g256, 256, 0, s>>>(a.off + a.P, a.cap, a.pair_elem, a.ecount);
         count_launch();
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         if ((err = scan_exclusive(a.ecount, a.estart, a.E, a.scan_tmp, s)) != cudaSuccess) return err;
         if ((err = cudaMemsetAsync(a.ecount, 0, sizeof(int32_t) * a.E, s)) != cudaSuccess) return err;
-        k_escatter<<<(unsigned)((npairs + 255) / 256), 256, 0, s>>>(npairs, a.pair_elem, a.estart, a.ecount, a.order);
+        k_escatter<<<g256, 256, 0, s>>>(a.off + a.P, a.cap, a.pair_elem, a.estart, a.ecount, a.order);
         count_launch();
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         if (a.ev[1]) cudaEventRecord(a.ev[1], s);

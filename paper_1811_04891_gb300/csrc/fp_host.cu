@@ -533,6 +533,111 @@ fp_status fp_find(fp_handle* h, int64_t P, const double* pts, const int32_t* qse
     return FP_OK;
 }
 
+struct fp_workspace {
+    const fp_handle* owner = nullptr;
+    int64_t max_points = 0, max_pairs = 0, last_P = 0;
+    int persistent_blocks = 0;
+    int32_t *cnt = nullptr, *off = nullptr, *scan_tmp = nullptr;
+    int32_t *pair_elem = nullptr, *pair_pt = nullptr, *order = nullptr;
+    int32_t *ecount = nullptr, *estart = nullptr;
+    double *pres = nullptr, *prst = nullptr;
+};
+
+static void ws_release(fp_workspace* w)
+{
+    dfree(w->cnt); dfree(w->off); dfree(w->scan_tmp); dfree(w->pair_elem); dfree(w->pair_pt);
+    dfree(w->order); dfree(w->ecount); dfree(w->estart); dfree(w->pres); dfree(w->prst);
+}
+
+fp_status fp_workspace_create(const fp_handle* h, int64_t max_points, int64_t max_pairs, fp_workspace** out)
+{
+    if (!out) return FP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (max_points < 1 || max_points >= (int64_t(1) << 31)) return FP_ERR_INVALID_ARG;
+    if (max_pairs <= 0) max_pairs = 2 * max_points;
+    if (max_pairs >= (int64_t(1) << 31)) return FP_ERR_INVALID_ARG;
+    fp_workspace* w = new fp_workspace();
+    w->owner = h;
+    w->max_points = max_points;
+    w->max_pairs = max_pairs;
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    w->persistent_blocks = 4 * nsm;
+    cudaError_t e;
+    if ((e = dalloc(&w->cnt, max_points)) != cudaSuccess || (e = dalloc(&w->off, max_points + 1)) != cudaSuccess ||
+        (e = dalloc(&w->scan_tmp, std::max(scan_tmp_elems(max_points), scan_tmp_elems(h->E)))) != cudaSuccess ||
+        (e = dalloc(&w->pair_elem, max_pairs)) != cudaSuccess || (e = dalloc(&w->pair_pt, max_pairs)) != cudaSuccess ||
+        (e = dalloc(&w->order, max_pairs)) != cudaSuccess || (e = dalloc(&w->ecount, h->E)) != cudaSuccess ||
+        (e = dalloc(&w->estart, h->E + 1)) != cudaSuccess || (e = dalloc(&w->pres, max_pairs)) != cudaSuccess ||
+        (e = dalloc(&w->prst, 3 * max_pairs)) != cudaSuccess) {
+        ws_release(w);
+        delete w;
+        return e == cudaErrorMemoryAllocation ? FP_ERR_OOM : FP_ERR_CUDA;
+    }
+    *out = w;
+    return FP_OK;
+}
+
+void fp_workspace_free(fp_workspace* w)
+{
+    if (!w) return;
+    cudaDeviceSynchronize();
+    ws_release(w);
+    delete w;
+}
+
+fp_status fp_workspace_last_pairs(fp_workspace* w, int64_t* npairs)
+{
+    if (!w) return FP_ERR_INVALID_ARG;
+    int32_t t = 0;
+    if (w->last_P > 0) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaMemcpy(&t, w->off + w->last_P, sizeof(int32_t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return FP_ERR_CUDA;
+    }
+    if (npairs) *npairs = t;
+    return FP_OK;
+}
+
+fp_status fp_find_ws(fp_handle* h, fp_workspace* w, int64_t P, const double* pts, const int32_t* qsess,
+                     int32_t* code, int32_t* sub, int32_t* elem, double* rst, double* dist2, void* stream)
+{
+    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    h->err.clear();
+    if (!w || w->owner != h) return fail(h, FP_ERR_INVALID_ARG, "fp_find_ws: workspace belongs to another handle");
+    if (P < 0 || P > w->max_points) return fail(h, FP_ERR_INVALID_ARG, "fp_find_ws: P outside [0, max_points]");
+    if (P == 0) return FP_OK;
+    if (!pts || !code || !sub || !elem || !rst || !dist2)
+        return fail(h, FP_ERR_INVALID_ARG, "fp_find_ws: null pointer argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    FindArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = h->n; a.E = h->E; a.P = P; a.pts = pts; a.qsess = qsess;
+    a.coords = h->coords; a.coords32 = h->coords32; a.sub = h->sub;
+    a.dist = h->nsub > 1 ? h->dist : nullptr;
+    a.boxes = h->boxes; a.grid = &h->grid; a.cell_start = h->cell_start; a.cell_elems = h->cell_elems;
+    a.cnt = w->cnt; a.off = w->off; a.scan_tmp = w->scan_tmp; a.ecount = w->ecount; a.estart = w->estart;
+    a.pair_elem = w->pair_elem; a.pair_pt = w->pair_pt; a.order = w->order; a.pres = w->pres; a.prst = w->prst;
+    a.cap = w->max_pairs;
+    a.persistent_blocks = w->persistent_blocks;
+    a.code = code; a.osub = sub; a.oelem = elem; a.rst = rst; a.dist2 = dist2;
+    FindParams fp;
+    fp.tol_accept = h->opts.tol_accept;
+    fp.tol_border = h->opts.tol_border;
+    fp.band = h->opts.tie_band * h->L;
+    fp.max_newton = h->opts.max_newton;
+    fp.mixed = h->opts.precision == FP_PREC_MIXED;
+    const int block = h->opts.points_per_block > 0 ? h->opts.points_per_block : 128;
+    cudaError_t err = find_count(a, h->tab, fp, s);
+    if (err == cudaSuccess) err = find_emit(a, s);
+    if (err == cudaSuccess) err = find_solve(a, w->max_pairs, h->tab, fp, block, s);
+    if (err != cudaSuccess) return cuda_fail(h, err, "fp_find_ws");
+    w->last_P = P;
+    return FP_OK;
+}
+
 fp_status fp_eval(fp_handle* h, int64_t P, const int32_t* code, const int32_t* elem, const double* rst, int F,
                   const double* fields, double* out, void* stream)
 {

@@ -64,7 +64,8 @@ struct FindArgs {
     double* pres;                 // [cap]
     double* prst;                 // [3][cap]
     int32_t* scan_tmp;
-    int64_t cap;
+    int64_t cap;                  // pair capacity
+    int persistent_blocks;        // 0: pair count known on the host; >0: device-side count, this many blocks
     // optional timing events (null = off): [0,1] sort, [2,3] newton, [4,5] rank
     cudaEvent_t ev[6];
     // outputs
