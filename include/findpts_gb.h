@@ -193,6 +193,47 @@ fp_status fp_find_ws(fp_handle *h, fp_workspace *ws, int64_t P, const double *pt
  * (synchronises the device; for diagnostics). */
 fp_status fp_workspace_last_pairs(fp_workspace *ws, int64_t *npairs);
 
+/* Batches: many independent meshes (instances) of different E and N located
+ * and interpolated in one launch sequence (the paper posts all meshes of all
+ * sessions to one findpts_setup, Sec. 2.1; here independent problems share
+ * the device).  Instances of the same N form a group whose geometry, boxes,
+ * subdomain ids and fields are copied into group-resident arrays at creation;
+ * each run screens every instance against its own hash grid, then solves all
+ * candidate pairs of a group with one grid-stride Newton launch, classifies,
+ * evaluates and scatters the results back to instance order.  A run never
+ * waits on the host, so it can be captured into one CUDA graph.
+ *   handles  [ninst] set-up handles (same precision, tolerances and
+ *            max_newton); they must outlive the batch
+ *   npts     [ninst] host array: points per instance (instance i owns points
+ *            [sum_{k<i} npts_k, sum_{k<=i} npts_k) of every run)
+ *   F        fields per instance (0 = find only)
+ *   fields   [ninst] host array of device pointers, instance i's fields laid
+ *            out [F][E_i][n_i^3] (NULL when F = 0); copied at creation
+ *   pairs_per_point  pair capacity per point of each group (<= 0: 2.0);
+ *            points beyond it come back as FP_CODE_RETRY
+ * The tie band of a group uses the largest L of its instances.
+ * fp_batch_run: pts [3][Ptot], outputs as fp_find over Ptot points plus
+ * out [F][Ptot] (may be NULL).  fp_batch_tune times every Newton schedule
+ * (threads per block 64/128/256 x blocks per SM 1/2/4/8) with `reps` runs on
+ * the given data, keeps the fastest and returns its time (synchronises).
+ * fp_batch_schedule reads (and, for positive inputs, sets) the schedule.
+ * fp_batch_capture records one run on the given buffers into a CUDA graph;
+ * fp_batch_launch replays it on `stream` (same buffers, new contents). */
+typedef struct fp_batch fp_batch;
+fp_status fp_batch_create(fp_batch **b, int ninst, fp_handle *const *handles, const int64_t *npts,
+                          int F, const double *const *fields, double pairs_per_point);
+fp_status fp_batch_run(fp_batch *b, const double *pts, int32_t *code, int32_t *sub, int32_t *elem,
+                       double *rst, double *dist2, double *out, void *stream);
+fp_status fp_batch_tune(fp_batch *b, const double *pts, int32_t *code, int32_t *sub, int32_t *elem,
+                        double *rst, double *dist2, double *out, void *stream, int reps,
+                        double *best_ms);
+fp_status fp_batch_schedule(fp_batch *b, int *block, int *blocks_per_sm);
+fp_status fp_batch_capture(fp_batch *b, const double *pts, int32_t *code, int32_t *sub,
+                           int32_t *elem, double *rst, double *dist2, double *out);
+fp_status fp_batch_launch(fp_batch *b, void *stream);
+const char *fp_batch_last_error(const fp_batch *b);
+void fp_batch_free(fp_batch *b);
+
 /* Release every device resource of the handle (synchronises it first).
    NULL is a no-op. */
 void fp_free(fp_handle *h);

@@ -69,6 +69,23 @@ def _load():
     L.fp_find_ws.restype = ci
     L.fp_workspace_last_pairs.argtypes = [vp, ctypes.POINTER(i64)]
     L.fp_workspace_last_pairs.restype = ci
+    L.fp_batch_create.argtypes = [ctypes.POINTER(vp), ci, ctypes.POINTER(vp), ctypes.POINTER(i64), ci,
+                                  ctypes.POINTER(vp), ctypes.c_double]
+    L.fp_batch_create.restype = ci
+    L.fp_batch_run.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.fp_batch_run.restype = ci
+    L.fp_batch_tune.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, ci, ctypes.POINTER(ctypes.c_double)]
+    L.fp_batch_tune.restype = ci
+    L.fp_batch_schedule.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci)]
+    L.fp_batch_schedule.restype = ci
+    L.fp_batch_capture.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    L.fp_batch_capture.restype = ci
+    L.fp_batch_launch.argtypes = [vp, vp]
+    L.fp_batch_launch.restype = ci
+    L.fp_batch_last_error.argtypes = [vp]
+    L.fp_batch_last_error.restype = ctypes.c_char_p
+    L.fp_batch_free.argtypes = [vp]
+    L.fp_batch_free.restype = None
     L.fp_eval.argtypes = [vp, i64, vp, vp, vp, ci, vp, vp, vp]
     L.fp_eval.restype = ci
     L.fp_free.argtypes = [vp]
@@ -232,6 +249,78 @@ def fp_find_ws(h: Handle, ws: Workspace, pts: torch.Tensor, qsess: Optional[torc
                           _ptr(dist2), _stream(stream))
     _check(st, h.ptr)
     return code, sub, elem, rst, dist2
+
+
+class Batch:
+    """Independent instances (handles) located and interpolated together
+    (fp_batch_*).  Inputs/outputs are concatenated in instance order."""
+
+    def __init__(self, handles, npts, fields=None, pairs_per_point: float = 2.0):
+        L = lib()
+        self.handles = list(handles)             # keep them alive
+        self.npts = [int(x) for x in npts]
+        self.P = sum(self.npts)
+        self.fields = None if fields is None else [_dev(f, torch.float64, "fields") for f in fields]
+        F = 0 if fields is None else int(self.fields[0].shape[0])
+        self.F = F
+        hp = (ctypes.c_void_p * len(self.handles))(*[h.ptr.value for h in self.handles])
+        npa = (ctypes.c_int64 * len(self.npts))(*self.npts)
+        fp_arr = None
+        if fields is not None:
+            fp_arr = (ctypes.c_void_p * len(self.fields))(*[f.data_ptr() for f in self.fields])
+        self.ptr = ctypes.c_void_p()
+        st = L.fp_batch_create(ctypes.byref(self.ptr), len(self.handles), hp, npa, F, fp_arr,
+                               float(pairs_per_point))
+        if st != FP_OK:
+            raise FindptsError(st, "fp_batch_create failed")
+
+    def __del__(self):
+        if getattr(self, "ptr", None) is not None and self.ptr.value:
+            try:
+                lib().fp_batch_free(self.ptr)
+            except Exception:
+                pass
+            self.ptr = ctypes.c_void_p(None)
+
+    def _chk(self, st):
+        if st != FP_OK:
+            raise FindptsError(st, lib().fp_batch_last_error(self.ptr).decode())
+
+    def outputs(self, device=None):
+        dev = device or torch.device("cuda")
+        P = self.P
+        return (torch.empty(P, dtype=torch.int32, device=dev), torch.empty(P, dtype=torch.int32, device=dev),
+                torch.empty(P, dtype=torch.int32, device=dev), torch.empty((3, P), dtype=torch.float64, device=dev),
+                torch.empty(P, dtype=torch.float64, device=dev),
+                torch.empty((max(self.F, 1), P), dtype=torch.float64, device=dev))
+
+    def _args(self, pts, outs):
+        code, sub, elem, rst, d2, val = outs
+        return (_ptr(pts), _ptr(code), _ptr(sub), _ptr(elem), _ptr(rst), _ptr(d2),
+                _ptr(val) if self.F > 0 else None)
+
+    def run(self, pts, outs, stream=None):
+        pts = _dev(pts, torch.float64, "pts")
+        self._chk(lib().fp_batch_run(self.ptr, *self._args(pts, outs), _stream(stream)))
+        return outs
+
+    def tune(self, pts, outs, reps: int = 2, stream=None) -> float:
+        pts = _dev(pts, torch.float64, "pts")
+        ms = ctypes.c_double()
+        self._chk(lib().fp_batch_tune(self.ptr, *self._args(pts, outs), _stream(stream), int(reps), ctypes.byref(ms)))
+        return ms.value
+
+    def schedule(self, block: int = 0, blocks_per_sm: int = 0):
+        b, s = ctypes.c_int(block), ctypes.c_int(blocks_per_sm)
+        self._chk(lib().fp_batch_schedule(self.ptr, ctypes.byref(b), ctypes.byref(s)))
+        return b.value, s.value
+
+    def capture(self, pts, outs):
+        pts = _dev(pts, torch.float64, "pts")
+        self._chk(lib().fp_batch_capture(self.ptr, *self._args(pts, outs)))
+
+    def launch(self, stream=None):
+        self._chk(lib().fp_batch_launch(self.ptr, _stream(stream)))
 
 
 STATIC_MAX_POINTS = 16384

@@ -54,6 +54,9 @@ struct ScreenArgs {
     int32_t* pair_elem;
     int32_t* pair_pt;
     int64_t cap;          // pair capacity: pairs at positions >= cap are not written
+    int64_t stride;       // row stride of pts (and offset of y, z rows); 0 means P
+    int32_t pt_base;      // added to the point index written into pair_pt
+    int32_t elem_base;    // added to the element index written into pair_elem
 };
 
 template <bool EMIT>
@@ -61,7 +64,8 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs A)
 {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= A.P) return;
-    const double x = A.pts[p], y = A.pts[A.P + p], z = A.pts[2 * A.P + p];
+    const int64_t ld = A.stride ? A.stride : A.P;
+    const double x = A.pts[p], y = A.pts[ld + p], z = A.pts[2 * ld + p];
     const int tag = A.qsess ? A.qsess[p] : -1;
     int c = 0;
     int base = EMIT ? A.off[p] : 0;
@@ -81,8 +85,8 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs A)
                 if (tag >= 0 && __ldg(A.sub + e) == tag) continue;
                 if (!inside_boxes(A.boxes + e, x, y, z)) continue;
                 if (EMIT && base + c < A.cap) {
-                    A.pair_elem[base + c] = e;
-                    A.pair_pt[base + c] = (int32_t)p;
+                    A.pair_elem[base + c] = A.elem_base + e;
+                    A.pair_pt[base + c] = A.pt_base + (int32_t)p;
                 }
                 ++c;
             }
@@ -629,6 +633,9 @@ static ScreenArgs screen_args(const FindArgs& a)
     s.pair_elem = a.pair_elem;
     s.pair_pt = a.pair_pt;
     s.cap = a.cap;
+    s.stride = a.pts_stride;
+    s.pt_base = a.pt_base;
+    s.elem_base = a.elem_base;
     return s;
 }
 
@@ -649,6 +656,14 @@ cudaError_t find_count(const FindArgs& a, const BasisTab&, const FindParams&, cu
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     return scan_exclusive(a.cnt, a.off, a.P, a.scan_tmp, s);
+}
+
+cudaError_t find_screen_count(const FindArgs& a, cudaStream_t s)
+{
+    ScreenArgs sa = screen_args(a);
+    k_screen<false><<<(unsigned)((a.P + 255) / 256), 256, 0, s>>>(sa);
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t find_emit(const FindArgs& a, cudaStream_t s)

@@ -66,6 +66,9 @@ struct FindArgs {
     int32_t* scan_tmp;
     int64_t cap;                  // pair capacity
     int persistent_blocks;        // 0: pair count known on the host; >0: device-side count, this many blocks
+    int64_t pts_stride;           // screen only: row stride of pts (0 = P)
+    int32_t pt_base;              // screen only: offset added to emitted point indices
+    int32_t elem_base;            // screen only: offset added to emitted element indices
     // optional timing events (null = off): [0,1] sort, [2,3] newton, [4,5] rank
     cudaEvent_t ev[6];
     // outputs
@@ -76,6 +79,7 @@ struct FindArgs {
     double* dist2;
 };
 cudaError_t find_count(const FindArgs& a, const BasisTab& tab, const FindParams& fp, cudaStream_t s);
+cudaError_t find_screen_count(const FindArgs& a, cudaStream_t s);   // counts only, no scan
 cudaError_t find_emit(const FindArgs& a, cudaStream_t s);
 cudaError_t find_solve(const FindArgs& a, int64_t npairs, const BasisTab& tab, const FindParams& fp,
                        int block, cudaStream_t s);

@@ -1,0 +1,103 @@
+"""GPU tests of the batched form: many independent deformed-box instances of
+different E and N in one run must give, instance by instance, exactly what
+fp_find + fp_eval give alone, and agree with the CPU oracle; the autotuned
+schedule and the captured CUDA graph must not change any result."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import TOL_EVAL_REL, TOL_RST
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1811_04891_gb300 as fg
+    fg.lib()
+    return fg
+
+
+def _instances(n_inst, seed, prec, fg, with_empty=False):
+    insts = synth.config3(n_inst=n_inst, seed=seed, E_range=(8, 300), P_range=(50, 4000))
+    dev = torch.device("cuda:0")
+    handles, fields, pts = [], [], []
+    for k, (mesh, q) in enumerate(insts):
+        handles.append(fg.fp_setup(torch.from_numpy(mesh.coords).to(dev), mesh.N, torch.from_numpy(mesh.sub).to(dev),
+                                   opts=fg.default_opts(precision=prec)))
+        fields.append(torch.from_numpy(q.fields).to(dev))
+        p = q.pts if not (with_empty and k == 1) else np.zeros((3, 0))
+        pts.append(p)
+    return insts, handles, fields, pts
+
+
+def _check_against_single(fg, insts, handles, fields, pts, outs):
+    code, sub, elem, rst, d2, val = [x.cpu().numpy() for x in outs]
+    off = np.concatenate([[0], np.cumsum([p.shape[1] for p in pts])])
+    dev = torch.device("cuda:0")
+    for k, h in enumerate(handles):
+        if pts[k].shape[1] == 0:
+            continue
+        t = torch.from_numpy(np.ascontiguousarray(pts[k])).to(dev)
+        r = fg.fp_find(h, t)
+        v = fg.fp_eval(h, r[0], r[2], r[3], fields[k]).cpu().numpy()
+        r = [x.cpu().numpy() for x in r]
+        sl = slice(off[k], off[k + 1])
+        np.testing.assert_array_equal(code[sl], r[0])
+        np.testing.assert_array_equal(sub[sl], r[1])
+        np.testing.assert_array_equal(elem[sl], r[2])
+        np.testing.assert_array_equal(rst[:, sl], r[3])
+        np.testing.assert_array_equal(d2[sl], r[4])
+        np.testing.assert_array_equal(val[:, sl], v)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_equals_single_instance_runs(fg, prec):
+    insts, handles, fields, pts = _instances(9, 31, prec, fg, with_empty=True)
+    assert len({m.N for m, _ in insts}) > 1
+    batch = fg.Batch(handles, [p.shape[1] for p in pts], fields)
+    allp = torch.from_numpy(np.ascontiguousarray(np.concatenate(pts, axis=1))).cuda()
+    outs = batch.run(allp, batch.outputs())
+    torch.cuda.synchronize()
+    _check_against_single(fg, insts, handles, fields, pts, outs)
+    # and against the oracle on two instances
+    code, sub, elem, rst, d2, val = [x.cpu().numpy() for x in outs]
+    off = np.concatenate([[0], np.cumsum([p.shape[1] for p in pts])])
+    for k in (0, len(insts) - 1):
+        mesh, q = insts[k]
+        ref = oracle.find(mesh.coords, mesh.N, mesh.sub, pts[k])
+        sl = slice(off[k], off[k + 1])
+        np.testing.assert_array_equal(code[sl], ref["code"])
+        np.testing.assert_array_equal(elem[sl], ref["elem"])
+        assert np.abs(rst[:, sl] - ref["rst"]).max() <= TOL_RST[prec]
+        rv = oracle.evaluate(mesh.N, ref["code"], ref["elem"], ref["rst"], q.fields)
+        assert np.abs(val[:, sl] - rv).max() <= TOL_EVAL_REL * np.abs(q.fields).max()
+
+
+def test_batch_tune_and_graph_replay(fg):
+    insts, handles, fields, pts = _instances(7, 32, 1, fg)
+    batch = fg.Batch(handles, [p.shape[1] for p in pts], fields)
+    allp = torch.from_numpy(np.ascontiguousarray(np.concatenate(pts, axis=1))).cuda()
+    outs = batch.outputs()
+    ms = batch.tune(allp, outs, reps=1)
+    assert ms > 0
+    blk, bps = batch.schedule()
+    assert blk in (64, 128, 256) and bps in (1, 2, 4, 8)
+    ref = [x.clone() for x in batch.run(allp, batch.outputs())]
+    batch.capture(allp, outs)
+    for x in outs:
+        x.zero_()
+    batch.launch()
+    torch.cuda.synchronize()
+    for a, b in zip(ref, outs):
+        assert torch.equal(a, b)
+    # new contents in the captured input buffer
+    pts2 = [synth.uniform_points(p.shape[1], seed=900 + k) for k, p in enumerate(pts)]
+    allp.copy_(torch.from_numpy(np.concatenate(pts2, axis=1)))
+    batch.launch()
+    torch.cuda.synchronize()
+    _check_against_single(fg, insts, handles, fields, pts2, outs)
