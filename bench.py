@@ -64,6 +64,12 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--served-requests", type=int, default=200)
+    ap.add_argument("--served-load", type=float, default=0.7)
+    ap.add_argument("--served-scale", type=float, default=1.0,
+                    help="element-count scale of the served mesh (1.0 = 193,536 elements)")
     return ap.parse_args()
 
 
@@ -191,6 +197,99 @@ def run_reference(args):
                              "sample": f"strided samples of {min(samples)}-{max(samples)} of the {q.P} points per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# batched form: 64 deformed-box instances, E logU[64,8192], N in {5,7,9}
+# ---------------------------------------------------------------------------
+def run_batched(args, fg, dev, barrier, max_over_ranks, world):
+    import torch
+
+    import synth
+    insts = synth.config3()
+    out = {"instances": len(insts), "elements": int(sum(m.E for m, _ in insts)),
+           "points_per_step": int(sum(q.P for _, q in insts)), "orders": sorted({m.N for m, _ in insts})}
+    pts = torch.from_numpy(np.ascontiguousarray(np.concatenate([q.pts for _, q in insts], axis=1))).to(dev)
+    fields = [torch.from_numpy(q.fields).to(dev) for _, q in insts]
+    P = pts.shape[1]
+    for form, prec in (("mixed", fg.PREC_MIXED), ("fp64", fg.PREC_FP64)):
+        handles = [fg.fp_setup(torch.from_numpy(m.coords).to(dev), m.N, torch.from_numpy(m.sub).to(dev),
+                               opts=fg.default_opts(precision=prec)) for m, _ in insts]
+        b = fg.Batch(handles, [q.P for _, q in insts], fields)
+        outs = b.outputs(dev)
+        tuned_ms = b.tune(pts, outs, reps=1)
+        block, bps = b.schedule()
+        b.capture(pts, outs)
+        for _ in range(max(1, args.warmup)):
+            b.launch()
+        torch.cuda.synchronize()
+        barrier()
+        l0 = fg.fp_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            b.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+        codes = torch.bincount(outs[0].long(), minlength=4).tolist()
+        out[form] = {"value": world * P / (ms / 1e3), "ms_per_step": ms, "tuned_ms": tuned_ms,
+                     "schedule": {"threads_per_block": block, "blocks_per_sm": bps},
+                     "gpu_launches": (fg.fp_launch_count() - l0) // max(1, args.steps),
+                     "codes": {"inside": codes[0], "border": codes[1], "not_found": codes[2], "retry": codes[3]}}
+        del b, handles
+    out["unit"] = UNIT
+    out["note"] = "one CUDA-graph launch per step over all instances; Newton schedule autotuned"
+    return out
+
+
+# ---------------------------------------------------------------------------
+# served form: resident box + two rotated annular cylinders, Poisson requests
+# ---------------------------------------------------------------------------
+def run_served(args, fg, dev):
+    import torch
+
+    import synth
+    from paper_1811_04891_gb300 import serve
+    sc = args.served_scale
+    box = tuple(max(2, int(round(v * sc ** (1 / 3)))) for v in (80, 40, 40))
+    cyl = tuple(max(2, int(round(v * sc ** (1 / 3)))) for v in (64, 8, 64))
+    mesh, iface = synth.config4_mesh(box_shape=box, cyl_shape=cyl)
+    F = 4
+    coords_d = torch.from_numpy(mesh.coords).to(dev)
+    x, y, z = coords_d[0], coords_d[1], coords_d[2]
+    # u, v, w, p: closed-form fields sampled at the nodes (evaluated on the device)
+    fields_d = torch.stack([torch.sin(np.pi * x) * torch.cos(np.pi * y) * torch.exp(z),
+                            -torch.cos(np.pi * x) * torch.sin(np.pi * y) * torch.exp(z),
+                            torch.sin(np.pi * z) * x, x * x + y * y - z * z]).contiguous()
+    del x, y, z
+    h = fg.fp_setup(coords_d, mesh.N, torch.from_numpy(mesh.sub).to(dev), torch.from_numpy(mesh.dist).to(dev),
+                    opts=fg.default_opts(precision=fg.PREC_MIXED))
+    resident = (mesh.coords.nbytes * 1.5 + fields_d.numel() * 8 + mesh.dist.nbytes)
+    del coords_d
+    # capacity: a 1M-point mixed request stream served back to back
+    cal = synth.config4_requests(iface, 4, seed=40, size_range=(10 ** 6, 10 ** 6))
+    srv = serve.Server(h, fields_d, slots=4, slot_points=1 << 19, budget_bytes=40e9, resident_bytes=resident)
+    done, span = serve.run_stream(srv, [serve.Request(i, 0.0, r["pts"], r["qsess"]) for i, r in enumerate(cal)])
+    capacity = sum(r.P for r in done) / span
+    mean_size = (10 ** 6 - 10 ** 2) / np.log(10 ** 4)
+    rate = args.served_load * capacity / mean_size
+    reqs = synth.config4_requests(iface, args.served_requests, seed=4, rate_hz=rate)
+    srv = serve.Server(h, fields_d, slots=4, slot_points=1 << 19, budget_bytes=40e9, resident_bytes=resident)
+    done, span = serve.run_stream(srv, [serve.Request(i, r["t_arrive"], r["pts"], r["qsess"])
+                                        for i, r in enumerate(reqs)])
+    st = serve.latency_stats(done)
+    tot = sum(r.P for r in done)
+    codes = np.bincount(np.concatenate([r.code for r in done]), minlength=4).tolist()
+    return {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "requests": st["requests"],
+            "points": int(tot), "points_per_s": tot / span, "capacity_points_per_s": capacity,
+            "arrival_rate_hz": rate, "load": args.served_load, "slots": srv.max_slots,
+            "slot_points": srv.slot_points, "launches": srv.launches, "elements": int(mesh.E), "N": mesh.N,
+            "form": "mixed", "codes": {"inside": codes[0], "border": codes[1], "not_found": codes[2],
+                                       "retry": codes[3]},
+            "note": "Poisson arrivals, sizes logU[1e2,1e6], 50% uniform untagged + 50% cylinder interface "
+                    "nodes tagged with their session; latency = arrival to results in host memory"}
 
 
 # ---------------------------------------------------------------------------
@@ -335,6 +434,14 @@ def main():
         e2e = {"value": world * P * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(pts_h.numel() * 8),
                "d2h_bytes_per_step": int(out_h.numel() * 8 + code_h.numel() * 4)}
 
+    batched = None
+    if not args.no_batched:
+        del handles
+        batched = run_batched(args, fg, dev, barrier, max_over_ranks, world)
+    served = None
+    if rank == 0 and not args.no_served:
+        served = run_served(args, fg, dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, m, cores, dt = oracle_rate(mesh, q, args.cpu_seconds)
@@ -350,7 +457,7 @@ def main():
                               "kernel_ms": v["kernel_ms"], "codes": v["codes"],
                               "pairs_per_point": v["pairs_per_point"]} for k, v in results.items()},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": R["gpu_launches"],
-                "clocks": R["clocks"]}
+                "clocks": R["clocks"], "batched": batched, "serving": served}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
