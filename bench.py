@@ -270,13 +270,16 @@ def run_served(args, fg, dev):
     del coords_d
     # capacity: a 1M-point mixed request stream served back to back
     cal = synth.config4_requests(iface, 4, seed=40, size_range=(10 ** 6, 10 ** 6))
-    srv = serve.Server(h, fields_d, slots=4, slot_points=1 << 19, budget_bytes=40e9, resident_bytes=resident)
+    posted = fg.Fields(h, fields_d)
+    srv = serve.Server(h, fields_d, slots=4, slot_points=1 << 19, budget_bytes=40e9, resident_bytes=resident,
+                       posted=posted)
     done, span = serve.run_stream(srv, [serve.Request(i, 0.0, r["pts"], r["qsess"]) for i, r in enumerate(cal)])
     capacity = sum(r.P for r in done) / span
     mean_size = (10 ** 6 - 10 ** 2) / np.log(10 ** 4)
     rate = args.served_load * capacity / mean_size
     reqs = synth.config4_requests(iface, args.served_requests, seed=4, rate_hz=rate)
-    srv = serve.Server(h, fields_d, slots=4, slot_points=1 << 19, budget_bytes=40e9, resident_bytes=resident)
+    srv = serve.Server(h, fields_d, slots=4, slot_points=1 << 19, budget_bytes=40e9, resident_bytes=resident,
+                       posted=posted)
     done, span = serve.run_stream(srv, [serve.Request(i, r["t_arrive"], r["pts"], r["qsess"])
                                         for i, r in enumerate(reqs)])
     st = serve.latency_stats(done)
@@ -355,10 +358,13 @@ def main():
         setup_ms = 1e3 * (time.perf_counter() - t0)
         fg.fp_reserve(h, P)
         handles[form] = h
+        # mixed form: fields posted once as double-float pairs, evaluated on the FP32 pipes
+        posted = fg.Fields(h, fields) if form == "mixed" else None
+        handles[form + "_fields"] = posted
 
-        def step():
-            fg.fp_find(h, pts, None, out=outs)
-            fg.fp_eval(h, code, elem, rst, fields, out=out)
+        def step(h=h, posted=posted):
+            # one fused call: find, then eval in the element-sorted pair order
+            fg.fp_find_eval(h, pts, None, fields=fields, posted=posted, out=outs, values=out)
 
         for _ in range(max(args.warmup, 1)):
             step()
@@ -410,6 +416,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         h = handles[head]
+        posted = handles.get(head + "_fields")
         pts_h = torch.from_numpy(q.pts).pin_memory()
         out_h = torch.empty((F, P), dtype=torch.float64).pin_memory()
         code_h = torch.empty(P, dtype=torch.int32).pin_memory()
@@ -417,8 +424,7 @@ def main():
 
         def e2e_step():
             pts_d.copy_(pts_h, non_blocking=True)
-            fg.fp_find(h, pts_d, None, out=outs)
-            fg.fp_eval(h, code, elem, rst, fields, out=out)
+            fg.fp_find_eval(h, pts_d, None, fields=fields, posted=posted, out=outs, values=out)
             out_h.copy_(out, non_blocking=True)
             code_h.copy_(code, non_blocking=True)
 

@@ -234,6 +234,41 @@ fp_status fp_batch_launch(fp_batch *b, void *stream);
 const char *fp_batch_last_error(const fp_batch *b);
 void fp_batch_free(fp_batch *b);
 
+typedef struct fp_fields fp_fields;
+
+/* Posted fields for the mixed form's evaluation.  fp_fields_create copies F
+ * nodal fields [F][E][n3] (FP64, the handle's mesh) to the device as pairs of
+ * floats (hi, lo) with hi + lo equal to the value to 48 bits (allocates;
+ * enqueued on `stream`).  fp_eval_df interpolates them at located points like
+ * fp_eval, but with double-float arithmetic on the FP32 pipes: exact leading
+ * products, error-free two-sums, basis values computed in FP64 and split the
+ * same way.  The result is rounded to FP64; its error is a few 2^-48 times
+ * the sum of |f_ijk h_i h_j h_k| (measured against the FP64 oracle: below
+ * 1e-13 of the field's largest nodal magnitude on the test meshes).  NaN
+ * where code is NOT_FOUND or RETRY.  Allocates nothing. */
+fp_status fp_fields_create(const fp_handle *h, int F, const double *fields, fp_fields **out,
+                           void *stream);
+void fp_fields_free(fp_fields *f);
+fp_status fp_eval_df(fp_handle *h, const fp_fields *f, int64_t P, const int32_t *code,
+                     const int32_t *elem, const double *rst, double *out, void *stream);
+
+/* fp_find_eval / fp_find_eval_ws -- fp_find (or fp_find_ws) followed by the
+ * interpolation of F fields, fused into the same launch sequence: after
+ * classification each point's winning (point, element) pair is evaluated in
+ * the element-sorted pair order of the Newton stage, so neighbouring threads
+ * share an element's field rows.  Fields are either posted double-float
+ * fields (`posted`, see fp_fields_create; F must equal its count) or FP64
+ * fields [F][E][n3] (`fields`, 16-byte aligned for even n) when posted is
+ * NULL.  out [F][P] FP64; NaN for points not found (or RETRY).  The other
+ * arguments, outputs and errors are those of fp_find / fp_find_ws. */
+fp_status fp_find_eval(fp_handle *h, int64_t P, const double *pts, const int32_t *qsess, int F,
+                       const double *fields, const fp_fields *posted, int32_t *code, int32_t *sub,
+                       int32_t *elem, double *rst, double *dist2, double *out, void *stream);
+fp_status fp_find_eval_ws(fp_handle *h, fp_workspace *ws, int64_t P, const double *pts,
+                          const int32_t *qsess, int F, const double *fields,
+                          const fp_fields *posted, int32_t *code, int32_t *sub, int32_t *elem,
+                          double *rst, double *dist2, double *out, void *stream);
+
 /* Release every device resource of the handle (synchronises it first).
    NULL is a no-op. */
 void fp_free(fp_handle *h);

@@ -86,6 +86,16 @@ def _load():
     L.fp_batch_last_error.restype = ctypes.c_char_p
     L.fp_batch_free.argtypes = [vp]
     L.fp_batch_free.restype = None
+    L.fp_fields_create.argtypes = [vp, ci, vp, ctypes.POINTER(vp), vp]
+    L.fp_fields_create.restype = ci
+    L.fp_fields_free.argtypes = [vp]
+    L.fp_fields_free.restype = None
+    L.fp_eval_df.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp]
+    L.fp_eval_df.restype = ci
+    L.fp_find_eval.argtypes = [vp, i64, vp, vp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.fp_find_eval.restype = ci
+    L.fp_find_eval_ws.argtypes = [vp, vp, i64, vp, vp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.fp_find_eval_ws.restype = ci
     L.fp_eval.argtypes = [vp, i64, vp, vp, vp, ci, vp, vp, vp]
     L.fp_eval.restype = ci
     L.fp_free.argtypes = [vp]
@@ -359,6 +369,88 @@ def fp_eval(h: Handle, code: torch.Tensor, elem: torch.Tensor, rst: torch.Tensor
                        _stream(stream))
     _check(st, h.ptr)
     return out
+
+
+class Fields:
+    """Fields posted as double-float pairs for fp_eval_df (mixed form)."""
+
+    def __init__(self, h: Handle, fields: torch.Tensor, stream=None):
+        fields = _dev(fields, torch.float64, "fields")
+        if fields.ndim == 2:
+            fields = fields.unsqueeze(0)
+        self.F = int(fields.shape[0])
+        self.handle = h
+        self.ptr = ctypes.c_void_p()
+        _check(lib().fp_fields_create(h.ptr, self.F, _ptr(fields), ctypes.byref(self.ptr), _stream(stream)), h.ptr)
+
+    def __del__(self):
+        if getattr(self, "ptr", None) is not None and self.ptr.value:
+            try:
+                lib().fp_fields_free(self.ptr)
+            except Exception:
+                pass
+            self.ptr = ctypes.c_void_p(None)
+
+
+def fp_eval_df(h: Handle, f: Fields, code: torch.Tensor, elem: torch.Tensor, rst: torch.Tensor,
+               out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Double-float interpolation of posted fields at located points -> [F][P]."""
+    P = code.shape[0]
+    if out is None:
+        out = torch.empty((f.F, P), dtype=torch.float64, device=code.device)
+    st = lib().fp_eval_df(h.ptr, f.ptr, P, _ptr(code), _ptr(elem), _ptr(rst), _ptr(out), _stream(stream))
+    _check(st, h.ptr)
+    return out
+
+
+def _find_outs(P, dev):
+    return (torch.empty(P, dtype=torch.int32, device=dev), torch.empty(P, dtype=torch.int32, device=dev),
+            torch.empty(P, dtype=torch.int32, device=dev), torch.empty((3, P), dtype=torch.float64, device=dev),
+            torch.empty(P, dtype=torch.float64, device=dev))
+
+
+def _eval_args(fields, posted):
+    if posted is not None:
+        return posted.F, None, posted.ptr
+    fields = _dev(fields, torch.float64, "fields")
+    if fields.ndim == 2:
+        fields = fields.unsqueeze(0)
+    return int(fields.shape[0]), fields, None
+
+
+def fp_find_eval(h: Handle, pts: torch.Tensor, qsess: Optional[torch.Tensor] = None, fields=None,
+                 posted: Optional["Fields"] = None, out=None, values: Optional[torch.Tensor] = None, stream=None):
+    """Fused find + eval: returns (code, sub, elem, rst, dist2, values [F][P]).
+    Uses posted double-float fields when given, else FP64 `fields`."""
+    pts = _dev(pts, torch.float64, "pts")
+    P = pts.shape[1]
+    qsess = None if qsess is None else _dev(qsess, torch.int32, "qsess")
+    F, f64, fptr = _eval_args(fields, posted)
+    out = out or _find_outs(P, pts.device)
+    if values is None:
+        values = torch.empty((F, P), dtype=torch.float64, device=pts.device)
+    code, sub, elem, rst, dist2 = out
+    st = lib().fp_find_eval(h.ptr, P, _ptr(pts), _ptr(qsess), F, _ptr(f64), fptr, _ptr(code), _ptr(sub), _ptr(elem),
+                            _ptr(rst), _ptr(dist2), _ptr(values), _stream(stream))
+    _check(st, h.ptr)
+    return code, sub, elem, rst, dist2, values
+
+
+def fp_find_eval_ws(h: Handle, ws: "Workspace", pts: torch.Tensor, qsess: Optional[torch.Tensor] = None, fields=None,
+                    posted: Optional["Fields"] = None, out=None, values: Optional[torch.Tensor] = None, stream=None):
+    """Asynchronous fused find + eval with the scratch in `ws`."""
+    pts = _dev(pts, torch.float64, "pts")
+    P = pts.shape[1]
+    qsess = None if qsess is None else _dev(qsess, torch.int32, "qsess")
+    F, f64, fptr = _eval_args(fields, posted)
+    out = out or _find_outs(P, pts.device)
+    if values is None:
+        values = torch.empty((F, P), dtype=torch.float64, device=pts.device)
+    code, sub, elem, rst, dist2 = out
+    st = lib().fp_find_eval_ws(h.ptr, ws.ptr, P, _ptr(pts), _ptr(qsess), F, _ptr(f64), fptr, _ptr(code), _ptr(sub),
+                               _ptr(elem), _ptr(rst), _ptr(dist2), _ptr(values), _stream(stream))
+    _check(st, h.ptr)
+    return code, sub, elem, rst, dist2, values
 
 
 PROF_KINDS = {"screen": 0, "sort": 1, "newton": 2, "rank": 3, "eval": 4}

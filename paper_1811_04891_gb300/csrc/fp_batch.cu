@@ -46,6 +46,7 @@ struct Group {
     ElemBox* boxes = nullptr;
     double* dist = nullptr;
     double* fields = nullptr;
+    float2* fields_df = nullptr;  // mixed form: double-float copy of the fields
     // per-run buffers
     double* pts = nullptr;
     int32_t *code = nullptr, *osub = nullptr, *oelem = nullptr;
@@ -72,6 +73,7 @@ void release(T*& p)
 void release_group(Group& g)
 {
     release(g.coords); release(g.coords32); release(g.sub); release(g.boxes); release(g.dist); release(g.fields);
+    release(g.fields_df);
     release(g.pts); release(g.code); release(g.osub); release(g.oelem); release(g.rst); release(g.dist2);
     release(g.out); release(g.cnt); release(g.off); release(g.scan_tmp); release(g.pair_elem); release(g.pair_pt);
     release(g.order); release(g.ecount); release(g.estart); release(g.pres); release(g.prst);
@@ -229,6 +231,12 @@ extern "C" fp_status fp_batch_create(fp_batch** out, int ninst, fp_handle* const
                                sizeof(double) * Ei * n3, cudaMemcpyDeviceToDevice);
             }
         }
+        if (e == cudaSuccess && F > 0 && g.fp.mixed) {
+            const int64_t nv = (int64_t)F * g.E * n3;
+            e = alloc(&g.fields_df, nv);
+            if (e == cudaSuccess) e = launch_split_df(nv, g.fields, g.fields_df, 0);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        }
         if (e == cudaSuccess) e = alloc(&g.pts, 3 * g.P);
         if (e == cudaSuccess) e = alloc(&g.code, g.P);
         if (e == cudaSuccess) e = alloc(&g.osub, g.P);
@@ -283,7 +291,7 @@ static cudaError_t batch_run(fp_batch* b, const double* pts, int32_t* code, int3
             fp_handle* h = b->h[i];
             a.n = g.n; a.E = h->E; a.P = b->npts[i];
             a.pts = g.pts + g.goff[k]; a.pts_stride = g.P; a.qsess = nullptr;
-            a.sub = h->sub; a.boxes = h->boxes; a.grid = &h->grid;
+            a.sub = h->sub; a.boxes = h->boxes; a.boxes32 = h->boxes32; a.grid = &h->grid;
             a.cell_start = h->cell_start; a.cell_elems = h->cell_elems;
             a.cnt = g.cnt + g.goff[k];
             e = find_screen_count(a, s);
@@ -295,7 +303,7 @@ static cudaError_t batch_run(fp_batch* b, const double* pts, int32_t* code, int3
             fp_handle* h = b->h[i];
             a.n = g.n; a.E = h->E; a.P = b->npts[i];
             a.pts = g.pts + g.goff[k]; a.pts_stride = g.P; a.qsess = nullptr;
-            a.sub = h->sub; a.boxes = h->boxes; a.grid = &h->grid;
+            a.sub = h->sub; a.boxes = h->boxes; a.boxes32 = h->boxes32; a.grid = &h->grid;
             a.cell_start = h->cell_start; a.cell_elems = h->cell_elems;
             a.off = g.off + g.goff[k];
             a.pair_elem = g.pair_elem; a.pair_pt = g.pair_pt; a.cap = g.cap;
@@ -313,9 +321,9 @@ static cudaError_t batch_run(fp_batch* b, const double* pts, int32_t* code, int3
         c.cap = g.cap;
         c.persistent_blocks = b->bps * b->nsm;
         c.code = g.code; c.osub = g.osub; c.oelem = g.oelem; c.rst = g.rst; c.dist2 = g.dist2;
+        if (b->F > 0 && out)   // fused eval in the element-sorted pair order
+            c.eval = EvalSpec{b->F, g.fields_df ? nullptr : g.fields, g.fields_df, g.out};
         e = find_solve(c, g.cap, g.tab, g.fp, b->block, s);
-        if (e == cudaSuccess && b->F > 0 && out)
-            e = launch_eval(g.n, g.E, g.P, g.code, g.oelem, g.rst, b->F, g.fields, g.out, g.tab, s);
         // scatter back to instance order
         for (int k = 0; k < m && e == cudaSuccess; ++k) {
             const int i = g.inst[k];

@@ -32,6 +32,16 @@ struct ElemBox {
     double spare;
 };
 
+// FP32 copy of ElemBox for the mixed form's screen, rounded outward with
+// margins that cover the FP32 evaluation of the tests (never tighter than
+// the FP64 boxes).
+struct ElemBox32 {
+    float c[3];
+    float Ai[9];
+    float olo[3], ohi[3];
+    float blo[3], bhi[3];
+};
+
 struct HashGrid {
     double org[3];
     double inv[3];      // 1 / cell size

@@ -1,6 +1,8 @@
 // fp_eval.cu -- findpts_eval (Sec. 2.1): interpolate F nodal fields at located
 // points by sum factorisation, out[f][p] = sum_ijk F_ijk h_i(r) h_j(s) h_k(t),
 // in FP64; quiet NaN for points that were not found.
+#include <algorithm>
+
 #include "fp_common.cuh"
 #include "fp_internal.h"
 
@@ -45,6 +47,289 @@ cudaError_t launch_eval(int n, int64_t E, int64_t P, const int32_t* code, const 
     switch (n) {
 #define FP_CASE(NN) \
     case NN: k_eval<NN><<<grid, 128, 0, s>>>(a, tab); break;
+        FP_CASE(2) FP_CASE(3) FP_CASE(4) FP_CASE(5) FP_CASE(6) FP_CASE(7) FP_CASE(8) FP_CASE(9)
+        FP_CASE(10) FP_CASE(11) FP_CASE(12) FP_CASE(13) FP_CASE(14) FP_CASE(15) FP_CASE(16)
+#undef FP_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace fpg
+
+// ---------------------------------------------------------------------------
+// Double-float evaluation for the mixed form.
+//
+// Every nodal value f is posted once as an unevaluated sum of two floats,
+// f = f_hi + f_lo (f_hi = fl(f), f_lo = fl(f - f_hi), 48 significant bits),
+// and each basis value h(r), computed in FP64, is split the same way.  The
+// contraction then runs on the FP32 pipes: each product f*h is formed exactly
+// in its leading part (p = f_hi*h_hi, e = fma(f_hi, h_hi, -p)) plus the
+// first-order cross terms, and the sum is carried as a (hi, lo) pair with an
+// error-free two-sum.  The result is rounded to FP64 at the end.  Relative
+// error is a few units of 2^-48 times the sum of |terms|.
+// ---------------------------------------------------------------------------
+namespace fpg {
+
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_split(double v)
+{
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+
+// acc += a * b for double-floats a (value) and b (basis)
+__device__ __forceinline__ void df_fma_acc(df& acc, float ah, float al, float bh, float bl)
+{
+    const float p = ah * bh;
+    const float pe = fmaf(ah, bh, -p);
+    const float t = fmaf(ah, bl, fmaf(al, bh, pe));
+    const float s = acc.hi + p;
+    const float bb = s - acc.hi;
+    const float err = (acc.hi - (s - bb)) + (p - bb);
+    acc.hi = s;
+    acc.lo += err + t;
+}
+
+// acc += a * b where a is a double-float partial sum and b a double-float basis value
+__device__ __forceinline__ void df_fma_acc(df& acc, const df& a, float bh, float bl)
+{
+    df_fma_acc(acc, a.hi, a.lo, bh, bl);
+}
+
+struct Eval2Args {
+    int64_t E;
+    int64_t P;
+    const int32_t* code;
+    const int32_t* elem;
+    const double* rst;
+    int F;
+    const float2* fields;     // [F][E][n3] (hi, lo)
+    double* out;
+};
+
+template <int n>
+__global__ void __launch_bounds__(128) k_eval_df(Eval2Args A, BasisTab tab)
+{
+    constexpr int n3 = n * n * n;
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= A.P) return;
+    const int e = A.elem[p];
+    if (A.code[p] == FP_CODE_NOT_FOUND || A.code[p] == FP_CODE_RETRY || e < 0 || e >= A.E) {
+        for (int f = 0; f < A.F; ++f) A.out[(int64_t)f * A.P + p] = __longlong_as_double(0x7ff8000000000000ULL);
+        return;
+    }
+    double hr[n], hs[n], ht[n];
+    lagrange_h<n, double>(tab.xi, tab.ci, A.rst[p], hr);
+    lagrange_h<n, double>(tab.xi, tab.ci, A.rst[A.P + p], hs);
+    lagrange_h<n, double>(tab.xi, tab.ci, A.rst[2 * A.P + p], ht);
+    float rh[n], rl[n], sh[n], sl[n], th[n], tl[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        df a = df_split(hr[i]), b = df_split(hs[i]), c = df_split(ht[i]);
+        rh[i] = a.hi; rl[i] = a.lo; sh[i] = b.hi; sl[i] = b.lo; th[i] = c.hi; tl[i] = c.lo;
+    }
+    for (int f = 0; f < A.F; ++f) {
+        const float2* Fe = A.fields + ((int64_t)f * A.E + e) * n3;
+        df acc = {0.0f, 0.0f};
+#pragma unroll 1
+        for (int k = 0; k < n; ++k) {
+            df ck = {0.0f, 0.0f};
+#pragma unroll
+            for (int j = 0; j < n; ++j) {
+                const float4* row = reinterpret_cast<const float4*>(Fe + n * (j + n * k));
+                df u = {0.0f, 0.0f};
+                if constexpr (n % 2 == 0) {
+#pragma unroll
+                    for (int i2 = 0; i2 < n / 2; ++i2) {
+                        const float4 v = __ldg(row + i2);
+                        df_fma_acc(u, v.x, v.y, rh[2 * i2], rl[2 * i2]);
+                        df_fma_acc(u, v.z, v.w, rh[2 * i2 + 1], rl[2 * i2 + 1]);
+                    }
+                } else {
+                    const float2* r2 = Fe + n * (j + n * k);
+#pragma unroll
+                    for (int i = 0; i < n; ++i) {
+                        const float2 v = __ldg(r2 + i);
+                        df_fma_acc(u, v.x, v.y, rh[i], rl[i]);
+                    }
+                }
+                {   // renormalise (fast two-sum): keeps |lo| below one unit of hi
+                    const float t = u.hi + u.lo;
+                    u.lo = u.lo - (t - u.hi);
+                    u.hi = t;
+                }
+                df_fma_acc(ck, u, sh[j], sl[j]);
+            }
+            {
+                const float t = ck.hi + ck.lo;
+                ck.lo = ck.lo - (t - ck.hi);
+                ck.hi = t;
+            }
+            // t-basis by runtime index k: read from the split arrays
+            df_fma_acc(acc, ck, th[k], tl[k]);
+        }
+        A.out[(int64_t)f * A.P + p] = (double)acc.hi + (double)acc.lo;
+    }
+}
+
+__global__ void k_split_df(int64_t n, const double* __restrict__ src, float2* __restrict__ dst)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = src[i];
+        const float h = (float)v;
+        dst[i] = make_float2(h, (float)(v - (double)h));
+    }
+}
+
+cudaError_t launch_split_df(int64_t n, const double* src, float2* dst, cudaStream_t s)
+{
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 32);
+    k_split_df<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(n, src, dst);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval_df(int n, int64_t E, int64_t P, const int32_t* code, const int32_t* elem, const double* rst,
+                           int F, const float2* fields, double* out, const BasisTab& tab, cudaStream_t s)
+{
+    if (P == 0) return cudaSuccess;
+    Eval2Args a{E, P, code, elem, rst, F, fields, out};
+    const unsigned grid = (unsigned)((P + 127) / 128);
+    switch (n) {
+#define FP_CASE(NN) \
+    case NN: k_eval_df<NN><<<grid, 128, 0, s>>>(a, tab); break;
+        FP_CASE(2) FP_CASE(3) FP_CASE(4) FP_CASE(5) FP_CASE(6) FP_CASE(7) FP_CASE(8) FP_CASE(9)
+        FP_CASE(10) FP_CASE(11) FP_CASE(12) FP_CASE(13) FP_CASE(14) FP_CASE(15) FP_CASE(16)
+#undef FP_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace fpg
+
+// ---------------------------------------------------------------------------
+// Fused evaluation in the element-sorted pair order of the find (one thread
+// per winning pair; neighbouring threads work on the same element, so its
+// field rows are served from L1 instead of being re-read from DRAM).
+// ---------------------------------------------------------------------------
+namespace fpg {
+
+template <int n>
+__device__ __forceinline__ void eval_point_f64(const double* __restrict__ F64, int64_t E, int F, int e, double r0,
+                                               double r1, double r2, const BasisTab& tab, double* __restrict__ out,
+                                               int64_t P, int64_t p)
+{
+    constexpr int n3 = n * n * n;
+    double hr[n], hs[n], ht[n];
+    lagrange_h<n, double>(tab.xi, tab.ci, r0, hr);
+    lagrange_h<n, double>(tab.xi, tab.ci, r1, hs);
+    lagrange_h<n, double>(tab.xi, tab.ci, r2, ht);
+    for (int f = 0; f < F; ++f)
+        out[(int64_t)f * P + p] = contract<n, double>(F64 + ((int64_t)f * E + e) * n3, hr, hs, ht);
+}
+
+template <int n>
+__device__ __forceinline__ void eval_point_df(const float2* __restrict__ Fdf, int64_t E, int F, int e, double r0,
+                                              double r1, double r2, const BasisTab& tab, double* __restrict__ out,
+                                              int64_t P, int64_t p)
+{
+    constexpr int n3 = n * n * n;
+    double hr[n], hs[n], ht[n];
+    lagrange_h<n, double>(tab.xi, tab.ci, r0, hr);
+    lagrange_h<n, double>(tab.xi, tab.ci, r1, hs);
+    lagrange_h<n, double>(tab.xi, tab.ci, r2, ht);
+    float rh[n], rl[n], sh[n], sl[n], th[n], tl[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        df a = df_split(hr[i]), b = df_split(hs[i]), c = df_split(ht[i]);
+        rh[i] = a.hi; rl[i] = a.lo; sh[i] = b.hi; sl[i] = b.lo; th[i] = c.hi; tl[i] = c.lo;
+    }
+    for (int f = 0; f < F; ++f) {
+        const float2* Fe = Fdf + ((int64_t)f * E + e) * n3;
+        df acc = {0.0f, 0.0f};
+#pragma unroll 1
+        for (int k = 0; k < n; ++k) {
+            df ck = {0.0f, 0.0f};
+#pragma unroll
+            for (int j = 0; j < n; ++j) {
+                df u = {0.0f, 0.0f};
+                if constexpr (n % 2 == 0) {
+                    const float4* row = reinterpret_cast<const float4*>(Fe + n * (j + n * k));
+#pragma unroll
+                    for (int i2 = 0; i2 < n / 2; ++i2) {
+                        const float4 v = __ldg(row + i2);
+                        df_fma_acc(u, v.x, v.y, rh[2 * i2], rl[2 * i2]);
+                        df_fma_acc(u, v.z, v.w, rh[2 * i2 + 1], rl[2 * i2 + 1]);
+                    }
+                } else {
+                    const float2* r2p = Fe + n * (j + n * k);
+#pragma unroll
+                    for (int i = 0; i < n; ++i) {
+                        const float2 v = __ldg(r2p + i);
+                        df_fma_acc(u, v.x, v.y, rh[i], rl[i]);
+                    }
+                }
+                const float t = u.hi + u.lo;
+                u.lo = u.lo - (t - u.hi);
+                u.hi = t;
+                df_fma_acc(ck, u, sh[j], sl[j]);
+            }
+            const float t = ck.hi + ck.lo;
+            ck.lo = ck.lo - (t - ck.hi);
+            ck.hi = t;
+            df_fma_acc(acc, ck, th[k], tl[k]);
+        }
+        out[(int64_t)f * P + p] = (double)acc.hi + (double)acc.lo;
+    }
+}
+
+struct EvalPairsArgs {
+    int64_t E, P, cap;
+    const int32_t* dcount;
+    const int32_t* order;
+    const int32_t* pair_elem;
+    const int32_t* pair_pt;
+    const double* prst;
+    EvalSpec ev;
+};
+
+template <int n, bool DF>
+__global__ void __launch_bounds__(128) k_eval_pairs(EvalPairsArgs A, BasisTab tab)
+{
+    const int64_t t = *A.dcount;
+    const int64_t npairs = t < A.cap ? t : A.cap;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < npairs; s += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t q = A.order[s];
+        const int32_t p = A.pair_pt[q];
+        if (p < 0) continue;                              // not the point's winning pair
+        const int e = A.pair_elem[q];
+        const double r0 = A.prst[q], r1 = A.prst[A.cap + q], r2 = A.prst[2 * A.cap + q];
+        if (DF)
+            eval_point_df<n>(A.ev.fdf, A.E, A.ev.F, e, r0, r1, r2, tab, A.ev.out, A.P, p);
+        else
+            eval_point_f64<n>(A.ev.f64, A.E, A.ev.F, e, r0, r1, r2, tab, A.ev.out, A.P, p);
+    }
+}
+
+cudaError_t launch_eval_pairs(int n, int64_t E, int64_t P, const int32_t* dcount, int64_t cap, const int32_t* order,
+                              const int32_t* pair_elem, const int32_t* pair_pt, const double* prst,
+                              const EvalSpec& ev, const BasisTab& tab, unsigned grid, cudaStream_t s)
+{
+    EvalPairsArgs a{E, P, cap, dcount, order, pair_elem, pair_pt, prst, ev};
+    const bool df = ev.fdf != nullptr;
+    switch (n) {
+#define FP_CASE(NN)                                                   \
+    case NN:                                                          \
+        if (df) k_eval_pairs<NN, true><<<grid, 128, 0, s>>>(a, tab);  \
+        else k_eval_pairs<NN, false><<<grid, 128, 0, s>>>(a, tab);    \
+        break;
         FP_CASE(2) FP_CASE(3) FP_CASE(4) FP_CASE(5) FP_CASE(6) FP_CASE(7) FP_CASE(8) FP_CASE(9)
         FP_CASE(10) FP_CASE(11) FP_CASE(12) FP_CASE(13) FP_CASE(14) FP_CASE(15) FP_CASE(16)
 #undef FP_CASE

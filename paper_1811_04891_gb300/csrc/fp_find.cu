@@ -40,12 +40,29 @@ __device__ __forceinline__ bool inside_boxes(const ElemBox* __restrict__ bp, dou
     return true;
 }
 
+__device__ __forceinline__ bool inside_boxes32(const ElemBox32* __restrict__ bp, float x, float y, float z)
+{
+    const float* b = reinterpret_cast<const float*>(bp);
+    // ElemBox32 layout: c[0..2], Ai[3..11], olo[12..14], ohi[15..17], blo[18..20], bhi[21..23]
+    if (x < __ldg(b + 18) || x > __ldg(b + 21) || y < __ldg(b + 19) || y > __ldg(b + 22) ||
+        z < __ldg(b + 20) || z > __ldg(b + 23))
+        return false;
+    const float dx = x - __ldg(b + 0), dy = y - __ldg(b + 1), dz = z - __ldg(b + 2);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float v = __ldg(b + 3 + 3 * a) * dx + __ldg(b + 4 + 3 * a) * dy + __ldg(b + 5 + 3 * a) * dz;
+        if (v < __ldg(b + 12 + a) || v > __ldg(b + 15 + a)) return false;
+    }
+    return true;
+}
+
 struct ScreenArgs {
     int64_t P;
     const double* pts;
     const int32_t* qsess;
     const int32_t* sub;
     const ElemBox* boxes;
+    const ElemBox32* boxes32;
     HashGrid g;
     const int32_t* cell_start;
     const int32_t* cell_elems;
@@ -59,7 +76,7 @@ struct ScreenArgs {
     int32_t elem_base;    // added to the element index written into pair_elem
 };
 
-template <bool EMIT>
+template <bool EMIT, bool F32>
 __global__ void __launch_bounds__(256) k_screen(ScreenArgs A)
 {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -70,9 +87,16 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs A)
     int c = 0;
     int base = EMIT ? A.off[p] : 0;
     if (isfinite(x) && isfinite(y) && isfinite(z)) {
-        const double u0 = (x - A.g.org[0]) * A.g.inv[0];
-        const double u1 = (y - A.g.org[1]) * A.g.inv[1];
-        const double u2 = (z - A.g.org[2]) * A.g.inv[2];
+        double u0, u1, u2;
+        if (F32) {
+            u0 = (double)(((float)x - (float)A.g.org[0]) * (float)A.g.inv[0]);
+            u1 = (double)(((float)y - (float)A.g.org[1]) * (float)A.g.inv[1]);
+            u2 = (double)(((float)z - (float)A.g.org[2]) * (float)A.g.inv[2]);
+        } else {
+            u0 = (x - A.g.org[0]) * A.g.inv[0];
+            u1 = (y - A.g.org[1]) * A.g.inv[1];
+            u2 = (z - A.g.org[2]) * A.g.inv[2];
+        }
         if (u0 >= 0.0 && u1 >= 0.0 && u2 >= 0.0 && u0 <= (double)A.g.dim[0] && u1 <= (double)A.g.dim[1] &&
             u2 <= (double)A.g.dim[2]) {
             const int i = min((int)u0, A.g.dim[0] - 1);
@@ -83,7 +107,11 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs A)
             for (int q = b; q < en; ++q) {
                 const int e = __ldg(A.cell_elems + q);
                 if (tag >= 0 && __ldg(A.sub + e) == tag) continue;
-                if (!inside_boxes(A.boxes + e, x, y, z)) continue;
+                if (F32) {
+                    if (!inside_boxes32(A.boxes32 + e, (float)x, (float)y, (float)z)) continue;
+                } else if (!inside_boxes(A.boxes + e, x, y, z)) {
+                    continue;
+                }
                 if (EMIT && base + c < A.cap) {
                     A.pair_elem[base + c] = A.elem_base + e;
                     A.pair_pt[base + c] = A.pt_base + (int32_t)p;
@@ -481,6 +509,9 @@ __global__ void __launch_bounds__(256) k_newton(NewtonArgs A, BasisTab tab)
 // ---------------------------------------------------------------------------
 struct RankArgs {
     int64_t P;
+    int32_t* pair_pt;       // non-winning pairs are marked -1 for the fused eval
+    int F;                  // fused eval: write NaN for points without a winner
+    double* out;
     int64_t E;
     const int32_t* off;
     const int32_t* pair_elem;
@@ -516,6 +547,8 @@ __global__ void __launch_bounds__(128) k_rank(RankArgs A, FindParams fp, BasisTa
     if (p >= A.P) return;
     const int b = A.off[p], en = A.off[p + 1];
     if (en > A.cap) {                                  // pairs dropped: not searched
+        for (int q = b; q < A.cap; ++q) A.pair_pt[q] = -1;
+        for (int f = 0; f < A.F; ++f) A.out[(int64_t)f * A.P + p] = __longlong_as_double(0x7ff8000000000000ULL);
         A.code[p] = FP_CODE_RETRY;
         A.osub[p] = -1;
         A.oelem[p] = -1;
@@ -593,6 +626,10 @@ __global__ void __launch_bounds__(128) k_rank(RankArgs A, FindParams fp, BasisTa
         }
         code = 1;
     }
+    for (int q = b; q < en; ++q)
+        if (q != pick) A.pair_pt[q] = -1;
+    if (pick < 0)
+        for (int f = 0; f < A.F; ++f) A.out[(int64_t)f * A.P + p] = __longlong_as_double(0x7ff8000000000000ULL);
     if (pick >= 0) {
         const int e = A.pair_elem[pick];
         A.code[p] = code;
@@ -625,6 +662,7 @@ static ScreenArgs screen_args(const FindArgs& a)
     s.qsess = a.qsess;
     s.sub = a.sub;
     s.boxes = a.boxes;
+    s.boxes32 = a.boxes32;
     s.g = *a.grid;
     s.cell_start = a.cell_start;
     s.cell_elems = a.cell_elems;
@@ -651,7 +689,10 @@ static unsigned grid_for(int64_t work, int block, int persistent)
 cudaError_t find_count(const FindArgs& a, const BasisTab&, const FindParams&, cudaStream_t s)
 {
     ScreenArgs sa = screen_args(a);
-    k_screen<false><<<(unsigned)((a.P + 255) / 256), 256, 0, s>>>(sa);
+    if (a.boxes32)
+        k_screen<false, true><<<(unsigned)((a.P + 255) / 256), 256, 0, s>>>(sa);
+    else
+        k_screen<false, false><<<(unsigned)((a.P + 255) / 256), 256, 0, s>>>(sa);
     count_launch();
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
@@ -661,7 +702,10 @@ cudaError_t find_count(const FindArgs& a, const BasisTab&, const FindParams&, cu
 cudaError_t find_screen_count(const FindArgs& a, cudaStream_t s)
 {
     ScreenArgs sa = screen_args(a);
-    k_screen<false><<<(unsigned)((a.P + 255) / 256), 256, 0, s>>>(sa);
+    if (a.boxes32)
+        k_screen<false, true><<<(unsigned)((a.P + 255) / 256), 256, 0, s>>>(sa);
+    else
+        k_screen<false, false><<<(unsigned)((a.P + 255) / 256), 256, 0, s>>>(sa);
     count_launch();
     return cudaGetLastError();
 }
@@ -669,7 +713,10 @@ cudaError_t find_screen_count(const FindArgs& a, cudaStream_t s)
 cudaError_t find_emit(const FindArgs& a, cudaStream_t s)
 {
     ScreenArgs sa = screen_args(a);
-    k_screen<true><<<(unsigned)((a.P + 255) / 256), 256, 0, s>>>(sa);
+    if (a.boxes32)
+        k_screen<true, true><<<(unsigned)((a.P + 255) / 256), 256, 0, s>>>(sa);
+    else
+        k_screen<true, false><<<(unsigned)((a.P + 255) / 256), 256, 0, s>>>(sa);
     count_launch();
     return cudaGetLastError();
 }
@@ -722,11 +769,20 @@ static cudaError_t solve_n(const FindArgs& a, int64_t npairs, const BasisTab& ta
     ra.oelem = a.oelem;
     ra.rst = a.rst;
     ra.dist2 = a.dist2;
+    ra.pair_pt = a.pair_pt;
+    ra.F = a.eval.F;
+    ra.out = a.eval.out;
     if (a.ev[4]) cudaEventRecord(a.ev[4], s);
     k_rank<n><<<(unsigned)((a.P + 127) / 128), 128, 0, s>>>(ra, fp, tab);
     count_launch();
     if (a.ev[5]) cudaEventRecord(a.ev[5], s);
-    return cudaGetLastError();
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess || a.eval.F == 0 || npairs == 0) return err;
+    if (a.ev[6]) cudaEventRecord(a.ev[6], s);
+    err = launch_eval_pairs(n, a.E, a.P, a.off + a.P, a.cap, a.order, a.pair_elem, a.pair_pt, a.prst, a.eval, tab,
+                            grid_for(npairs, 128, a.persistent_blocks ? 4 * a.persistent_blocks : 0), s);
+    if (a.ev[7]) cudaEventRecord(a.ev[7], s);
+    return err;
 }
 
 cudaError_t find_solve(const FindArgs& a, int64_t npairs, const BasisTab& tab, const FindParams& fp, int block,

@@ -26,6 +26,7 @@ struct fp_handle {
     int32_t* sub = nullptr;        // [E]
     double* dist = nullptr;        // [E][n3] or null
     fpg::ElemBox* boxes = nullptr;      // [E]
+    fpg::ElemBox32* boxes32 = nullptr;  // [E] mixed form only
     int32_t* cell_start = nullptr; // [ncell+1]
     int32_t* cell_elems = nullptr; // [nnz]
     int32_t* ecount = nullptr;     // [E]

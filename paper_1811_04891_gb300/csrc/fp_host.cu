@@ -179,7 +179,7 @@ void release(fp_handle* h)
     }
     for (auto e : h->ev_free) cudaEventDestroy(e);
     h->ev_free.clear();
-    dfree(h->coords); dfree(h->coords32); dfree(h->sub); dfree(h->dist); dfree(h->boxes);
+    dfree(h->coords); dfree(h->coords32); dfree(h->sub); dfree(h->dist); dfree(h->boxes); dfree(h->boxes32);
     dfree(h->cell_start); dfree(h->cell_elems); dfree(h->ecount); dfree(h->estart); dfree(h->escan_tmp);
     dfree(h->cnt); dfree(h->off); dfree(h->scan_tmp); dfree(h->pair_elem); dfree(h->pair_pt);
     dfree(h->order); dfree(h->pres); dfree(h->prst);
@@ -361,7 +361,21 @@ fp_status fp_setup(fp_handle** hout, const double* coords, int64_t E, int N, con
         h->L = sqrt(sq);
     }
 
-    // A2: hash grid over the global padded box
+    // A2: hash grid over the global padded box, widened by hpad, the margin
+    // that keeps FP32 cell lookups (mixed form) inside a listing cell
+    double hpad;
+    {
+        double xmax = 0.0, extm = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            xmax = std::max(xmax, std::max(fabs(glo[a]), fabs(ghi[a])));
+            extm = std::max(extm, ghi[a] - glo[a]);
+        }
+        hpad = 9.5367431640625e-07 * (2.0 * xmax + extm);   // 2^-20 (2 max|x| + extent)
+        for (int a = 0; a < 3; ++a) {
+            glo[a] -= hpad;
+            ghi[a] += hpad;
+        }
+    }
     {
         double ext[3], vol = 1.0;
         int nd = 0;
@@ -395,7 +409,7 @@ fp_status fp_setup(fp_handle** hout, const double* coords, int64_t E, int N, con
     CK(dalloc(&h->cell_start, ncell + 1), "alloc cell start");
     CK(dalloc(&d_tmp, scan_tmp_elems(ncell)), "alloc scan tmp");
     CK(cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * ncell, s), "zero hash count");
-    CK(launch_hash_count(E, h->boxes, h->grid, d_cnt, s), "hash count");
+    CK(launch_hash_count(E, h->boxes, h->grid, hpad, d_cnt, s), "hash count");
     CK(scan_exclusive(d_cnt, h->cell_start, ncell, d_tmp, s), "hash scan");
     CK(cudaMemcpyAsync(h->h_total, h->cell_start + ncell, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read nnz");
     CK(cudaStreamSynchronize(s), "sync hash");
@@ -403,7 +417,7 @@ fp_status fp_setup(fp_handle** hout, const double* coords, int64_t E, int N, con
     if (h->nnz < 0) BAD("fp_setup: hash grid overflow");
     CK(dalloc(&h->cell_elems, h->nnz), "alloc cell elems");
     CK(cudaMemcpyAsync(d_cnt, h->cell_start, sizeof(int32_t) * ncell, cudaMemcpyDeviceToDevice, s), "copy cursor");
-    CK(launch_hash_fill(E, h->boxes, h->grid, d_cnt, h->cell_elems, s), "hash fill");
+    CK(launch_hash_fill(E, h->boxes, h->grid, hpad, d_cnt, h->cell_elems, s), "hash fill");
     CK(launch_hash_sort(ncell, h->cell_start, h->cell_elems, s), "hash sort");
     CK(cudaStreamSynchronize(s), "sync hash fill");
     cudaFree(d_cnt);
@@ -446,6 +460,8 @@ fp_status fp_setup(fp_handle** hout, const double* coords, int64_t E, int N, con
     if (o.precision == FP_PREC_MIXED) {
         CK(dalloc(&h->coords32, ncoord), "alloc coords32");
         CK(launch_local32(n, E, h->coords, h->boxes, h->coords32, s), "local32");
+        CK(dalloc(&h->boxes32, E), "alloc boxes32");
+        CK(launch_box32(E, h->boxes, h->boxes32, s), "box32");
     }
     CK(dalloc(&h->ecount, E), "alloc ecount");
     CK(dalloc(&h->estart, E + 1), "alloc estart");
@@ -465,11 +481,9 @@ fp_status fp_reserve(fp_handle* h, int64_t P)
     return grow_pairs(h, 2 * P);
 }
 
-fp_status fp_find(fp_handle* h, int64_t P, const double* pts, const int32_t* qsess, int32_t* code, int32_t* sub,
-                  int32_t* elem, double* rst, double* dist2, void* stream)
+static fp_status find_impl(fp_handle* h, int64_t P, const double* pts, const int32_t* qsess, int32_t* code,
+                           int32_t* sub, int32_t* elem, double* rst, double* dist2, const EvalSpec& ev, void* stream)
 {
-    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
-    h->err.clear();
     if (P < 0 || P >= (int64_t(1) << 31)) return fail(h, FP_ERR_INVALID_ARG, "fp_find: P out of range");
     if (P == 0) return FP_OK;
     if (!pts || !code || !sub || !elem || !rst || !dist2)
@@ -482,12 +496,14 @@ fp_status fp_find(fp_handle* h, int64_t P, const double* pts, const int32_t* qse
     a.n = h->n; a.E = h->E; a.P = P; a.pts = pts; a.qsess = qsess;
     a.coords = h->coords; a.coords32 = h->coords32; a.sub = h->sub;
     a.dist = h->nsub > 1 ? h->dist : nullptr;
-    a.boxes = h->boxes; a.grid = &h->grid; a.cell_start = h->cell_start; a.cell_elems = h->cell_elems;
+    a.boxes = h->boxes; a.boxes32 = h->boxes32; a.grid = &h->grid;
+    a.cell_start = h->cell_start; a.cell_elems = h->cell_elems;
     a.cnt = h->cnt; a.off = h->off; a.ecount = h->ecount; a.estart = h->estart; a.scan_tmp = h->scan_tmp;
     a.code = code; a.osub = sub; a.oelem = elem; a.rst = rst; a.dist2 = dist2;
+    a.eval = ev;
     cudaEvent_t scr0 = nullptr, scr1 = nullptr;
     if (h->prof) {
-        for (int q = 0; q < 6; ++q) a.ev[q] = ev_get(h);
+        for (int q = 0; q < (ev.F > 0 ? 8 : 6); ++q) a.ev[q] = ev_get(h);
         scr0 = ev_get(h);
         scr1 = ev_get(h);
         cudaEventRecord(scr0, s);
@@ -524,13 +540,60 @@ fp_status fp_find(fp_handle* h, int64_t P, const double* pts, const int32_t* qse
         if (npairs > 0) {
             h->ev_pend[PROF_SORT].push_back({a.ev[0], a.ev[1]});
             h->ev_pend[PROF_NEWTON].push_back({a.ev[2], a.ev[3]});
+            if (ev.F > 0) h->ev_pend[PROF_EVAL].push_back({a.ev[6], a.ev[7]});
         } else {
             for (int q = 0; q < 4; ++q) h->ev_free.push_back(a.ev[q]);
+            if (ev.F > 0) { h->ev_free.push_back(a.ev[6]); h->ev_free.push_back(a.ev[7]); }
         }
         h->ev_pend[PROF_RANK].push_back({a.ev[4], a.ev[5]});
     }
     if (err != cudaSuccess) return cuda_fail(h, err, "fp_find solve");
     return FP_OK;
+}
+
+fp_status fp_find(fp_handle* h, int64_t P, const double* pts, const int32_t* qsess, int32_t* code, int32_t* sub,
+                  int32_t* elem, double* rst, double* dist2, void* stream)
+{
+    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    h->err.clear();
+    EvalSpec ev{0, nullptr, nullptr, nullptr};
+    return find_impl(h, P, pts, qsess, code, sub, elem, rst, dist2, ev, stream);
+}
+
+struct fp_fields {
+    const fp_handle* owner = nullptr;
+    int F = 0;
+    float2* data = nullptr;
+};
+
+// fused-eval arguments: posted double-float fields, else FP64 fields
+static fp_status eval_spec(fp_handle* h, int F, const double* fields, const fp_fields* posted, double* out,
+                           EvalSpec* ev)
+{
+    if (!out) return fail(h, FP_ERR_INVALID_ARG, "fp_find_eval: null out");
+    if (posted) {
+        if (posted->owner != h) return fail(h, FP_ERR_INVALID_ARG, "fp_find_eval: fields posted for another handle");
+        if (F != posted->F) return fail(h, FP_ERR_INVALID_ARG, "fp_find_eval: F differs from the posted fields");
+        *ev = EvalSpec{posted->F, nullptr, posted->data, out};
+        return FP_OK;
+    }
+    if (!fields || F < 1) return fail(h, FP_ERR_INVALID_ARG, "fp_find_eval: no fields");
+    if ((h->n % 2 == 0) && ((uintptr_t)fields % 16) != 0)
+        return fail(h, FP_ERR_INVALID_ARG, "fp_find_eval: fields must be 16-byte aligned for even n");
+    *ev = EvalSpec{F, fields, nullptr, out};
+    return FP_OK;
+}
+
+fp_status fp_find_eval(fp_handle* h, int64_t P, const double* pts, const int32_t* qsess, int F, const double* fields,
+                       const fp_fields* posted, int32_t* code, int32_t* sub, int32_t* elem, double* rst, double* dist2,
+                       double* out, void* stream)
+{
+    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    h->err.clear();
+    EvalSpec ev;
+    fp_status st = eval_spec(h, F, fields, posted, out, &ev);
+    if (st != FP_OK) return st;
+    return find_impl(h, P, pts, qsess, code, sub, elem, rst, dist2, ev, stream);
 }
 
 struct fp_workspace {
@@ -601,11 +664,10 @@ fp_status fp_workspace_last_pairs(fp_workspace* w, int64_t* npairs)
     return FP_OK;
 }
 
-fp_status fp_find_ws(fp_handle* h, fp_workspace* w, int64_t P, const double* pts, const int32_t* qsess,
-                     int32_t* code, int32_t* sub, int32_t* elem, double* rst, double* dist2, void* stream)
+static fp_status find_ws_impl(fp_handle* h, fp_workspace* w, int64_t P, const double* pts, const int32_t* qsess,
+                              int32_t* code, int32_t* sub, int32_t* elem, double* rst, double* dist2,
+                              const EvalSpec& ev, void* stream)
 {
-    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
-    h->err.clear();
     if (!w || w->owner != h) return fail(h, FP_ERR_INVALID_ARG, "fp_find_ws: workspace belongs to another handle");
     if (P < 0 || P > w->max_points) return fail(h, FP_ERR_INVALID_ARG, "fp_find_ws: P outside [0, max_points]");
     if (P == 0) return FP_OK;
@@ -617,12 +679,14 @@ fp_status fp_find_ws(fp_handle* h, fp_workspace* w, int64_t P, const double* pts
     a.n = h->n; a.E = h->E; a.P = P; a.pts = pts; a.qsess = qsess;
     a.coords = h->coords; a.coords32 = h->coords32; a.sub = h->sub;
     a.dist = h->nsub > 1 ? h->dist : nullptr;
-    a.boxes = h->boxes; a.grid = &h->grid; a.cell_start = h->cell_start; a.cell_elems = h->cell_elems;
+    a.boxes = h->boxes; a.boxes32 = h->boxes32; a.grid = &h->grid;
+    a.cell_start = h->cell_start; a.cell_elems = h->cell_elems;
     a.cnt = w->cnt; a.off = w->off; a.scan_tmp = w->scan_tmp; a.ecount = w->ecount; a.estart = w->estart;
     a.pair_elem = w->pair_elem; a.pair_pt = w->pair_pt; a.order = w->order; a.pres = w->pres; a.prst = w->prst;
     a.cap = w->max_pairs;
     a.persistent_blocks = w->persistent_blocks;
     a.code = code; a.osub = sub; a.oelem = elem; a.rst = rst; a.dist2 = dist2;
+    a.eval = ev;
     FindParams fp;
     fp.tol_accept = h->opts.tol_accept;
     fp.tol_border = h->opts.tol_border;
@@ -635,6 +699,80 @@ fp_status fp_find_ws(fp_handle* h, fp_workspace* w, int64_t P, const double* pts
     if (err == cudaSuccess) err = find_solve(a, w->max_pairs, h->tab, fp, block, s);
     if (err != cudaSuccess) return cuda_fail(h, err, "fp_find_ws");
     w->last_P = P;
+    return FP_OK;
+}
+
+fp_status fp_find_ws(fp_handle* h, fp_workspace* w, int64_t P, const double* pts, const int32_t* qsess,
+                     int32_t* code, int32_t* sub, int32_t* elem, double* rst, double* dist2, void* stream)
+{
+    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    h->err.clear();
+    EvalSpec ev{0, nullptr, nullptr, nullptr};
+    return find_ws_impl(h, w, P, pts, qsess, code, sub, elem, rst, dist2, ev, stream);
+}
+
+fp_status fp_find_eval_ws(fp_handle* h, fp_workspace* w, int64_t P, const double* pts, const int32_t* qsess, int F,
+                          const double* fields, const fp_fields* posted, int32_t* code, int32_t* sub, int32_t* elem,
+                          double* rst, double* dist2, double* out, void* stream)
+{
+    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    h->err.clear();
+    EvalSpec ev;
+    fp_status st = eval_spec(h, F, fields, posted, out, &ev);
+    if (st != FP_OK) return st;
+    return find_ws_impl(h, w, P, pts, qsess, code, sub, elem, rst, dist2, ev, stream);
+}
+
+fp_status fp_fields_create(const fp_handle* h, int F, const double* fields, fp_fields** out, void* stream)
+{
+    if (!out) return FP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (F < 1 || !fields) return FP_ERR_INVALID_ARG;
+    const int64_t n = (int64_t)F * h->E * h->n * h->n * h->n;
+    fp_fields* f = new fp_fields();
+    f->owner = h;
+    f->F = F;
+    cudaError_t e = dalloc(&f->data, n);
+    if (e == cudaSuccess) e = launch_split_df(n, fields, f->data, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        dfree(f->data);
+        delete f;
+        return e == cudaErrorMemoryAllocation ? FP_ERR_OOM : FP_ERR_CUDA;
+    }
+    *out = f;
+    return FP_OK;
+}
+
+void fp_fields_free(fp_fields* f)
+{
+    if (!f) return;
+    cudaDeviceSynchronize();
+    dfree(f->data);
+    delete f;
+}
+
+fp_status fp_eval_df(fp_handle* h, const fp_fields* f, int64_t P, const int32_t* code, const int32_t* elem,
+                     const double* rst, double* out, void* stream)
+{
+    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    h->err.clear();
+    if (!f || f->owner != h) return fail(h, FP_ERR_INVALID_ARG, "fp_eval_df: fields posted for another handle");
+    if (P < 0) return fail(h, FP_ERR_INVALID_ARG, "fp_eval_df: P < 0");
+    if (P == 0) return FP_OK;
+    if (!code || !elem || !rst || !out) return fail(h, FP_ERR_INVALID_ARG, "fp_eval_df: null pointer");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->prof) {
+        e0 = ev_get(h);
+        e1 = ev_get(h);
+        cudaEventRecord(e0, (cudaStream_t)stream);
+    }
+    cudaError_t err = launch_eval_df(h->n, h->E, P, code, elem, rst, f->F, f->data, out, h->tab, (cudaStream_t)stream);
+    if (h->prof) {
+        cudaEventRecord(e1, (cudaStream_t)stream);
+        h->ev_pend[PROF_EVAL].push_back({e0, e1});
+    }
+    if (err != cudaSuccess) return cuda_fail(h, err, "fp_eval_df");
     return FP_OK;
 }
 

@@ -10,6 +10,7 @@ namespace fpg {
 void count_launch(int k = 1);
 
 struct ElemBox;
+struct ElemBox32;
 struct HashGrid;
 struct BasisTab;
 struct FindParams;
@@ -19,9 +20,11 @@ cudaError_t launch_hull(int n, int64_t E, const double* coords, const double* bi
                         double pad_conv, ElemBox* boxes, double* nodebox, cudaStream_t s);
 cudaError_t launch_reduce_boxes(int64_t E, const ElemBox* boxes, const double* nodebox, double* out,
                                 int nblocks, cudaStream_t s);
-cudaError_t launch_hash_count(int64_t E, const ElemBox* boxes, const HashGrid& g, int32_t* cnt, cudaStream_t s);
-cudaError_t launch_hash_fill(int64_t E, const ElemBox* boxes, const HashGrid& g, int32_t* cur, int32_t* elems,
-                             cudaStream_t s);
+cudaError_t launch_hash_count(int64_t E, const ElemBox* boxes, const HashGrid& g, double hpad, int32_t* cnt,
+                              cudaStream_t s);
+cudaError_t launch_hash_fill(int64_t E, const ElemBox* boxes, const HashGrid& g, double hpad, int32_t* cur,
+                             int32_t* elems, cudaStream_t s);
+cudaError_t launch_box32(int64_t E, const ElemBox* boxes, ElemBox32* out, cudaStream_t s);
 cudaError_t launch_hash_sort(int64_t ncell, const int32_t* start, int32_t* elems, cudaStream_t s);
 cudaError_t launch_face_corners(int n, int64_t E, const double* coords, double* fc, cudaStream_t s);
 cudaError_t launch_face_boundary(int64_t E, const double* fc, const int32_t* sub, const HashGrid& g,
@@ -39,6 +42,15 @@ int64_t scan_tmp_elems(int64_t n);
 cudaError_t scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, cudaStream_t s);
 
 // find (fp_find.cu)
+// Optional fused evaluation after classification, in the element-sorted pair
+// order: F fields, FP64 ([F][E][n3]) or double-float pairs; out [F][P].
+struct EvalSpec {
+    int F;
+    const double* f64;
+    const float2* fdf;
+    double* out;
+};
+
 struct FindArgs {
     int n;
     int64_t E;
@@ -50,6 +62,7 @@ struct FindArgs {
     const int32_t* sub;
     const double* dist;
     const ElemBox* boxes;
+    const ElemBox32* boxes32;     // non-null: screen with FP32 boxes and FP32 hashing
     const HashGrid* grid;         // host copy
     const int32_t* cell_start;
     const int32_t* cell_elems;
@@ -69,8 +82,9 @@ struct FindArgs {
     int64_t pts_stride;           // screen only: row stride of pts (0 = P)
     int32_t pt_base;              // screen only: offset added to emitted point indices
     int32_t elem_base;            // screen only: offset added to emitted element indices
-    // optional timing events (null = off): [0,1] sort, [2,3] newton, [4,5] rank
-    cudaEvent_t ev[6];
+    // optional timing events (null = off): [0,1] sort, [2,3] newton, [4,5] rank, [6,7] fused eval
+    cudaEvent_t ev[8];
+    EvalSpec eval;                // eval.F == 0: find only
     // outputs
     int32_t* code;
     int32_t* osub;
@@ -87,6 +101,12 @@ cudaError_t find_solve_unsorted(const FindArgs& a, int64_t npairs, const BasisTa
                                 int block, cudaStream_t s);
 
 // eval (fp_eval.cu)
+cudaError_t launch_eval_pairs(int n, int64_t E, int64_t P, const int32_t* dcount, int64_t cap, const int32_t* order,
+                              const int32_t* pair_elem, const int32_t* pair_pt, const double* prst,
+                              const EvalSpec& ev, const BasisTab& tab, unsigned grid, cudaStream_t s);
+cudaError_t launch_split_df(int64_t n, const double* src, float2* dst, cudaStream_t s);
+cudaError_t launch_eval_df(int n, int64_t E, int64_t P, const int32_t* code, const int32_t* elem, const double* rst,
+                           int F, const float2* fields, double* out, const BasisTab& tab, cudaStream_t s);
 cudaError_t launch_eval(int n, int64_t E, int64_t P, const int32_t* code, const int32_t* elem, const double* rst,
                         int F, const double* fields, double* out, const BasisTab& tab, cudaStream_t s);
 

@@ -243,8 +243,11 @@ __device__ __forceinline__ int cell_coord(double x, double org, double inv, int 
     return min(max(i, 0), dim - 1);
 }
 
+// Elements are listed in every cell their padded axis box overlaps, widened
+// by `hpad` so that a query whose cell is computed in FP32 (off by at most a
+// few ulps of the coordinates) still lands in a cell that lists it.
 template <bool FILL>
-__global__ void k_hash(int64_t E, const ElemBox* __restrict__ boxes, HashGrid g,
+__global__ void k_hash(int64_t E, const ElemBox* __restrict__ boxes, HashGrid g, double hpad,
                        int32_t* __restrict__ cnt, int32_t* __restrict__ cur,
                        int32_t* __restrict__ elems)
 {
@@ -253,8 +256,8 @@ __global__ void k_hash(int64_t E, const ElemBox* __restrict__ boxes, HashGrid g,
     const ElemBox& b = boxes[e];
     int i0[3], i1[3];
     for (int a = 0; a < 3; ++a) {
-        i0[a] = cell_coord(b.blo[a], g.org[a], g.inv[a], g.dim[a]);
-        i1[a] = cell_coord(b.bhi[a], g.org[a], g.inv[a], g.dim[a]);
+        i0[a] = cell_coord(b.blo[a] - hpad, g.org[a], g.inv[a], g.dim[a]);
+        i1[a] = cell_coord(b.bhi[a] + hpad, g.org[a], g.inv[a], g.dim[a]);
     }
     for (int k = i0[2]; k <= i1[2]; ++k)
         for (int j = i0[1]; j <= i1[1]; ++j)
@@ -410,6 +413,45 @@ __global__ void k_count_nonfinite(int64_t n, const double* __restrict__ x, int32
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicAdd(out, 1);
 }
 
+// FP32 boxes for the mixed form's screen.  The axis box is rounded outward
+// and widened by 2^-22 max|bound| (the query coordinate is rounded to FP32
+// before the comparison).  The frame box is widened by the bound on the FP32
+// error of y = Ai (x - c) for x inside the axis box: rounding of x, c and
+// Ai, and of the subtraction and the three-term dot product.
+__global__ void k_box32(int64_t E, const ElemBox* __restrict__ boxes, ElemBox32* __restrict__ out)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    const ElemBox& b = boxes[e];
+    ElemBox32 o;
+    const double u = 5.9604644775390625e-08;           // 2^-24
+    double xmax = 0.0, ext = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        xmax = fmax(xmax, fmax(fabs(b.blo[a]), fabs(b.bhi[a])));
+        ext = fmax(ext, b.bhi[a] - b.blo[a]);
+        const double m = 4.0 * u * fmax(fabs(b.blo[a]), fabs(b.bhi[a]));
+        o.blo[a] = __double2float_rd(b.blo[a] - m);
+        o.bhi[a] = __double2float_ru(b.bhi[a] + m);
+        o.c[a] = (float)b.c[a];
+    }
+    for (int q = 0; q < 9; ++q) o.Ai[q] = (float)b.Ai[q];
+    for (int a = 0; a < 3; ++a) {
+        const double arow = fabs(b.Ai[3 * a]) + fabs(b.Ai[3 * a + 1]) + fabs(b.Ai[3 * a + 2]);
+        // |dy| <= |Ai| (|dx| + |dc| + |d(x-c)|) + |dAi| |x-c| + dot-product rounding
+        const double m = 16.0 * u * arow * (2.0 * xmax + 2.0 * ext) + 16.0 * u * fmax(fabs(b.olo[a]), fabs(b.ohi[a]));
+        o.olo[a] = __double2float_rd(b.olo[a] - m);
+        o.ohi[a] = __double2float_ru(b.ohi[a] + m);
+    }
+    out[e] = o;
+}
+
+cudaError_t launch_box32(int64_t E, const ElemBox* boxes, ElemBox32* out, cudaStream_t s)
+{
+    k_box32<<<(unsigned)((E + 255) / 256), 256, 0, s>>>(E, boxes, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
 // element-local FP32 copy of the geometry for the mixed form: float(x - c)
 __global__ void k_local32(int n3, int64_t E, const double* __restrict__ coords, const ElemBox* __restrict__ boxes,
                           float* __restrict__ c32)
@@ -443,17 +485,18 @@ cudaError_t launch_reduce_boxes(int64_t E, const ElemBox* boxes, const double* n
     return cudaGetLastError();
 }
 
-cudaError_t launch_hash_count(int64_t E, const ElemBox* boxes, const HashGrid& g, int32_t* cnt, cudaStream_t s)
+cudaError_t launch_hash_count(int64_t E, const ElemBox* boxes, const HashGrid& g, double hpad, int32_t* cnt,
+                              cudaStream_t s)
 {
-    k_hash<false><<<(unsigned)((E + 255) / 256), 256, 0, s>>>(E, boxes, g, cnt, nullptr, nullptr);
+    k_hash<false><<<(unsigned)((E + 255) / 256), 256, 0, s>>>(E, boxes, g, hpad, cnt, nullptr, nullptr);
     count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_hash_fill(int64_t E, const ElemBox* boxes, const HashGrid& g, int32_t* cur, int32_t* elems,
-                             cudaStream_t s)
+cudaError_t launch_hash_fill(int64_t E, const ElemBox* boxes, const HashGrid& g, double hpad, int32_t* cur,
+                             int32_t* elems, cudaStream_t s)
 {
-    k_hash<true><<<(unsigned)((E + 255) / 256), 256, 0, s>>>(E, boxes, g, nullptr, cur, elems);
+    k_hash<true><<<(unsigned)((E + 255) / 256), 256, 0, s>>>(E, boxes, g, hpad, nullptr, cur, elems);
     count_launch();
     return cudaGetLastError();
 }

@@ -119,7 +119,8 @@ extern "C" fp_status fp_find_static(fp_handle* h, int64_t P, const double* pts, 
     a.n = h->n; a.E = h->E; a.P = P; a.pts = pts; a.qsess = qsess;
     a.coords = h->coords; a.coords32 = h->coords32; a.sub = h->sub;
     a.dist = h->nsub > 1 ? h->dist : nullptr;
-    a.boxes = h->boxes; a.grid = &h->grid; a.cell_start = h->cell_start; a.cell_elems = h->cell_elems;
+    a.boxes = h->boxes; a.boxes32 = h->boxes32; a.grid = &h->grid;
+    a.cell_start = h->cell_start; a.cell_elems = h->cell_elems;
     a.cnt = reinterpret_cast<int32_t*>(b + kOffCnt);
     a.off = reinterpret_cast<int32_t*>(b + kOffOff);
     a.scan_tmp = reinterpret_cast<int32_t*>(b + kOffScan);

@@ -71,9 +71,10 @@ class _Slot:
 
 class Server:
     def __init__(self, handle, fields: torch.Tensor, slots: int = 4, slot_points: int = 1 << 20,
-                 budget_bytes: float = 40e9, resident_bytes: float = 0.0, device=None):
+                 budget_bytes: float = 40e9, resident_bytes: float = 0.0, device=None, posted=None):
         self.h = handle
         self.fields = fields
+        self.posted = posted                  # fg.Fields (double-float) or None for FP64 eval
         self.F = int(fields.shape[0])
         self.dev = device or fields.device
         per_slot = slot_points * (24 + 4 + 24 + 4 * 3 + 8 + 8 * self.F) + 2 * slot_points * (4 * 3 + 8 + 24) + \
@@ -143,8 +144,8 @@ class Server:
             qs_d = slot.qs_d[:n]
             qs_d.copy_(slot.qs_h[:n], non_blocking=True)
             code, osub, elem, d2 = slot.outs[0][:n], slot.outs[1][:n], slot.outs[2][:n], slot.outs[4][:n]
-            fg.fp_find_ws(self.h, slot.ws, pts_c, qs_d, out=(code, osub, elem, rst_c, d2), stream=slot.stream)
-            fg.fp_eval(self.h, code, elem, rst_c, self.fields, out=val_c, stream=slot.stream)
+            fg.fp_find_eval_ws(self.h, slot.ws, pts_c, qs_d, fields=self.fields, posted=self.posted,
+                               out=(code, osub, elem, rst_c, d2), values=val_c, stream=slot.stream)
             slot.code_h[:n].copy_(code, non_blocking=True)
             slot.elem_h[:n].copy_(elem, non_blocking=True)
             slot.rst_h.view(-1)[:3 * n].copy_(rst_c.view(-1), non_blocking=True)

@@ -22,6 +22,13 @@ def fg():
     return fg
 
 
+_MIXED = set()
+
+
+def h_mixed(fg, h):
+    return id(h) in _MIXED
+
+
 def _instances(n_inst, seed, prec, fg, with_empty=False):
     insts = synth.config3(n_inst=n_inst, seed=seed, E_range=(8, 300), P_range=(50, 4000))
     dev = torch.device("cuda:0")
@@ -29,6 +36,8 @@ def _instances(n_inst, seed, prec, fg, with_empty=False):
     for k, (mesh, q) in enumerate(insts):
         handles.append(fg.fp_setup(torch.from_numpy(mesh.coords).to(dev), mesh.N, torch.from_numpy(mesh.sub).to(dev),
                                    opts=fg.default_opts(precision=prec)))
+        if prec == fg.PREC_MIXED:
+            _MIXED.add(id(handles[-1]))
         fields.append(torch.from_numpy(q.fields).to(dev))
         p = q.pts if not (with_empty and k == 1) else np.zeros((3, 0))
         pts.append(p)
@@ -44,7 +53,10 @@ def _check_against_single(fg, insts, handles, fields, pts, outs):
             continue
         t = torch.from_numpy(np.ascontiguousarray(pts[k])).to(dev)
         r = fg.fp_find(h, t)
-        v = fg.fp_eval(h, r[0], r[2], r[3], fields[k]).cpu().numpy()
+        if h_mixed(fg, h):   # the mixed form evaluates with double-float fields
+            v = fg.fp_eval_df(h, fg.Fields(h, fields[k]), r[0], r[2], r[3]).cpu().numpy()
+        else:
+            v = fg.fp_eval(h, r[0], r[2], r[3], fields[k]).cpu().numpy()
         r = [x.cpu().numpy() for x in r]
         sl = slice(off[k], off[k + 1])
         np.testing.assert_array_equal(code[sl], r[0])

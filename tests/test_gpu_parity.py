@@ -214,3 +214,42 @@ def test_errors_are_reported():
     with pytest.raises(fg.FindptsError):
         fg.fp_setup(torch.zeros((3, 2, 8), dtype=torch.float64, device=dev), 1,
                     torch.tensor([0, 70000], dtype=torch.int32, device=dev))
+
+
+@pytest.mark.parametrize("cfg", ["config0", "config1", "config2s", "N3", "N15"])
+def test_eval_double_float_parity(cfg):
+    """fp_eval_df (double-float on the FP32 pipes) against the oracle's FP64
+    triple sums and the FP64 kernel, on located points."""
+    import paper_1811_04891_gb300 as fg
+    if cfg == "config0":
+        mesh, q = synth.config0()
+        pts, fields = q.pts, q.fields
+    elif cfg == "config1":
+        mesh, q = synth.config1()
+        pts, fields = q.pts, q.fields
+    elif cfg == "config2s":
+        mesh, q = synth.config2(ne=6, P_uniform=20000, P_face=3000)
+        pts, fields = q.pts, q.fields
+    else:
+        N = 3 if cfg == "N3" else 15
+        coords = synth.box_mesh((2, 2, 2), N, amp_frac=0.1)
+        mesh = synth.Mesh(coords=coords, N=N, sub=np.zeros(8, np.int32))
+        fields = np.stack([synth.field_u(coords), synth.sine_product_field(coords, 3)])
+        pts = synth.uniform_points(3001, 17, lo=(-0.01,) * 3, hi=(1.01,) * 3)
+    dev = torch.device("cuda:0")
+    g = gpu_find(mesh, pts, prec=1)
+    h = g["handle"]
+    f = fg.Fields(h, torch.from_numpy(fields).to(dev))
+    code = torch.from_numpy(g["code"]).to(dev)
+    elem = torch.from_numpy(g["elem"]).to(dev)
+    rst = torch.from_numpy(g["rst"]).to(dev)
+    vdf = fg.fp_eval_df(h, f, code, elem, rst).cpu().numpy()
+    v64 = fg.fp_eval(h, code, elem, rst, torch.from_numpy(fields).to(dev)).cpu().numpy()
+    ref = oracle.evaluate(mesh.N, g["code"], g["elem"], g["rst"], fields)
+    assert np.array_equal(np.isnan(vdf), np.isnan(ref))
+    scale = np.abs(fields).reshape(fields.shape[0], -1).max(axis=1)[:, None]
+    ok = ~np.isnan(ref)
+    err_df = (np.where(ok, np.abs(vdf - ref), 0.0) / scale).max()
+    err_64 = (np.where(ok, np.abs(v64 - ref), 0.0) / scale).max()
+    assert err_df <= 1e-12, err_df
+    assert err_64 <= 1e-12, err_64
