@@ -388,6 +388,7 @@ def main():
         launches = fg.fp_launch_count() - l0
         ms = ev0.elapsed_time(ev1)
         clk = clocks.stop()
+        paths = fg.fp_newton_paths(h) if form == "mixed" else None
         fg.fp_profile(h, False)
         kt = {k: fg.fp_profile_read(h, k) for k in fg.PROF_KINDS}
         ms_max = max_over_ranks(ms)
@@ -397,7 +398,8 @@ def main():
                          "setup_ms": setup_ms, "gpu_launches": launches, "clocks": clk,
                          "kernel_ms": {k: (v[0] / max(v[1], 1)) for k, v in kt.items()},
                          "codes": {"inside": counts[0], "border": counts[1], "not_found": counts[2]},
-                         "pairs_per_point": npairs / P}
+                         "pairs_per_point": npairs / P, "newton_paths_per_step": None if paths is None else
+                         {k: v // max(1, args.steps) for k, v in paths.items()}}
 
     head = "mixed" if "mixed" in results else forms[0]
     R = results[head]
@@ -461,7 +463,8 @@ def main():
                 "data": "synthetic", "config": config_dict(args, mesh, q), "form": head,
                 "forms": {k: {"value": v["value"], "ms_per_step": v["ms_per_step"], "setup_ms": v["setup_ms"],
                               "kernel_ms": v["kernel_ms"], "codes": v["codes"],
-                              "pairs_per_point": v["pairs_per_point"]} for k, v in results.items()},
+                              "pairs_per_point": v["pairs_per_point"],
+                              "newton_paths_per_step": v["newton_paths_per_step"]} for k, v in results.items()},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": R["gpu_launches"],
                 "clocks": R["clocks"], "batched": batched, "serving": served}
         print(json.dumps(line), flush=True)

@@ -289,6 +289,13 @@ const char *fp_last_error(const fp_handle *h);
 fp_status fp_profile(fp_handle *h, int enable);
 fp_status fp_profile_read(fp_handle *h, int kind, double *total_ms, int64_t *launches);
 
+/* Mixed form, while profiling is enabled: how many pairs took each Newton
+ * path since the previous read -- counts[0] rejected after the FP32 phase
+ * (converged away from the element), [1] FP32 phase not converged, [2]
+ * confirmed by the single FP64 step, [3] sent to the full FP64 Newton.
+ * Synchronises the device and resets the counters. */
+fp_status fp_newton_paths(fp_handle *h, int64_t *counts);
+
 /* Number of kernels the library has launched in this process. */
 int64_t fp_launch_count(void);
 

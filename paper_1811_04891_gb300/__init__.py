@@ -117,6 +117,8 @@ def _load():
     L.fp_launch_count.restype = i64
     L.fp_last_find_stats.argtypes = [vp, ctypes.POINTER(i64)]
     L.fp_last_find_stats.restype = ci
+    L.fp_newton_paths.argtypes = [vp, ctypes.POINTER(i64)]
+    L.fp_newton_paths.restype = ci
     _lib = L
     return L
 
@@ -472,6 +474,13 @@ def fp_last_find_stats(h: Handle) -> int:
     n = ctypes.c_int64()
     _check(lib().fp_last_find_stats(h.ptr, ctypes.byref(n)), h.ptr)
     return n.value
+
+
+def fp_newton_paths(h: Handle) -> dict:
+    """Mixed-form Newton path counts since the last read (profiling on)."""
+    c = (ctypes.c_int64 * 4)()
+    _check(lib().fp_newton_paths(h.ptr, c), h.ptr)
+    return {"rejected_fp32": c[0], "fp32_not_converged": c[1], "fp64_step_converged": c[2], "fallback": c[3]}
 
 
 def fp_launch_count() -> int:

@@ -42,6 +42,7 @@ struct Group {
     FindParams fp{};
     double* coords = nullptr;
     float* coords32 = nullptr;
+    float* coords32lo = nullptr;
     int32_t* sub = nullptr;
     ElemBox* boxes = nullptr;
     double* dist = nullptr;
@@ -72,7 +73,7 @@ void release(T*& p)
 
 void release_group(Group& g)
 {
-    release(g.coords); release(g.coords32); release(g.sub); release(g.boxes); release(g.dist); release(g.fields);
+    release(g.coords); release(g.coords32); release(g.coords32lo); release(g.sub); release(g.boxes); release(g.dist); release(g.fields);
     release(g.fields_df);
     release(g.pts); release(g.code); release(g.osub); release(g.oelem); release(g.rst); release(g.dist2);
     release(g.out); release(g.cnt); release(g.off); release(g.scan_tmp); release(g.pair_elem); release(g.pair_pt);
@@ -201,6 +202,7 @@ extern "C" fp_status fp_batch_create(fp_batch** out, int ninst, fp_handle* const
         g.fp.mixed = o.precision == FP_PREC_MIXED;
         if (e == cudaSuccess) e = alloc(&g.coords, 3 * g.E * n3);
         if (e == cudaSuccess && g.fp.mixed) e = alloc(&g.coords32, 3 * g.E * n3);
+        if (e == cudaSuccess && g.fp.mixed) e = alloc(&g.coords32lo, 3 * g.E * n3);
         if (e == cudaSuccess) e = alloc(&g.sub, g.E);
         if (e == cudaSuccess) e = alloc(&g.boxes, g.E);
         if (e == cudaSuccess && multi) e = alloc(&g.dist, g.E * n3);
@@ -213,6 +215,9 @@ extern "C" fp_status fp_batch_create(fp_batch** out, int ninst, fp_handle* const
                                cudaMemcpyDeviceToDevice);
                 if (e == cudaSuccess && g.fp.mixed)
                     e = cudaMemcpy(g.coords32 + (a * g.E + eo) * n3, h->coords32 + a * Ei * n3,
+                                   sizeof(float) * Ei * n3, cudaMemcpyDeviceToDevice);
+                if (e == cudaSuccess && g.fp.mixed)
+                    e = cudaMemcpy(g.coords32lo + (a * g.E + eo) * n3, h->coords32lo + a * Ei * n3,
                                    sizeof(float) * Ei * n3, cudaMemcpyDeviceToDevice);
             }
             if (e == cudaSuccess) e = cudaMemcpy(g.sub + eo, h->sub, sizeof(int32_t) * Ei, cudaMemcpyDeviceToDevice);
@@ -315,7 +320,7 @@ static cudaError_t batch_run(fp_batch* b, const double* pts, int32_t* code, int3
         FindArgs c;
         memset(&c, 0, sizeof(c));
         c.n = g.n; c.E = g.E; c.P = g.P; c.pts = g.pts;
-        c.coords = g.coords; c.coords32 = g.coords32; c.sub = g.sub; c.dist = g.dist; c.boxes = g.boxes;
+        c.coords = g.coords; c.coords32 = g.coords32; c.coords32lo = g.coords32lo; c.sub = g.sub; c.dist = g.dist; c.boxes = g.boxes;
         c.cnt = g.cnt; c.off = g.off; c.scan_tmp = g.scan_tmp; c.ecount = g.ecount; c.estart = g.estart;
         c.pair_elem = g.pair_elem; c.pair_pt = g.pair_pt; c.order = g.order; c.pres = g.pres; c.prst = g.prst;
         c.cap = g.cap;

@@ -175,7 +175,7 @@ __device__ __forceinline__ void map_jac(const T* __restrict__ X0, const T* __res
 #pragma unroll 1
     for (int k = 0; k < n; ++k) {
         T c[3] = {0, 0, 0}, cs[3] = {0, 0, 0}, cr[3] = {0, 0, 0};
-#pragma unroll
+#pragma unroll 1
         for (int j = 0; j < n; ++j) {
             const int off = n * (j + n * k);
 #pragma unroll
@@ -221,7 +221,7 @@ __device__ __forceinline__ T contract(const T* __restrict__ F, const T (&hr)[n],
 #pragma unroll 1
     for (int k = 0; k < n; ++k) {
         T c = 0;
-#pragma unroll
+#pragma unroll 1
         for (int j = 0; j < n; ++j) {
             T v[n];
             load_row<n>(F + n * (j + n * k), v);

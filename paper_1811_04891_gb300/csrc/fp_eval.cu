@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(128) k_eval_df(Eval2Args A, BasisTab tab)
 #pragma unroll 1
         for (int k = 0; k < n; ++k) {
             df ck = {0.0f, 0.0f};
-#pragma unroll
+#pragma unroll 1
             for (int j = 0; j < n; ++j) {
                 const float4* row = reinterpret_cast<const float4*>(Fe + n * (j + n * k));
                 df u = {0.0f, 0.0f};
@@ -257,7 +257,7 @@ __device__ __forceinline__ void eval_point_df(const float2* __restrict__ Fdf, in
 #pragma unroll 1
         for (int k = 0; k < n; ++k) {
             df ck = {0.0f, 0.0f};
-#pragma unroll
+#pragma unroll 1
             for (int j = 0; j < n; ++j) {
                 df u = {0.0f, 0.0f};
                 if constexpr (n % 2 == 0) {

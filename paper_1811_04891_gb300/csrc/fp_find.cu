@@ -401,10 +401,12 @@ __device__ T newton(const ElemPtr<T>& el, const BasisTab& tab, const T (&xs)[3],
             else if (ratio < T(0.25)) rho = T(0.25) * sn;
         } else {
             rho = T(0.25) * sn;
-            if (rho < Lim<T>::rho_min) break;
+            // a radius collapsed below the rounding level: converged as far as
+            // this precision resolves (the FP32 phase only supplies a start)
+            if (rho < Lim<T>::rho_min) return sqrt(T(2) * phi);
         }
     }
-    converged = false;                                     // iteration cap or collapsed radius
+    converged = false;                                     // iteration cap
     return sqrt(T(2) * phi);
 }
 
@@ -442,12 +444,15 @@ struct NewtonArgs {
     const double* pts;
     const double* coords;
     const float* coords32;
+    const float* coords32lo;  // mixed form: low parts of the element-local coordinates
     const ElemBox* boxes;
     double* pres;
     double* prst;
     int64_t cap;
     double reject32;      // mixed: reject after FP32 when residual > reject32 * h_e
     int max_newton;
+    unsigned long long* stats;  // optional path counters (profiling): [0] rejected after FP32,
+                                // [1] FP32 not converged, [2] FP64 step converged, [3] sent to the fallback
 };
 
 template <int n, bool MIXED>
@@ -494,6 +499,292 @@ __device__ __forceinline__ void solve_pair(const NewtonArgs& A, const BasisTab& 
     A.prst[q] = r[0];
     A.prst[A.cap + q] = r[1];
     A.prst[2 * A.cap + q] = r[2];
+}
+
+// ---- compensated FP32 residual for the refinement steps of the mixed form ----
+// x_local(r) - x*_local with node offsets X - c held as float pairs (hi, lo),
+// basis values computed in FP64 and split, products formed exactly in their
+// leading part and summed with error-free two-sums (about 48 significant
+// bits in element-local units).  Runs on the FP32 pipes.
+struct df2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void df2_acc(df2& acc, float ah, float al, float bh, float bl)
+{
+    const float p = ah * bh;
+    const float pe = fmaf(ah, bh, -p);
+    const float t = fmaf(ah, bl, fmaf(al, bh, pe));
+    const float s = acc.hi + p;
+    const float bb = s - acc.hi;
+    const float err = (acc.hi - (s - bb)) + (p - bb);
+    acc.hi = s;
+    acc.lo += err + t;
+}
+
+__device__ __forceinline__ void df2_norm(df2& a)
+{
+    const float t = a.hi + a.lo;
+    a.lo = a.lo - (t - a.hi);
+    a.hi = t;
+}
+
+template <int n>
+__device__ __forceinline__ void resid_df(const ElemPtr<float>& hi, const ElemPtr<float>& lo, const BasisTab& tab,
+                                         const double (&r)[3], const double (&xl)[3], float (&f)[3])
+{
+    double hr[n], hs[n], ht[n];
+    lagrange_h<n, double>(tab.xi, tab.ci, r[0], hr);
+    lagrange_h<n, double>(tab.xi, tab.ci, r[1], hs);
+    lagrange_h<n, double>(tab.xi, tab.ci, r[2], ht);
+    float rh[n], rl[n], sh[n], sl[n], th[n], tl[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        rh[i] = (float)hr[i]; rl[i] = (float)(hr[i] - (double)rh[i]);
+        sh[i] = (float)hs[i]; sl[i] = (float)(hs[i] - (double)sh[i]);
+        th[i] = (float)ht[i]; tl[i] = (float)(ht[i] - (double)th[i]);
+    }
+    df2 acc[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+#pragma unroll 1
+    for (int k = 0; k < n; ++k) {
+        df2 ck[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+#pragma unroll 1
+        for (int j = 0; j < n; ++j) {
+            const int off = n * (j + n * k);
+            df2 u0[3], u1[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {             // three coordinates x two partial sums: six chains
+                const float* Xh = (a == 0 ? hi.X0 : (a == 1 ? hi.X1 : hi.X2)) + off;
+                const float* Xl = (a == 0 ? lo.X0 : (a == 1 ? lo.X1 : lo.X2)) + off;
+                float vh[n], vl[n];
+                load_row<n>(Xh, vh);
+                load_row<n>(Xl, vl);
+                u0[a] = {0.0f, 0.0f};
+                u1[a] = {0.0f, 0.0f};
+#pragma unroll
+                for (int i = 0; i < n; i += 2) {
+                    df2_acc(u0[a], vh[i], vl[i], rh[i], rl[i]);
+                    if (i + 1 < n) df2_acc(u1[a], vh[i + 1], vl[i + 1], rh[i + 1], rl[i + 1]);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                df2 u = u0[a];
+                df2_acc(u, u1[a].hi, u1[a].lo, 1.0f, 0.0f);
+                df2_norm(u);
+                df2_acc(ck[a], u.hi, u.lo, sh[j], sl[j]);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            df2_norm(ck[a]);
+            df2_acc(acc[a], ck[a].hi, ck[a].lo, th[k], tl[k]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float xh = (float)xl[a];
+        const float xlo = (float)(xl[a] - (double)xh);
+        f[a] = (acc[a].hi - xh) + (acc[a].lo - xlo);
+    }
+}
+
+// ---- mixed form in three passes, so that the FP64 pipe sees uniform work ----
+// pass 1 (FP32): seed + FP32 Newton on element-local coordinates.  Writes the
+// FP32 solution to prst and its residual to pres, or -1 when the FP32 phase
+// did not converge (the pair then goes to the full FP64 Newton of pass 3).
+template <int n>
+__global__ void __launch_bounds__(256) k_newton32(NewtonArgs A, BasisTab tab)
+{
+    constexpr int n3 = n * n * n;
+    const int64_t npairs = live_pairs(A.dcount, A.cap);
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < npairs; s += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t q = A.order[s];
+        const int e = A.pair_elem[q];
+        const int64_t p = A.pair_pt[q];
+        const double* c = A.boxes[e].c;
+        const float xl[3] = {(float)(A.pts[p] - c[0]), (float)(A.pts[A.P + p] - c[1]),
+                             (float)(A.pts[2 * A.P + p] - c[2])};
+        const ElemPtr<float> el32 = {A.coords32 + (int64_t)e * n3, A.coords32 + (A.E + e) * n3,
+                                     A.coords32 + (2 * A.E + e) * n3};
+        float r32[3], J32[9];
+        seed_nearest<n, float>(el32, tab, xl, r32);
+        bool conv32;
+        const float res32 = newton<n, float, false>(el32, tab, xl, r32, J32, A.max_newton, conv32);
+        double r[3] = {r32[0], r32[1], r32[2]};
+        // refinement for interior solutions near the element: compensated FP32
+        // residuals and FP32 Jacobian steps, r carried in FP64
+        if (conv32 && (double)res32 <= A.reject32 * A.boxes[e].he && fabsf(r32[0]) < 1.0f &&
+            fabsf(r32[1]) < 1.0f && fabsf(r32[2]) < 1.0f) {
+            const ElemPtr<float> lo32 = {A.coords32lo + (int64_t)e * n3, A.coords32lo + (A.E + e) * n3,
+                                         A.coords32lo + (2 * A.E + e) * n3};
+            const double xd[3] = {A.pts[p] - c[0], A.pts[A.P + p] - c[1], A.pts[2 * A.P + p] - c[2]};
+            for (int it = 0; it < 2; ++it) {
+                float f[3], d[3];
+                resid_df<n>(el32, lo32, tab, r, xd, f);
+                if (!newton_solve3<float>(J32, f, d)) break;
+                double rn[3];
+                bool inside = true;
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    rn[b] = r[b] + (double)d[b];
+                    inside = inside && fabs(rn[b]) < 1.0;
+                }
+                if (!inside) break;                          // the FP64 passes handle the bounds
+                r[0] = rn[0]; r[1] = rn[1]; r[2] = rn[2];
+                if (fmaxf(fabsf(d[0]), fmaxf(fabsf(d[1]), fabsf(d[2]))) <= 1e-14f) break;
+            }
+        }
+        A.prst[q] = r[0];
+        A.prst[A.cap + q] = r[1];
+        A.prst[2 * A.cap + q] = r[2];
+        A.pres[q] = conv32 ? (double)res32 : -1.0;
+    }
+}
+
+// pass 2 (FP64): every pair whose FP32 phase converged near the element takes
+// one FP64 Newton step -- FP64 residual and FP64 3x3 solve (active set) with
+// the FP32 Jacobian at the refined solution.  A step below 1e-13 confirms
+// convergence: r is kept with its FP64 residual.  Otherwise the step is
+// taken and the pair is marked for pass 3.  Pairs that converged well away
+// from the element keep their FP32 residual (they cannot be INSIDE or
+// BORDER).  Every pair does the same FP64 work, so warps stay full.
+template <int n>
+__global__ void __launch_bounds__(256) k_newton64_chord(NewtonArgs A, BasisTab tab)
+{
+    constexpr int n3 = n * n * n;
+    const int64_t npairs = live_pairs(A.dcount, A.cap);
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < npairs; s += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t q = A.order[s];
+        const double v = A.pres[q];
+        if (v < 0.0) continue;                                  // pass 3
+        const int e = A.pair_elem[q];
+        if (v > A.reject32 * A.boxes[e].he) continue;           // converged away from the element
+        const int64_t p = A.pair_pt[q];
+        const double xs[3] = {A.pts[p], A.pts[A.P + p], A.pts[2 * A.P + p]};
+        const double* c = A.boxes[e].c;
+        const float xl[3] = {(float)(xs[0] - c[0]), (float)(xs[1] - c[1]), (float)(xs[2] - c[2])};
+        const ElemPtr<float> el32 = {A.coords32 + (int64_t)e * n3, A.coords32 + (A.E + e) * n3,
+                                     A.coords32 + (2 * A.E + e) * n3};
+        const ElemPtr<double> el64 = {A.coords + (int64_t)e * n3, A.coords + (A.E + e) * n3,
+                                      A.coords + (2 * A.E + e) * n3};
+        double r[3] = {A.prst[q], A.prst[A.cap + q], A.prst[2 * A.cap + q]};
+        float r32[3] = {(float)r[0], (float)r[1], (float)r[2]}, f32[3], J32[9];
+        eval_fJ<n, float>(el32, tab, r32, xl, f32, J32);       // FP32 Jacobian at the refined solution
+        double J[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) J[k] = (double)J32[k];
+        double res;
+        const bool ok = chord64<n>(el64, tab, xs, r, J, res, 1);
+        A.prst[q] = r[0];
+        A.prst[A.cap + q] = r[1];
+        A.prst[2 * A.cap + q] = r[2];
+        A.pres[q] = ok ? res : -1.0;
+    }
+}
+
+// passes 1 and 2 in one kernel: the FP32 work of some warps overlaps the
+// FP64 work of others.
+template <int n>
+__global__ void __launch_bounds__(256) k_newton_mixed(NewtonArgs A, BasisTab tab)
+{
+    constexpr int n3 = n * n * n;
+    const int64_t npairs = live_pairs(A.dcount, A.cap);
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < npairs; s += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t q = A.order[s];
+        const int e = A.pair_elem[q];
+        const int64_t p = A.pair_pt[q];
+        const double xs[3] = {A.pts[p], A.pts[A.P + p], A.pts[2 * A.P + p]};
+        const double* c = A.boxes[e].c;
+        const double xd[3] = {xs[0] - c[0], xs[1] - c[1], xs[2] - c[2]};
+        const float xl[3] = {(float)xd[0], (float)xd[1], (float)xd[2]};
+        const ElemPtr<float> el32 = {A.coords32 + (int64_t)e * n3, A.coords32 + (A.E + e) * n3,
+                                     A.coords32 + (2 * A.E + e) * n3};
+        float r32[3], J32[9];
+        seed_nearest<n, float>(el32, tab, xl, r32);
+        bool conv32;
+        const float res32 = newton<n, float, false>(el32, tab, xl, r32, J32, A.max_newton, conv32);
+        double r[3] = {r32[0], r32[1], r32[2]};
+        double res = conv32 ? (double)res32 : -1.0;
+        if (A.stats) {
+            if (!conv32) atomicAdd(A.stats + 1, 1ULL);
+            else if ((double)res32 > A.reject32 * A.boxes[e].he) atomicAdd(A.stats + 0, 1ULL);
+        }
+        if (conv32 && (double)res32 <= A.reject32 * A.boxes[e].he) {
+            // refinement: compensated FP32 residuals, FP32 Jacobian, active-set
+            // step (constrained solutions on a face, edge or vertex too)
+            {
+                const ElemPtr<float> lo32 = {A.coords32lo + (int64_t)e * n3, A.coords32lo + (A.E + e) * n3,
+                                             A.coords32lo + (2 * A.E + e) * n3};
+                for (int it = 0; it < 2; ++it) {
+                    float f[3], d[3];
+                    resid_df<n>(el32, lo32, tab, r, xd, f);
+                    const float rf[3] = {(float)r[0], (float)r[1], (float)r[2]};
+                    if (gn_step<float>(J32, f, rf, d) == 0) break;
+                    const double dd[3] = {(double)d[0], (double)d[1], (double)d[2]};
+                    double rn[3];
+                    box_step<double>(r, dd, rn);
+                    const double sn = fmax(fabs(rn[0] - r[0]), fmax(fabs(rn[1] - r[1]), fabs(rn[2] - r[2])));
+                    r[0] = rn[0]; r[1] = rn[1]; r[2] = rn[2];
+                    if (sn <= 1e-14) break;
+                }
+            }
+            // the final Newton step in FP64: FP64 residual, FP64 3x3 solve
+            const ElemPtr<double> el64 = {A.coords + (int64_t)e * n3, A.coords + (A.E + e) * n3,
+                                          A.coords + (2 * A.E + e) * n3};
+            double J[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) J[k] = (double)J32[k];
+            double r64res;
+            res = chord64<n>(el64, tab, xs, r, J, r64res, 1) ? r64res : -1.0;
+            if (A.stats) atomicAdd(A.stats + (res < 0.0 ? 3 : 2), 1ULL);
+        }
+        A.prst[q] = r[0];
+        A.prst[A.cap + q] = r[1];
+        A.prst[2 * A.cap + q] = r[2];
+        A.pres[q] = res;
+    }
+}
+
+// pass 3 (FP64): full trust-region Newton for the pairs marked -1, from the
+// point the earlier passes reached.  These pairs are few and scattered, so
+// each block first gathers the marked pairs of a chunk of slots into shared
+// memory and then solves them with consecutive threads (dense warps).
+template <int n>
+__global__ void __launch_bounds__(256) k_newton64_full(NewtonArgs A, BasisTab tab)
+{
+    constexpr int n3 = n * n * n;
+    constexpr int CH = 8192;                                    // slots gathered per round
+    __shared__ int32_t list[CH];
+    __shared__ int count;
+    const int64_t npairs = live_pairs(A.dcount, A.cap);
+    for (int64_t base = (int64_t)blockIdx.x * CH; base < npairs; base += (int64_t)gridDim.x * CH) {
+        if (threadIdx.x == 0) count = 0;
+        __syncthreads();
+        const int64_t end = base + CH < npairs ? base + CH : npairs;
+        for (int64_t s = base + threadIdx.x; s < end; s += blockDim.x) {
+            const int32_t q = A.order[s];
+            if (A.pres[q] < 0.0) list[atomicAdd(&count, 1)] = q;
+        }
+        __syncthreads();
+        const int m = count;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) {
+            const int32_t q = list[t];
+            const int e = A.pair_elem[q];
+            const int64_t p = A.pair_pt[q];
+            const double xs[3] = {A.pts[p], A.pts[A.P + p], A.pts[2 * A.P + p]};
+            const ElemPtr<double> el64 = {A.coords + (int64_t)e * n3, A.coords + (A.E + e) * n3,
+                                          A.coords + (2 * A.E + e) * n3};
+            double r[3] = {A.prst[q], A.prst[A.cap + q], A.prst[2 * A.cap + q]}, J[9];
+            bool conv;
+            const double res = newton<n, double, true>(el64, tab, xs, r, J, A.max_newton, conv);
+            A.prst[q] = r[0];
+            A.prst[A.cap + q] = r[1];
+            A.prst[2 * A.cap + q] = r[2];
+            A.pres[q] = res;
+        }
+        __syncthreads();
+    }
 }
 
 template <int n, bool MIXED>
@@ -736,19 +1027,24 @@ static cudaError_t solve_n(const FindArgs& a, int64_t npairs, const BasisTab& ta
         na.pts = a.pts;
         na.coords = a.coords;
         na.coords32 = a.coords32;
+        na.coords32lo = a.coords32lo;
         na.boxes = a.boxes;
         na.pres = a.pres;
         na.prst = a.prst;
         na.cap = a.cap;
         na.reject32 = 1e-4;
         na.max_newton = fp.max_newton;
+        na.stats = a.stats;
         const unsigned grid = grid_for(npairs, block, a.persistent_blocks);
         if (a.ev[2]) cudaEventRecord(a.ev[2], s);
-        if (fp.mixed)
-            k_newton<n, true><<<grid, block, 0, s>>>(na, tab);
-        else
+        if (fp.mixed) {
+            k_newton_mixed<n><<<grid, block, 0, s>>>(na, tab);
+            k_newton64_full<n><<<grid, block, 0, s>>>(na, tab);
+            count_launch(2);
+        } else {
             k_newton<n, false><<<grid, block, 0, s>>>(na, tab);
-        count_launch();
+            count_launch();
+        }
         cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return err;
         if (a.ev[3]) cudaEventRecord(a.ev[3], s);

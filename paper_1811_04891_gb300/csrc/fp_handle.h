@@ -23,6 +23,7 @@ struct fp_handle {
     // resident device state
     double* coords = nullptr;      // [3][E][n3]
     float* coords32 = nullptr;     // [3][E][n3] element-local FP32 (mixed form)
+    float* coords32lo = nullptr;   // [3][E][n3] low parts: (x - c) - coords32 (mixed form)
     int32_t* sub = nullptr;        // [E]
     double* dist = nullptr;        // [E][n3] or null
     fpg::ElemBox* boxes = nullptr;      // [E]
@@ -47,6 +48,7 @@ struct fp_handle {
     std::string err;
     // optional per-kernel timing with CUDA events on the launching stream
     bool prof = false;
+    unsigned long long* stats = nullptr;   // device [4] Newton path counters while profiling
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pend[PROF_KINDS];
 };

@@ -179,7 +179,8 @@ void release(fp_handle* h)
     }
     for (auto e : h->ev_free) cudaEventDestroy(e);
     h->ev_free.clear();
-    dfree(h->coords); dfree(h->coords32); dfree(h->sub); dfree(h->dist); dfree(h->boxes); dfree(h->boxes32);
+    dfree(h->stats);
+    dfree(h->coords); dfree(h->coords32); dfree(h->coords32lo); dfree(h->sub); dfree(h->dist); dfree(h->boxes); dfree(h->boxes32);
     dfree(h->cell_start); dfree(h->cell_elems); dfree(h->ecount); dfree(h->estart); dfree(h->escan_tmp);
     dfree(h->cnt); dfree(h->off); dfree(h->scan_tmp); dfree(h->pair_elem); dfree(h->pair_pt);
     dfree(h->order); dfree(h->pres); dfree(h->prst);
@@ -460,6 +461,8 @@ fp_status fp_setup(fp_handle** hout, const double* coords, int64_t E, int N, con
     if (o.precision == FP_PREC_MIXED) {
         CK(dalloc(&h->coords32, ncoord), "alloc coords32");
         CK(launch_local32(n, E, h->coords, h->boxes, h->coords32, s), "local32");
+        CK(dalloc(&h->coords32lo, ncoord), "alloc coords32lo");
+        CK(launch_local32lo(n, E, h->coords, h->boxes, h->coords32, h->coords32lo, s), "local32lo");
         CK(dalloc(&h->boxes32, E), "alloc boxes32");
         CK(launch_box32(E, h->boxes, h->boxes32, s), "box32");
     }
@@ -494,13 +497,14 @@ static fp_status find_impl(fp_handle* h, int64_t P, const double* pts, const int
     FindArgs a;
     memset(&a, 0, sizeof(a));
     a.n = h->n; a.E = h->E; a.P = P; a.pts = pts; a.qsess = qsess;
-    a.coords = h->coords; a.coords32 = h->coords32; a.sub = h->sub;
+    a.coords = h->coords; a.coords32 = h->coords32; a.coords32lo = h->coords32lo; a.sub = h->sub;
     a.dist = h->nsub > 1 ? h->dist : nullptr;
     a.boxes = h->boxes; a.boxes32 = h->boxes32; a.grid = &h->grid;
     a.cell_start = h->cell_start; a.cell_elems = h->cell_elems;
     a.cnt = h->cnt; a.off = h->off; a.ecount = h->ecount; a.estart = h->estart; a.scan_tmp = h->scan_tmp;
     a.code = code; a.osub = sub; a.oelem = elem; a.rst = rst; a.dist2 = dist2;
     a.eval = ev;
+    a.stats = h->prof ? h->stats : nullptr;
     cudaEvent_t scr0 = nullptr, scr1 = nullptr;
     if (h->prof) {
         for (int q = 0; q < (ev.F > 0 ? 8 : 6); ++q) a.ev[q] = ev_get(h);
@@ -677,7 +681,7 @@ static fp_status find_ws_impl(fp_handle* h, fp_workspace* w, int64_t P, const do
     FindArgs a;
     memset(&a, 0, sizeof(a));
     a.n = h->n; a.E = h->E; a.P = P; a.pts = pts; a.qsess = qsess;
-    a.coords = h->coords; a.coords32 = h->coords32; a.sub = h->sub;
+    a.coords = h->coords; a.coords32 = h->coords32; a.coords32lo = h->coords32lo; a.sub = h->sub;
     a.dist = h->nsub > 1 ? h->dist : nullptr;
     a.boxes = h->boxes; a.boxes32 = h->boxes32; a.grid = &h->grid;
     a.cell_start = h->cell_start; a.cell_elems = h->cell_elems;
@@ -813,6 +817,11 @@ fp_status fp_profile(fp_handle* h, int enable)
 {
     if (!h || !h->coords) return FP_ERR_NOT_SETUP;
     h->prof = enable != 0;
+    if (h->prof && !h->stats) {
+        cudaError_t e = dalloc(&h->stats, 4);
+        if (e == cudaSuccess) e = cudaMemset(h->stats, 0, 4 * sizeof(unsigned long long));
+        if (e != cudaSuccess) return cuda_fail(h, e, "fp_profile");
+    }
     return FP_OK;
 }
 
@@ -844,6 +853,20 @@ fp_status fp_last_find_stats(const fp_handle* h, int64_t* npairs)
 {
     if (!h || !h->coords) return FP_ERR_NOT_SETUP;
     if (npairs) *npairs = h->last_pairs;
+    return FP_OK;
+}
+
+fp_status fp_newton_paths(fp_handle* h, int64_t* counts)
+{
+    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    unsigned long long c[4] = {0, 0, 0, 0};
+    if (h->stats) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaMemcpy(c, h->stats, sizeof(c), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemset(h->stats, 0, sizeof(c));
+        if (e != cudaSuccess) return cuda_fail(h, e, "fp_newton_paths");
+    }
+    for (int k = 0; k < 4; ++k) counts[k] = (int64_t)c[k];
     return FP_OK;
 }
 

@@ -35,6 +35,8 @@ cudaError_t launch_dist_default(int n, int64_t E, const double* coords, const in
                                 const int32_t* bs, int64_t nb, double* D, cudaStream_t s);
 cudaError_t launch_local32(int n, int64_t E, const double* coords, const ElemBox* boxes, float* c32,
                            cudaStream_t s);
+cudaError_t launch_local32lo(int n, int64_t E, const double* coords, const ElemBox* boxes, const float* c32,
+                             float* c32lo, cudaStream_t s);
 
 // scans (fp_scan.cu): out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
 // tmp must hold scan_tmp_elems(n) int32 entries.
@@ -59,6 +61,7 @@ struct FindArgs {
     const int32_t* qsess;
     const double* coords;
     const float* coords32;
+    const float* coords32lo;
     const int32_t* sub;
     const double* dist;
     const ElemBox* boxes;
@@ -85,6 +88,7 @@ struct FindArgs {
     // optional timing events (null = off): [0,1] sort, [2,3] newton, [4,5] rank, [6,7] fused eval
     cudaEvent_t ev[8];
     EvalSpec eval;                // eval.F == 0: find only
+    unsigned long long* stats;    // optional Newton path counters (4 words), null = off
     // outputs
     int32_t* code;
     int32_t* osub;

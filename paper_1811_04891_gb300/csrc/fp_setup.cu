@@ -463,6 +463,17 @@ __global__ void k_local32(int n3, int64_t E, const double* __restrict__ coords, 
     c32[q] = (float)(coords[q] - boxes[e].c[a]);
 }
 
+// low parts of the element-local coordinates: (x - c) - hi, rounded to FP32
+__global__ void k_local32lo(int n3, int64_t E, const double* __restrict__ coords, const ElemBox* __restrict__ boxes,
+                            const float* __restrict__ c32, float* __restrict__ c32lo)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= 3 * E * n3) return;
+    int64_t a = q / (E * n3);
+    int64_t e = (q / n3) % E;
+    c32lo[q] = (float)((coords[q] - boxes[e].c[a]) - (double)c32[q]);
+}
+
 // ---------------------------------------------------------------------------
 // host-side launchers
 // ---------------------------------------------------------------------------
@@ -545,6 +556,15 @@ cudaError_t launch_count_nonfinite(int64_t n, const double* x, int32_t* out, cud
     int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
     if (blocks < 1) blocks = 1;
     k_count_nonfinite<<<(unsigned)blocks, 256, 0, s>>>(n, x, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_local32lo(int n, int64_t E, const double* coords, const ElemBox* boxes, const float* c32,
+                             float* c32lo, cudaStream_t s)
+{
+    int n3 = n * n * n;
+    k_local32lo<<<(unsigned)((3 * E * n3 + 255) / 256), 256, 0, s>>>(n3, E, coords, boxes, c32, c32lo);
     count_launch();
     return cudaGetLastError();
 }

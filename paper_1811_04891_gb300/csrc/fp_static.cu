@@ -117,7 +117,7 @@ extern "C" fp_status fp_find_static(fp_handle* h, int64_t P, const double* pts, 
     FindArgs a;
     memset(&a, 0, sizeof(a));
     a.n = h->n; a.E = h->E; a.P = P; a.pts = pts; a.qsess = qsess;
-    a.coords = h->coords; a.coords32 = h->coords32; a.sub = h->sub;
+    a.coords = h->coords; a.coords32 = h->coords32; a.coords32lo = h->coords32lo; a.sub = h->sub;
     a.dist = h->nsub > 1 ? h->dist : nullptr;
     a.boxes = h->boxes; a.boxes32 = h->boxes32; a.grid = &h->grid;
     a.cell_start = h->cell_start; a.cell_elems = h->cell_elems;
