@@ -74,6 +74,10 @@ def lib():
         _lib.or_eval.argtypes = [ctypes.c_int, i64, i64, ip, ip, dp, ctypes.c_int, dp, dp]
         _lib.or_dist_default.argtypes = [ctypes.c_int, i64, dp, ip, dp]
         _lib.or_num_threads.restype = ctypes.c_int
+        i8p = ctypes.POINTER(ctypes.c_int8)
+        _lib.or_bfaces.argtypes = [ctypes.c_int, i64, dp, i8p, dp, dp, dp, i8p]
+        _lib.or_bfaces.restype = i64
+        _lib.or_flux_correct.argtypes = [i64, dp, dp, dp, i8p, dp, dp, dp]
     return _lib
 
 
@@ -166,6 +170,37 @@ def evaluate(N: int, code, elem, rst, fields):
     out = np.zeros((F, P))
     lib().or_eval(N, E, P, _i(code), _i(elem), _d(rst), F, _d(fields), _d(out))
     return out
+
+
+def bfaces(coords, N: int, kind):
+    """Boundary-face quadrature of the faces marked in kind [E][6] (1 =
+    prescribed data, 2 = interface): node positions [3][M], outward unit
+    normals [3][M], weights dA [M], node kinds [M]."""
+    coords = _f64(coords)
+    E = coords.shape[1]
+    kind = np.ascontiguousarray(kind, dtype=np.int8).reshape(-1)
+    cap = int((kind != 0).sum()) * (N + 1) ** 2
+    x = np.zeros((max(cap, 1), 3))
+    nr = np.zeros((max(cap, 1), 3))
+    dA = np.zeros(max(cap, 1))
+    nk = np.zeros(max(cap, 1), np.int8)
+    i8 = ctypes.POINTER(ctypes.c_int8)
+    M = lib().or_bfaces(N, E, _d(coords), kind.ctypes.data_as(i8), _d(x), _d(nr), _d(dA), nk.ctypes.data_as(i8))
+    return x[:M].T.copy(), nr[:M].T.copy(), dA[:M].copy(), nk[:M].copy()
+
+
+def flux_correct(u, nrm, dA, nkind):
+    """Eq. consv2 / corr on listed face nodes: u, nrm [3][M] -> (u_out [3][M], gamma, flux)."""
+    M = dA.shape[0]
+    uu = np.ascontiguousarray(np.asarray(u, dtype=np.float64).T)
+    nn = np.ascontiguousarray(np.asarray(nrm, dtype=np.float64).T)
+    out = np.zeros_like(uu)
+    g = ctypes.c_double()
+    fl = ctypes.c_double()
+    nk = np.ascontiguousarray(nkind, dtype=np.int8)
+    lib().or_flux_correct(M, _d(uu), _d(nn), _d(_f64(dA)), nk.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                          _d(out), ctypes.byref(g), ctypes.byref(fl))
+    return out.T.copy(), g.value, fl.value
 
 
 def dist_default(coords, N: int, sub):

@@ -685,3 +685,99 @@ int or_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Mass-flux correction on a subdomain boundary (Sec. 2.2, Eqs. consv1,     */
+/* corr, consv2)                                                            */
+/* ------------------------------------------------------------------------ */
+
+/* Boundary-face quadrature.  kind[6E]: 0 = not used, 1 = boundary face with
+   prescribed (Dirichlet) data, 2 = interface face (interpolated data).  The
+   marked faces are listed in (element, face) order; face f's node (a,b) is
+   numbered as in face_node().  For every listed node: position x, outward
+   unit normal nrm and quadrature weight dA = w_a w_b |t_1 x t_2| (GLL
+   weights, tangents t along the two face directions, from the derivative
+   of the Lagrange interpolant of the node positions).  Outward: the face at
+   the +1 end of a reference direction points along +(t_1 x t_2) for the
+   cyclic pair (t_1, t_2) of the other two directions, times the sign of the
+   element's Jacobian determinant at its centre.  Returns the number of
+   listed nodes (arrays must hold 6*E*n^2 entries). */
+int64_t or_bfaces(int N, int64_t E, const double *coords, const int8_t *kind, double *x, double *nrm,
+                  double *dA, int8_t *nkind)
+{
+    double xg[OR_NMAX], wg[OR_NMAX];
+    if (or_gll(N, xg, wg)) return -1;
+    int n = N + 1, n3 = n * n * n;
+    /* derivative of each Lagrange basis function at each GLL node */
+    double Dm[OR_NMAX][OR_NMAX];
+    for (int a = 0; a < n; ++a) {
+        double h[OR_NMAX], dh[OR_NMAX];
+        or_lagrange(N, xg, xg[a], h, dh);
+        for (int i = 0; i < n; ++i) Dm[a][i] = dh[i];
+    }
+    int64_t m = 0;
+    for (int64_t e = 0; e < E; ++e) {
+        const double *X[3] = { coords + e * n3, coords + (E + e) * n3, coords + (2 * E + e) * n3 };
+        /* handedness: sign of det J at the element centre */
+        or_elem el = { N, n, xg, { X[0], X[1], X[2] } };
+        double r0[3] = { 0, 0, 0 }, xc[3], Jc[9];
+        or_map_elem(&el, r0, xc, Jc);
+        double det = Jc[0] * (Jc[4] * Jc[8] - Jc[5] * Jc[7]) - Jc[1] * (Jc[3] * Jc[8] - Jc[5] * Jc[6]) +
+                     Jc[2] * (Jc[3] * Jc[7] - Jc[4] * Jc[6]);
+        double hand = det < 0 ? -1.0 : 1.0;
+        for (int f = 0; f < 6; ++f) {
+            if (!kind[6 * e + f]) continue;
+            int ax = f / 2;
+            double sgn = (f % 2 ? 1.0 : -1.0) * hand;
+            for (int b = 0; b < n; ++b)
+                for (int a = 0; a < n; ++a) {
+                    double t1[3], t2[3];
+                    for (int c = 0; c < 3; ++c) {
+                        double s1 = 0.0, s2 = 0.0;
+                        for (int q = 0; q < n; ++q) {
+                            /* t1 along the first face variable, t2 along the second */
+                            s1 += Dm[a][q] * X[c][face_node(n, f, q, b)];
+                            s2 += Dm[b][q] * X[c][face_node(n, f, a, q)];
+                        }
+                        t1[c] = s1;
+                        t2[c] = s2;
+                    }
+                    /* face variables: ax 0 -> (s,t), ax 1 -> (r,t), ax 2 -> (r,s);
+                       cyclic normal: ax 0: s x t, ax 1: t x r = -(r x t), ax 2: r x s */
+                    double nv[3] = { t1[1] * t2[2] - t1[2] * t2[1], t1[2] * t2[0] - t1[0] * t2[2],
+                                     t1[0] * t2[1] - t1[1] * t2[0] };
+                    double o = (ax == 1 ? -1.0 : 1.0) * sgn;
+                    double len = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+                    int idx = face_node(n, f, a, b);
+                    for (int c = 0; c < 3; ++c) {
+                        x[3 * m + c] = X[c][idx];
+                        nrm[3 * m + c] = o * nv[c] / len;
+                    }
+                    dA[m] = wg[a] * wg[b] * len;
+                    nkind[m] = kind[6 * e + f];
+                    ++m;
+                }
+        }
+    }
+    return m;
+}
+
+/* gamma = -(sum over all listed nodes of u.n dA) / (sum over interface nodes
+   of n.n dA) and u_out = u + gamma n on interface nodes, u elsewhere
+   (Eq. consv2, Eq. corr).  u, u_out are [M][3]. */
+void or_flux_correct(int64_t M, const double *u, const double *nrm, const double *dA, const int8_t *nkind,
+                     double *u_out, double *gamma, double *flux)
+{
+    double fl = 0.0, area = 0.0;
+    for (int64_t m = 0; m < M; ++m) {
+        double un = u[3 * m] * nrm[3 * m] + u[3 * m + 1] * nrm[3 * m + 1] + u[3 * m + 2] * nrm[3 * m + 2];
+        fl += un * dA[m];
+        if (nkind[m] == 2)
+            area += (nrm[3 * m] * nrm[3 * m] + nrm[3 * m + 1] * nrm[3 * m + 1] + nrm[3 * m + 2] * nrm[3 * m + 2]) * dA[m];
+    }
+    double g = area > 0.0 ? -fl / area : 0.0;
+    for (int64_t m = 0; m < M; ++m)
+        for (int c = 0; c < 3; ++c) u_out[3 * m + c] = u[3 * m + c] + (nkind[m] == 2 ? g * nrm[3 * m + c] : 0.0);
+    *gamma = g;
+    if (flux) *flux = fl;
+}
