@@ -73,6 +73,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-interface", action="store_true")
     ap.add_argument("--served-requests", type=int, default=200)
     ap.add_argument("--served-load", type=float, default=0.7)
     ap.add_argument("--served-scale", type=float, default=1.0,
@@ -248,6 +249,78 @@ def run_batched(args, fg, dev, barrier, max_over_ranks, world):
         del b, handles
     out["unit"] = UNIT
     out["note"] = "one CUDA-graph launch per step over all instances; Newton schedule autotuned"
+    return out
+
+
+# ---------------------------------------------------------------------------
+# interface update of the box + annulus overlap (config 1): the cylinder's
+# radial faces take velocity and pressure interpolated from the box, its end
+# walls keep prescribed data, and the interpolated velocity is flux-corrected
+# ---------------------------------------------------------------------------
+def run_interface(args, fg, dev):
+    import torch
+
+    import synth
+    mesh, q = synth.config1()
+    n_rad, n_az, n_ax = 4, 32, 8
+    kind = np.zeros((mesh.E, 6), np.int8)
+    for e in range(1024, mesh.E):
+        el = e - 1024
+        er, ez = el % n_rad, el // (n_rad * n_az)
+        kind[e, 0] = 2 if er == 0 else 0
+        kind[e, 1] = 2 if er == n_rad - 1 else 0
+        kind[e, 4] = 1 if ez == 0 else 0
+        kind[e, 5] = 1 if ez == n_ax - 1 else 0
+    out = {}
+    for form, prec in (("mixed", fg.PREC_MIXED), ("fp64", fg.PREC_FP64)):
+        h = fg.fp_setup(torch.from_numpy(mesh.coords).to(dev), mesh.N, torch.from_numpy(mesh.sub).to(dev),
+                        torch.from_numpy(mesh.dist).to(dev), opts=fg.default_opts(precision=prec))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bf = fg.BFaces(h, torch.from_numpy(kind).to(dev))
+        torch.cuda.synchronize()
+        bf_ms = 1e3 * (time.perf_counter() - t0)
+        x, nr, dA, nk = bf.nodes(dev)
+        iface = (nk == 2).nonzero().squeeze(1)
+        pts = x[:, iface].contiguous()
+        qs = torch.ones(pts.shape[1], dtype=torch.int32, device=dev)
+        fields = torch.from_numpy(q.fields).to(dev)            # u, v, w, p
+        posted = fg.Fields(h, fields) if form == "mixed" else None
+        P = pts.shape[1]
+        found = fg.fp_find_eval(h, pts, qs, fields=fields, posted=posted)
+        code, elem, rst = found[0], found[2], found[3]
+        vals = torch.empty((4, P), dtype=torch.float64, device=dev)
+        u = torch.zeros((3, bf.M), dtype=torch.float64, device=dev)
+        uo = torch.empty_like(u)
+
+        def find_step():
+            fg.fp_find_eval(h, pts, qs, fields=fields, posted=posted, out=found[:5], values=vals)
+
+        def iterate():      # one Schwarz sub-iteration: re-interpolate at the found points, correct
+            if posted is not None:
+                fg.fp_eval_df(h, posted, code, elem, rst, out=vals)
+            else:
+                fg.fp_eval(h, code, elem, rst, fields, out=vals)
+            u[:, iface] = vals[:3]
+            fg.fp_flux_correct(bf, u, uo)
+
+        res = {}
+        for name, fn, reps in (("find_eval", find_step, 20), ("iteration", iterate, 200)):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            res[name + "_ms"] = e0.elapsed_time(e1) / reps
+        out[form] = {"interface_points": int(P), "face_nodes": int(bf.M), "bfaces_setup_ms": bf_ms,
+                     **res, "iteration_points_per_s": P / (res["iteration_ms"] / 1e3)}
+        del bf, h
+    out["note"] = ("per Schwarz sub-iteration: eval of u,v,w,p at the found interface points + flux "
+                   "correction (Eq. consv2); find_eval = locate + eval once (static mesh)")
     return out
 
 
@@ -464,6 +537,9 @@ def main():
     served = None
     if rank == 0 and not args.no_served:
         served = run_served(args, fg, dev)
+    interface = None
+    if rank == 0 and not args.no_interface:
+        interface = run_interface(args, fg, dev)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -481,7 +557,7 @@ def main():
                               "pairs_per_point": v["pairs_per_point"],
                               "newton_paths_per_step": v["newton_paths_per_step"]} for k, v in results.items()},
                 "roofline": roof, "roofline_other_forms": roof_other, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": R["gpu_launches"],
-                "clocks": R["clocks"], "batched": batched, "serving": served}
+                "clocks": R["clocks"], "batched": batched, "serving": served, "interface": interface}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

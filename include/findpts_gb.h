@@ -269,6 +269,37 @@ fp_status fp_find_eval_ws(fp_handle *h, fp_workspace *ws, int64_t P, const doubl
                           const fp_fields *posted, int32_t *code, int32_t *sub, int32_t *elem,
                           double *rst, double *dist2, double *out, void *stream);
 
+/* Mass-flux correction of interpolated interface velocity (Sec. 2.2,
+ * Eqs. consv1, corr, consv2).
+ * fp_bfaces_create: kind [E][6] int8 on the device marks faces of the
+ * handle's mesh: 0 = not used, 1 = boundary face of the subdomain with
+ * prescribed (Dirichlet) data, 2 = interface face whose data is
+ * interpolated.  The marked faces are listed in (element, face) order; for
+ * each, its (N+1)^2 GLL nodes (node (a,b) of face f numbered with a fastest
+ * along the face's first reference direction: r-faces (s,t), s-faces (r,t),
+ * t-faces (r,s)) get their position, outward unit normal and area weight
+ * dA = w_a w_b |t_1 x t_2|.  Allocates; synchronises `stream`.
+ * fp_bfaces_info: number of listed faces and of face nodes M.
+ * fp_bfaces_nodes: copy positions [3][M], normals [3][M], dA [M], node kinds
+ * [M] (int8) to device buffers (any may be NULL).  The interface nodes are
+ * the query points for the interpolation of boundary data.
+ * fp_flux_correct: u [3][M] velocity at the face nodes (prescribed or
+ * interpolated); writes u_out [3][M] = u + gamma n on interface nodes and u
+ * elsewhere, with gamma = -(sum u.n dA over all nodes) / (sum n.n dA over
+ * interface nodes) (0 when there is no interface), so that the corrected flux
+ * through the listed faces vanishes.  gamma and flux (before correction) are
+ * written to device scalars if non-NULL.  Deterministic fixed-order sums;
+ * allocates nothing; enqueued on `stream`.  Edge and corner nodes appear once
+ * per face, each with its own face's normal. */
+typedef struct fp_bfaces fp_bfaces;
+fp_status fp_bfaces_create(const fp_handle *h, const int8_t *kind, fp_bfaces **out, void *stream);
+void fp_bfaces_free(fp_bfaces *b);
+fp_status fp_bfaces_info(const fp_bfaces *b, int64_t *nfaces, int64_t *nnodes);
+fp_status fp_bfaces_nodes(const fp_bfaces *b, double *x, double *normal, double *dA, int8_t *kind,
+                          void *stream);
+fp_status fp_flux_correct(const fp_bfaces *b, const double *u, double *u_out, double *gamma,
+                          double *flux, void *stream);
+
 /* Release every device resource of the handle (synchronises it first).
    NULL is a no-op. */
 void fp_free(fp_handle *h);

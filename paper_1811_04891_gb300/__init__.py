@@ -96,6 +96,16 @@ def _load():
     L.fp_find_eval.restype = ci
     L.fp_find_eval_ws.argtypes = [vp, vp, i64, vp, vp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.fp_find_eval_ws.restype = ci
+    L.fp_bfaces_create.argtypes = [vp, vp, ctypes.POINTER(vp), vp]
+    L.fp_bfaces_create.restype = ci
+    L.fp_bfaces_free.argtypes = [vp]
+    L.fp_bfaces_free.restype = None
+    L.fp_bfaces_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.fp_bfaces_info.restype = ci
+    L.fp_bfaces_nodes.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.fp_bfaces_nodes.restype = ci
+    L.fp_flux_correct.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.fp_flux_correct.restype = ci
     L.fp_eval.argtypes = [vp, i64, vp, vp, vp, ci, vp, vp, vp]
     L.fp_eval.restype = ci
     L.fp_free.argtypes = [vp]
@@ -453,6 +463,59 @@ def fp_find_eval_ws(h: Handle, ws: "Workspace", pts: torch.Tensor, qsess: Option
                                _ptr(elem), _ptr(rst), _ptr(dist2), _ptr(values), _stream(stream))
     _check(st, h.ptr)
     return code, sub, elem, rst, dist2, values
+
+
+class BFaces:
+    """Boundary-face quadrature of marked faces (fp_bfaces_*) for the
+    mass-flux correction of interpolated interface data."""
+
+    def __init__(self, h: Handle, kind: torch.Tensor, stream=None):
+        if not isinstance(kind, torch.Tensor) or not kind.is_cuda or kind.dtype != torch.int8:
+            raise TypeError("kind: expected an int8 CUDA tensor [E][6]")
+        kind = kind.contiguous()
+        self.handle = h
+        self.ptr = ctypes.c_void_p()
+        st = lib().fp_bfaces_create(h.ptr, _ptr(kind), ctypes.byref(self.ptr), _stream(stream))
+        if st != FP_OK:
+            raise FindptsError(st, "fp_bfaces_create failed")
+        nf, M = ctypes.c_int64(), ctypes.c_int64()
+        lib().fp_bfaces_info(self.ptr, ctypes.byref(nf), ctypes.byref(M))
+        self.nfaces, self.M = nf.value, M.value
+
+    def __del__(self):
+        if getattr(self, "ptr", None) is not None and self.ptr.value:
+            try:
+                lib().fp_bfaces_free(self.ptr)
+            except Exception:
+                pass
+            self.ptr = ctypes.c_void_p(None)
+
+    def nodes(self, device=None):
+        """(x [3][M], normal [3][M], dA [M], kind [M]) as device tensors."""
+        dev = device or torch.device("cuda")
+        M = self.M
+        x = torch.empty((3, M), dtype=torch.float64, device=dev)
+        nr = torch.empty((3, M), dtype=torch.float64, device=dev)
+        dA = torch.empty(M, dtype=torch.float64, device=dev)
+        kd = torch.empty(M, dtype=torch.int8, device=dev)
+        st = lib().fp_bfaces_nodes(self.ptr, _ptr(x), _ptr(nr), _ptr(dA), _ptr(kd), _stream(None))
+        if st != FP_OK:
+            raise FindptsError(st, "fp_bfaces_nodes failed")
+        return x, nr, dA, kd
+
+
+def fp_flux_correct(bf: BFaces, u: torch.Tensor, u_out: Optional[torch.Tensor] = None, stream=None):
+    """Eq. consv2 / corr: returns (u_out [3][M], gamma, flux) with gamma and
+    flux as one-element device tensors."""
+    u = _dev(u, torch.float64, "u")
+    if u_out is None:
+        u_out = torch.empty_like(u)
+    g = torch.empty(1, dtype=torch.float64, device=u.device)
+    fl = torch.empty(1, dtype=torch.float64, device=u.device)
+    st = lib().fp_flux_correct(bf.ptr, _ptr(u), _ptr(u_out), _ptr(g), _ptr(fl), _stream(stream))
+    if st != FP_OK:
+        raise FindptsError(st, "fp_flux_correct failed")
+    return u_out, g, fl
 
 
 PROF_KINDS = {"screen": 0, "sort": 1, "newton": 2, "rank": 3, "eval": 4}

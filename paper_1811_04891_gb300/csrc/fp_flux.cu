@@ -1,0 +1,321 @@
+// fp_flux.cu -- mass-flux correction of interpolated interface velocity
+// (Sec. 2.2, Eqs. consv1, corr, consv2).
+//
+// fp_bfaces_create lists the faces a caller marks on the handle's mesh
+// (1 = boundary with prescribed data, 2 = interface with interpolated data),
+// in (element, face) order, and computes for every face node its position,
+// outward unit normal and GLL area weight dA = w_a w_b |t_1 x t_2| (tangents
+// from the derivative matrix of the Lagrange basis applied along the face).
+// fp_flux_correct then computes
+//     flux  = sum over all listed nodes of u.n dA        (int u.n over dOmega^j)
+//     area  = sum over interface nodes of n.n dA          (int n.n over dOmega_i)
+//     gamma = -flux / area                                (Eq. consv2)
+// and u_out = u + gamma n on interface nodes, u elsewhere (Eq. corr), with a
+// fixed-order two-level reduction (the same bits on every run).
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "fp_common.cuh"
+#include "fp_handle.h"
+#include "fp_internal.h"
+
+using namespace fpg;
+
+struct DerivTab {
+    double D[NMAX * NMAX];   // D[a*n + i] = h_i'(xi_a)
+    double w[NMAX];          // GLL quadrature weights
+};
+
+struct fp_bfaces {
+    const fp_handle* owner = nullptr;
+    int n = 0;
+    int64_t nf = 0, M = 0;
+    int32_t* face = nullptr;      // [nf] e*6 + f
+    double* x = nullptr;          // [3][M]
+    double* nrm = nullptr;        // [3][M]
+    double* dA = nullptr;         // [M]
+    int8_t* kind = nullptr;       // [M]
+    double* partial = nullptr;    // [2 * nblk]
+    double* result = nullptr;     // [3]: flux, area, gamma
+    int nblk = 0;
+};
+
+namespace fpg {
+
+__global__ void k_face_flags(int64_t F, const int8_t* __restrict__ kind, int32_t* __restrict__ flag)
+{
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f < F) flag[f] = kind[f] != 0;
+}
+
+__global__ void k_face_list(int64_t F, const int8_t* __restrict__ kind, const int32_t* __restrict__ off,
+                            int32_t* __restrict__ face)
+{
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f < F && kind[f] != 0) face[off[f]] = (int32_t)f;
+}
+
+__device__ __forceinline__ int fnode(int n, int f, int a, int b)
+{
+    const int end = (f & 1) ? n - 1 : 0;
+    switch (f >> 1) {
+        case 0: return end + n * (a + n * b);
+        case 1: return a + n * (end + n * b);
+        default: return a + n * (b + n * end);
+    }
+}
+
+template <int n>
+__global__ void k_bface_geom(int64_t E, int64_t M, const double* __restrict__ coords, const ElemBox* __restrict__ boxes,
+                             const int8_t* __restrict__ kind, const int32_t* __restrict__ face, DerivTab tab,
+                             double* __restrict__ x, double* __restrict__ nrm, double* __restrict__ dA,
+                             int8_t* __restrict__ nkind)
+{
+    constexpr int n2 = n * n, n3 = n2 * n;
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const int fid = face[m / n2];
+    const int64_t e = fid / 6;
+    const int f = fid % 6;
+    const int a = (int)(m % n2) % n, b = (int)(m % n2) / n;
+    // handedness of the element: sign of det of its affine frame (det Ai has the sign of det A)
+    const double* Ai = boxes[e].Ai;
+    const double detAi = Ai[0] * (Ai[4] * Ai[8] - Ai[5] * Ai[7]) - Ai[1] * (Ai[3] * Ai[8] - Ai[5] * Ai[6]) +
+                         Ai[2] * (Ai[3] * Ai[7] - Ai[4] * Ai[6]);
+    const double hand = detAi < 0.0 ? -1.0 : 1.0;
+    double t1[3], t2[3], xn[3];
+    for (int c = 0; c < 3; ++c) {
+        const double* X = coords + ((int64_t)c * E + e) * n3;
+        double s1 = 0.0, s2 = 0.0;
+#pragma unroll
+        for (int q = 0; q < n; ++q) {
+            s1 = fma(tab.D[a * n + q], X[fnode(n, f, q, b)], s1);
+            s2 = fma(tab.D[b * n + q], X[fnode(n, f, a, q)], s2);
+        }
+        t1[c] = s1;
+        t2[c] = s2;
+        xn[c] = X[fnode(n, f, a, b)];
+    }
+    // cyclic orientation of the face variables: r-faces (s,t), s-faces (t,r), t-faces (r,s)
+    double nv[3] = {t1[1] * t2[2] - t1[2] * t2[1], t1[2] * t2[0] - t1[0] * t2[2], t1[0] * t2[1] - t1[1] * t2[0]};
+    const double o = ((f >> 1) == 1 ? -1.0 : 1.0) * ((f & 1) ? 1.0 : -1.0) * hand;
+    const double len = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+    for (int c = 0; c < 3; ++c) {
+        x[c * M + m] = xn[c];
+        nrm[c * M + m] = o * nv[c] / len;
+    }
+    dA[m] = tab.w[a] * tab.w[b] * len;
+    nkind[m] = kind[fid];
+}
+
+constexpr int FLUX_THREADS = 256;
+
+// per block: sum of u.n dA and of interface n.n dA over a contiguous chunk
+__global__ void __launch_bounds__(FLUX_THREADS) k_flux_partial(int64_t M, int64_t chunk, const double* __restrict__ u,
+                                                               const double* __restrict__ nrm,
+                                                               const double* __restrict__ dA,
+                                                               const int8_t* __restrict__ kind,
+                                                               double* __restrict__ partial)
+{
+    __shared__ double s0[FLUX_THREADS], s1[FLUX_THREADS];
+    const int64_t lo = blockIdx.x * chunk, hi = min(M, lo + chunk);
+    double a0 = 0.0, a1 = 0.0;
+    for (int64_t m = lo + threadIdx.x; m < hi; m += blockDim.x) {
+        const double nx = nrm[m], ny = nrm[M + m], nz = nrm[2 * M + m];
+        const double un = u[m] * nx + u[M + m] * ny + u[2 * M + m] * nz;
+        a0 += un * dA[m];
+        if (kind[m] == 2) a1 += (nx * nx + ny * ny + nz * nz) * dA[m];
+    }
+    s0[threadIdx.x] = a0;
+    s1[threadIdx.x] = a1;
+    __syncthreads();
+    for (int w = FLUX_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            s0[threadIdx.x] += s0[threadIdx.x + w];
+            s1[threadIdx.x] += s1[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = s0[0];
+        partial[2 * blockIdx.x + 1] = s1[0];
+    }
+}
+
+__global__ void k_flux_final(int nblk, const double* __restrict__ partial, double* __restrict__ result)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double fl = 0.0, area = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+        fl += partial[2 * b];
+        area += partial[2 * b + 1];
+    }
+    result[0] = fl;
+    result[1] = area;
+    result[2] = area > 0.0 ? -fl / area : 0.0;
+}
+
+__global__ void k_flux_apply(int64_t M, const double* __restrict__ u, const double* __restrict__ nrm,
+                             const int8_t* __restrict__ kind, const double* __restrict__ result,
+                             double* __restrict__ u_out)
+{
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const double g = kind[m] == 2 ? result[2] : 0.0;
+    for (int c = 0; c < 3; ++c) u_out[c * M + m] = u[c * M + m] + g * nrm[c * M + m];
+}
+
+__global__ void k_flux_out(const double* __restrict__ result, double* gamma, double* flux)
+{
+    if (gamma) *gamma = result[2];
+    if (flux) *flux = result[0];
+}
+
+}  // namespace fpg
+
+static void bf_release(fp_bfaces* b)
+{
+    cudaFree(b->face); cudaFree(b->x); cudaFree(b->nrm); cudaFree(b->dA); cudaFree(b->kind);
+    cudaFree(b->partial); cudaFree(b->result);
+}
+
+extern "C" fp_status fp_bfaces_create(const fp_handle* h, const int8_t* kind, fp_bfaces** out, void* stream)
+{
+    if (!out) return FP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (!kind) return FP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = h->n;
+    const int64_t F = 6 * h->E;
+    fp_bfaces* b = new fp_bfaces();
+    b->owner = h;
+    b->n = n;
+    int32_t *flag = nullptr, *off = nullptr, *tmp = nullptr;
+    int32_t total = 0;
+    cudaError_t e = cudaMalloc(&flag, sizeof(int32_t) * F);
+    if (e == cudaSuccess) e = cudaMalloc(&off, sizeof(int32_t) * (F + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, sizeof(int32_t) * scan_tmp_elems(F));
+    if (e == cudaSuccess) {
+        k_face_flags<<<(unsigned)((F + 255) / 256), 256, 0, s>>>(F, kind, flag);
+        count_launch();
+        e = scan_exclusive(flag, off, F, tmp, s);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&total, off + F, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    b->nf = total;
+    b->M = (int64_t)total * n * n;
+    if (e == cudaSuccess) e = cudaMalloc(&b->face, sizeof(int32_t) * std::max<int64_t>(b->nf, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->x, sizeof(double) * 3 * std::max<int64_t>(b->M, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->nrm, sizeof(double) * 3 * std::max<int64_t>(b->M, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->dA, sizeof(double) * std::max<int64_t>(b->M, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->kind, std::max<int64_t>(b->M, 1));
+    b->nblk = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (b->M + 4095) / 4096));
+    if (e == cudaSuccess) e = cudaMalloc(&b->partial, sizeof(double) * 2 * b->nblk);
+    if (e == cudaSuccess) e = cudaMalloc(&b->result, sizeof(double) * 3);
+    if (e == cudaSuccess && b->nf > 0) {
+        k_face_list<<<(unsigned)((F + 255) / 256), 256, 0, s>>>(F, kind, off, b->face);
+        count_launch();
+        DerivTab t;
+        memset(&t, 0, sizeof(t));
+        const double* xi = h->tab.xi;
+        const int N = n - 1;
+        for (int a = 0; a < n; ++a) {
+            double dsum = 0.0;
+            for (int i = 0; i < n; ++i) {
+                if (i == a) continue;
+                // h_i'(xi_a) for i != a: the factor (r - xi_a) is the only one that vanishes
+                double p = h->tab.ci[i];
+                for (int m = 0; m < n; ++m)
+                    if (m != i && m != a) p *= (xi[a] - xi[m]);
+                t.D[a * n + i] = p;
+                dsum += 1.0 / (xi[a] - xi[i]);
+            }
+            t.D[a * n + a] = dsum;
+            // GLL weight 2 / (N (N+1) P_N(xi_a)^2), P_N by the three-term recurrence
+            double p0 = 1.0, p1 = xi[a];
+            for (int k = 1; k < N; ++k) {
+                double p2 = ((2 * k + 1) * xi[a] * p1 - k * p0) / (k + 1);
+                p0 = p1;
+                p1 = p2;
+            }
+            const double PN = N == 0 ? 1.0 : p1;
+            t.w[a] = 2.0 / (N * (N + 1.0) * PN * PN);
+        }
+        const unsigned grid = (unsigned)((b->M + 127) / 128);
+        switch (n) {
+#define FP_CASE(NN) \
+    case NN: k_bface_geom<NN><<<grid, 128, 0, s>>>(h->E, b->M, h->coords, h->boxes, kind, b->face, t, b->x, b->nrm, b->dA, b->kind); break;
+            FP_CASE(2) FP_CASE(3) FP_CASE(4) FP_CASE(5) FP_CASE(6) FP_CASE(7) FP_CASE(8) FP_CASE(9)
+            FP_CASE(10) FP_CASE(11) FP_CASE(12) FP_CASE(13) FP_CASE(14) FP_CASE(15) FP_CASE(16)
+#undef FP_CASE
+            default: e = cudaErrorInvalidValue;
+        }
+        count_launch();
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(flag);
+    cudaFree(off);
+    cudaFree(tmp);
+    if (e != cudaSuccess) {
+        bf_release(b);
+        delete b;
+        return e == cudaErrorMemoryAllocation ? FP_ERR_OOM : FP_ERR_CUDA;
+    }
+    *out = b;
+    return FP_OK;
+}
+
+extern "C" void fp_bfaces_free(fp_bfaces* b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    bf_release(b);
+    delete b;
+}
+
+extern "C" fp_status fp_bfaces_info(const fp_bfaces* b, int64_t* nfaces, int64_t* nnodes)
+{
+    if (!b) return FP_ERR_INVALID_ARG;
+    if (nfaces) *nfaces = b->nf;
+    if (nnodes) *nnodes = b->M;
+    return FP_OK;
+}
+
+extern "C" fp_status fp_bfaces_nodes(const fp_bfaces* b, double* x, double* normal, double* dA, int8_t* kind,
+                                     void* stream)
+{
+    if (!b) return FP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (x && b->M) e = cudaMemcpyAsync(x, b->x, sizeof(double) * 3 * b->M, cudaMemcpyDeviceToDevice, s);
+    if (normal && b->M && e == cudaSuccess)
+        e = cudaMemcpyAsync(normal, b->nrm, sizeof(double) * 3 * b->M, cudaMemcpyDeviceToDevice, s);
+    if (dA && b->M && e == cudaSuccess) e = cudaMemcpyAsync(dA, b->dA, sizeof(double) * b->M, cudaMemcpyDeviceToDevice, s);
+    if (kind && b->M && e == cudaSuccess) e = cudaMemcpyAsync(kind, b->kind, b->M, cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? FP_OK : FP_ERR_CUDA;
+}
+
+extern "C" fp_status fp_flux_correct(const fp_bfaces* b, const double* u, double* u_out, double* gamma, double* flux,
+                                     void* stream)
+{
+    if (!b || !u || !u_out) return FP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (b->M == 0) {
+        k_flux_final<<<1, 1, 0, s>>>(0, b->partial, b->result);
+        k_flux_out<<<1, 1, 0, s>>>(b->result, gamma, flux);
+        count_launch(2);
+        return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ERR_CUDA;
+    }
+    const int64_t chunk = (b->M + b->nblk - 1) / b->nblk;
+    k_flux_partial<<<b->nblk, FLUX_THREADS, 0, s>>>(b->M, chunk, u, b->nrm, b->dA, b->kind, b->partial);
+    k_flux_final<<<1, 1, 0, s>>>(b->nblk, b->partial, b->result);
+    k_flux_apply<<<(unsigned)((b->M + 255) / 256), 256, 0, s>>>(b->M, u, b->nrm, b->kind, b->result, u_out);
+    k_flux_out<<<1, 1, 0, s>>>(b->result, gamma, flux);
+    count_launch(4);
+    return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ERR_CUDA;
+}
