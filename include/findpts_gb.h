@@ -300,6 +300,26 @@ fp_status fp_bfaces_nodes(const fp_bfaces *b, double *x, double *normal, double 
 fp_status fp_flux_correct(const fp_bfaces *b, const double *u, double *u_out, double *gamma,
                           double *flux, void *stream);
 
+/* Interface-data pipeline helpers.
+ * fp_bfaces_iface: number of interface nodes Mi and (if pts != NULL) their
+ * positions [3][Mi] in listing order -- the query points of the
+ * interpolation of interface data.
+ * fp_flux_correct_iface: fp_flux_correct with the velocity given as the
+ * interpolated values at the interface nodes u_iface [3][Mi] (e.g. the
+ * first three rows of an fp_eval output at the fp_bfaces_iface points) and
+ * the prescribed values u_pres [3][M] (read at the other nodes only).
+ * fp_extrapolate: out[i] = sum_{j=1..m} c_j hist[j-1][i] for i < len, the
+ * order-m extrapolation in time of interface data over equal time steps from
+ * the m newest values (hist: host array of m device pointers, newest first),
+ * c = (1), (2,-1), (3,-3,1) for m = 1, 2, 3 (Sec. 2: lagged or extrapolated
+ * boundary data, refined by kappa sub-iterations).  These calls allocate
+ * nothing and never wait, so an eval + correction sub-iteration can be
+ * captured in a CUDA graph and replayed kappa times. */
+fp_status fp_bfaces_iface(const fp_bfaces *b, int64_t *n_iface, double *pts, void *stream);
+fp_status fp_flux_correct_iface(const fp_bfaces *b, const double *u_iface, const double *u_pres,
+                                double *u_out, double *gamma, double *flux, void *stream);
+fp_status fp_extrapolate(int m, int64_t len, const double *const *hist, double *out, void *stream);
+
 /* Release every device resource of the handle (synchronises it first).
    NULL is a no-op. */
 void fp_free(fp_handle *h);

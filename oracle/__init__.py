@@ -203,6 +203,23 @@ def flux_correct(u, nrm, dA, nkind):
     return out.T.copy(), g.value, fl.value
 
 
+def extrapolate(hist):
+    """Order-m extrapolation in time over equal steps from the m newest
+    values (newest first): the polynomial of degree m-1 through
+    (t_{n}, h_0), (t_{n-1}, h_1), ... evaluated at t_{n+1}, written out as
+    Lagrange weights on the equally spaced abscissae."""
+    m = len(hist)
+    ts = [-float(j) for j in range(m)]          # t_n = 0, t_{n-1} = -1, ...
+    out = np.zeros_like(np.asarray(hist[0], dtype=np.float64))
+    for j in range(m):
+        w = 1.0
+        for k in range(m):
+            if k != j:
+                w *= (1.0 - ts[k]) / (ts[j] - ts[k])
+        out = out + w * np.asarray(hist[j], dtype=np.float64)
+    return out
+
+
 def dist_default(coords, N: int, sub):
     """Default nodal distance field D^k [E][n^3] (brute force)."""
     coords = _f64(coords)

@@ -106,6 +106,12 @@ def _load():
     L.fp_bfaces_nodes.restype = ci
     L.fp_flux_correct.argtypes = [vp, vp, vp, vp, vp, vp]
     L.fp_flux_correct.restype = ci
+    L.fp_flux_correct_iface.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.fp_flux_correct_iface.restype = ci
+    L.fp_bfaces_iface.argtypes = [vp, ctypes.POINTER(i64), vp, vp]
+    L.fp_bfaces_iface.restype = ci
+    L.fp_extrapolate.argtypes = [ci, i64, ctypes.POINTER(vp), vp, vp]
+    L.fp_extrapolate.restype = ci
     L.fp_eval.argtypes = [vp, i64, vp, vp, vp, ci, vp, vp, vp]
     L.fp_eval.restype = ci
     L.fp_free.argtypes = [vp]
@@ -481,6 +487,17 @@ class BFaces:
         nf, M = ctypes.c_int64(), ctypes.c_int64()
         lib().fp_bfaces_info(self.ptr, ctypes.byref(nf), ctypes.byref(M))
         self.nfaces, self.M = nf.value, M.value
+        mi = ctypes.c_int64()
+        lib().fp_bfaces_iface(self.ptr, ctypes.byref(mi), None, None)
+        self.Mi = mi.value
+
+    def iface_points(self, device=None):
+        """Positions [3][Mi] of the interface nodes (listing order)."""
+        pts = torch.empty((3, self.Mi), dtype=torch.float64, device=device or torch.device("cuda"))
+        st = lib().fp_bfaces_iface(self.ptr, None, _ptr(pts), _stream(None))
+        if st != FP_OK:
+            raise FindptsError(st, "fp_bfaces_iface failed")
+        return pts
 
     def __del__(self):
         if getattr(self, "ptr", None) is not None and self.ptr.value:
@@ -516,6 +533,33 @@ def fp_flux_correct(bf: BFaces, u: torch.Tensor, u_out: Optional[torch.Tensor] =
     if st != FP_OK:
         raise FindptsError(st, "fp_flux_correct failed")
     return u_out, g, fl
+
+
+def fp_flux_correct_iface(bf: "BFaces", u_iface: torch.Tensor, u_pres: torch.Tensor, u_out=None, stream=None):
+    """Flux correction with interpolated interface values u_iface [3][Mi] and
+    prescribed values u_pres [3][M]; returns (u_out, gamma, flux)."""
+    if u_out is None:
+        u_out = torch.empty_like(u_pres)
+    g = torch.empty(1, dtype=torch.float64, device=u_pres.device)
+    fl = torch.empty(1, dtype=torch.float64, device=u_pres.device)
+    st = lib().fp_flux_correct_iface(bf.ptr, _ptr(u_iface), _ptr(u_pres), _ptr(u_out), _ptr(g), _ptr(fl),
+                                     _stream(stream))
+    if st != FP_OK:
+        raise FindptsError(st, "fp_flux_correct_iface failed")
+    return u_out, g, fl
+
+
+def fp_extrapolate(hist, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Order-len(hist) extrapolation in time (newest first), equal steps."""
+    m = len(hist)
+    h0 = hist[0]
+    if out is None:
+        out = torch.empty_like(h0)
+    arr = (ctypes.c_void_p * m)(*[t.data_ptr() for t in hist])
+    st = lib().fp_extrapolate(m, h0.numel(), arr, _ptr(out), _stream(stream))
+    if st != FP_OK:
+        raise FindptsError(st, "fp_extrapolate failed")
+    return out
 
 
 PROF_KINDS = {"screen": 0, "sort": 1, "newton": 2, "rank": 3, "eval": 4}

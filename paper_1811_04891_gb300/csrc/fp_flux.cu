@@ -38,6 +38,8 @@ struct fp_bfaces {
     double* nrm = nullptr;        // [3][M]
     double* dA = nullptr;         // [M]
     int8_t* kind = nullptr;       // [M]
+    int32_t* ipos = nullptr;      // [M] index of the node among the interface nodes, -1 otherwise
+    int64_t Mi = 0;               // interface nodes
     double* partial = nullptr;    // [2 * nblk]
     double* result = nullptr;     // [3]: flux, area, gamma
     int nblk = 0;
@@ -113,8 +115,26 @@ __global__ void k_bface_geom(int64_t E, int64_t M, const double* __restrict__ co
 
 constexpr int FLUX_THREADS = 256;
 
+// velocity component c at face node m: from u [3][M], or -- split form --
+// from the interpolated interface values ui [3][Mi] on interface nodes and
+// the prescribed values up [3][M] elsewhere
+struct UView {
+    const double* u;
+    const double* ui;
+    const int32_t* ipos;
+    int64_t M, Mi;
+    __device__ __forceinline__ double at(int c, int64_t m) const
+    {
+        if (ui) {
+            const int32_t k = ipos[m];
+            if (k >= 0) return ui[c * Mi + k];
+        }
+        return u[c * M + m];
+    }
+};
+
 // per block: sum of u.n dA and of interface n.n dA over a contiguous chunk
-__global__ void __launch_bounds__(FLUX_THREADS) k_flux_partial(int64_t M, int64_t chunk, const double* __restrict__ u,
+__global__ void __launch_bounds__(FLUX_THREADS) k_flux_partial(int64_t M, int64_t chunk, UView u,
                                                                const double* __restrict__ nrm,
                                                                const double* __restrict__ dA,
                                                                const int8_t* __restrict__ kind,
@@ -125,7 +145,7 @@ __global__ void __launch_bounds__(FLUX_THREADS) k_flux_partial(int64_t M, int64_
     double a0 = 0.0, a1 = 0.0;
     for (int64_t m = lo + threadIdx.x; m < hi; m += blockDim.x) {
         const double nx = nrm[m], ny = nrm[M + m], nz = nrm[2 * M + m];
-        const double un = u[m] * nx + u[M + m] * ny + u[2 * M + m] * nz;
+        const double un = u.at(0, m) * nx + u.at(1, m) * ny + u.at(2, m) * nz;
         a0 += un * dA[m];
         if (kind[m] == 2) a1 += (nx * nx + ny * ny + nz * nz) * dA[m];
     }
@@ -158,14 +178,53 @@ __global__ void k_flux_final(int nblk, const double* __restrict__ partial, doubl
     result[2] = area > 0.0 ? -fl / area : 0.0;
 }
 
-__global__ void k_flux_apply(int64_t M, const double* __restrict__ u, const double* __restrict__ nrm,
-                             const int8_t* __restrict__ kind, const double* __restrict__ result,
-                             double* __restrict__ u_out)
+__global__ void k_flux_apply(int64_t M, UView u, const double* __restrict__ nrm, const int8_t* __restrict__ kind,
+                             const double* __restrict__ result, double* __restrict__ u_out)
 {
     const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (m >= M) return;
     const double g = kind[m] == 2 ? result[2] : 0.0;
-    for (int c = 0; c < 3; ++c) u_out[c * M + m] = u[c * M + m] + g * nrm[c * M + m];
+    for (int c = 0; c < 3; ++c) u_out[c * M + m] = u.at(c, m) + g * nrm[c * M + m];
+}
+
+__global__ void k_iface_pos(int64_t M, const int8_t* __restrict__ kind, const int32_t* __restrict__ off,
+                            int32_t* __restrict__ ipos)
+{
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m < M) ipos[m] = kind[m] == 2 ? off[m] : -1;
+}
+
+__global__ void k_iface_flags(int64_t M, const int8_t* __restrict__ kind, int32_t* __restrict__ flag)
+{
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m < M) flag[m] = kind[m] == 2;
+}
+
+__global__ void k_iface_points(int64_t M, int64_t Mi, const int32_t* __restrict__ ipos, const double* __restrict__ x,
+                               double* __restrict__ pts)
+{
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const int32_t k = ipos[m];
+    if (k >= 0)
+        for (int c = 0; c < 3; ++c) pts[c * Mi + k] = x[c * M + m];
+}
+
+// out = sum_j c_j hist_j (temporal extrapolation of interface data)
+struct ExtArgs {
+    const double* h[3];
+    double c[3];
+    int m;
+};
+
+__global__ void k_extrapolate(int64_t len, ExtArgs A, double* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = A.c[0] * A.h[0][i];
+        if (A.m > 1) v = fma(A.c[1], A.h[1][i], v);
+        if (A.m > 2) v = fma(A.c[2], A.h[2][i], v);
+        out[i] = v;
+    }
 }
 
 __global__ void k_flux_out(const double* __restrict__ result, double* gamma, double* flux)
@@ -178,6 +237,7 @@ __global__ void k_flux_out(const double* __restrict__ result, double* gamma, dou
 
 static void bf_release(fp_bfaces* b)
 {
+    cudaFree(b->ipos);
     cudaFree(b->face); cudaFree(b->x); cudaFree(b->nrm); cudaFree(b->dA); cudaFree(b->kind);
     cudaFree(b->partial); cudaFree(b->result);
 }
@@ -257,6 +317,30 @@ extern "C" fp_status fp_bfaces_create(const fp_handle* h, const int8_t* kind, fp
         count_launch();
         if (e == cudaSuccess) e = cudaGetLastError();
     }
+    // positions of the interface nodes among themselves (listing order)
+    if (e == cudaSuccess) e = cudaMalloc(&b->ipos, sizeof(int32_t) * std::max<int64_t>(b->M, 1));
+    if (e == cudaSuccess && b->M > 0) {
+        int32_t *nf = nullptr, *noff = nullptr, *ntmp = nullptr;
+        e = cudaMalloc(&nf, sizeof(int32_t) * b->M);
+        if (e == cudaSuccess) e = cudaMalloc(&noff, sizeof(int32_t) * (b->M + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&ntmp, sizeof(int32_t) * scan_tmp_elems(b->M));
+        if (e == cudaSuccess) {
+            k_iface_flags<<<(unsigned)((b->M + 255) / 256), 256, 0, s>>>(b->M, b->kind, nf);
+            count_launch();
+            e = scan_exclusive(nf, noff, b->M, ntmp, s);
+        }
+        if (e == cudaSuccess) {
+            k_iface_pos<<<(unsigned)((b->M + 255) / 256), 256, 0, s>>>(b->M, b->kind, noff, b->ipos);
+            count_launch();
+            int32_t mi = 0;
+            e = cudaMemcpyAsync(&mi, noff + b->M, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            b->Mi = mi;
+        }
+        cudaFree(nf);
+        cudaFree(noff);
+        cudaFree(ntmp);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(flag);
     cudaFree(off);
@@ -286,6 +370,38 @@ extern "C" fp_status fp_bfaces_info(const fp_bfaces* b, int64_t* nfaces, int64_t
     return FP_OK;
 }
 
+extern "C" fp_status fp_bfaces_iface(const fp_bfaces* b, int64_t* n_iface, double* pts, void* stream)
+{
+    if (!b) return FP_ERR_INVALID_ARG;
+    if (n_iface) *n_iface = b->Mi;
+    if (pts && b->M > 0) {
+        k_iface_points<<<(unsigned)((b->M + 255) / 256), 256, 0, (cudaStream_t)stream>>>(b->M, b->Mi, b->ipos, b->x,
+                                                                                          pts);
+        count_launch();
+        if (cudaGetLastError() != cudaSuccess) return FP_ERR_CUDA;
+    }
+    return FP_OK;
+}
+
+extern "C" fp_status fp_extrapolate(int m, int64_t len, const double* const* hist, double* out, void* stream)
+{
+    if (m < 1 || m > 3 || len < 0 || !hist || !out) return FP_ERR_INVALID_ARG;
+    ExtArgs a;
+    memset(&a, 0, sizeof(a));
+    a.m = m;
+    static const double coef[3][3] = {{1.0, 0.0, 0.0}, {2.0, -1.0, 0.0}, {3.0, -3.0, 1.0}};
+    for (int j = 0; j < m; ++j) {
+        if (!hist[j]) return FP_ERR_INVALID_ARG;
+        a.h[j] = hist[j];
+        a.c[j] = coef[m - 1][j];
+    }
+    if (len == 0) return FP_OK;
+    const int64_t blocks = std::min<int64_t>((len + 255) / 256, 4096);
+    k_extrapolate<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(len, a, out);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ERR_CUDA;
+}
+
 extern "C" fp_status fp_bfaces_nodes(const fp_bfaces* b, double* x, double* normal, double* dA, int8_t* kind,
                                      void* stream)
 {
@@ -300,11 +416,8 @@ extern "C" fp_status fp_bfaces_nodes(const fp_bfaces* b, double* x, double* norm
     return e == cudaSuccess ? FP_OK : FP_ERR_CUDA;
 }
 
-extern "C" fp_status fp_flux_correct(const fp_bfaces* b, const double* u, double* u_out, double* gamma, double* flux,
-                                     void* stream)
+static fp_status flux_impl(const fp_bfaces* b, UView u, double* u_out, double* gamma, double* flux, cudaStream_t s)
 {
-    if (!b || !u || !u_out) return FP_ERR_INVALID_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
     if (b->M == 0) {
         k_flux_final<<<1, 1, 0, s>>>(0, b->partial, b->result);
         k_flux_out<<<1, 1, 0, s>>>(b->result, gamma, flux);
@@ -318,4 +431,20 @@ extern "C" fp_status fp_flux_correct(const fp_bfaces* b, const double* u, double
     k_flux_out<<<1, 1, 0, s>>>(b->result, gamma, flux);
     count_launch(4);
     return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ERR_CUDA;
+}
+
+extern "C" fp_status fp_flux_correct(const fp_bfaces* b, const double* u, double* u_out, double* gamma, double* flux,
+                                     void* stream)
+{
+    if (!b || !u || !u_out) return FP_ERR_INVALID_ARG;
+    UView v{u, nullptr, nullptr, b->M, b->Mi};
+    return flux_impl(b, v, u_out, gamma, flux, (cudaStream_t)stream);
+}
+
+extern "C" fp_status fp_flux_correct_iface(const fp_bfaces* b, const double* u_iface, const double* u_pres,
+                                           double* u_out, double* gamma, double* flux, void* stream)
+{
+    if (!b || !u_iface || !u_pres || !u_out) return FP_ERR_INVALID_ARG;
+    UView v{u_pres, u_iface, b->ipos, b->M, b->Mi};
+    return flux_impl(b, v, u_out, gamma, flux, (cudaStream_t)stream);
 }

@@ -97,3 +97,19 @@ def test_flux_correction_zeroes_flux_and_moves_only_interface():
     np.testing.assert_array_equal(u_out[:, nk == 1], u[:, nk == 1])     # prescribed data untouched
     d = u_out[:, nk == 2] - u[:, nk == 2]
     np.testing.assert_allclose(d, g * nr[:, nk == 2], atol=1e-15)      # correction along n (Eq. corr)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_extrapolation_exact_for_degree_m_minus_1(m):
+    """Order-m extrapolation over equal steps reproduces polynomials in time
+    of degree m-1 exactly and keeps constants."""
+    rng = np.random.default_rng(m)
+    coef = rng.uniform(-1, 1, (m, 5))
+    def val(t):
+        return sum(coef[d] * t ** d for d in range(m))
+    hist = [val(float(-j)) for j in range(m)]         # t_n = 0, t_{n-1} = -1, ...
+    np.testing.assert_allclose(oracle.extrapolate(hist), val(1.0), atol=1e-13)
+    np.testing.assert_allclose(oracle.extrapolate([np.full(5, 2.5)] * m), 2.5, atol=1e-15)
+    if m > 1:   # degree m is not reproduced (guards against a wrong order)
+        hist = [np.full(5, float(-j) ** m) for j in range(m)]
+        assert np.abs(oracle.extrapolate(hist) - 1.0).max() > 0.5
