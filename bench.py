@@ -74,6 +74,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-interface", action="store_true")
+    ap.add_argument("--no-moving", action="store_true")
     ap.add_argument("--served-requests", type=int, default=200)
     ap.add_argument("--served-load", type=float, default=0.7)
     ap.add_argument("--served-scale", type=float, default=1.0,
@@ -316,12 +317,103 @@ def run_interface(args, fg, dev):
             e1.record()
             torch.cuda.synchronize()
             res[name + "_ms"] = e0.elapsed_time(e1) / reps
+        # the Schwarz step through the graph-replayed pipeline: predict
+        # (order-m extrapolation), kappa captured eval + correction
+        # sub-iterations, commit; (m, kappa) = (1, 1), (2, 4), (3, 7)
+        from paper_1811_04891_gb300.schwarz import InterfaceExchange
+        steps = {}
+        for m, kappa in ((1, 1), (2, 4), (3, 7)):
+            xch = InterfaceExchange(h, bf, 1, fields, posted=posted, order=m)
+            for _ in range(m + 2):
+                xch.step(kappa)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 50
+            e0.record()
+            for _ in range(reps):
+                xch.step(kappa)
+            e1.record()
+            torch.cuda.synchronize()
+            steps[f"m{m}_kappa{kappa}_ms"] = e0.elapsed_time(e1) / reps
+            del xch
         out[form] = {"interface_points": int(P), "face_nodes": int(bf.M), "bfaces_setup_ms": bf_ms,
-                     **res, "iteration_points_per_s": P / (res["iteration_ms"] / 1e3)}
+                     **res, "iteration_points_per_s": P / (res["iteration_ms"] / 1e3),
+                     "graph_step": steps}
         del bf, h
     out["note"] = ("per Schwarz sub-iteration: eval of u,v,w,p at the found interface points + flux "
-                   "correction (Eq. consv2); find_eval = locate + eval once (static mesh)")
+                   "correction (Eq. consv2); find_eval = locate + eval once (static mesh); graph_step = "
+                   "extrapolation of order m + kappa graph-replayed sub-iterations + history update")
     return out
+
+
+def run_moving(args, fg, dev, mesh, coords, sub, pts, fields):
+    """Moving mesh: the deformed cube turns about its vertical axis by 0.02
+    degrees and drifts by 2e-4 (0.6 % of an element) per time step while the
+    query points stay, so every donor is found again each step.  Per step:
+    fp_update_coords (boxes, hash grid, FP32 geometry rebuilt in place) and a
+    find + eval warm-started from the previous step's (e, r); the cold find +
+    eval on the same moved mesh and a fresh fp_setup are timed beside it."""
+    import math
+
+    import torch
+    P = pts.shape[1]
+    h = fg.fp_setup(coords, mesh.N, sub, opts=fg.default_opts(precision=fg.PREC_MIXED))
+    fg.fp_reserve(h, P)
+    posted = fg.Fields(h, fields)
+    moved = torch.empty_like(coords)
+
+    def position(k):                 # the mesh motion itself (the flow solver's job, untimed)
+        a = math.radians(0.02 * k)
+        x, y = coords[0] - 0.5, coords[1] - 0.5
+        moved[0].copy_(x).mul_(math.cos(a)).add_(y, alpha=-math.sin(a)).add_(0.5 + 2e-4 * k)
+        moved[1].copy_(y).mul_(math.cos(a)).add_(x, alpha=math.sin(a)).add_(0.5)
+        moved[2].copy_(coords[2])
+
+    F = fields.shape[0]
+    outs = fg._find_outs(P, dev)
+    vals = torch.empty((F, P), dtype=torch.float64, device=dev)
+    fg.fp_find_eval(h, pts, None, posted=posted, out=outs, values=vals)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    t_upd = t_find = 0.0
+    k = 0
+    for it in range(args.warmup + args.steps):
+        k += 1
+        position(k)
+        ev[0].record()
+        fg.fp_update_coords(h, moved)
+        ev[1].record()
+        fg.fp_find_warm(h, pts, warm=(outs[2], outs[3]), posted=posted, out=outs, values=vals)
+        ev[2].record()
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            t_upd += ev[0].elapsed_time(ev[1])
+            t_find += ev[1].elapsed_time(ev[2])
+    K = args.steps
+    counts = torch.bincount(outs[0].long(), minlength=3).tolist()
+    cold = fg._find_outs(P, dev)
+    for _ in range(2):
+        fg.fp_find_eval(h, pts, None, posted=posted, out=cold, values=vals)
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(K):
+        fg.fp_find_eval(h, pts, None, posted=posted, out=cold, values=vals)
+    ev[1].record()
+    torch.cuda.synchronize()
+    t_cold = ev[0].elapsed_time(ev[1]) / K
+    same = all(bool(torch.equal(outs[a], cold[a])) for a in (0, 1, 2))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h2 = fg.fp_setup(moved, mesh.N, sub, opts=fg.default_opts(precision=fg.PREC_MIXED))
+    torch.cuda.synchronize()
+    setup_ms = 1e3 * (time.perf_counter() - t0)
+    del h2
+    step_ms = (t_upd + t_find) / K
+    return {"update_ms": t_upd / K, "find_eval_warm_ms": t_find / K, "find_eval_cold_ms": t_cold,
+            "step_ms": step_ms, "points_per_s": P / (step_ms / 1e3), "fresh_setup_ms": setup_ms,
+            "codes": {"inside": counts[0], "border": counts[1], "not_found": counts[2]},
+            "warm_equals_cold_ids": same,
+            "note": "deformed cube 32^3 N=7 turning 0.02 deg + drifting 2e-4 per step, 1.01e7 fixed points, "
+                    "mixed form with posted fields; step = update + warm find + eval"}
 
 
 # ---------------------------------------------------------------------------
@@ -495,7 +587,7 @@ def main():
         return {"bound": "alu", "achieved": achieved / 1e12, "peak": P64_NOMINAL / 1e12,
                 "unit": "TFLOP/s (FP64-equivalent: FP64 flops + FP32 flops x P64/P32)",
                 "frac": t_roof / kn, "traffic": TRAFFIC_PER_PAIR[form] * pairs,
-                "kernel": ("k_newton_mixed<8> + k_newton64_full<8>" if form == "mixed" else "k_newton<8,false>"),
+                "kernel": ("k_newton_mixed<8> + k_newton64_full<8>" if form == "mixed" else "k_newton<8>"),
                 "units_per_launch": pairs, "unit_work": w,
                 "peak_source": "of nominal: GB300 FP64 1.25 TFLOP/s; FP32 152 SMs x 128 lanes x 2 x 2.07 GHz"}
 
@@ -531,6 +623,9 @@ def main():
                "d2h_bytes_per_step": int(out_h.numel() * 8 + code_h.numel() * 4)}
 
     batched = None
+    moving = None
+    if not args.no_moving:
+        moving = run_moving(args, fg, dev, mesh, coords, sub, pts, fields)
     if not args.no_batched:
         del handles
         batched = run_batched(args, fg, dev, barrier, max_over_ranks, world)
@@ -557,7 +652,8 @@ def main():
                               "pairs_per_point": v["pairs_per_point"],
                               "newton_paths_per_step": v["newton_paths_per_step"]} for k, v in results.items()},
                 "roofline": roof, "roofline_other_forms": roof_other, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": R["gpu_launches"],
-                "clocks": R["clocks"], "batched": batched, "serving": served, "interface": interface}
+                "clocks": R["clocks"], "batched": batched, "serving": served, "interface": interface,
+                "moving": moving}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -269,6 +269,51 @@ fp_status fp_find_eval_ws(fp_handle *h, fp_workspace *ws, int64_t P, const doubl
                           const fp_fields *posted, int32_t *code, int32_t *sub, int32_t *elem,
                           double *rst, double *dist2, double *out, void *stream);
 
+/* Moving meshes (Sec. 1: donor elements are found again after every time
+ * step when meshes move or deform).
+ *
+ * fp_update_coords -- replace the node coordinates of the handle's mesh (same
+ * E, N, subdomain ids and options) and rebuild what depends on them: element
+ * boxes, global box, hash grid and, in the mixed form, the element-local FP32
+ * geometry.  A later fp_find gives exactly what fp_find on a new handle set
+ * up with these coordinates gives.
+ *   coords [3][E][n3] FP64, device or host memory; checked for non-finite
+ *          values before the handle changes
+ *   dist   [E][n3] new D^k field, or NULL to keep the current one (exact
+ *          when every subdomain moves rigidly: D^k moves with its mesh)
+ *   flags  0, or FP_UPDATE_DEFAULT_DIST to recompute the library's default D
+ *          (only with dist == NULL; brute force, see fp_setup)
+ * Work is enqueued on `stream` after what is already there; the call
+ * synchronises `stream` twice (global box, hash size).  Scratch is kept in
+ * the handle and only grows: an update whose hash grid fits the room of an
+ * earlier one allocates nothing.  Objects that copied geometry at creation
+ * (fp_bfaces, fp_batch) and CUDA graphs captured before the update must be
+ * created or captured again.  Errors: FP_ERR_NOT_SETUP, FP_ERR_INVALID_ARG
+ * (null or non-finite coords, bad flags; the handle is unchanged),
+ * FP_ERR_OOM, FP_ERR_CUDA (the handle is then unusable until an update
+ * succeeds).
+ *
+ * fp_find_warm -- fp_find (F == 0 and posted == NULL; out may be NULL) or
+ * fp_find_eval with a warm start: warm_elem [P] and warm_rst [3][P] are each
+ * point's element and reference coordinates from an earlier find (typically
+ * the previous time step).  The candidate pair (p, warm_elem[p]), if the
+ * screen keeps it, starts Newton from warm_rst[p] clamped to [-1,1]^3 instead
+ * of the nearest GLL node; elem = -1 or a non-finite warm_rst means no warm
+ * start for that point.  Only Newton's starting point changes, so INSIDE
+ * results equal fp_find's up to the Newton tolerance (the root in an element
+ * is unique); a BORDER point's clamped r is the local minimiser reached from
+ * the start.  warm_elem / warm_rst may be the same buffers as elem / rst (the
+ * warm values are read before the outputs are written).  Both NULL = cold
+ * start.  Errors as fp_find / fp_find_eval. */
+#define FP_UPDATE_DEFAULT_DIST 1
+fp_status fp_update_coords(fp_handle *h, const double *coords, const double *dist, int flags,
+                           void *stream);
+fp_status fp_find_warm(fp_handle *h, int64_t P, const double *pts, const int32_t *qsess,
+                       const int32_t *warm_elem, const double *warm_rst, int F,
+                       const double *fields, const fp_fields *posted, int32_t *code,
+                       int32_t *sub, int32_t *elem, double *rst, double *dist2, double *out,
+                       void *stream);
+
 /* Mass-flux correction of interpolated interface velocity (Sec. 2.2,
  * Eqs. consv1, corr, consv2).
  * fp_bfaces_create: kind [E][6] int8 on the device marks faces of the
@@ -299,6 +344,11 @@ fp_status fp_bfaces_nodes(const fp_bfaces *b, double *x, double *normal, double 
                           void *stream);
 fp_status fp_flux_correct(const fp_bfaces *b, const double *u, double *u_out, double *gamma,
                           double *flux, void *stream);
+/* fp_bfaces_refresh: recompute positions, normals and weights of the listed
+ * face nodes from the owner handle's current coordinates (after
+ * fp_update_coords on a moving mesh); the face list, node kinds and the
+ * interface numbering stay.  Allocates nothing; enqueued on `stream`. */
+fp_status fp_bfaces_refresh(fp_bfaces *b, void *stream);
 
 /* Interface-data pipeline helpers.
  * fp_bfaces_iface: number of interface nodes Mi and (if pts != NULL) their

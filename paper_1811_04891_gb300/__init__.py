@@ -94,6 +94,10 @@ def _load():
     L.fp_eval_df.restype = ci
     L.fp_find_eval.argtypes = [vp, i64, vp, vp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.fp_find_eval.restype = ci
+    L.fp_find_warm.argtypes = [vp, i64, vp, vp, vp, vp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.fp_find_warm.restype = ci
+    L.fp_update_coords.argtypes = [vp, vp, vp, ci, vp]
+    L.fp_update_coords.restype = ci
     L.fp_find_eval_ws.argtypes = [vp, vp, i64, vp, vp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.fp_find_eval_ws.restype = ci
     L.fp_bfaces_create.argtypes = [vp, vp, ctypes.POINTER(vp), vp]
@@ -110,6 +114,8 @@ def _load():
     L.fp_flux_correct_iface.restype = ci
     L.fp_bfaces_iface.argtypes = [vp, ctypes.POINTER(i64), vp, vp]
     L.fp_bfaces_iface.restype = ci
+    L.fp_bfaces_refresh.argtypes = [vp, vp]
+    L.fp_bfaces_refresh.restype = ci
     L.fp_extrapolate.argtypes = [ci, i64, ctypes.POINTER(vp), vp, vp]
     L.fp_extrapolate.restype = ci
     L.fp_eval.argtypes = [vp, i64, vp, vp, vp, ci, vp, vp, vp]
@@ -471,6 +477,47 @@ def fp_find_eval_ws(h: Handle, ws: "Workspace", pts: torch.Tensor, qsess: Option
     return code, sub, elem, rst, dist2, values
 
 
+UPDATE_DEFAULT_DIST = 1
+
+
+def fp_update_coords(h: Handle, coords: torch.Tensor, dist: Optional[torch.Tensor] = None,
+                     default_dist: bool = False, stream=None):
+    """Moving mesh: replace the node coordinates [3][E][(N+1)^3] of the
+    handle's mesh and rebuild boxes, hash grid and FP32 geometry in place.
+    `coords` may be a CUDA tensor or a CPU tensor (pinned for speed)."""
+    if not isinstance(coords, torch.Tensor) or coords.dtype != torch.float64 or not coords.is_contiguous():
+        raise TypeError("coords: expected a contiguous float64 tensor")
+    if tuple(coords.shape) != (3, h.E, (h.N + 1) ** 3):
+        raise ValueError("coords must be [3][E][(N+1)^3] of the handle's mesh")
+    dist = None if dist is None else _dev(dist, torch.float64, "dist")
+    st = lib().fp_update_coords(h.ptr, _ptr(coords), _ptr(dist), UPDATE_DEFAULT_DIST if default_dist else 0,
+                                _stream(stream))
+    _check(st, h.ptr)
+
+
+def fp_find_warm(h: Handle, pts: torch.Tensor, warm=None, qsess: Optional[torch.Tensor] = None, fields=None,
+                 posted: Optional["Fields"] = None, out=None, values: Optional[torch.Tensor] = None, stream=None):
+    """find (+ eval when fields or posted are given) with Newton warm-started
+    from `warm` = (elem [P], rst [3][P]) of an earlier find; `out` may be the
+    tuple that holds `warm` (in-place update).  Returns fp_find's tuple, plus
+    the values [F][P] when evaluating."""
+    pts = _dev(pts, torch.float64, "pts")
+    P = pts.shape[1]
+    qsess = None if qsess is None else _dev(qsess, torch.int32, "qsess")
+    we, wr = (None, None) if warm is None else (_dev(warm[0], torch.int32, "warm elem"),
+                                                _dev(warm[1], torch.float64, "warm rst"))
+    F, f64, fptr = (0, None, None) if fields is None and posted is None else _eval_args(fields, posted)
+    out = out or _find_outs(P, pts.device)
+    if F and values is None:
+        values = torch.empty((F, P), dtype=torch.float64, device=pts.device)
+    code, sub, elem, rst, dist2 = out
+    st = lib().fp_find_warm(h.ptr, P, _ptr(pts), _ptr(qsess), _ptr(we), _ptr(wr), F, _ptr(f64), fptr, _ptr(code),
+                            _ptr(sub), _ptr(elem), _ptr(rst), _ptr(dist2), _ptr(values if F else None),
+                            _stream(stream))
+    _check(st, h.ptr)
+    return (code, sub, elem, rst, dist2, values) if F else (code, sub, elem, rst, dist2)
+
+
 class BFaces:
     """Boundary-face quadrature of marked faces (fp_bfaces_*) for the
     mass-flux correction of interpolated interface data."""
@@ -491,9 +538,16 @@ class BFaces:
         lib().fp_bfaces_iface(self.ptr, ctypes.byref(mi), None, None)
         self.Mi = mi.value
 
-    def iface_points(self, device=None):
+    def refresh(self, stream=None):
+        """Recompute node positions, normals and weights after fp_update_coords."""
+        st = lib().fp_bfaces_refresh(self.ptr, _stream(stream))
+        if st != FP_OK:
+            raise FindptsError(st, "fp_bfaces_refresh failed")
+
+    def iface_points(self, device=None, out: Optional[torch.Tensor] = None):
         """Positions [3][Mi] of the interface nodes (listing order)."""
-        pts = torch.empty((3, self.Mi), dtype=torch.float64, device=device or torch.device("cuda"))
+        pts = out if out is not None else torch.empty((3, self.Mi), dtype=torch.float64,
+                                                      device=device or torch.device("cuda"))
         st = lib().fp_bfaces_iface(self.ptr, None, _ptr(pts), _stream(None))
         if st != FP_OK:
             raise FindptsError(st, "fp_bfaces_iface failed")

@@ -8,11 +8,15 @@
 //  4. k_ehist / scan / k_escatter   counting sort of the pairs by element, so
 //                      neighbouring threads work on the same element and its
 //                      geometry is served by broadcast loads from L1.
-//  5. k_newton<n,MIXED>  per pair: seed at the nearest mapped GLL node, then
+//  5. Newton         per pair: seed at the nearest mapped GLL node (or the
+//                      point's previous (e, r) on a moving mesh), then
 //                      box-constrained trust-region Newton on
-//                      ||x^e(r) - x*||^2; MIXED runs the seed and the early
-//                      iterations in FP32 on element-local coordinates and the
-//                      last step(s), the residual and the chord check in FP64.
+//                      ||x^e(r) - x*||^2.  FP64 form: k_newton<n>.  Mixed
+//                      form: k_newton_mixed<n> runs the seed and the early
+//                      iterations in FP32 on element-local coordinates, a
+//                      compensated refinement and one FP64 step;
+//                      k_newton64_full<n> finishes the pairs that step did
+//                      not confirm in full FP64.
 //  6. k_rank<n>        per point: classify its pairs (INSIDE / BORDER), lowest
 //                      element id within a subdomain, owner = argmax of the
 //                      interpolated distance field D^k with lower-id tie band.
@@ -453,9 +457,28 @@ struct NewtonArgs {
     int max_newton;
     unsigned long long* stats;  // optional path counters (profiling): [0] rejected after FP32,
                                 // [1] FP32 not converged, [2] FP64 step converged, [3] sent to the fallback
+    const int32_t* warm_elem;   // optional [P]: each point's element at the previous mesh position
+    const double* warm_rst;     // [3][P]: its reference coordinates there
 };
 
-template <int n, bool MIXED>
+// warm start (moving meshes): a pair whose element is the point's previous
+// element starts from the previous reference coordinates, clamped to the
+// reference cube, instead of the nearest node.  Only the start changes; a
+// non-finite previous value falls back to the nearest node.
+__device__ __forceinline__ bool warm_seed(const NewtonArgs& A, int64_t p, int e, double (&r)[3])
+{
+    if (!A.warm_elem || A.warm_elem[p] != e) return false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double v = A.warm_rst[a * A.P + p];
+        if (!(fabs(v) <= 2.0)) return false;
+        r[a] = fmin(1.0, fmax(-1.0, v));
+    }
+    return true;
+}
+
+// FP64 form: nearest-node (or warm) start, full FP64 trust-region Newton
+template <int n>
 __device__ __forceinline__ void solve_pair(const NewtonArgs& A, const BasisTab& tab, int64_t s)
 {
     constexpr int n3 = n * n * n;
@@ -466,35 +489,9 @@ __device__ __forceinline__ void solve_pair(const NewtonArgs& A, const BasisTab& 
     const ElemPtr<double> el64 = {A.coords + (int64_t)e * n3, A.coords + (A.E + e) * n3,
                                   A.coords + (2 * A.E + e) * n3};
     double r[3], J[9];
-    double res;
-    if (MIXED) {
-        const double* c = A.boxes[e].c;
-        const float xl[3] = {(float)(xs[0] - c[0]), (float)(xs[1] - c[1]), (float)(xs[2] - c[2])};
-        const ElemPtr<float> el32 = {A.coords32 + (int64_t)e * n3, A.coords32 + (A.E + e) * n3,
-                                     A.coords32 + (2 * A.E + e) * n3};
-        float r32[3], J32[9];
-        seed_nearest<n, float>(el32, tab, xl, r32);
-        bool conv32;
-        const float res32 = newton<n, float, false>(el32, tab, xl, r32, J32, A.max_newton, conv32);
-        r[0] = r32[0]; r[1] = r32[1]; r[2] = r32[2];
-        bool conv64;
-        if (conv32 && (double)res32 > A.reject32 * A.boxes[e].he) {
-            res = (double)res32;                   // converged well away from the element
-        } else if (!conv32) {
-            res = newton<n, double, true>(el64, tab, xs, r, J, A.max_newton, conv64);
-        } else {
-            // FP64 final steps: FP64 residuals and 3x3 solves, Jacobian from
-            // the FP32 phase (chord); full FP64 Newton if that stalls
-#pragma unroll
-            for (int q = 0; q < 9; ++q) J[q] = (double)J32[q];
-            if (!chord64<n>(el64, tab, xs, r, J, res, 4))
-                res = newton<n, double, true>(el64, tab, xs, r, J, A.max_newton, conv64);
-        }
-    } else {
-        seed_nearest<n, double>(el64, tab, xs, r);
-        bool conv64;
-        res = newton<n, double, true>(el64, tab, xs, r, J, A.max_newton, conv64);
-    }
+    if (!warm_seed(A, p, e, r)) seed_nearest<n, double>(el64, tab, xs, r);
+    bool conv64;
+    const double res = newton<n, double, true>(el64, tab, xs, r, J, A.max_newton, conv64);
     A.pres[q] = res;
     A.prst[q] = r[0];
     A.prst[A.cap + q] = r[1];
@@ -589,100 +586,6 @@ __device__ __forceinline__ void resid_df(const ElemPtr<float>& hi, const ElemPtr
     }
 }
 
-// ---- mixed form in three passes, so that the FP64 pipe sees uniform work ----
-// pass 1 (FP32): seed + FP32 Newton on element-local coordinates.  Writes the
-// FP32 solution to prst and its residual to pres, or -1 when the FP32 phase
-// did not converge (the pair then goes to the full FP64 Newton of pass 3).
-template <int n>
-__global__ void __launch_bounds__(256) k_newton32(NewtonArgs A, BasisTab tab)
-{
-    constexpr int n3 = n * n * n;
-    const int64_t npairs = live_pairs(A.dcount, A.cap);
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < npairs; s += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t q = A.order[s];
-        const int e = A.pair_elem[q];
-        const int64_t p = A.pair_pt[q];
-        const double* c = A.boxes[e].c;
-        const float xl[3] = {(float)(A.pts[p] - c[0]), (float)(A.pts[A.P + p] - c[1]),
-                             (float)(A.pts[2 * A.P + p] - c[2])};
-        const ElemPtr<float> el32 = {A.coords32 + (int64_t)e * n3, A.coords32 + (A.E + e) * n3,
-                                     A.coords32 + (2 * A.E + e) * n3};
-        float r32[3], J32[9];
-        seed_nearest<n, float>(el32, tab, xl, r32);
-        bool conv32;
-        const float res32 = newton<n, float, false>(el32, tab, xl, r32, J32, A.max_newton, conv32);
-        double r[3] = {r32[0], r32[1], r32[2]};
-        // refinement for interior solutions near the element: compensated FP32
-        // residuals and FP32 Jacobian steps, r carried in FP64
-        if (conv32 && (double)res32 <= A.reject32 * A.boxes[e].he && fabsf(r32[0]) < 1.0f &&
-            fabsf(r32[1]) < 1.0f && fabsf(r32[2]) < 1.0f) {
-            const ElemPtr<float> lo32 = {A.coords32lo + (int64_t)e * n3, A.coords32lo + (A.E + e) * n3,
-                                         A.coords32lo + (2 * A.E + e) * n3};
-            const double xd[3] = {A.pts[p] - c[0], A.pts[A.P + p] - c[1], A.pts[2 * A.P + p] - c[2]};
-            for (int it = 0; it < 2; ++it) {
-                float f[3], d[3];
-                resid_df<n>(el32, lo32, tab, r, xd, f);
-                if (!newton_solve3<float>(J32, f, d)) break;
-                double rn[3];
-                bool inside = true;
-#pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    rn[b] = r[b] + (double)d[b];
-                    inside = inside && fabs(rn[b]) < 1.0;
-                }
-                if (!inside) break;                          // the FP64 passes handle the bounds
-                r[0] = rn[0]; r[1] = rn[1]; r[2] = rn[2];
-                if (fmaxf(fabsf(d[0]), fmaxf(fabsf(d[1]), fabsf(d[2]))) <= 1e-14f) break;
-            }
-        }
-        A.prst[q] = r[0];
-        A.prst[A.cap + q] = r[1];
-        A.prst[2 * A.cap + q] = r[2];
-        A.pres[q] = conv32 ? (double)res32 : -1.0;
-    }
-}
-
-// pass 2 (FP64): every pair whose FP32 phase converged near the element takes
-// one FP64 Newton step -- FP64 residual and FP64 3x3 solve (active set) with
-// the FP32 Jacobian at the refined solution.  A step below 1e-13 confirms
-// convergence: r is kept with its FP64 residual.  Otherwise the step is
-// taken and the pair is marked for pass 3.  Pairs that converged well away
-// from the element keep their FP32 residual (they cannot be INSIDE or
-// BORDER).  Every pair does the same FP64 work, so warps stay full.
-template <int n>
-__global__ void __launch_bounds__(256) k_newton64_chord(NewtonArgs A, BasisTab tab)
-{
-    constexpr int n3 = n * n * n;
-    const int64_t npairs = live_pairs(A.dcount, A.cap);
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < npairs; s += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t q = A.order[s];
-        const double v = A.pres[q];
-        if (v < 0.0) continue;                                  // pass 3
-        const int e = A.pair_elem[q];
-        if (v > A.reject32 * A.boxes[e].he) continue;           // converged away from the element
-        const int64_t p = A.pair_pt[q];
-        const double xs[3] = {A.pts[p], A.pts[A.P + p], A.pts[2 * A.P + p]};
-        const double* c = A.boxes[e].c;
-        const float xl[3] = {(float)(xs[0] - c[0]), (float)(xs[1] - c[1]), (float)(xs[2] - c[2])};
-        const ElemPtr<float> el32 = {A.coords32 + (int64_t)e * n3, A.coords32 + (A.E + e) * n3,
-                                     A.coords32 + (2 * A.E + e) * n3};
-        const ElemPtr<double> el64 = {A.coords + (int64_t)e * n3, A.coords + (A.E + e) * n3,
-                                      A.coords + (2 * A.E + e) * n3};
-        double r[3] = {A.prst[q], A.prst[A.cap + q], A.prst[2 * A.cap + q]};
-        float r32[3] = {(float)r[0], (float)r[1], (float)r[2]}, f32[3], J32[9];
-        eval_fJ<n, float>(el32, tab, r32, xl, f32, J32);       // FP32 Jacobian at the refined solution
-        double J[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) J[k] = (double)J32[k];
-        double res;
-        const bool ok = chord64<n>(el64, tab, xs, r, J, res, 1);
-        A.prst[q] = r[0];
-        A.prst[A.cap + q] = r[1];
-        A.prst[2 * A.cap + q] = r[2];
-        A.pres[q] = ok ? res : -1.0;
-    }
-}
-
 // passes 1 and 2 in one kernel: the FP32 work of some warps overlaps the
 // FP64 work of others.
 template <int n>
@@ -701,7 +604,14 @@ __global__ void __launch_bounds__(256) k_newton_mixed(NewtonArgs A, BasisTab tab
         const ElemPtr<float> el32 = {A.coords32 + (int64_t)e * n3, A.coords32 + (A.E + e) * n3,
                                      A.coords32 + (2 * A.E + e) * n3};
         float r32[3], J32[9];
-        seed_nearest<n, float>(el32, tab, xl, r32);
+        {
+            double rw[3];
+            if (warm_seed(A, p, e, rw)) {
+                r32[0] = (float)rw[0]; r32[1] = (float)rw[1]; r32[2] = (float)rw[2];
+            } else {
+                seed_nearest<n, float>(el32, tab, xl, r32);
+            }
+        }
         bool conv32;
         const float res32 = newton<n, float, false>(el32, tab, xl, r32, J32, A.max_newton, conv32);
         double r[3] = {r32[0], r32[1], r32[2]};
@@ -787,12 +697,12 @@ __global__ void __launch_bounds__(256) k_newton64_full(NewtonArgs A, BasisTab ta
     }
 }
 
-template <int n, bool MIXED>
+template <int n>
 __global__ void __launch_bounds__(256) k_newton(NewtonArgs A, BasisTab tab)
 {
     const int64_t npairs = live_pairs(A.dcount, A.cap);
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < npairs; s += (int64_t)gridDim.x * blockDim.x)
-        solve_pair<n, MIXED>(A, tab, s);
+        solve_pair<n>(A, tab, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -1035,6 +945,8 @@ static cudaError_t solve_n(const FindArgs& a, int64_t npairs, const BasisTab& ta
         na.reject32 = 1e-4;
         na.max_newton = fp.max_newton;
         na.stats = a.stats;
+        na.warm_elem = a.warm_elem;
+        na.warm_rst = a.warm_rst;
         const unsigned grid = grid_for(npairs, block, a.persistent_blocks);
         if (a.ev[2]) cudaEventRecord(a.ev[2], s);
         if (fp.mixed) {
@@ -1042,7 +954,7 @@ static cudaError_t solve_n(const FindArgs& a, int64_t npairs, const BasisTab& ta
             k_newton64_full<n><<<grid, block, 0, s>>>(na, tab);
             count_launch(2);
         } else {
-            k_newton<n, false><<<grid, block, 0, s>>>(na, tab);
+            k_newton<n><<<grid, block, 0, s>>>(na, tab);
             count_launch();
         }
         cudaError_t err = cudaGetLastError();

@@ -43,6 +43,8 @@ struct fp_bfaces {
     double* partial = nullptr;    // [2 * nblk]
     double* result = nullptr;     // [3]: flux, area, gamma
     int nblk = 0;
+    int8_t* fkind = nullptr;      // [6E] copy of the caller's face marks (for fp_bfaces_refresh)
+    DerivTab tab{};
 };
 
 namespace fpg {
@@ -238,15 +240,34 @@ __global__ void k_flux_out(const double* __restrict__ result, double* gamma, dou
 static void bf_release(fp_bfaces* b)
 {
     cudaFree(b->ipos);
+    cudaFree(b->fkind);
     cudaFree(b->face); cudaFree(b->x); cudaFree(b->nrm); cudaFree(b->dA); cudaFree(b->kind);
     cudaFree(b->partial); cudaFree(b->result);
+}
+
+// node positions, normals and weights of the listed faces from the owner's
+// current coordinates
+static cudaError_t bf_geom(fp_bfaces* b, const fp_handle* h, const int8_t* kind, cudaStream_t s)
+{
+    if (b->M == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((b->M + 127) / 128);
+    switch (b->n) {
+#define FP_CASE(NN) \
+    case NN: k_bface_geom<NN><<<grid, 128, 0, s>>>(h->E, b->M, h->coords, h->boxes, kind, b->face, b->tab, b->x, b->nrm, b->dA, b->kind); break;
+        FP_CASE(2) FP_CASE(3) FP_CASE(4) FP_CASE(5) FP_CASE(6) FP_CASE(7) FP_CASE(8) FP_CASE(9)
+        FP_CASE(10) FP_CASE(11) FP_CASE(12) FP_CASE(13) FP_CASE(14) FP_CASE(15) FP_CASE(16)
+#undef FP_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    count_launch();
+    return cudaGetLastError();
 }
 
 extern "C" fp_status fp_bfaces_create(const fp_handle* h, const int8_t* kind, fp_bfaces** out, void* stream)
 {
     if (!out) return FP_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
     if (!kind) return FP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int n = h->n;
@@ -259,6 +280,8 @@ extern "C" fp_status fp_bfaces_create(const fp_handle* h, const int8_t* kind, fp
     cudaError_t e = cudaMalloc(&flag, sizeof(int32_t) * F);
     if (e == cudaSuccess) e = cudaMalloc(&off, sizeof(int32_t) * (F + 1));
     if (e == cudaSuccess) e = cudaMalloc(&tmp, sizeof(int32_t) * scan_tmp_elems(F));
+    if (e == cudaSuccess) e = cudaMalloc(&b->fkind, F);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->fkind, kind, F, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) {
         k_face_flags<<<(unsigned)((F + 255) / 256), 256, 0, s>>>(F, kind, flag);
         count_launch();
@@ -305,17 +328,8 @@ extern "C" fp_status fp_bfaces_create(const fp_handle* h, const int8_t* kind, fp
             const double PN = N == 0 ? 1.0 : p1;
             t.w[a] = 2.0 / (N * (N + 1.0) * PN * PN);
         }
-        const unsigned grid = (unsigned)((b->M + 127) / 128);
-        switch (n) {
-#define FP_CASE(NN) \
-    case NN: k_bface_geom<NN><<<grid, 128, 0, s>>>(h->E, b->M, h->coords, h->boxes, kind, b->face, t, b->x, b->nrm, b->dA, b->kind); break;
-            FP_CASE(2) FP_CASE(3) FP_CASE(4) FP_CASE(5) FP_CASE(6) FP_CASE(7) FP_CASE(8) FP_CASE(9)
-            FP_CASE(10) FP_CASE(11) FP_CASE(12) FP_CASE(13) FP_CASE(14) FP_CASE(15) FP_CASE(16)
-#undef FP_CASE
-            default: e = cudaErrorInvalidValue;
-        }
-        count_launch();
-        if (e == cudaSuccess) e = cudaGetLastError();
+        b->tab = t;
+        e = bf_geom(b, h, b->fkind, s);
     }
     // positions of the interface nodes among themselves (listing order)
     if (e == cudaSuccess) e = cudaMalloc(&b->ipos, sizeof(int32_t) * std::max<int64_t>(b->M, 1));
@@ -360,6 +374,13 @@ extern "C" void fp_bfaces_free(fp_bfaces* b)
     cudaDeviceSynchronize();
     bf_release(b);
     delete b;
+}
+
+extern "C" fp_status fp_bfaces_refresh(fp_bfaces* b, void* stream)
+{
+    if (!b) return FP_ERR_INVALID_ARG;
+    if (!fp_live(b->owner)) return FP_ERR_NOT_SETUP;
+    return bf_geom(b, b->owner, b->fkind, (cudaStream_t)stream) == cudaSuccess ? FP_OK : FP_ERR_CUDA;
 }
 
 extern "C" fp_status fp_bfaces_info(const fp_bfaces* b, int64_t* nfaces, int64_t* nnodes)

@@ -44,6 +44,19 @@ struct fp_handle {
     double* pres = nullptr;
     double* prst = nullptr;
     int32_t* h_total = nullptr;    // pinned host word for the pair count
+    // geometry scratch kept for fp_update_coords (moving meshes)
+    double* binv = nullptr;        // [n][n] inverse Bernstein-to-Lagrange matrix
+    double pad_conv = 0.0;         // hull padding for the rounding of the conversion
+    double hpad = 0.0;             // hash widening for FP32 lookups (mixed form)
+    double* nodebox = nullptr;     // [6E]
+    double* red = nullptr;         // [12 * nred]
+    int nred = 0;
+    int32_t* hcnt = nullptr;       // [ncell_cap] hash counts / fill cursor
+    int32_t* htmp = nullptr;       // scan scratch for ncell_cap cells
+    int32_t* flag = nullptr;       // [1] non-finite counter
+    int64_t ncell_cap = 0, nnz_cap = 0;
+    bool dist_default = false;     // dist was computed by the library (default field)
+    bool stale = false;            // a failed fp_update_coords left the geometry inconsistent
     int64_t last_pairs = 0;
     std::string err;
     // optional per-kernel timing with CUDA events on the launching stream
@@ -52,4 +65,7 @@ struct fp_handle {
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pend[PROF_KINDS];
 };
+
+// a handle that holds a complete, consistent mesh
+inline bool fp_live(const fp_handle* h) { return h && h->coords && !h->stale; }
 

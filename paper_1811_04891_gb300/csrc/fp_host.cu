@@ -2,6 +2,8 @@
 // resident mesh state, workspace, and the orchestration of the setup, find
 // and eval kernels.
 #include <math.h>
+
+#include <cmath>
 #include <stdio.h>
 #include <string.h>
 
@@ -184,6 +186,7 @@ void release(fp_handle* h)
     dfree(h->cell_start); dfree(h->cell_elems); dfree(h->ecount); dfree(h->estart); dfree(h->escan_tmp);
     dfree(h->cnt); dfree(h->off); dfree(h->scan_tmp); dfree(h->pair_elem); dfree(h->pair_pt);
     dfree(h->order); dfree(h->pres); dfree(h->prst);
+    dfree(h->binv); dfree(h->nodebox); dfree(h->red); dfree(h->hcnt); dfree(h->htmp); dfree(h->flag);
     if (h->h_total) cudaFreeHost(h->h_total);
     h->h_total = nullptr;
 }
@@ -227,6 +230,171 @@ fp_status grow_pairs(fp_handle* h, int64_t np)
 namespace fpg {
 cudaError_t launch_count_nonfinite(int64_t n, const double* x, int32_t* out, cudaStream_t s);
 }
+namespace {
+
+// A1 (element hulls), A2 (hash grid), the default distance field when asked
+// for, and the mixed form's element-local FP32 geometry, all from h->coords.
+// Used by fp_setup and by fp_update_coords; scratch lives in the handle and
+// only grows, so an update of a mesh whose hash needs no more room than
+// before allocates nothing.
+fp_status build_geometry(fp_handle* h, cudaStream_t s, bool default_dist)
+{
+    const int n = h->n, n3 = n * n * n;
+    const int64_t E = h->E;
+    const fp_opts& o = h->opts;
+    cudaError_t err;
+#define GK(call, where) do { if ((err = (call)) != cudaSuccess) return cuda_fail(h, err, where); } while (0)
+    if (!h->boxes) GK(dalloc(&h->boxes, E), "alloc boxes");
+    if (!h->nodebox) GK(dalloc(&h->nodebox, 6 * E), "alloc nodebox");
+    if (!h->red) {
+        h->nred = (int)std::min<int64_t>(1024, (E + 255) / 256);
+        GK(dalloc(&h->red, 12 * h->nred), "alloc red");
+    }
+    GK(launch_hull(n, E, h->coords, h->binv, o.tol_border, h->pad_conv, h->boxes, h->nodebox, s), "hull");
+    GK(launch_reduce_boxes(E, h->boxes, h->nodebox, h->red, h->nred, s), "reduce boxes");
+    std::vector<double> red(12 * h->nred);
+    GK(cudaMemcpyAsync(red.data(), h->red, sizeof(double) * 12 * h->nred, cudaMemcpyDeviceToHost, s), "read red");
+    GK(cudaStreamSynchronize(s), "sync hull");
+    double glo[3], ghi[3], nlo[3], nhi[3];
+    for (int a = 0; a < 3; ++a) {
+        glo[a] = INFINITY; ghi[a] = -INFINITY; nlo[a] = INFINITY; nhi[a] = -INFINITY;
+        for (int b = 0; b < h->nred; ++b) {
+            glo[a] = std::min(glo[a], red[12 * b + a]);
+            ghi[a] = std::max(ghi[a], red[12 * b + 3 + a]);
+            nlo[a] = std::min(nlo[a], red[12 * b + 6 + a]);
+            nhi[a] = std::max(nhi[a], red[12 * b + 9 + a]);
+        }
+    }
+    {
+        double dx = nhi[0] - nlo[0], dy = nhi[1] - nlo[1], dz = nhi[2] - nlo[2];
+        double sq = dx * dx;
+        sq = sq + dy * dy;
+        sq = sq + dz * dz;
+        h->L = sqrt(sq);
+    }
+
+    // A2: hash grid over the global padded box, widened by hpad, the margin
+    // that keeps FP32 cell lookups (mixed form) inside a listing cell
+    double hpad;
+    {
+        double xmax = 0.0, extm = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            xmax = std::max(xmax, std::max(fabs(glo[a]), fabs(ghi[a])));
+            extm = std::max(extm, ghi[a] - glo[a]);
+        }
+        hpad = 9.5367431640625e-07 * (2.0 * xmax + extm);   // 2^-20 (2 max|x| + extent)
+        for (int a = 0; a < 3; ++a) {
+            glo[a] -= hpad;
+            ghi[a] += hpad;
+        }
+    }
+    h->hpad = hpad;
+    {
+        double ext[3], vol = 1.0;
+        int nd = 0;
+        for (int a = 0; a < 3; ++a) {
+            ext[a] = ghi[a] - glo[a];
+            if (ext[a] > 0) { vol *= ext[a]; ++nd; }
+        }
+        double target = std::max(1.0, o.hash_cells_per_elem * (double)E);
+        double hc = nd > 0 ? pow(vol / target, 1.0 / nd) : 1.0;
+        int64_t dims[3];
+        for (int it = 0; it < 64; ++it) {
+            int64_t tot = 1;
+            for (int a = 0; a < 3; ++a) {
+                dims[a] = ext[a] > 0 ? std::max<int64_t>(1, (int64_t)ceil(ext[a] / hc)) : 1;
+                dims[a] = std::min<int64_t>(dims[a], 1 << 20);
+                tot *= dims[a];
+            }
+            if (tot <= (int64_t(1) << 26)) break;
+            hc *= 1.25;
+        }
+        for (int a = 0; a < 3; ++a) {
+            h->grid.org[a] = glo[a];
+            h->grid.dim[a] = (int)dims[a];
+            h->grid.inv[a] = ext[a] > 0 ? (double)dims[a] / ext[a] : 0.0;
+        }
+        h->grid.ncell = dims[0] * dims[1] * dims[2];
+    }
+    const int64_t ncell = h->grid.ncell;
+    if (ncell > h->ncell_cap) {
+        const int64_t cap = ncell + ncell / 8;
+        cudaStreamSynchronize(s);
+        dfree(h->hcnt); dfree(h->cell_start); dfree(h->htmp);
+        h->ncell_cap = 0;
+        GK(dalloc(&h->hcnt, cap), "alloc hash count");
+        GK(dalloc(&h->cell_start, cap + 1), "alloc cell start");
+        GK(dalloc(&h->htmp, scan_tmp_elems(cap)), "alloc scan tmp");
+        h->ncell_cap = cap;
+    }
+    GK(cudaMemsetAsync(h->hcnt, 0, sizeof(int32_t) * ncell, s), "zero hash count");
+    GK(launch_hash_count(E, h->boxes, h->grid, hpad, h->hcnt, s), "hash count");
+    GK(scan_exclusive(h->hcnt, h->cell_start, ncell, h->htmp, s), "hash scan");
+    GK(cudaMemcpyAsync(h->h_total, h->cell_start + ncell, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read nnz");
+    GK(cudaStreamSynchronize(s), "sync hash");
+    h->nnz = h->h_total[0];
+    if (h->nnz < 0) return fail(h, FP_ERR_INVALID_ARG, "hash grid overflow");
+    if (h->nnz > h->nnz_cap || !h->cell_elems) {
+        const int64_t cap = std::max<int64_t>(h->nnz + h->nnz / 8, 1);
+        dfree(h->cell_elems);
+        h->nnz_cap = 0;
+        GK(dalloc(&h->cell_elems, cap), "alloc cell elems");
+        h->nnz_cap = cap;
+    }
+    GK(cudaMemcpyAsync(h->hcnt, h->cell_start, sizeof(int32_t) * ncell, cudaMemcpyDeviceToDevice, s), "copy cursor");
+    GK(launch_hash_fill(E, h->boxes, h->grid, hpad, h->hcnt, h->cell_elems, s), "hash fill");
+    GK(launch_hash_sort(ncell, h->cell_start, h->cell_elems, s), "hash sort");
+
+    // default distance field for the owner rule
+    if (default_dist) {
+        double* fc = nullptr;
+        int32_t *nb = nullptr, *nboff = nullptr, *tmp2 = nullptr;
+        double* bx = nullptr;
+        int32_t* bs = nullptr;
+        auto cleanup = [&]() { dfree(fc); dfree(nb); dfree(nboff); dfree(tmp2); dfree(bx); dfree(bs); };
+#define DK(call, where) do { if ((err = (call)) != cudaSuccess) { cleanup(); return cuda_fail(h, err, where); } } while (0)
+        DK(cudaStreamSynchronize(s), "sync hash fill");
+        DK(dalloc(&fc, 72 * E), "alloc face corners");
+        DK(dalloc(&nb, 6 * E), "alloc face flags");
+        DK(dalloc(&nboff, 6 * E + 1), "alloc face offsets");
+        DK(dalloc(&tmp2, scan_tmp_elems(6 * E)), "alloc face scan");
+        DK(launch_face_corners(n, E, h->coords, fc, s), "face corners");
+        DK(launch_face_boundary(E, fc, h->sub, h->grid, h->cell_start, h->cell_elems, nb, s), "face boundary");
+        DK(scan_exclusive(nb, nboff, 6 * E, tmp2, s), "face scan");
+        DK(cudaMemcpyAsync(h->h_total, nboff + 6 * E, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read nbnd");
+        DK(cudaStreamSynchronize(s), "sync faces");
+        const int64_t nbf = h->h_total[0];
+        const int64_t nbn = nbf * n * n;
+        if ((double)E * n3 * (double)nbn > 137438953472.0) {   // 2^37 node x boundary-node pairs
+            cleanup();
+            return fail(h, FP_ERR_INVALID_ARG, "mesh too large for the default distance field; pass dist");
+        }
+        DK(dalloc(&bx, 3 * std::max<int64_t>(nbn, 1)), "alloc boundary nodes");
+        DK(dalloc(&bs, std::max<int64_t>(nbn, 1)), "alloc boundary subs");
+        if (!h->dist) DK(dalloc(&h->dist, (size_t)E * n3), "alloc dist");
+        DK(launch_face_gather(n, E, h->coords, h->sub, nboff, bx, bs, nbn, s), "face gather");
+        DK(launch_dist_default(n, E, h->coords, h->sub, bx, bs, nbn, h->dist, s), "dist default");
+        DK(cudaStreamSynchronize(s), "sync dist");
+        cleanup();
+#undef DK
+        h->dist_default = true;
+    }
+
+    // mixed form: element-local FP32 geometry
+    if (o.precision == FP_PREC_MIXED) {
+        const size_t ncoord = (size_t)3 * E * n3;
+        if (!h->coords32) GK(dalloc(&h->coords32, ncoord), "alloc coords32");
+        if (!h->coords32lo) GK(dalloc(&h->coords32lo, ncoord), "alloc coords32lo");
+        if (!h->boxes32) GK(dalloc(&h->boxes32, E), "alloc boxes32");
+        GK(launch_local32(n, E, h->coords, h->boxes, h->coords32, s), "local32");
+        GK(launch_local32lo(n, E, h->coords, h->boxes, h->coords32, h->coords32lo, s), "local32lo");
+        GK(launch_box32(E, h->boxes, h->boxes32, s), "box32");
+    }
+#undef GK
+    return FP_OK;
+}
+}  // namespace
+
 
 extern "C" {
 
@@ -298,13 +466,11 @@ fp_status fp_setup(fp_handle** hout, const double* coords, int64_t E, int N, con
 
     // validation: finite coordinates, subdomain ids in range
     {
-        int32_t* d_bad;
-        CK(dalloc(&d_bad, 1), "alloc flag");
-        cudaMemsetAsync(d_bad, 0, sizeof(int32_t), s);
-        err = launch_count_nonfinite((int64_t)ncoord, h->coords, d_bad, s);
-        if (err == cudaSuccess) err = cudaMemcpyAsync(h->h_total, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        CK(dalloc(&h->flag, 1), "alloc flag");
+        CK(cudaMemsetAsync(h->flag, 0, sizeof(int32_t), s), "zero flag");
+        err = launch_count_nonfinite((int64_t)ncoord, h->coords, h->flag, s);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(h->h_total, h->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (err == cudaSuccess) err = cudaStreamSynchronize(s);
-        cudaFree(d_bad);
         CK(err, "check coords");
         if (h->h_total[0] != 0) BAD("fp_setup: non-finite coordinates");
         std::vector<int32_t> hs(E);
@@ -318,153 +484,30 @@ fp_status fp_setup(fp_handle** hout, const double* coords, int64_t E, int N, con
         h->nsub = ns;
     }
 
-    // A1: hulls
-    std::vector<double> binv;
-    double binv_norm = 1.0;
     {
         double xi[NMAX];
+        std::vector<double> binv;
         for (int i = 0; i < n; ++i) xi[i] = h->tab.xi[i];
+        double binv_norm = 1.0;
         if (!bernstein_inverse(N, xi, binv, &binv_norm)) BAD("fp_setup: Bernstein matrix singular");
+        h->pad_conv = 64.0 * 2.220446049250313e-16 * binv_norm * n;
+        CK(dalloc(&h->binv, binv.size()), "alloc binv");
+        CK(cudaMemcpyAsync(h->binv, binv.data(), sizeof(double) * binv.size(), cudaMemcpyHostToDevice, s),
+           "copy binv");
+        CK(cudaStreamSynchronize(s), "sync binv");
     }
-    double* d_binv = nullptr;
-    double* d_nodebox = nullptr;
-    CK(dalloc(&d_binv, binv.size()), "alloc binv");
-    CK(cudaMemcpyAsync(d_binv, binv.data(), sizeof(double) * binv.size(), cudaMemcpyHostToDevice, s), "copy binv");
-    CK(dalloc(&h->boxes, E), "alloc boxes");
-    CK(dalloc(&d_nodebox, 6 * E), "alloc nodebox");
-    const double pad_conv = 64.0 * 2.220446049250313e-16 * binv_norm * n;
-    CK(launch_hull(n, E, h->coords, d_binv, o.tol_border, pad_conv, h->boxes, d_nodebox, s), "hull");
-    const int nred = (int)std::min<int64_t>(1024, (E + 255) / 256);
-    double* d_red = nullptr;
-    CK(dalloc(&d_red, 12 * nred), "alloc red");
-    CK(launch_reduce_boxes(E, h->boxes, d_nodebox, d_red, nred, s), "reduce boxes");
-    std::vector<double> red(12 * nred);
-    CK(cudaMemcpyAsync(red.data(), d_red, sizeof(double) * 12 * nred, cudaMemcpyDeviceToHost, s), "read red");
-    CK(cudaStreamSynchronize(s), "sync hull");
-    cudaFree(d_red);
-    cudaFree(d_binv);
-    cudaFree(d_nodebox);
-    double glo[3], ghi[3], nlo[3], nhi[3];
-    for (int a = 0; a < 3; ++a) {
-        glo[a] = INFINITY; ghi[a] = -INFINITY; nlo[a] = INFINITY; nhi[a] = -INFINITY;
-        for (int b = 0; b < nred; ++b) {
-            glo[a] = std::min(glo[a], red[12 * b + a]);
-            ghi[a] = std::max(ghi[a], red[12 * b + 3 + a]);
-            nlo[a] = std::min(nlo[a], red[12 * b + 6 + a]);
-            nhi[a] = std::max(nhi[a], red[12 * b + 9 + a]);
-        }
-    }
-    {
-        double dx = nhi[0] - nlo[0], dy = nhi[1] - nlo[1], dz = nhi[2] - nlo[2];
-        double sq = dx * dx;
-        sq = sq + dy * dy;
-        sq = sq + dz * dz;
-        h->L = sqrt(sq);
-    }
-
-    // A2: hash grid over the global padded box, widened by hpad, the margin
-    // that keeps FP32 cell lookups (mixed form) inside a listing cell
-    double hpad;
-    {
-        double xmax = 0.0, extm = 0.0;
-        for (int a = 0; a < 3; ++a) {
-            xmax = std::max(xmax, std::max(fabs(glo[a]), fabs(ghi[a])));
-            extm = std::max(extm, ghi[a] - glo[a]);
-        }
-        hpad = 9.5367431640625e-07 * (2.0 * xmax + extm);   // 2^-20 (2 max|x| + extent)
-        for (int a = 0; a < 3; ++a) {
-            glo[a] -= hpad;
-            ghi[a] += hpad;
-        }
-    }
-    {
-        double ext[3], vol = 1.0;
-        int nd = 0;
-        for (int a = 0; a < 3; ++a) {
-            ext[a] = ghi[a] - glo[a];
-            if (ext[a] > 0) { vol *= ext[a]; ++nd; }
-        }
-        double target = std::max(1.0, o.hash_cells_per_elem * (double)E);
-        double hc = nd > 0 ? pow(vol / target, 1.0 / nd) : 1.0;
-        int64_t dims[3];
-        for (int it = 0; it < 64; ++it) {
-            int64_t tot = 1;
-            for (int a = 0; a < 3; ++a) {
-                dims[a] = ext[a] > 0 ? std::max<int64_t>(1, (int64_t)ceil(ext[a] / hc)) : 1;
-                dims[a] = std::min<int64_t>(dims[a], 1 << 20);
-                tot *= dims[a];
-            }
-            if (tot <= (int64_t(1) << 26)) break;
-            hc *= 1.25;
-        }
-        for (int a = 0; a < 3; ++a) {
-            h->grid.org[a] = glo[a];
-            h->grid.dim[a] = (int)dims[a];
-            h->grid.inv[a] = ext[a] > 0 ? (double)dims[a] / ext[a] : 0.0;
-        }
-        h->grid.ncell = dims[0] * dims[1] * dims[2];
-    }
-    const int64_t ncell = h->grid.ncell;
-    int32_t *d_cnt = nullptr, *d_tmp = nullptr;
-    CK(dalloc(&d_cnt, ncell), "alloc hash count");
-    CK(dalloc(&h->cell_start, ncell + 1), "alloc cell start");
-    CK(dalloc(&d_tmp, scan_tmp_elems(ncell)), "alloc scan tmp");
-    CK(cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * ncell, s), "zero hash count");
-    CK(launch_hash_count(E, h->boxes, h->grid, hpad, d_cnt, s), "hash count");
-    CK(scan_exclusive(d_cnt, h->cell_start, ncell, d_tmp, s), "hash scan");
-    CK(cudaMemcpyAsync(h->h_total, h->cell_start + ncell, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read nnz");
-    CK(cudaStreamSynchronize(s), "sync hash");
-    h->nnz = h->h_total[0];
-    if (h->nnz < 0) BAD("fp_setup: hash grid overflow");
-    CK(dalloc(&h->cell_elems, h->nnz), "alloc cell elems");
-    CK(cudaMemcpyAsync(d_cnt, h->cell_start, sizeof(int32_t) * ncell, cudaMemcpyDeviceToDevice, s), "copy cursor");
-    CK(launch_hash_fill(E, h->boxes, h->grid, hpad, d_cnt, h->cell_elems, s), "hash fill");
-    CK(launch_hash_sort(ncell, h->cell_start, h->cell_elems, s), "hash sort");
-    CK(cudaStreamSynchronize(s), "sync hash fill");
-    cudaFree(d_cnt);
-    cudaFree(d_tmp);
-
-    // distance field for the owner rule
     if (dist) {
         CK(dalloc(&h->dist, (size_t)E * n3), "alloc dist");
         CK(cudaMemcpyAsync(h->dist, dist, sizeof(double) * E * n3, cudaMemcpyDefault, s), "copy dist");
-    } else if (h->nsub > 1) {
-        double* fc = nullptr;
-        int32_t *nb = nullptr, *nboff = nullptr, *tmp2 = nullptr;
-        CK(dalloc(&fc, 72 * E), "alloc face corners");
-        CK(dalloc(&nb, 6 * E), "alloc face flags");
-        CK(dalloc(&nboff, 6 * E + 1), "alloc face offsets");
-        CK(dalloc(&tmp2, scan_tmp_elems(6 * E)), "alloc face scan");
-        CK(launch_face_corners(n, E, h->coords, fc, s), "face corners");
-        CK(launch_face_boundary(E, fc, h->sub, h->grid, h->cell_start, h->cell_elems, nb, s), "face boundary");
-        CK(scan_exclusive(nb, nboff, 6 * E, tmp2, s), "face scan");
-        CK(cudaMemcpyAsync(h->h_total, nboff + 6 * E, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read nbnd");
-        CK(cudaStreamSynchronize(s), "sync faces");
-        const int64_t nbf = h->h_total[0];
-        const int64_t nbn = nbf * n * n;
-        if ((double)E * n3 * (double)nbn > 137438953472.0) {   // 2^37 node x boundary-node pairs
-            cudaFree(fc); cudaFree(nb); cudaFree(nboff); cudaFree(tmp2);
-            BAD("fp_setup: mesh too large for the default distance field; pass dist");
-        }
-        double* bx = nullptr;
-        int32_t* bs = nullptr;
-        CK(dalloc(&bx, 3 * std::max<int64_t>(nbn, 1)), "alloc boundary nodes");
-        CK(dalloc(&bs, std::max<int64_t>(nbn, 1)), "alloc boundary subs");
-        CK(dalloc(&h->dist, (size_t)E * n3), "alloc dist");
-        CK(launch_face_gather(n, E, h->coords, h->sub, nboff, bx, bs, nbn, s), "face gather");
-        CK(launch_dist_default(n, E, h->coords, h->sub, bx, bs, nbn, h->dist, s), "dist default");
-        CK(cudaStreamSynchronize(s), "sync dist");
-        cudaFree(fc); cudaFree(nb); cudaFree(nboff); cudaFree(tmp2); cudaFree(bx); cudaFree(bs);
     }
-
-    // mixed form: element-local FP32 geometry
-    if (o.precision == FP_PREC_MIXED) {
-        CK(dalloc(&h->coords32, ncoord), "alloc coords32");
-        CK(launch_local32(n, E, h->coords, h->boxes, h->coords32, s), "local32");
-        CK(dalloc(&h->coords32lo, ncoord), "alloc coords32lo");
-        CK(launch_local32lo(n, E, h->coords, h->boxes, h->coords32, h->coords32lo, s), "local32lo");
-        CK(dalloc(&h->boxes32, E), "alloc boxes32");
-        CK(launch_box32(E, h->boxes, h->boxes32, s), "box32");
+    {
+        fp_status st = build_geometry(h, s, !dist && h->nsub > 1);
+        if (st != FP_OK) {
+            g_setup_err = h->err;
+            release(h);
+            delete h;
+            return st;
+        }
     }
     CK(dalloc(&h->ecount, E), "alloc ecount");
     CK(dalloc(&h->estart, E + 1), "alloc estart");
@@ -477,7 +520,7 @@ fp_status fp_setup(fp_handle** hout, const double* coords, int64_t E, int N, con
 
 fp_status fp_reserve(fp_handle* h, int64_t P)
 {
-    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
     if (P < 0) return fail(h, FP_ERR_INVALID_ARG, "fp_reserve: P < 0");
     fp_status st = grow_points(h, P);
     if (st != FP_OK) return st;
@@ -485,7 +528,8 @@ fp_status fp_reserve(fp_handle* h, int64_t P)
 }
 
 static fp_status find_impl(fp_handle* h, int64_t P, const double* pts, const int32_t* qsess, int32_t* code,
-                           int32_t* sub, int32_t* elem, double* rst, double* dist2, const EvalSpec& ev, void* stream)
+                           int32_t* sub, int32_t* elem, double* rst, double* dist2, const EvalSpec& ev, void* stream,
+                           const int32_t* warm_elem = nullptr, const double* warm_rst = nullptr)
 {
     if (P < 0 || P >= (int64_t(1) << 31)) return fail(h, FP_ERR_INVALID_ARG, "fp_find: P out of range");
     if (P == 0) return FP_OK;
@@ -505,6 +549,8 @@ static fp_status find_impl(fp_handle* h, int64_t P, const double* pts, const int
     a.code = code; a.osub = sub; a.oelem = elem; a.rst = rst; a.dist2 = dist2;
     a.eval = ev;
     a.stats = h->prof ? h->stats : nullptr;
+    a.warm_elem = warm_elem;
+    a.warm_rst = warm_rst;
     cudaEvent_t scr0 = nullptr, scr1 = nullptr;
     if (h->prof) {
         for (int q = 0; q < (ev.F > 0 ? 8 : 6); ++q) a.ev[q] = ev_get(h);
@@ -558,7 +604,7 @@ static fp_status find_impl(fp_handle* h, int64_t P, const double* pts, const int
 fp_status fp_find(fp_handle* h, int64_t P, const double* pts, const int32_t* qsess, int32_t* code, int32_t* sub,
                   int32_t* elem, double* rst, double* dist2, void* stream)
 {
-    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
     h->err.clear();
     EvalSpec ev{0, nullptr, nullptr, nullptr};
     return find_impl(h, P, pts, qsess, code, sub, elem, rst, dist2, ev, stream);
@@ -592,12 +638,73 @@ fp_status fp_find_eval(fp_handle* h, int64_t P, const double* pts, const int32_t
                        const fp_fields* posted, int32_t* code, int32_t* sub, int32_t* elem, double* rst, double* dist2,
                        double* out, void* stream)
 {
-    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
     h->err.clear();
     EvalSpec ev;
     fp_status st = eval_spec(h, F, fields, posted, out, &ev);
     if (st != FP_OK) return st;
     return find_impl(h, P, pts, qsess, code, sub, elem, rst, dist2, ev, stream);
+}
+
+fp_status fp_find_warm(fp_handle* h, int64_t P, const double* pts, const int32_t* qsess, const int32_t* warm_elem,
+                       const double* warm_rst, int F, const double* fields, const fp_fields* posted, int32_t* code,
+                       int32_t* sub, int32_t* elem, double* rst, double* dist2, double* out, void* stream)
+{
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
+    h->err.clear();
+    if ((warm_elem == nullptr) != (warm_rst == nullptr))
+        return fail(h, FP_ERR_INVALID_ARG, "fp_find_warm: warm_elem and warm_rst must both be given or both be null");
+    EvalSpec ev{0, nullptr, nullptr, nullptr};
+    if (F != 0 || posted) {
+        fp_status st = eval_spec(h, F, fields, posted, out, &ev);
+        if (st != FP_OK) return st;
+    }
+    return find_impl(h, P, pts, qsess, code, sub, elem, rst, dist2, ev, stream, warm_elem, warm_rst);
+}
+
+fp_status fp_update_coords(fp_handle* h, const double* coords, const double* dist, int flags, void* stream)
+{
+    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    h->err.clear();
+    if (!coords) return fail(h, FP_ERR_INVALID_ARG, "fp_update_coords: null coords");
+    if ((flags & ~FP_UPDATE_DEFAULT_DIST) != 0 || (dist && (flags & FP_UPDATE_DEFAULT_DIST)))
+        return fail(h, FP_ERR_INVALID_ARG, "fp_update_coords: bad flags");
+    const int n3 = h->n * h->n * h->n;
+    const size_t ncoord = (size_t)3 * h->E * n3;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t err;
+    // validate the new coordinates before the handle changes
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, coords) != cudaSuccess) {
+        cudaGetLastError();
+        at.type = cudaMemoryTypeUnregistered;
+    }
+    int64_t bad = 0;
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+        err = cudaMemsetAsync(h->flag, 0, sizeof(int32_t), s);
+        if (err == cudaSuccess) err = launch_count_nonfinite((int64_t)ncoord, coords, h->flag, s);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(h->h_total, h->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+        if (err != cudaSuccess) return cuda_fail(h, err, "fp_update_coords: check coords");
+        bad = h->h_total[0];
+    } else {
+        for (size_t i = 0; i < ncoord; ++i) bad += !std::isfinite(coords[i]);
+    }
+    if (bad) return fail(h, FP_ERR_INVALID_ARG, "fp_update_coords: non-finite coordinates");
+    h->stale = true;
+    err = cudaMemcpyAsync(h->coords, coords, sizeof(double) * ncoord, cudaMemcpyDefault, s);
+    if (err != cudaSuccess) return cuda_fail(h, err, "fp_update_coords: copy coords");
+    if (dist) {
+        if (!h->dist && (err = dalloc(&h->dist, (size_t)h->E * n3)) != cudaSuccess)
+            return cuda_fail(h, err, "fp_update_coords: alloc dist");
+        err = cudaMemcpyAsync(h->dist, dist, sizeof(double) * h->E * n3, cudaMemcpyDefault, s);
+        if (err != cudaSuccess) return cuda_fail(h, err, "fp_update_coords: copy dist");
+        h->dist_default = false;
+    }
+    fp_status st = build_geometry(h, s, (flags & FP_UPDATE_DEFAULT_DIST) && h->nsub > 1);
+    if (st != FP_OK) return st;
+    h->stale = false;
+    return FP_OK;
 }
 
 struct fp_workspace {
@@ -620,7 +727,7 @@ fp_status fp_workspace_create(const fp_handle* h, int64_t max_points, int64_t ma
 {
     if (!out) return FP_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
     if (max_points < 1 || max_points >= (int64_t(1) << 31)) return FP_ERR_INVALID_ARG;
     if (max_pairs <= 0) max_pairs = 2 * max_points;
     if (max_pairs >= (int64_t(1) << 31)) return FP_ERR_INVALID_ARG;
@@ -709,7 +816,7 @@ static fp_status find_ws_impl(fp_handle* h, fp_workspace* w, int64_t P, const do
 fp_status fp_find_ws(fp_handle* h, fp_workspace* w, int64_t P, const double* pts, const int32_t* qsess,
                      int32_t* code, int32_t* sub, int32_t* elem, double* rst, double* dist2, void* stream)
 {
-    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
     h->err.clear();
     EvalSpec ev{0, nullptr, nullptr, nullptr};
     return find_ws_impl(h, w, P, pts, qsess, code, sub, elem, rst, dist2, ev, stream);
@@ -719,7 +826,7 @@ fp_status fp_find_eval_ws(fp_handle* h, fp_workspace* w, int64_t P, const double
                           const double* fields, const fp_fields* posted, int32_t* code, int32_t* sub, int32_t* elem,
                           double* rst, double* dist2, double* out, void* stream)
 {
-    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
     h->err.clear();
     EvalSpec ev;
     fp_status st = eval_spec(h, F, fields, posted, out, &ev);
@@ -731,7 +838,7 @@ fp_status fp_fields_create(const fp_handle* h, int F, const double* fields, fp_f
 {
     if (!out) return FP_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
     if (F < 1 || !fields) return FP_ERR_INVALID_ARG;
     const int64_t n = (int64_t)F * h->E * h->n * h->n * h->n;
     fp_fields* f = new fp_fields();
@@ -759,7 +866,7 @@ void fp_fields_free(fp_fields* f)
 fp_status fp_eval_df(fp_handle* h, const fp_fields* f, int64_t P, const int32_t* code, const int32_t* elem,
                      const double* rst, double* out, void* stream)
 {
-    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
     h->err.clear();
     if (!f || f->owner != h) return fail(h, FP_ERR_INVALID_ARG, "fp_eval_df: fields posted for another handle");
     if (P < 0) return fail(h, FP_ERR_INVALID_ARG, "fp_eval_df: P < 0");
@@ -783,7 +890,7 @@ fp_status fp_eval_df(fp_handle* h, const fp_fields* f, int64_t P, const int32_t*
 fp_status fp_eval(fp_handle* h, int64_t P, const int32_t* code, const int32_t* elem, const double* rst, int F,
                   const double* fields, double* out, void* stream)
 {
-    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
     h->err.clear();
     if (P < 0 || F < 1) return fail(h, FP_ERR_INVALID_ARG, "fp_eval: P < 0 or F < 1");
     if (P == 0) return FP_OK;
@@ -815,7 +922,7 @@ void fp_free(fp_handle* h)
 
 fp_status fp_profile(fp_handle* h, int enable)
 {
-    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
     h->prof = enable != 0;
     if (h->prof && !h->stats) {
         cudaError_t e = dalloc(&h->stats, 4);
@@ -827,7 +934,7 @@ fp_status fp_profile(fp_handle* h, int enable)
 
 fp_status fp_profile_read(fp_handle* h, int kind, double* total_ms, int64_t* launches)
 {
-    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
     if (kind < 0 || kind >= PROF_KINDS) return fail(h, FP_ERR_INVALID_ARG, "fp_profile_read: kind out of range");
     double tot = 0.0;
     int64_t cnt = 0;
@@ -851,14 +958,14 @@ int64_t fp_launch_count(void) { return fpg::g_launches.load(); }
 
 fp_status fp_last_find_stats(const fp_handle* h, int64_t* npairs)
 {
-    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
     if (npairs) *npairs = h->last_pairs;
     return FP_OK;
 }
 
 fp_status fp_newton_paths(fp_handle* h, int64_t* counts)
 {
-    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
     unsigned long long c[4] = {0, 0, 0, 0};
     if (h->stats) {
         cudaError_t e = cudaDeviceSynchronize();
@@ -872,7 +979,7 @@ fp_status fp_newton_paths(fp_handle* h, int64_t* counts)
 
 fp_status fp_info(const fp_handle* h, int64_t* E, int* N, int64_t* ncell, int64_t* nnz, int* nsub)
 {
-    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
     if (E) *E = h->E;
     if (N) *N = h->N;
     if (ncell) *ncell = h->grid.ncell;
@@ -884,7 +991,7 @@ fp_status fp_info(const fp_handle* h, int64_t* E, int* N, int64_t* ncell, int64_
 fp_status fp_debug_boxes(const fp_handle* h, double* aabb, double* grid, int32_t* cell_start, int32_t* cell_elems,
                          void* stream)
 {
-    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t err = cudaSuccess;
     if (aabb) {

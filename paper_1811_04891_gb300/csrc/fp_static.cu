@@ -91,7 +91,7 @@ extern "C" fp_status fp_find_static(fp_handle* h, int64_t P, const double* pts, 
                                     int32_t* sub, int32_t* elem, double* rst, double* dist2, void* stream)
 {
     using namespace fpg;
-    if (!h || !h->coords) return FP_ERR_NOT_SETUP;
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
     h->err.clear();
     if (P < 0 || P > kMaxPoints) {
         h->err = "fp_find_static: P must be in [0, FP_STATIC_MAX_POINTS = 16384]";

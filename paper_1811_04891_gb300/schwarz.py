@@ -43,9 +43,21 @@ class InterfaceExchange:
 
     def locate(self):
         """(Re)locate the interface points in the donors (after mesh motion)."""
-        self.found = fg.fp_find_eval(self.h, self.pts, self.qs, fields=self.fields, posted=self.posted,
-                                     values=self.vals)
+        self.found = fg.fp_find_eval(self.h, self.pts, self.qs, fields=None if self.posted else self.fields,
+                                     posted=self.posted, values=self.vals)
         self.graph = None
+
+    def move(self, coords: torch.Tensor, dist: Optional[torch.Tensor] = None):
+        """The meshes moved (Sec. 1: donors are found again after every step
+        on moving meshes): post the new coordinates, refresh the face
+        geometry and the interface points, and relocate them warm-started
+        from the previous donors.  Results are written into the buffers the
+        captured sub-iteration reads, so the graph stays valid."""
+        fg.fp_update_coords(self.h, coords, dist)
+        self.bf.refresh()
+        self.bf.iface_points(out=self.pts)
+        fg.fp_find_warm(self.h, self.pts, warm=(self.found[2], self.found[3]), qsess=self.qs, fields=self.fields,
+                        posted=self.posted, out=self.found[:5], values=self.vals)
 
     def _correct_eager(self):
         code, elem, rst = self.found[0], self.found[2], self.found[3]

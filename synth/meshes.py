@@ -32,7 +32,7 @@ __all__ = [
     "box_distance", "annulus_distance", "uniform_points", "near_face_points",
     "boundary_face_nodes", "field_u", "sine_product_field", "random_poly_field",
     "config0", "config1", "config2", "config3", "config4_mesh", "config4_requests",
-    "tiny_overlap", "spiral_element", "reference_poly_field",
+    "tiny_overlap", "spiral_element", "reference_poly_field", "rigid_motion",
 ]
 
 
@@ -504,3 +504,20 @@ def spiral_element(N=15):
     X = amap(R, S, T)                                       # [3][i][j][k]
     coords = np.ascontiguousarray(X.transpose(0, 3, 2, 1).reshape(3, 1, n ** 3))
     return coords, amap
+
+
+def rigid_motion(coords: np.ndarray, sub: np.ndarray, moving: int, angle_deg: float = 0.0,
+                 shift=(0.0, 0.0, 0.0), center=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """Coordinates after the elements of subdomain `moving` turn by angle_deg
+    about the z axis through `center` and then shift by `shift` (a moving
+    mesh); the other elements stay.  Returns a new [3][E][n^3] array."""
+    out = np.array(coords, dtype=np.float64, copy=True)
+    m = np.asarray(sub) == moving
+    a = np.deg2rad(angle_deg)
+    c, s = np.cos(a), np.sin(a)
+    x = out[0, m] - center[0]
+    y = out[1, m] - center[1]
+    out[0, m] = center[0] + c * x - s * y + shift[0]
+    out[1, m] = center[1] + s * x + c * y + shift[1]
+    out[2, m] = out[2, m] + shift[2]
+    return out
