@@ -78,6 +78,11 @@ def lib():
         _lib.or_bfaces.argtypes = [ctypes.c_int, i64, dp, i8p, dp, dp, dp, i8p]
         _lib.or_bfaces.restype = i64
         _lib.or_flux_correct.argtypes = [i64, dp, dp, dp, i8p, dp, dp, dp]
+        _lib.or_find_d.argtypes = [ctypes.c_int] + list(_lib.or_find.argtypes)
+        _lib.or_find_d.restype = i64
+        _lib.or_eval_d.argtypes = [ctypes.c_int] + list(_lib.or_eval.argtypes)
+        _lib.or_map_d.argtypes = [ctypes.c_int] + list(_lib.or_map.argtypes)
+        _lib.or_dist_default_2d.argtypes = [ctypes.c_int, i64, dp, ip, dp]
     return _lib
 
 
@@ -120,21 +125,25 @@ def lagrange(N: int, r: float):
 
 
 def map_points(coords, N: int, e: int, r):
-    """x^e(r) and J for reference points r [3][M]; returns ([3][M], [9][M])."""
+    """x^e(r) and J for reference points r [d][M] on a d-dimensional mesh
+    (coords [d][E][n^d], d = 2 or 3); returns ([d][M], [d*d][M])."""
     coords = _f64(coords)
+    d = coords.shape[0]
     r = _f64(r)
     M = r.shape[1]
-    x = np.zeros((3, M))
-    J = np.zeros((9, M))
-    lib().or_map(N, _d(coords), coords.shape[1], int(e), M, _d(r), _d(x), _d(J))
+    x = np.zeros((d, M))
+    J = np.zeros((d * d, M))
+    lib().or_map_d(d, N, _d(coords), coords.shape[1], int(e), M, _d(r), _d(x), _d(J))
     return x, J
 
 
 def find(coords, N: int, sub, pts, qsess=None, dist=None, params: Params | None = None):
-    """Brute-force findpts.  Returns dict(code, sub, elem, rst [3][P], dist2,
-    bad_prefilter)."""
+    """Brute-force findpts on a hex (coords [3][E][n^3], pts [3][P]) or quad
+    (coords [2][E][n^2], pts [2][P]) mesh.  Returns dict(code, sub, elem,
+    rst [d][P], dist2, bad_prefilter)."""
     prm = params or Params()
     coords = _f64(coords)
+    dim = coords.shape[0]
     E = coords.shape[1]
     sub = _i32(sub)
     pts = _f64(pts)
@@ -144,11 +153,13 @@ def find(coords, N: int, sub, pts, qsess=None, dist=None, params: Params | None 
     code = np.zeros(P, np.int32)
     osub = np.zeros(P, np.int32)
     oel = np.zeros(P, np.int32)
-    rst = np.zeros((3, P))
+    rst = np.zeros((dim, P))
     d2 = np.zeros(P)
     cp = _Params(prm.tol_accept, prm.tol_border, prm.tie_band, prm.max_newton,
                  prm.n_restarts, int(prm.prefilter))
-    bad = lib().or_find(N, E, _d(coords), _i(sub), None if dist is None else _d(dist), P,
+    if pts.shape[0] != dim:
+        raise ValueError("pts must have as many rows as the mesh has dimensions")
+    bad = lib().or_find_d(dim, N, E, _d(coords), _i(sub), None if dist is None else _d(dist), P,
                         _d(pts), None if qs is None else _i(qs), ctypes.byref(cp),
                         _i(code), _i(osub), _i(oel), _d(rst), _d(d2))
     if bad < 0:
@@ -158,7 +169,8 @@ def find(coords, N: int, sub, pts, qsess=None, dist=None, params: Params | None 
 
 
 def evaluate(N: int, code, elem, rst, fields):
-    """findpts_eval by full triple sums; fields [F][E][n^3] -> out [F][P]."""
+    """findpts_eval by full triple (2D: double) sums; fields [F][E][n^d],
+    rst [d][P] -> out [F][P]."""
     fields = _f64(fields)
     if fields.ndim == 2:
         fields = fields[None]
@@ -168,7 +180,10 @@ def evaluate(N: int, code, elem, rst, fields):
     rst = _f64(rst)
     P = code.shape[0]
     out = np.zeros((F, P))
-    lib().or_eval(N, E, P, _i(code), _i(elem), _d(rst), F, _d(fields), _d(out))
+    dim = rst.shape[0]
+    if fields.shape[2] != (N + 1) ** dim:
+        raise ValueError("fields must be [F][E][(N+1)^d] with d = rst rows")
+    lib().or_eval_d(dim, N, E, P, _i(code), _i(elem), _d(rst), F, _d(fields), _d(out))
     return out
 
 
@@ -221,9 +236,13 @@ def extrapolate(hist):
 
 
 def dist_default(coords, N: int, sub):
-    """Default nodal distance field D^k [E][n^3] (brute force)."""
+    """Default nodal distance field D^k [E][n^d] (brute force), d = 2 or 3."""
     coords = _f64(coords)
     E = coords.shape[1]
+    if coords.shape[0] == 2:
+        D = np.zeros((E, (N + 1) ** 2))
+        lib().or_dist_default_2d(N, E, _d(coords), _i(_i32(sub)), _d(D))
+        return D
     D = np.zeros((E, (N + 1) ** 3))
     lib().or_dist_default(N, E, _d(coords), _i(_i32(sub)), _d(D))
     return D

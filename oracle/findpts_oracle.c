@@ -18,6 +18,11 @@
  * The result is a code (inside / border / not found), subdomain, element and
  * (r,s,t); findpts_eval then returns sum_ijk f_ijk h_i h_j h_k at that point.
  *
+ * The 2D variant (quadrilateral meshes, coords [2][E][n^2], r in [-1,1]^2;
+ * the paper's 2D overset examples, Sec. 3) runs the same steps with the
+ * double sum x^e(r,s) = sum_ij x^e_ij h_i(r) h_j(s): or_find_d / or_eval_d /
+ * or_map_d with d = 2, or_dist_default_2d.
+ *
  * Deliberately naive: the map and its Jacobian are full triple sums (no sum
  * factorisation), the Lagrange basis is the product formula, every element is
  * a candidate (a permissive, self-checked prefilter is optional).
@@ -137,15 +142,33 @@ void or_lagrange(int N, const double *xg, double r, double *h, double *dh)
 
 typedef struct {
     int N, n;
+    int d;                       /* dimension: 3 (hexahedra) or 2 (quadrilaterals) */
     const double *xg;            /* GLL points */
-    const double *X[3];          /* this element's node coordinates, n^3 each */
+    const double *X[3];          /* this element's node coordinates, n^d each (X[2] unused in 2D) */
 } or_elem;
 
-/* x(r) = sum_ijk X_ijk h_i(r0) h_j(r1) h_k(r2) and J[a][b] = dx_a/dr_b. */
+/* x(r) = sum_ijk X_ijk h_i(r0) h_j(r1) h_k(r2) and J[a][b] = dx_a/dr_b
+   (J stored with row stride 3).  In 2D: x(r) = sum_ij X_ij h_i(r0) h_j(r1). */
 static void or_map_elem(const or_elem *el, const double r[3], double x[3], double J[9])
 {
     int n = el->n, N = el->N;
     double h[3][OR_NMAX], dh[3][OR_NMAX];
+    if (el->d == 2) {
+        for (int d = 0; d < 2; ++d) or_lagrange(N, el->xg, r[d], h[d], dh[d]);
+        for (int a = 0; a < 2; ++a) {
+            double v = 0.0, vr = 0.0, vs = 0.0;
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < n; ++i) {
+                    double c = el->X[a][i + n * j];
+                    v  += c * h[0][i]  * h[1][j];
+                    vr += c * dh[0][i] * h[1][j];
+                    vs += c * h[0][i]  * dh[1][j];
+                }
+            x[a] = v;
+            if (J) { J[3 * a + 0] = vr; J[3 * a + 1] = vs; }
+        }
+        return;
+    }
     for (int d = 0; d < 3; ++d) or_lagrange(N, el->xg, r[d], h[d], dh[d]);
     for (int a = 0; a < 3; ++a) {
         double v = 0.0, vr = 0.0, vs = 0.0, vt = 0.0;
@@ -163,20 +186,29 @@ static void or_map_elem(const or_elem *el, const double r[3], double x[3], doubl
     }
 }
 
-/* Exported for tests: map M points (r given [3][M]) through element e. */
-void or_map(int N, const double *coords, int64_t E, int64_t e, int64_t M,
-            const double *r, double *x, double *J)
+/* Exported for tests: map M points (r given [d][M]) through element e of a
+   d-dimensional mesh (coords [d][E][n^d]); x [d][M], J [d*d][M] row-major. */
+void or_map_d(int d, int N, const double *coords, int64_t E, int64_t e, int64_t M,
+              const double *r, double *x, double *J)
 {
     double xg[OR_NMAX];
     or_gll(N, xg, NULL);
-    int n = N + 1, n3 = n * n * n;
-    or_elem el = { N, n, xg, { coords + e * n3, coords + (E + e) * n3, coords + (2 * E + e) * n3 } };
+    int n = N + 1, nd = d == 2 ? n * n : n * n * n;
+    or_elem el = { N, n, d, xg, { coords + e * nd, coords + (E + e) * nd, d == 3 ? coords + (2 * E + e) * nd : NULL } };
     for (int64_t m = 0; m < M; ++m) {
-        double rr[3] = { r[m], r[M + m], r[2 * M + m] }, xx[3], JJ[9];
+        double rr[3] = { r[m], r[M + m], d == 3 ? r[2 * M + m] : 0.0 }, xx[3], JJ[9];
         or_map_elem(&el, rr, xx, JJ);
-        for (int a = 0; a < 3; ++a) x[a * M + m] = xx[a];
-        if (J) for (int q = 0; q < 9; ++q) J[q * M + m] = JJ[q];
+        for (int a = 0; a < d; ++a) x[a * M + m] = xx[a];
+        if (J)
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b) J[(a * d + b) * M + m] = JJ[3 * a + b];
     }
+}
+
+void or_map(int N, const double *coords, int64_t E, int64_t e, int64_t M,
+            const double *r, double *x, double *J)
+{
+    or_map_d(3, N, coords, E, e, M, r, x, J);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -227,36 +259,47 @@ static int solve_small(int k, double A[3][3], double b[3], double z[3])
    length when it is below 0.25 (standard trust-region updates).  Stop when an
    accepted step is below 1e-13 in every coordinate, the residual is exactly
    zero, the radius collapses below 1e-15, or after max_it iterations. */
+static double sumsq(int d, const double *v)
+{
+    double s = v[0] * v[0];
+    for (int a = 1; a < d; ++a) s += v[a] * v[a];
+    return s;
+}
+
 static double or_newton(const or_elem *el, const double xs[3], double r[3], int max_it)
 {
-    double x[3], J[9], f[3];
+    const int dim = el->d;
+    double x[3], J[9], f[3] = { 0, 0, 0 };
     or_map_elem(el, r, x, J);
-    for (int a = 0; a < 3; ++a) f[a] = x[a] - xs[a];
-    double phi = 0.5 * (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    for (int a = 0; a < dim; ++a) f[a] = x[a] - xs[a];
+    double phi = 0.5 * sumsq(dim, f);
     double rho = 1.0;
     for (int it = 0; it < max_it; ++it) {
         if (phi == 0.0) break;
-        double g[3];
-        for (int b = 0; b < 3; ++b) g[b] = J[b] * f[0] + J[3 + b] * f[1] + J[6 + b] * f[2];
+        double g[3] = { 0, 0, 0 };
+        for (int b = 0; b < dim; ++b) {
+            g[b] = J[b] * f[0];
+            for (int a = 1; a < dim; ++a) g[b] += J[3 * a + b] * f[a];
+        }
         /* active set: bound coordinates whose descent direction points out
            of the box; grown while the Gauss-Newton step on the free
            coordinates would push a free bound coordinate outward */
-        int act[3];
-        for (int b = 0; b < 3; ++b)
+        int act[3] = { 1, 1, 1 };
+        for (int b = 0; b < dim; ++b)
             act[b] = (r[b] <= -1.0 && g[b] > 0.0) || (r[b] >= 1.0 && g[b] < 0.0);
         double d[3];
         int k;
         for (int pass = 0; pass < 4; ++pass) {
             int fr[3];
             k = 0;
-            for (int b = 0; b < 3; ++b) if (!act[b]) fr[k++] = b;
+            for (int b = 0; b < dim; ++b) if (!act[b]) fr[k++] = b;
             d[0] = d[1] = d[2] = 0.0;
             if (k == 0) break;
             double A[3][3], rhs[3], z[3];
             for (int p = 0; p < k; ++p) {
                 for (int q = 0; q < k; ++q) {
                     double sacc = 0.0;
-                    for (int a = 0; a < 3; ++a) sacc += J[3 * a + fr[p]] * J[3 * a + fr[q]];
+                    for (int a = 0; a < dim; ++a) sacc += J[3 * a + fr[p]] * J[3 * a + fr[q]];
                     A[p][q] = sacc;
                 }
                 rhs[p] = -g[fr[p]];
@@ -265,7 +308,7 @@ static double or_newton(const or_elem *el, const double xs[3], double r[3], int 
                 for (int p = 0; p < k; ++p) z[p] = rhs[p];   /* singular: steepest descent */
             for (int p = 0; p < k; ++p) d[fr[p]] = z[p];
             int grew = 0;
-            for (int b = 0; b < 3; ++b)
+            for (int b = 0; b < dim; ++b)
                 if (!act[b] && ((r[b] <= -1.0 && d[b] < 0.0) || (r[b] >= 1.0 && d[b] > 0.0))) {
                     act[b] = 1;
                     grew = 1;
@@ -279,12 +322,12 @@ static double or_newton(const or_elem *el, const double xs[3], double r[3], int 
         if (dn > rho) for (int b = 0; b < 3; ++b) d[b] *= rho / dn;
         /* stay in the box: largest t <= 1 with r + t d in [-1,1]^3 */
         double t = 1.0;
-        for (int b = 0; b < 3; ++b) {
+        for (int b = 0; b < dim; ++b) {
             if (d[b] > 0.0 && r[b] + d[b] > 1.0) t = fmin(t, (1.0 - r[b]) / d[b]);
             if (d[b] < 0.0 && r[b] + d[b] < -1.0) t = fmin(t, (-1.0 - r[b]) / d[b]);
         }
-        double rn[3], s[3];
-        for (int b = 0; b < 3; ++b) {
+        double rn[3] = { 0, 0, 0 }, s[3] = { 0, 0, 0 };
+        for (int b = 0; b < dim; ++b) {
             rn[b] = r[b] + t * d[b];
             if (rn[b] > 1.0) rn[b] = 1.0;
             if (rn[b] < -1.0) rn[b] = -1.0;
@@ -297,13 +340,15 @@ static double or_newton(const or_elem *el, const double xs[3], double r[3], int 
         if (sn == 0.0) break;
         /* predicted decrease of the Gauss-Newton model */
         double mf[3];
-        for (int a = 0; a < 3; ++a)
-            mf[a] = f[a] + J[3 * a] * s[0] + J[3 * a + 1] * s[1] + J[3 * a + 2] * s[2];
-        double pred = phi - 0.5 * (mf[0] * mf[0] + mf[1] * mf[1] + mf[2] * mf[2]);
-        double xn[3], Jn[9], fn[3];
+        for (int a = 0; a < dim; ++a) {
+            mf[a] = f[a];
+            for (int b = 0; b < dim; ++b) mf[a] += J[3 * a + b] * s[b];
+        }
+        double pred = phi - 0.5 * sumsq(dim, mf);
+        double xn[3], Jn[9], fn[3] = { 0, 0, 0 };
         or_map_elem(el, rn, xn, Jn);
-        for (int a = 0; a < 3; ++a) fn[a] = xn[a] - xs[a];
-        double phin = 0.5 * (fn[0] * fn[0] + fn[1] * fn[1] + fn[2] * fn[2]);
+        for (int a = 0; a < dim; ++a) fn[a] = xn[a] - xs[a];
+        double phin = 0.5 * sumsq(dim, fn);
         double dec = phi - phin;
         if (sn <= 1e-13) {                        /* converged in r */
             if (phin <= phi) { memcpy(r, rn, sizeof rn); phi = phin; }
@@ -329,9 +374,10 @@ static double or_newton(const or_elem *el, const double xs[3], double r[3], int 
 /* Per-element helpers                                                      */
 /* ------------------------------------------------------------------------ */
 
-static void node_box(const double *const X[3], int n3, double lo[3], double hi[3])
+static void node_box(const double *const X[3], int d, int n3, double lo[3], double hi[3])
 {
-    for (int a = 0; a < 3; ++a) {
+    lo[2] = hi[2] = 0.0;
+    for (int a = 0; a < d; ++a) {
         double mn = X[a][0], mx = X[a][0];
         for (int q = 1; q < n3; ++q) {
             if (X[a][q] < mn) mn = X[a][q];
@@ -353,7 +399,7 @@ static double diag3(const double lo[3], const double hi[3])
    first `nskip` ranks so that restarts can take the next-nearest nodes. */
 static int nearest_node(const or_elem *el, const double xs[3], int rank_wanted)
 {
-    int n3 = el->n * el->n * el->n;
+    int n3 = el->d == 2 ? el->n * el->n : el->n * el->n * el->n;
     /* select the rank_wanted-th smallest distance (0 = nearest) by repeated
        minimum search; plain and slow on purpose */
     double last = -1.0;
@@ -362,8 +408,12 @@ static int nearest_node(const or_elem *el, const double xs[3], int rank_wanted)
         double bd = INFINITY;
         int bi = -1;
         for (int q = 0; q < n3; ++q) {
-            double dx = el->X[0][q] - xs[0], dy = el->X[1][q] - xs[1], dz = el->X[2][q] - xs[2];
-            double d2 = dx * dx + dy * dy + dz * dz;
+            double dx = el->X[0][q] - xs[0], dy = el->X[1][q] - xs[1];
+            double d2 = dx * dx + dy * dy;
+            if (el->d == 3) {
+                double dz = el->X[2][q] - xs[2];
+                d2 = d2 + dz * dz;
+            }
             /* strictly after (last, last_idx) in (distance, index) order */
             int after = (d2 > last) || (d2 == last && q > last_idx);
             if (!after) continue;
@@ -382,15 +432,20 @@ static void node_rst(const or_elem *el, int q, double r[3])
     int n = el->n;
     r[0] = el->xg[q % n];
     r[1] = el->xg[(q / n) % n];
-    r[2] = el->xg[q / (n * n)];
+    r[2] = el->d == 3 ? el->xg[q / (n * n)] : 0.0;
 }
 
-static double interp_elem(int N, const double *xg, const double *f, const double r[3])
+static double interp_elem(int N, int dim, const double *xg, const double *f, const double r[3])
 {
     int n = N + 1;
     double h[3][OR_NMAX];
-    for (int d = 0; d < 3; ++d) or_lagrange(N, xg, r[d], h[d], NULL);
+    for (int d = 0; d < dim; ++d) or_lagrange(N, xg, r[d], h[d], NULL);
     double v = 0.0;
+    if (dim == 2) {
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) v += f[i + n * j] * h[0][i] * h[1][j];
+        return v;
+    }
     for (int k = 0; k < n; ++k)
         for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i)
@@ -414,21 +469,21 @@ typedef struct {
 
 /* Returns the number of points for which the optional prefilter check found
    a dropped answer (always 0 unless the prefilter is unsound for the mesh). */
-int64_t or_find(int N, int64_t E, const double *coords, const int32_t *sub,
-                const double *dist, int64_t P, const double *pts, const int32_t *qsess,
-                const or_params *prm, int32_t *code, int32_t *osub, int32_t *oelem,
-                double *rst, double *dist2)
+int64_t or_find_d(int dim, int N, int64_t E, const double *coords, const int32_t *sub,
+                  const double *dist, int64_t P, const double *pts, const int32_t *qsess,
+                  const or_params *prm, int32_t *code, int32_t *osub, int32_t *oelem,
+                  double *rst, double *dist2)
 {
     double xg[OR_NMAX];
-    if (or_gll(N, xg, NULL)) return -1;
-    int n = N + 1, n3 = n * n * n;
+    if ((dim != 2 && dim != 3) || or_gll(N, xg, NULL)) return -1;
+    int n = N + 1, n3 = dim == 2 ? n * n : n * n * n;
     double *elo = (double *)malloc(sizeof(double) * 3 * E);
     double *ehi = (double *)malloc(sizeof(double) * 3 * E);
     double *he = (double *)malloc(sizeof(double) * E);
     double glo[3] = { INFINITY, INFINITY, INFINITY }, ghi[3] = { -INFINITY, -INFINITY, -INFINITY };
     for (int64_t e = 0; e < E; ++e) {
-        const double *X[3] = { coords + e * n3, coords + (E + e) * n3, coords + (2 * E + e) * n3 };
-        node_box(X, n3, elo + 3 * e, ehi + 3 * e);
+        const double *X[3] = { coords + e * n3, coords + (E + e) * n3, dim == 3 ? coords + (2 * E + e) * n3 : NULL };
+        node_box(X, dim, n3, elo + 3 * e, ehi + 3 * e);
         he[e] = diag3(elo + 3 * e, ehi + 3 * e);
         for (int a = 0; a < 3; ++a) {
             if (elo[3 * e + a] < glo[a]) glo[a] = elo[3 * e + a];
@@ -441,12 +496,12 @@ int64_t or_find(int N, int64_t E, const double *coords, const int32_t *sub,
 
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : bad_prefilter)
     for (int64_t p = 0; p < P; ++p) {
-        double xs[3] = { pts[p], pts[P + p], pts[2 * P + p] };
+        double xs[3] = { pts[p], pts[P + p], dim == 3 ? pts[2 * P + p] : 0.0 };
         int32_t tag = qsess ? qsess[p] : -1;
         code[p] = OR_NOT_FOUND;
         osub[p] = -1;
         oelem[p] = -1;
-        rst[p] = rst[P + p] = rst[2 * P + p] = 0.0;
+        for (int a = 0; a < dim; ++a) rst[a * P + p] = 0.0;
         dist2[p] = INFINITY;
         if (!isfinite(xs[0]) || !isfinite(xs[1]) || !isfinite(xs[2])) continue;
 
@@ -471,13 +526,14 @@ int64_t or_find(int N, int64_t E, const double *coords, const int32_t *sub,
             const double *lo = elo + 3 * e, *hi = ehi + 3 * e;
             if (prm->prefilter) {
                 int out = 0;
-                for (int a = 0; a < 3; ++a) {
+                for (int a = 0; a < dim; ++a) {
                     double g = 0.25 * (hi[a] - lo[a]) + prm->tol_border * he[e];
                     if (xs[a] < lo[a] - g || xs[a] > hi[a] + g) out = 1;
                 }
                 if (out) continue;
             }
-            or_elem el = { N, n, xg, { coords + e * n3, coords + (E + e) * n3, coords + (2 * E + e) * n3 } };
+            or_elem el = { N, n, dim, xg, { coords + e * n3, coords + (E + e) * n3,
+                                            dim == 3 ? coords + (2 * E + e) * n3 : NULL } };
             double r[3], best_r[3] = { 0, 0, 0 };
             double res = INFINITY;
             for (int k = 0; k <= prm->n_restarts && k < n3; ++k) {
@@ -517,7 +573,7 @@ int64_t or_find(int N, int64_t E, const double *coords, const int32_t *sub,
                    tie band the lower subdomain id wins (Sec. 2.1) */
                 double dl[MAXS], dmax = -INFINITY;
                 for (int s = 0; s < nin; ++s) {
-                    dl[s] = dist ? interp_elem(N, xg, dist + in_e[s] * n3, in_r[s]) : 0.0;
+                    dl[s] = dist ? interp_elem(N, dim, xg, dist + in_e[s] * n3, in_r[s]) : 0.0;
                     if (dl[s] > dmax) dmax = dl[s];
                 }
                 w = -1;
@@ -527,7 +583,7 @@ int64_t or_find(int N, int64_t E, const double *coords, const int32_t *sub,
             code[p] = OR_INSIDE;
             osub[p] = in_s[w];
             oelem[p] = (int32_t)in_e[w];
-            rst[p] = in_r[w][0]; rst[P + p] = in_r[w][1]; rst[2 * P + p] = in_r[w][2];
+            for (int a = 0; a < dim; ++a) rst[a * P + p] = in_r[w][a];
             dist2[p] = in_d[w] * in_d[w];
         } else if (nbc > 0) {
             for (int c = 0; c < nbc; ++c)
@@ -537,7 +593,7 @@ int64_t or_find(int N, int64_t E, const double *coords, const int32_t *sub,
             code[p] = OR_BORDER;
             osub[p] = sub[b_e];
             oelem[p] = (int32_t)b_e;
-            rst[p] = b_r[0]; rst[P + p] = b_r[1]; rst[2 * P + p] = b_r[2];
+            for (int a = 0; a < dim; ++a) rst[a * P + p] = b_r[a];
             dist2[p] = b_d * b_d;
         }
         free(bc_e); free(bc_d); free(bc_r);
@@ -545,7 +601,7 @@ int64_t or_find(int N, int64_t E, const double *coords, const int32_t *sub,
         /* self-check of the prefilter: the answer's element must pass it */
         if (prm->prefilter && oelem[p] >= 0) {
             int64_t e = oelem[p];
-            for (int a = 0; a < 3; ++a) {
+            for (int a = 0; a < dim; ++a) {
                 double g = 0.25 * (ehi[3 * e + a] - elo[3 * e + a]);
                 if (xs[a] < elo[3 * e + a] - g || xs[a] > ehi[3 * e + a] + g) { ++bad_prefilter; break; }
             }
@@ -555,26 +611,40 @@ int64_t or_find(int N, int64_t E, const double *coords, const int32_t *sub,
     return bad_prefilter;
 }
 
+int64_t or_find(int N, int64_t E, const double *coords, const int32_t *sub,
+                const double *dist, int64_t P, const double *pts, const int32_t *qsess,
+                const or_params *prm, int32_t *code, int32_t *osub, int32_t *oelem,
+                double *rst, double *dist2)
+{
+    return or_find_d(3, N, E, coords, sub, dist, P, pts, qsess, prm, code, osub, oelem, rst, dist2);
+}
+
 /* ------------------------------------------------------------------------ */
 /* findpts_eval: full triple sum                                            */
 /* ------------------------------------------------------------------------ */
 
 /* out[f][p] = sum_ijk F[f][e][ijk] h_i(r) h_j(s) h_k(t) at (elem[p], rst[.][p]);
    NaN where code is NOT_FOUND (Sec. 2.1, findpts_eval). */
-void or_eval(int N, int64_t E, int64_t P, const int32_t *code, const int32_t *elem,
-             const double *rst, int F, const double *fields, double *out)
+void or_eval_d(int dim, int N, int64_t E, int64_t P, const int32_t *code, const int32_t *elem,
+               const double *rst, int F, const double *fields, double *out)
 {
     double xg[OR_NMAX];
     or_gll(N, xg, NULL);
-    int n = N + 1, n3 = n * n * n;
+    int n = N + 1, n3 = dim == 2 ? n * n : n * n * n;
 #pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < P; ++p) {
-        double r[3] = { rst[p], rst[P + p], rst[2 * P + p] };
+        double r[3] = { rst[p], rst[P + p], dim == 3 ? rst[2 * P + p] : 0.0 };
         for (int f = 0; f < F; ++f) {
             if (code[p] == OR_NOT_FOUND || elem[p] < 0) { out[f * P + p] = NAN; continue; }
-            out[f * P + p] = interp_elem(N, xg, fields + ((int64_t)f * E + elem[p]) * n3, r);
+            out[f * P + p] = interp_elem(N, dim, xg, fields + ((int64_t)f * E + elem[p]) * n3, r);
         }
     }
+}
+
+void or_eval(int N, int64_t E, int64_t P, const int32_t *code, const int32_t *elem,
+             const double *rst, int F, const double *fields, double *out)
+{
+    or_eval_d(3, N, E, P, code, elem, rst, F, fields, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -675,6 +745,77 @@ int or_dist_default(int N, int64_t E, const double *coords, const int32_t *sub, 
     return 0;
 }
 
+/* The same field on a 2D quadrilateral mesh (coords [2][E][n^2]): boundary
+   edges are element edges whose two end points match no edge of another
+   element of the same subdomain; edge f = 0,1 is r = -1,+1 (nodes i = 0,N,
+   j = 0..N), f = 2,3 is s = -1,+1. */
+static int edge_node(int n, int f, int a)
+{
+    int end = (f % 2) ? n - 1 : 0;
+    return f / 2 == 0 ? end + n * a : a + n * end;
+}
+
+int or_dist_default_2d(int N, int64_t E, const double *coords, const int32_t *sub, double *D)
+{
+    int n = N + 1, n2 = n * n;
+    int64_t F = 4 * E;
+    char *bnd = (char *)malloc((size_t)F);
+    double (*cor)[2][2] = malloc(sizeof(double[2][2]) * (size_t)F);
+    for (int64_t e = 0; e < E; ++e)
+        for (int f = 0; f < 4; ++f) {
+            double *c0 = cor[4 * e + f][0], *c1 = cor[4 * e + f][1];
+            int i0 = edge_node(n, f, 0), i1 = edge_node(n, f, N);
+            for (int a = 0; a < 2; ++a) {
+                c0[a] = coords[(a * E + e) * n2 + i0];
+                c1[a] = coords[(a * E + e) * n2 + i1];
+            }
+            /* sort the two end points lexicographically */
+            if (c1[0] < c0[0] || (c1[0] == c0[0] && c1[1] < c0[1]))
+                for (int a = 0; a < 2; ++a) { double t = c0[a]; c0[a] = c1[a]; c1[a] = t; }
+        }
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t a = 0; a < F; ++a) {
+        int shared = 0;
+        for (int64_t b = 0; b < F && !shared; ++b) {
+            if (b / 4 == a / 4 || sub[b / 4] != sub[a / 4]) continue;
+            if (memcmp(cor[a], cor[b], sizeof(double[2][2])) == 0) shared = 1;
+        }
+        bnd[a] = !shared;
+    }
+    int64_t nb = 0;
+    for (int64_t a = 0; a < F; ++a) nb += bnd[a] ? n : 0;
+    double *bx = (double *)malloc(sizeof(double) * 2 * (nb ? nb : 1));
+    int32_t *bs = (int32_t *)malloc(sizeof(int32_t) * (nb ? nb : 1));
+    int64_t m = 0;
+    for (int64_t a = 0; a < F; ++a) {
+        if (!bnd[a]) continue;
+        int64_t e = a / 4;
+        for (int q = 0; q < n; ++q) {
+            int idx = edge_node(n, (int)(a % 4), q);
+            bx[2 * m] = coords[e * n2 + idx];
+            bx[2 * m + 1] = coords[(E + e) * n2 + idx];
+            bs[m] = sub[e];
+            ++m;
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t e = 0; e < E; ++e) {
+        for (int q = 0; q < n2; ++q) {
+            double x = coords[e * n2 + q], y = coords[(E + e) * n2 + q];
+            double best = INFINITY;
+            for (int64_t b = 0; b < nb; ++b) {
+                if (bs[b] != sub[e]) continue;
+                double dx = x - bx[2 * b], dy = y - bx[2 * b + 1];
+                double d2 = dx * dx + dy * dy;
+                if (d2 < best) best = d2;
+            }
+            D[e * n2 + q] = sqrt(best);
+        }
+    }
+    free(bnd); free(cor); free(bx); free(bs);
+    return 0;
+}
+
 /* number of OpenMP threads the oracle will use */
 int or_num_threads(void)
 {
@@ -719,7 +860,7 @@ int64_t or_bfaces(int N, int64_t E, const double *coords, const int8_t *kind, do
     for (int64_t e = 0; e < E; ++e) {
         const double *X[3] = { coords + e * n3, coords + (E + e) * n3, coords + (2 * E + e) * n3 };
         /* handedness: sign of det J at the element centre */
-        or_elem el = { N, n, xg, { X[0], X[1], X[2] } };
+        or_elem el = { N, n, 3, xg, { X[0], X[1], X[2] } };
         double r0[3] = { 0, 0, 0 }, xc[3], Jc[9];
         or_map_elem(&el, r0, xc, Jc);
         double det = Jc[0] * (Jc[4] * Jc[8] - Jc[5] * Jc[7]) - Jc[1] * (Jc[3] * Jc[8] - Jc[5] * Jc[6]) +

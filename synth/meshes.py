@@ -33,6 +33,8 @@ __all__ = [
     "boundary_face_nodes", "field_u", "sine_product_field", "random_poly_field",
     "config0", "config1", "config2", "config3", "config4_mesh", "config4_requests",
     "tiny_overlap", "spiral_element", "reference_poly_field", "rigid_motion",
+    "quad_mesh", "ring_mesh", "rect_distance", "uniform_points_2d", "edge_points_2d", "field_u_2d",
+    "reference_poly_field_2d", "tiny_overlap_2d", "walsh_2d",
 ]
 
 
@@ -521,3 +523,159 @@ def rigid_motion(coords: np.ndarray, sub: np.ndarray, moving: int, angle_deg: fl
     out[1, m] = center[1] + s * x + c * y + shift[1]
     out[2, m] = out[2, m] + shift[2]
     return out
+
+
+# ----------------------------------------------------------------------------
+# 2D (quadrilateral) meshes: coords [2][E][n^2], node (i,j) at i + n*j
+# ----------------------------------------------------------------------------
+def quad_mesh(shape, N: int, lo=(0.0, 0.0), hi=(1.0, 1.0), amp_frac: float = 0.0) -> np.ndarray:
+    """Quad mesh of the rectangle [lo,hi] with shape=(ex,ey) elements of
+    order N, element e = ei + ex*ej.  With amp_frac > 0 every node not on the
+    rectangle's boundary moves by d = amp_frac*h*sin(2 pi x') sin(2 pi y') in
+    both coordinates (x' = (x-lo)/(hi-lo), h the smallest element width)."""
+    ex, ey = (int(v) for v in shape)
+    xi = reference_grid(N)
+    n = N + 1
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    gx = _axis_nodes(ex, lo[0], hi[0], xi)
+    gy = _axis_nodes(ey, lo[1], hi[1], xi)
+    shp = (ey, ex, n, n)
+    X = np.broadcast_to(gx[None, :, None, :], shp)
+    Y = np.broadcast_to(gy[:, None, :, None], shp)
+    E = ex * ey
+    coords = np.empty((2, E, n * n), dtype=np.float64)
+    coords[0] = X.reshape(E, n * n)
+    coords[1] = Y.reshape(E, n * n)
+    if amp_frac:
+        h = float(np.min((hi - lo) / np.array([ex, ey])))
+        u = (coords[0] - lo[0]) / (hi[0] - lo[0])
+        v = (coords[1] - lo[1]) / (hi[1] - lo[1])
+        d = amp_frac * h * np.sin(2 * np.pi * u) * np.sin(2 * np.pi * v)
+        on_bnd = (coords[0] == lo[0]) | (coords[0] == hi[0]) | (coords[1] == lo[1]) | (coords[1] == hi[1])
+        d[on_bnd] = 0.0
+        coords += d[None]
+    return coords
+
+
+def ring_mesh(n_az: int, n_rad: int, N: int, r_in: float, r_out: float, center=(0.0, 0.0),
+              angle0: float = 0.0):
+    """Quad mesh of the annulus r_in <= rho <= r_out around `center`: n_az
+    azimuthal x n_rad radial elements, element e = er + n_rad*ea, reference r
+    radial, s azimuthal (counter-clockwise).  Returns (coords [2][E][n^2],
+    rho [E][n^2])."""
+    xi = reference_grid(N)
+    n = N + 1
+    rr = _axis_nodes(n_rad, r_in, r_out, xi)          # [n_rad][n]
+    th = _axis_nodes(n_az, angle0, angle0 + 2 * np.pi, xi)
+    shp = (n_az, n_rad, n, n)                          # [ea][er][j][i]
+    R = np.broadcast_to(rr[None, :, None, :], shp)
+    T = np.broadcast_to(th[:, None, :, None], shp)
+    E = n_az * n_rad
+    rho = R.reshape(E, n * n)
+    t = T.reshape(E, n * n)
+    coords = np.empty((2, E, n * n), dtype=np.float64)
+    coords[0] = center[0] + rho * np.cos(t)
+    coords[1] = center[1] + rho * np.sin(t)
+    return coords, np.ascontiguousarray(rho)
+
+
+def rect_distance(coords: np.ndarray, lo, hi) -> np.ndarray:
+    """Closed-form distance of each node of an undeformed quad mesh to the
+    rectangle's boundary.  [E][n^2]."""
+    d = np.minimum(np.minimum(coords[0] - lo[0], hi[0] - coords[0]),
+                   np.minimum(coords[1] - lo[1], hi[1] - coords[1]))
+    return np.maximum(d, 0.0)
+
+
+def uniform_points_2d(P: int, seed: int, lo=(0.0, 0.0), hi=(1.0, 1.0)) -> np.ndarray:
+    """P points uniform in [lo,hi), drawn as rng.random((P,2)); returns [2][P]."""
+    rng = np.random.default_rng(seed)
+    u = rng.random((P, 2))
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    return np.ascontiguousarray((lo + (hi - lo) * u).T)
+
+
+def edge_points_2d(coords: np.ndarray, N: int, M: int, seed: int) -> np.ndarray:
+    """M points within 1e-9 of element edges: interior GLL nodes of random
+    element edges moved along the edge's nominal normal axis by
+    +-10^U(-11,-9) (90 %) or 0 (10 %).  Returns [2][M]."""
+    rng = np.random.default_rng(seed)
+    n = N + 1
+    E = coords.shape[1]
+    e = rng.integers(0, E, M)
+    f = rng.integers(0, 4, M)
+    a = rng.integers(1, N, M) if N > 1 else np.zeros(M, int)
+    end = np.where(f % 2 == 1, N, 0)
+    idx = np.where(f // 2 == 0, end + n * a, a + n * end)
+    pts = np.stack([coords[0, e, idx], coords[1, e, idx]])
+    off = np.where(rng.random(M) < 0.9, rng.choice([-1.0, 1.0], M) * 10.0 ** rng.uniform(-11, -9, M), 0.0)
+    pts[f // 2, np.arange(M)] += off
+    return np.ascontiguousarray(pts)
+
+
+def field_u_2d(coords: np.ndarray) -> np.ndarray:
+    """u = sin(pi x) cos(pi y) exp(x y) at the nodes of a 2D mesh."""
+    return np.sin(np.pi * coords[0]) * np.cos(np.pi * coords[1]) * np.exp(coords[0] * coords[1])
+
+
+def reference_poly_field_2d(N: int, E: int, seed: int):
+    """Nodal values p(xi_i, xi_j) of a random p in Q_N(r, s), the same on
+    every element.  Returns (values [E][n^2], coefficients c[a,b] of r^a s^b)."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-1.0, 1.0, size=(N + 1, N + 1))
+    xi = reference_grid(N)
+    V = np.vander(xi, N + 1, increasing=True)
+    vals = np.einsum("ia,jb,ab->ji", V, V, c).reshape((N + 1) ** 2)
+    return np.ascontiguousarray(np.broadcast_to(vals, (E, (N + 1) ** 2))), c
+
+
+def tiny_overlap_2d(N=4):
+    """Three overlapping rectangles (sessions 0,1,2) spanning x in TINY_X and
+    y in [0,1], each 2x1 elements split at its x-midpoint; D^k = min(x - a_k,
+    b_k - x) is linear on every element (closed-form delta^k)."""
+    parts, dists = [], []
+    for a, b in TINY_X:
+        c = quad_mesh((2, 1), N, lo=(a, 0.0), hi=(b, 1.0))
+        parts.append(c)
+        dists.append(np.minimum(c[0] - a, b - c[0]))
+    return concat_meshes(parts, N, [0, 1, 2], dists, name="tiny-overlap-2d")
+
+
+def walsh_2d(N=7, n_box=16, ring=(16, 3)):
+    """2D overset workload modelled on the paper's 2D examples: the periodic
+    box [0,2pi]^2 (n_box x n_box quads, session 0, interior nodes displaced
+    by 0.05 h) overlapped by an annulus rho in [0.6, 1.4] around (pi, pi)
+    (ring = (n_az, n_rad), session 1).  Queries: the boundary GLL nodes of
+    each subdomain inside the other, tagged with their own session; fields
+    u, v, p: the Walsh-type eddy u = -cos(x) sin(y), v = sin(x) cos(y),
+    p = -(cos 2x + cos 2y)/4.  D^k in closed form."""
+    lo, hi = (0.0, 0.0), (2 * np.pi, 2 * np.pi)
+    cb = quad_mesh((n_box, n_box), N, lo=lo, hi=hi, amp_frac=0.05)
+    c0 = (np.pi, np.pi)
+    r_in, r_out = 0.6, 1.4
+    cr, rho = ring_mesh(ring[0], ring[1], N, r_in, r_out, center=c0)
+    db = rect_distance(cb, lo, hi)
+    dr = np.maximum(np.minimum(rho - r_in, r_out - rho), 0.0)
+    mesh = concat_meshes([cb, cr], N, [0, 1], [db, dr], name=f"walsh2d-N{N}")
+    n = N + 1
+    # annulus boundary nodes (inner and outer circles), deduplicated
+    nodes = []
+    for ea in range(ring[0]):
+        for er, i in ((0, 0), (ring[1] - 1, N)):
+            e = er + ring[1] * ea
+            for j in range(N):                      # skip j = N (next element's j = 0)
+                nodes.append(cr[:, e, i + n * j])
+    qr = np.array(nodes).T
+    # box nodes near the annulus: every box GLL node with r_in <= rho <= r_out (a volume set)
+    xb = cb.reshape(2, -1)
+    rb = np.hypot(xb[0] - c0[0], xb[1] - c0[1])
+    keep = (rb > r_in) & (rb < r_out)
+    qb = np.unique(np.round(xb[:, keep].T, 14), axis=0).T
+    pts = np.ascontiguousarray(np.concatenate([qb, qr], axis=1))
+    qsess = np.concatenate([np.zeros(qb.shape[1], np.int32), np.ones(qr.shape[1], np.int32)])
+    X, Y = mesh.coords
+    fields = np.stack([-np.cos(X) * np.sin(Y), np.sin(X) * np.cos(Y), -(np.cos(2 * X) + np.cos(2 * Y)) / 4])
+    return mesh, Queries(pts=pts, qsess=qsess, fields=np.ascontiguousarray(fields),
+                         info={"P_box": int(qb.shape[1]), "P_ring": int(qr.shape[1])})
