@@ -102,6 +102,23 @@ fp_status fp_setup(fp_handle **h, const double *coords, int64_t E, int N,
                    const int32_t *sub, const double *dist, const fp_opts *opts,
                    void *stream);
 
+/* fp_setup_2d -- the 2D (quadrilateral) variant (the paper's 2D overset
+ * examples, Sec. 3): the same set-up on a mesh of quads with
+ * x^e(r,s) = sum_ij x_ij h_i(r) h_j(s).
+ *   coords [2][E][n2] FP64 node coordinates x, y, node (i,j) at i + n*j,
+ *          n2 = n^2
+ *   dist   [E][n2] D^k, required when the mesh has more than one subdomain
+ *          (there is no default field in 2D)
+ *   opts   the FP64 form only (FP_PREC_MIXED gives FP_ERR_INVALID_ARG)
+ * On a 2D handle fp_find, fp_find_eval, fp_find_warm and fp_eval take
+ * points and reference coordinates as [2][P] and fields as [F][E][n2], with
+ * the same rules, codes and errors; fp_update_coords takes [2][E][n2].  The
+ * workspace, static, batch, posted-field and boundary-face calls accept
+ * hexahedral handles only (FP_ERR_INVALID_ARG otherwise). */
+fp_status fp_setup_2d(fp_handle **h, const double *coords, int64_t E, int N,
+                      const int32_t *sub, const double *dist, const fp_opts *opts,
+                      void *stream);
+
 /* fp_reserve -- pre-size the find workspace for up to P points, so that
  * later fp_find calls with at most P points allocate nothing (required before
  * capturing fp_find into a CUDA graph).  Synchronises the device. */

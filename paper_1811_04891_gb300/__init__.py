@@ -94,6 +94,8 @@ def _load():
     L.fp_eval_df.restype = ci
     L.fp_find_eval.argtypes = [vp, i64, vp, vp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.fp_find_eval.restype = ci
+    L.fp_setup_2d.argtypes = list(L.fp_setup.argtypes)
+    L.fp_setup_2d.restype = ci
     L.fp_find_warm.argtypes = [vp, i64, vp, vp, vp, vp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.fp_find_warm.restype = ci
     L.fp_update_coords.argtypes = [vp, vp, vp, ci, vp]
@@ -189,6 +191,7 @@ class Handle:
     ptr: ctypes.c_void_p
     E: int
     N: int
+    dim: int = 3
 
     def __del__(self):
         if getattr(self, "ptr", None) is not None and self.ptr.value:
@@ -223,20 +226,38 @@ def fp_setup(coords: torch.Tensor, N: int, sub: Optional[torch.Tensor] = None,
     return Handle(ptr=h, E=E, N=N)
 
 
+def fp_setup_2d(coords: torch.Tensor, N: int, sub: Optional[torch.Tensor] = None,
+                dist: Optional[torch.Tensor] = None, opts: Optional[fp_opts] = None,
+                stream=None) -> Handle:
+    """Post a 2D quadrilateral mesh: coords [2][E][(N+1)^2] float64 CUDA
+    tensor, sub [E] int32, dist [E][(N+1)^2] float64 (required with more than
+    one subdomain).  FP64 form only."""
+    coords = _dev(coords, torch.float64, "coords")
+    if coords.ndim != 3 or coords.shape[0] != 2 or coords.shape[2] != (N + 1) ** 2:
+        raise ValueError("coords must be [2][E][(N+1)^2]")
+    E = coords.shape[1]
+    sub = None if sub is None else _dev(sub, torch.int32, "sub")
+    dist = None if dist is None else _dev(dist, torch.float64, "dist")
+    h = ctypes.c_void_p()
+    st = lib().fp_setup_2d(ctypes.byref(h), _ptr(coords), E, N, _ptr(sub), _ptr(dist),
+                           None if opts is None else ctypes.byref(opts), _stream(stream))
+    _check(st, None)
+    return Handle(ptr=h, E=E, N=N, dim=2)
+
+
 def fp_reserve(h: Handle, P: int):
     _check(lib().fp_reserve(h.ptr, int(P)), h.ptr)
 
 
 def fp_find(h: Handle, pts: torch.Tensor, qsess: Optional[torch.Tensor] = None, out=None, stream=None):
-    """Locate points pts [3][P] float64.  Returns (code, sub, elem, rst [3][P], dist2)."""
+    """Locate points pts [d][P] float64 (d = the handle's dimension).
+    Returns (code, sub, elem, rst [d][P], dist2)."""
     pts = _dev(pts, torch.float64, "pts")
     P = pts.shape[1]
     qsess = None if qsess is None else _dev(qsess, torch.int32, "qsess")
     dev = pts.device
     if out is None:
-        out = (torch.empty(P, dtype=torch.int32, device=dev), torch.empty(P, dtype=torch.int32, device=dev),
-               torch.empty(P, dtype=torch.int32, device=dev), torch.empty((3, P), dtype=torch.float64, device=dev),
-               torch.empty(P, dtype=torch.float64, device=dev))
+        out = _find_outs(P, dev, h.dim)
     code, sub, elem, rst, dist2 = out
     st = lib().fp_find(h.ptr, P, _ptr(pts), _ptr(qsess), _ptr(code), _ptr(sub), _ptr(elem), _ptr(rst),
                        _ptr(dist2), _stream(stream))
@@ -275,9 +296,7 @@ def fp_find_ws(h: Handle, ws: Workspace, pts: torch.Tensor, qsess: Optional[torc
     qsess = None if qsess is None else _dev(qsess, torch.int32, "qsess")
     dev = pts.device
     if out is None:
-        out = (torch.empty(P, dtype=torch.int32, device=dev), torch.empty(P, dtype=torch.int32, device=dev),
-               torch.empty(P, dtype=torch.int32, device=dev), torch.empty((3, P), dtype=torch.float64, device=dev),
-               torch.empty(P, dtype=torch.float64, device=dev))
+        out = _find_outs(P, dev, h.dim)
     code, sub, elem, rst, dist2 = out
     st = lib().fp_find_ws(h.ptr, ws.ptr, P, _ptr(pts), _ptr(qsess), _ptr(code), _ptr(sub), _ptr(elem), _ptr(rst),
                           _ptr(dist2), _stream(stream))
@@ -369,9 +388,7 @@ def fp_find_static(h: Handle, pts: torch.Tensor, qsess: Optional[torch.Tensor] =
     qsess = None if qsess is None else _dev(qsess, torch.int32, "qsess")
     dev = pts.device
     if out is None:
-        out = (torch.empty(P, dtype=torch.int32, device=dev), torch.empty(P, dtype=torch.int32, device=dev),
-               torch.empty(P, dtype=torch.int32, device=dev), torch.empty((3, P), dtype=torch.float64, device=dev),
-               torch.empty(P, dtype=torch.float64, device=dev))
+        out = _find_outs(P, dev, h.dim)
     code, sub, elem, rst, dist2 = out
     st = lib().fp_find_static(h.ptr, P, _ptr(pts), _ptr(qsess), _ptr(code), _ptr(sub), _ptr(elem), _ptr(rst),
                               _ptr(dist2), _stream(stream))
@@ -427,9 +444,9 @@ def fp_eval_df(h: Handle, f: Fields, code: torch.Tensor, elem: torch.Tensor, rst
     return out
 
 
-def _find_outs(P, dev):
+def _find_outs(P, dev, dim: int = 3):
     return (torch.empty(P, dtype=torch.int32, device=dev), torch.empty(P, dtype=torch.int32, device=dev),
-            torch.empty(P, dtype=torch.int32, device=dev), torch.empty((3, P), dtype=torch.float64, device=dev),
+            torch.empty(P, dtype=torch.int32, device=dev), torch.empty((dim, P), dtype=torch.float64, device=dev),
             torch.empty(P, dtype=torch.float64, device=dev))
 
 
@@ -450,7 +467,7 @@ def fp_find_eval(h: Handle, pts: torch.Tensor, qsess: Optional[torch.Tensor] = N
     P = pts.shape[1]
     qsess = None if qsess is None else _dev(qsess, torch.int32, "qsess")
     F, f64, fptr = _eval_args(fields, posted)
-    out = out or _find_outs(P, pts.device)
+    out = out or _find_outs(P, pts.device, h.dim)
     if values is None:
         values = torch.empty((F, P), dtype=torch.float64, device=pts.device)
     code, sub, elem, rst, dist2 = out
@@ -467,7 +484,7 @@ def fp_find_eval_ws(h: Handle, ws: "Workspace", pts: torch.Tensor, qsess: Option
     P = pts.shape[1]
     qsess = None if qsess is None else _dev(qsess, torch.int32, "qsess")
     F, f64, fptr = _eval_args(fields, posted)
-    out = out or _find_outs(P, pts.device)
+    out = out or _find_outs(P, pts.device, h.dim)
     if values is None:
         values = torch.empty((F, P), dtype=torch.float64, device=pts.device)
     code, sub, elem, rst, dist2 = out
@@ -487,8 +504,8 @@ def fp_update_coords(h: Handle, coords: torch.Tensor, dist: Optional[torch.Tenso
     `coords` may be a CUDA tensor or a CPU tensor (pinned for speed)."""
     if not isinstance(coords, torch.Tensor) or coords.dtype != torch.float64 or not coords.is_contiguous():
         raise TypeError("coords: expected a contiguous float64 tensor")
-    if tuple(coords.shape) != (3, h.E, (h.N + 1) ** 3):
-        raise ValueError("coords must be [3][E][(N+1)^3] of the handle's mesh")
+    if tuple(coords.shape) != (h.dim, h.E, (h.N + 1) ** h.dim):
+        raise ValueError("coords must be [d][E][(N+1)^d] of the handle's mesh")
     dist = None if dist is None else _dev(dist, torch.float64, "dist")
     st = lib().fp_update_coords(h.ptr, _ptr(coords), _ptr(dist), UPDATE_DEFAULT_DIST if default_dist else 0,
                                 _stream(stream))
@@ -507,7 +524,7 @@ def fp_find_warm(h: Handle, pts: torch.Tensor, warm=None, qsess: Optional[torch.
     we, wr = (None, None) if warm is None else (_dev(warm[0], torch.int32, "warm elem"),
                                                 _dev(warm[1], torch.float64, "warm rst"))
     F, f64, fptr = (0, None, None) if fields is None and posted is None else _eval_args(fields, posted)
-    out = out or _find_outs(P, pts.device)
+    out = out or _find_outs(P, pts.device, h.dim)
     if F and values is None:
         values = torch.empty((F, P), dtype=torch.float64, device=pts.device)
     code, sub, elem, rst, dist2 = out

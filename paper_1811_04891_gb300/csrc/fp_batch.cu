@@ -145,7 +145,7 @@ extern "C" fp_status fp_batch_create(fp_batch** out, int ninst, fp_handle* const
     cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
     for (int i = 0; i < ninst; ++i) {
         fp_handle* h = handles[i];
-        if (!h || !h->coords || npts[i] < 0) {
+        if (!h || !h->coords || h->dim != 3 || npts[i] < 0) {
             delete b;
             return FP_ERR_INVALID_ARG;
         }

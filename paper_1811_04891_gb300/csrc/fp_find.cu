@@ -17,11 +17,12 @@
 //                      compensated refinement and one FP64 step;
 //                      k_newton64_full<n> finishes the pairs that step did
 //                      not confirm in full FP64.
-//  6. k_rank<n>        per point: classify its pairs (INSIDE / BORDER), lowest
+//  6. k_rank<n,3>      per point: classify its pairs (INSIDE / BORDER), lowest
 //                      element id within a subdomain, owner = argmax of the
 //                      interpolated distance field D^k with lower-id tie band.
 #include "fp_common.cuh"
 #include "fp_internal.h"
+#include "fp_rank.cuh"
 
 namespace fpg {
 
@@ -706,153 +707,6 @@ __global__ void __launch_bounds__(256) k_newton(NewtonArgs A, BasisTab tab)
 }
 
 // ---------------------------------------------------------------------------
-// classification and ownership
-// ---------------------------------------------------------------------------
-struct RankArgs {
-    int64_t P;
-    int32_t* pair_pt;       // non-winning pairs are marked -1 for the fused eval
-    int F;                  // fused eval: write NaN for points without a winner
-    double* out;
-    int64_t E;
-    const int32_t* off;
-    const int32_t* pair_elem;
-    const double* pres;
-    const double* prst;
-    int64_t cap;
-    const int32_t* sub;
-    const ElemBox* boxes;
-    const double* dist;
-    int32_t* code;
-    int32_t* osub;
-    int32_t* oelem;
-    double* rst;
-    double* dist2;
-};
-
-template <int n>
-__device__ __forceinline__ double interp_delta(const double* __restrict__ D, const BasisTab& tab, double r0, double r1,
-                                               double r2)
-{
-    double hr[n], hs[n], ht[n];
-    lagrange_h<n, double>(tab.xi, tab.ci, r0, hr);
-    lagrange_h<n, double>(tab.xi, tab.ci, r1, hs);
-    lagrange_h<n, double>(tab.xi, tab.ci, r2, ht);
-    return contract<n, double>(D, hr, hs, ht);
-}
-
-template <int n>
-__global__ void __launch_bounds__(128) k_rank(RankArgs A, FindParams fp, BasisTab tab)
-{
-    constexpr int n3 = n * n * n;
-    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= A.P) return;
-    const int b = A.off[p], en = A.off[p + 1];
-    if (en > A.cap) {                                  // pairs dropped: not searched
-        for (int q = b; q < A.cap; ++q) A.pair_pt[q] = -1;
-        for (int f = 0; f < A.F; ++f) A.out[(int64_t)f * A.P + p] = __longlong_as_double(0x7ff8000000000000ULL);
-        A.code[p] = FP_CODE_RETRY;
-        A.osub[p] = -1;
-        A.oelem[p] = -1;
-        A.rst[p] = 0.0;
-        A.rst[A.P + p] = 0.0;
-        A.rst[2 * A.P + p] = 0.0;
-        A.dist2[p] = INFINITY;
-        return;
-    }
-    // INSIDE winners: lowest element id per subdomain
-    int best_q = -1, nwin = 0;
-    double bmin = INFINITY;
-    for (int q = b; q < en; ++q) {
-        const int e = A.pair_elem[q];
-        const double he = A.boxes[e].he;
-        const double res = A.pres[q];
-        if (res <= fp.tol_accept * he) {
-            const int s = A.sub[e];
-            bool winner = true;
-            for (int q2 = b; q2 < en && winner; ++q2) {
-                const int e2 = A.pair_elem[q2];
-                if (q2 != q && A.sub[e2] == s && e2 < e && A.pres[q2] <= fp.tol_accept * A.boxes[e2].he) winner = false;
-            }
-            if (winner) {
-                ++nwin;
-                if (best_q < 0) best_q = q;
-            }
-        } else if (res <= fp.tol_border * he) {
-            bmin = fmin(bmin, res);
-        }
-    }
-    int pick = -1;
-    int code = 2;
-    if (nwin == 1) {
-        pick = best_q;
-        code = 0;
-    } else if (nwin > 1) {
-        // owner = argmax delta^k(x*), ties within the band -> lower subdomain id
-        double dmax = -INFINITY;
-        for (int pass = 0; pass < 2; ++pass) {
-            int bs = 0x7fffffff;
-            for (int q = b; q < en; ++q) {
-                const int e = A.pair_elem[q];
-                if (!(A.pres[q] <= fp.tol_accept * A.boxes[e].he)) continue;
-                const int s = A.sub[e];
-                bool winner = true;
-                for (int q2 = b; q2 < en && winner; ++q2) {
-                    const int e2 = A.pair_elem[q2];
-                    if (q2 != q && A.sub[e2] == s && e2 < e && A.pres[q2] <= fp.tol_accept * A.boxes[e2].he)
-                        winner = false;
-                }
-                if (!winner) continue;
-                const double dl = A.dist ? interp_delta<n>(A.dist + (int64_t)e * n3, tab, A.prst[q], A.prst[A.cap + q],
-                                                           A.prst[2 * A.cap + q])
-                                         : 0.0;
-                if (pass == 0) {
-                    dmax = fmax(dmax, dl);
-                } else if (dl >= dmax - fp.band && s < bs) {
-                    bs = s;
-                    pick = q;
-                }
-            }
-        }
-        code = 0;
-    } else if (bmin < INFINITY) {
-        int be = 0x7fffffff;
-        for (int q = b; q < en; ++q) {
-            const int e = A.pair_elem[q];
-            const double he = A.boxes[e].he;
-            const double res = A.pres[q];
-            if (res > fp.tol_accept * he && res <= fp.tol_border * he && res <= bmin + fp.band && e < be) {
-                be = e;
-                pick = q;
-            }
-        }
-        code = 1;
-    }
-    for (int q = b; q < en; ++q)
-        if (q != pick) A.pair_pt[q] = -1;
-    if (pick < 0)
-        for (int f = 0; f < A.F; ++f) A.out[(int64_t)f * A.P + p] = __longlong_as_double(0x7ff8000000000000ULL);
-    if (pick >= 0) {
-        const int e = A.pair_elem[pick];
-        A.code[p] = code;
-        A.osub[p] = A.sub[e];
-        A.oelem[p] = e;
-        A.rst[p] = A.prst[pick];
-        A.rst[A.P + p] = A.prst[A.cap + pick];
-        A.rst[2 * A.P + p] = A.prst[2 * A.cap + pick];
-        const double res = A.pres[pick];
-        A.dist2[p] = res * res;
-    } else {
-        A.code[p] = 2;
-        A.osub[p] = -1;
-        A.oelem[p] = -1;
-        A.rst[p] = 0.0;
-        A.rst[A.P + p] = 0.0;
-        A.rst[2 * A.P + p] = 0.0;
-        A.dist2[p] = INFINITY;
-    }
-}
-
-// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 static ScreenArgs screen_args(const FindArgs& a)
@@ -981,7 +835,7 @@ static cudaError_t solve_n(const FindArgs& a, int64_t npairs, const BasisTab& ta
     ra.F = a.eval.F;
     ra.out = a.eval.out;
     if (a.ev[4]) cudaEventRecord(a.ev[4], s);
-    k_rank<n><<<(unsigned)((a.P + 127) / 128), 128, 0, s>>>(ra, fp, tab);
+    k_rank<n, 3><<<(unsigned)((a.P + 127) / 128), 128, 0, s>>>(ra, fp, tab);
     count_launch();
     if (a.ev[5]) cudaEventRecord(a.ev[5], s);
     cudaError_t err = cudaGetLastError();
@@ -993,10 +847,9 @@ static cudaError_t solve_n(const FindArgs& a, int64_t npairs, const BasisTab& ta
     return err;
 }
 
-cudaError_t find_solve(const FindArgs& a, int64_t npairs, const BasisTab& tab, const FindParams& fp, int block,
-                       cudaStream_t s)
+cudaError_t find_sort(const FindArgs& a, int64_t npairs, cudaStream_t s)
 {
-    cudaError_t err;
+    cudaError_t err = cudaSuccess;
     if (npairs > 0) {
         if (a.ev[0]) cudaEventRecord(a.ev[0], s);
         err = cudaMemsetAsync(a.ecount, 0, sizeof(int32_t) * a.E, s);
@@ -1012,6 +865,14 @@ cudaError_t find_solve(const FindArgs& a, int64_t npairs, const BasisTab& tab, c
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         if (a.ev[1]) cudaEventRecord(a.ev[1], s);
     }
+    return err;
+}
+
+cudaError_t find_solve(const FindArgs& a, int64_t npairs, const BasisTab& tab, const FindParams& fp, int block,
+                       cudaStream_t s)
+{
+    cudaError_t err = find_sort(a, npairs, s);
+    if (err != cudaSuccess) return err;
     switch (a.n) {
 #define FP_CASE(NN) \
     case NN: return solve_n<NN>(a, npairs, tab, fp, block, s);

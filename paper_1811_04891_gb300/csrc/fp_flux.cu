@@ -268,7 +268,7 @@ extern "C" fp_status fp_bfaces_create(const fp_handle* h, const int8_t* kind, fp
     if (!out) return FP_ERR_INVALID_ARG;
     *out = nullptr;
     if (!fp_live(h)) return FP_ERR_NOT_SETUP;
-    if (!kind) return FP_ERR_INVALID_ARG;
+    if (!kind || h->dim != 3) return FP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int n = h->n;
     const int64_t F = 6 * h->E;

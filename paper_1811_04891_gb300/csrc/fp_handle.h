@@ -12,6 +12,7 @@
 enum { PROF_SCREEN = 0, PROF_SORT = 1, PROF_NEWTON = 2, PROF_RANK = 3, PROF_EVAL = 4, PROF_KINDS = 5 };
 
 struct fp_handle {
+    int dim = 3;                   // 3: hexahedra, coords [3][E][n^3]; 2: quadrilaterals, [2][E][n^2]
     int N = 0, n = 0;
     int64_t E = 0;
     int nsub = 0;

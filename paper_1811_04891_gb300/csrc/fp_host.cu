@@ -239,7 +239,7 @@ namespace {
 // before allocates nothing.
 fp_status build_geometry(fp_handle* h, cudaStream_t s, bool default_dist)
 {
-    const int n = h->n, n3 = n * n * n;
+    const int n = h->n, n3 = h->dim == 2 ? n * n : n * n * n;
     const int64_t E = h->E;
     const fp_opts& o = h->opts;
     cudaError_t err;
@@ -250,7 +250,10 @@ fp_status build_geometry(fp_handle* h, cudaStream_t s, bool default_dist)
         h->nred = (int)std::min<int64_t>(1024, (E + 255) / 256);
         GK(dalloc(&h->red, 12 * h->nred), "alloc red");
     }
-    GK(launch_hull(n, E, h->coords, h->binv, o.tol_border, h->pad_conv, h->boxes, h->nodebox, s), "hull");
+    if (h->dim == 2)
+        GK(launch_hull2(n, E, h->coords, h->binv, o.tol_border, h->pad_conv, h->boxes, h->nodebox, s), "hull");
+    else
+        GK(launch_hull(n, E, h->coords, h->binv, o.tol_border, h->pad_conv, h->boxes, h->nodebox, s), "hull");
     GK(launch_reduce_boxes(E, h->boxes, h->nodebox, h->red, h->nred, s), "reduce boxes");
     std::vector<double> red(12 * h->nred);
     GK(cudaMemcpyAsync(red.data(), h->red, sizeof(double) * 12 * h->nred, cudaMemcpyDeviceToHost, s), "read red");
@@ -294,6 +297,7 @@ fp_status build_geometry(fp_handle* h, cudaStream_t s, bool default_dist)
         int nd = 0;
         for (int a = 0; a < 3; ++a) {
             ext[a] = ghi[a] - glo[a];
+            if (a >= h->dim) ext[a] = 0.0;                   // 2D: one cell layer in z
             if (ext[a] > 0) { vol *= ext[a]; ++nd; }
         }
         double target = std::max(1.0, o.hash_cells_per_elem * (double)E);
@@ -346,6 +350,8 @@ fp_status build_geometry(fp_handle* h, cudaStream_t s, bool default_dist)
     GK(launch_hash_sort(ncell, h->cell_start, h->cell_elems, s), "hash sort");
 
     // default distance field for the owner rule
+    if (default_dist && h->dim == 2)
+        return fail(h, FP_ERR_INVALID_ARG, "2D meshes with more than one subdomain need dist");
     if (default_dist) {
         double* fc = nullptr;
         int32_t *nb = nullptr, *nboff = nullptr, *tmp2 = nullptr;
@@ -428,8 +434,8 @@ const char* fp_last_error(const fp_handle* h)
     return h ? h->err.c_str() : g_setup_err.c_str();
 }
 
-fp_status fp_setup(fp_handle** hout, const double* coords, int64_t E, int N, const int32_t* sub,
-                   const double* dist, const fp_opts* opts_in, void* stream)
+static fp_status setup_impl(fp_handle** hout, int dim, const double* coords, int64_t E, int N, const int32_t* sub,
+                            const double* dist, const fp_opts* opts_in, void* stream)
 {
     if (!hout) return fail(nullptr, FP_ERR_INVALID_ARG, "fp_setup: null handle pointer");
     *hout = nullptr;
@@ -445,15 +451,17 @@ fp_status fp_setup(fp_handle** hout, const double* coords, int64_t E, int N, con
         !(o.hash_cells_per_elem > 0) || !(o.tie_band >= 0) || o.points_per_block < 0 ||
         o.points_per_block > 256 || (o.points_per_block % 32) != 0)
         return fail(nullptr, FP_ERR_INVALID_ARG, "fp_setup: options out of range");
-    const int n = N + 1, n3 = n * n * n;
-    if ((int64_t)E * n3 * 3 >= (int64_t(1) << 40)) return fail(nullptr, FP_ERR_INVALID_ARG, "fp_setup: mesh too large");
+    if (dim == 2 && o.precision != FP_PREC_FP64)
+        return fail(nullptr, FP_ERR_INVALID_ARG, "fp_setup_2d: 2D meshes support the FP64 form only");
+    const int n = N + 1, n3 = dim == 2 ? n * n : n * n * n;
+    if ((int64_t)E * n3 * dim >= (int64_t(1) << 40)) return fail(nullptr, FP_ERR_INVALID_ARG, "fp_setup: mesh too large");
     cudaStream_t s = (cudaStream_t)stream;
 
     fp_handle* h = new fp_handle();
-    h->N = N; h->n = n; h->E = E; h->opts = o;
+    h->N = N; h->n = n; h->E = E; h->opts = o; h->dim = dim;
     make_tab(N, &h->tab);
     cudaError_t err;
-    const size_t ncoord = (size_t)3 * E * n3;
+    const size_t ncoord = (size_t)dim * E * n3;
 #define CK(call, where) do { if ((err = (call)) != cudaSuccess) { fp_status st = cuda_fail(nullptr, err, where); release(h); delete h; return st; } } while (0)
 #define BAD(msg) do { fail(nullptr, FP_ERR_INVALID_ARG, msg); release(h); delete h; return FP_ERR_INVALID_ARG; } while (0)
 
@@ -518,6 +526,18 @@ fp_status fp_setup(fp_handle** hout, const double* coords, int64_t E, int N, con
     return FP_OK;
 }
 
+fp_status fp_setup(fp_handle** hout, const double* coords, int64_t E, int N, const int32_t* sub,
+                   const double* dist, const fp_opts* opts, void* stream)
+{
+    return setup_impl(hout, 3, coords, E, N, sub, dist, opts, stream);
+}
+
+fp_status fp_setup_2d(fp_handle** hout, const double* coords, int64_t E, int N, const int32_t* sub,
+                      const double* dist, const fp_opts* opts, void* stream)
+{
+    return setup_impl(hout, 2, coords, E, N, sub, dist, opts, stream);
+}
+
 fp_status fp_reserve(fp_handle* h, int64_t P)
 {
     if (!fp_live(h)) return FP_ERR_NOT_SETUP;
@@ -564,7 +584,8 @@ static fp_status find_impl(fp_handle* h, int64_t P, const double* pts, const int
     fp.band = h->opts.tie_band * h->L;
     fp.max_newton = h->opts.max_newton;
     fp.mixed = h->opts.precision == FP_PREC_MIXED;
-    cudaError_t err = find_count(a, h->tab, fp, s);
+    const bool d2 = h->dim == 2;
+    cudaError_t err = d2 ? find_count2(a, s) : find_count(a, h->tab, fp, s);
     if (err != cudaSuccess) return cuda_fail(h, err, "fp_find count");
     err = cudaMemcpyAsync(h->h_total, h->off + P, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (err == cudaSuccess) err = cudaStreamSynchronize(s);
@@ -577,7 +598,7 @@ static fp_status find_impl(fp_handle* h, int64_t P, const double* pts, const int
     a.pair_elem = h->pair_elem; a.pair_pt = h->pair_pt; a.order = h->order;
     a.pres = h->pres; a.prst = h->prst; a.cap = h->cap_pairs;
     if (npairs > 0) {
-        err = find_emit(a, s);
+        err = d2 ? find_emit2(a, s) : find_emit(a, s);
         if (err != cudaSuccess) return cuda_fail(h, err, "fp_find emit");
     }
     if (h->prof) {
@@ -585,7 +606,7 @@ static fp_status find_impl(fp_handle* h, int64_t P, const double* pts, const int
         h->ev_pend[PROF_SCREEN].push_back({scr0, scr1});
     }
     const int block = h->opts.points_per_block > 0 ? h->opts.points_per_block : 128;
-    err = find_solve(a, npairs, h->tab, fp, block, s);
+    err = d2 ? find_solve2(a, npairs, h->tab, fp, block, s) : find_solve(a, npairs, h->tab, fp, block, s);
     if (h->prof) {
         if (npairs > 0) {
             h->ev_pend[PROF_SORT].push_back({a.ev[0], a.ev[1]});
@@ -669,8 +690,8 @@ fp_status fp_update_coords(fp_handle* h, const double* coords, const double* dis
     if (!coords) return fail(h, FP_ERR_INVALID_ARG, "fp_update_coords: null coords");
     if ((flags & ~FP_UPDATE_DEFAULT_DIST) != 0 || (dist && (flags & FP_UPDATE_DEFAULT_DIST)))
         return fail(h, FP_ERR_INVALID_ARG, "fp_update_coords: bad flags");
-    const int n3 = h->n * h->n * h->n;
-    const size_t ncoord = (size_t)3 * h->E * n3;
+    const int n3 = h->dim == 2 ? h->n * h->n : h->n * h->n * h->n;
+    const size_t ncoord = (size_t)h->dim * h->E * n3;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t err;
     // validate the new coordinates before the handle changes
@@ -728,6 +749,7 @@ fp_status fp_workspace_create(const fp_handle* h, int64_t max_points, int64_t ma
     if (!out) return FP_ERR_INVALID_ARG;
     *out = nullptr;
     if (!fp_live(h)) return FP_ERR_NOT_SETUP;
+    if (h->dim != 3) return FP_ERR_INVALID_ARG;          // workspaces serve hexahedral meshes
     if (max_points < 1 || max_points >= (int64_t(1) << 31)) return FP_ERR_INVALID_ARG;
     if (max_pairs <= 0) max_pairs = 2 * max_points;
     if (max_pairs >= (int64_t(1) << 31)) return FP_ERR_INVALID_ARG;
@@ -839,7 +861,7 @@ fp_status fp_fields_create(const fp_handle* h, int F, const double* fields, fp_f
     if (!out) return FP_ERR_INVALID_ARG;
     *out = nullptr;
     if (!fp_live(h)) return FP_ERR_NOT_SETUP;
-    if (F < 1 || !fields) return FP_ERR_INVALID_ARG;
+    if (F < 1 || !fields || h->dim != 3) return FP_ERR_INVALID_ARG;   // the mixed form is 3D only
     const int64_t n = (int64_t)F * h->E * h->n * h->n * h->n;
     fp_fields* f = new fp_fields();
     f->owner = h;
@@ -903,7 +925,9 @@ fp_status fp_eval(fp_handle* h, int64_t P, const int32_t* code, const int32_t* e
         e1 = ev_get(h);
         cudaEventRecord(e0, (cudaStream_t)stream);
     }
-    cudaError_t err = launch_eval(h->n, h->E, P, code, elem, rst, F, fields, out, h->tab, (cudaStream_t)stream);
+    cudaError_t err = h->dim == 2
+                          ? launch_eval2(h->n, h->E, P, code, elem, rst, F, fields, out, h->tab, (cudaStream_t)stream)
+                          : launch_eval(h->n, h->E, P, code, elem, rst, F, fields, out, h->tab, (cudaStream_t)stream);
     if (h->prof) {
         cudaEventRecord(e1, (cudaStream_t)stream);
         h->ev_pend[PROF_EVAL].push_back({e0, e1});

@@ -106,6 +106,19 @@ cudaError_t find_solve(const FindArgs& a, int64_t npairs, const BasisTab& tab, c
 cudaError_t find_solve_unsorted(const FindArgs& a, int64_t npairs, const BasisTab& tab, const FindParams& fp,
                                 int block, cudaStream_t s);
 
+// counting sort of the pairs by element (fp_find.cu), shared by both dimensions
+cudaError_t find_sort(const FindArgs& a, int64_t npairs, cudaStream_t s);
+
+// 2D quadrilateral variant (fp_find2.cu): coords [2][E][n^2], pts / rst [2][P]
+cudaError_t launch_hull2(int n, int64_t E, const double* coords, const double* binv, double pad_border,
+                         double pad_conv, ElemBox* boxes, double* nodebox, cudaStream_t s);
+cudaError_t find_count2(const FindArgs& a, cudaStream_t s);
+cudaError_t find_emit2(const FindArgs& a, cudaStream_t s);
+cudaError_t find_solve2(const FindArgs& a, int64_t npairs, const BasisTab& tab, const FindParams& fp, int block,
+                        cudaStream_t s);
+cudaError_t launch_eval2(int n, int64_t E, int64_t P, const int32_t* code, const int32_t* elem, const double* rst,
+                         int F, const double* fields, double* out, const BasisTab& tab, cudaStream_t s);
+
 // eval (fp_eval.cu)
 cudaError_t launch_eval_pairs(int n, int64_t E, int64_t P, const int32_t* dcount, int64_t cap, const int32_t* order,
                               const int32_t* pair_elem, const int32_t* pair_pt, const double* prst,

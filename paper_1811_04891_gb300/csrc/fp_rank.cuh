@@ -1,0 +1,166 @@
+// fp_rank.cuh -- classification and ownership of a point's candidate pairs
+// (Sec. 2.1): INSIDE / BORDER / NOT_FOUND, the lowest element id within a
+// subdomain, and the owner by the largest interpolated distance D^k with a
+// lower-id tie band.  Shared by the hexahedral and quadrilateral paths.
+#pragma once
+#include "fp_common.cuh"
+
+namespace fpg {
+
+// ---------------------------------------------------------------------------
+// classification and ownership
+// ---------------------------------------------------------------------------
+struct RankArgs {
+    int64_t P;
+    int32_t* pair_pt;       // non-winning pairs are marked -1 for the fused eval
+    int F;                  // fused eval: write NaN for points without a winner
+    double* out;
+    int64_t E;
+    const int32_t* off;
+    const int32_t* pair_elem;
+    const double* pres;
+    const double* prst;
+    int64_t cap;
+    const int32_t* sub;
+    const ElemBox* boxes;
+    const double* dist;
+    int32_t* code;
+    int32_t* osub;
+    int32_t* oelem;
+    double* rst;
+    double* dist2;
+};
+
+// D^k interpolated at (e, r) of a DIM-dimensional element (D: n^DIM values)
+template <int n, int DIM>
+__device__ __forceinline__ double interp_delta(const double* __restrict__ D, const BasisTab& tab, const double* prst,
+                                               int64_t cap, int64_t q)
+{
+    double hr[n], hs[n];
+    lagrange_h<n, double>(tab.xi, tab.ci, prst[q], hr);
+    lagrange_h<n, double>(tab.xi, tab.ci, prst[cap + q], hs);
+    if constexpr (DIM == 2) {
+        double acc = 0.0;
+#pragma unroll 1
+        for (int j = 0; j < n; ++j) {
+            double v[n];
+            load_row<n>(D + n * j, v);
+            double u = 0.0;
+#pragma unroll
+            for (int i = 0; i < n; ++i) u = fma(hr[i], v[i], u);
+            acc = fma(hs[j], u, acc);
+        }
+        return acc;
+    } else {
+        double ht[n];
+        lagrange_h<n, double>(tab.xi, tab.ci, prst[2 * cap + q], ht);
+        return contract<n, double>(D, hr, hs, ht);
+    }
+}
+
+// one thread per point; rst and prst hold DIM rows
+template <int n, int DIM>
+__global__ void __launch_bounds__(128) k_rank(RankArgs A, FindParams fp, BasisTab tab)
+{
+    constexpr int n3 = DIM == 2 ? n * n : n * n * n;
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= A.P) return;
+    const int b = A.off[p], en = A.off[p + 1];
+    if (en > A.cap) {                                  // pairs dropped: not searched
+        for (int q = b; q < A.cap; ++q) A.pair_pt[q] = -1;
+        for (int f = 0; f < A.F; ++f) A.out[(int64_t)f * A.P + p] = __longlong_as_double(0x7ff8000000000000ULL);
+        A.code[p] = FP_CODE_RETRY;
+        A.osub[p] = -1;
+        A.oelem[p] = -1;
+        for (int a = 0; a < DIM; ++a) A.rst[a * A.P + p] = 0.0;
+        A.dist2[p] = INFINITY;
+        return;
+    }
+    // INSIDE winners: lowest element id per subdomain
+    int best_q = -1, nwin = 0;
+    double bmin = INFINITY;
+    for (int q = b; q < en; ++q) {
+        const int e = A.pair_elem[q];
+        const double he = A.boxes[e].he;
+        const double res = A.pres[q];
+        if (res <= fp.tol_accept * he) {
+            const int s = A.sub[e];
+            bool winner = true;
+            for (int q2 = b; q2 < en && winner; ++q2) {
+                const int e2 = A.pair_elem[q2];
+                if (q2 != q && A.sub[e2] == s && e2 < e && A.pres[q2] <= fp.tol_accept * A.boxes[e2].he) winner = false;
+            }
+            if (winner) {
+                ++nwin;
+                if (best_q < 0) best_q = q;
+            }
+        } else if (res <= fp.tol_border * he) {
+            bmin = fmin(bmin, res);
+        }
+    }
+    int pick = -1;
+    int code = 2;
+    if (nwin == 1) {
+        pick = best_q;
+        code = 0;
+    } else if (nwin > 1) {
+        // owner = argmax delta^k(x*), ties within the band -> lower subdomain id
+        double dmax = -INFINITY;
+        for (int pass = 0; pass < 2; ++pass) {
+            int bs = 0x7fffffff;
+            for (int q = b; q < en; ++q) {
+                const int e = A.pair_elem[q];
+                if (!(A.pres[q] <= fp.tol_accept * A.boxes[e].he)) continue;
+                const int s = A.sub[e];
+                bool winner = true;
+                for (int q2 = b; q2 < en && winner; ++q2) {
+                    const int e2 = A.pair_elem[q2];
+                    if (q2 != q && A.sub[e2] == s && e2 < e && A.pres[q2] <= fp.tol_accept * A.boxes[e2].he)
+                        winner = false;
+                }
+                if (!winner) continue;
+                const double dl = A.dist ? interp_delta<n, DIM>(A.dist + (int64_t)e * n3, tab, A.prst, A.cap, q) : 0.0;
+                if (pass == 0) {
+                    dmax = fmax(dmax, dl);
+                } else if (dl >= dmax - fp.band && s < bs) {
+                    bs = s;
+                    pick = q;
+                }
+            }
+        }
+        code = 0;
+    } else if (bmin < INFINITY) {
+        int be = 0x7fffffff;
+        for (int q = b; q < en; ++q) {
+            const int e = A.pair_elem[q];
+            const double he = A.boxes[e].he;
+            const double res = A.pres[q];
+            if (res > fp.tol_accept * he && res <= fp.tol_border * he && res <= bmin + fp.band && e < be) {
+                be = e;
+                pick = q;
+            }
+        }
+        code = 1;
+    }
+    for (int q = b; q < en; ++q)
+        if (q != pick) A.pair_pt[q] = -1;
+    if (pick < 0)
+        for (int f = 0; f < A.F; ++f) A.out[(int64_t)f * A.P + p] = __longlong_as_double(0x7ff8000000000000ULL);
+    if (pick >= 0) {
+        const int e = A.pair_elem[pick];
+        A.code[p] = code;
+        A.osub[p] = A.sub[e];
+        A.oelem[p] = e;
+        for (int a = 0; a < DIM; ++a) A.rst[a * A.P + p] = A.prst[a * A.cap + pick];
+        const double res = A.pres[pick];
+        A.dist2[p] = res * res;
+    } else {
+        A.code[p] = 2;
+        A.osub[p] = -1;
+        A.oelem[p] = -1;
+        for (int a = 0; a < DIM; ++a) A.rst[a * A.P + p] = 0.0;
+        A.dist2[p] = INFINITY;
+    }
+}
+
+}  // namespace fpg

@@ -93,6 +93,10 @@ extern "C" fp_status fp_find_static(fp_handle* h, int64_t P, const double* pts, 
     using namespace fpg;
     if (!fp_live(h)) return FP_ERR_NOT_SETUP;
     h->err.clear();
+    if (h->dim != 3) {
+        h->err = "fp_find_static: hexahedral meshes only";
+        return FP_ERR_INVALID_ARG;
+    }
     if (P < 0 || P > kMaxPoints) {
         h->err = "fp_find_static: P must be in [0, FP_STATIC_MAX_POINTS = 16384]";
         return FP_ERR_INVALID_ARG;
