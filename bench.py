@@ -75,6 +75,7 @@ def parse():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-interface", action="store_true")
     ap.add_argument("--no-moving", action="store_true")
+    ap.add_argument("--no-planar", action="store_true")
     ap.add_argument("--served-requests", type=int, default=200)
     ap.add_argument("--served-load", type=float, default=0.7)
     ap.add_argument("--served-scale", type=float, default=1.0,
@@ -421,6 +422,69 @@ def _moving_form(args, fg, dev, mesh, coords, sub, pts, fields, form):
                     "step = update + warm find + eval"}
 
 
+def run_planar(args, fg, dev):
+    """2D variant (quadrilaterals, the paper's 2D overset examples): a
+    512 x 512 deformed quad mesh at N=7 (amplitude 0.1 h) with 1e7 uniform
+    points and three fields, find + eval per step (FP64 form); and the
+    box + annulus overset workload (session tags, owner rule), whose few
+    thousand interface points make it latency-bound."""
+    import torch
+
+    import synth
+    out = {}
+    ne = 512
+    coords = torch.from_numpy(synth.quad_mesh((ne, ne), 7, amp_frac=0.1)).to(dev)
+    E = coords.shape[1]
+    P = args.points
+    pts = torch.from_numpy(synth.uniform_points_2d(P, seed=0)).to(dev)
+    x, y = coords[0], coords[1]
+    fields = torch.stack([torch.sin(torch.pi * x) * torch.cos(torch.pi * y), x * y, torch.exp(x - y)]).contiguous()
+    h = fg.fp_setup_2d(coords, 7, torch.zeros(E, dtype=torch.int32, device=dev))
+    fg.fp_reserve(h, P)
+    outs = fg._find_outs(P, dev, 2)
+    vals = torch.empty((3, P), dtype=torch.float64, device=dev)
+    for _ in range(max(args.warmup, 1)):
+        fg.fp_find_eval(h, pts, None, fields=fields, out=outs, values=vals)
+    torch.cuda.synchronize()
+    fg.fp_profile(h, True)
+    for k in fg.PROF_KINDS:
+        fg.fp_profile_read(h, k)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        fg.fp_find_eval(h, pts, None, fields=fields, out=outs, values=vals)
+    e1.record()
+    torch.cuda.synchronize()
+    fg.fp_profile(h, False)
+    kt = {k: fg.fp_profile_read(h, k) for k in fg.PROF_KINDS}
+    ms = e0.elapsed_time(e1) / args.steps
+    counts = torch.bincount(outs[0].long(), minlength=3).tolist()
+    out["quad512_N7"] = {"E": E, "points": P, "fields": 3, "ms_per_step": ms, "points_per_s": P / (ms / 1e3),
+                         "pairs_per_point": fg.fp_last_find_stats(h) / P,
+                         "kernel_ms": {k: (v[0] / max(v[1], 1)) for k, v in kt.items()},
+                         "codes": {"inside": counts[0], "border": counts[1], "not_found": counts[2]}}
+    del h
+    mesh, q = synth.walsh_2d(N=7, n_box=16, ring=(16, 3))
+    h = fg.fp_setup_2d(torch.from_numpy(mesh.coords).to(dev), mesh.N, torch.from_numpy(mesh.sub).to(dev),
+                       torch.from_numpy(mesh.dist).to(dev))
+    pq = torch.from_numpy(q.pts).to(dev)
+    qs = torch.from_numpy(q.qsess).to(dev)
+    fq = torch.from_numpy(q.fields).to(dev)
+    found = fg.fp_find_eval(h, pq, qs, fields=fq)
+    for _ in range(3):
+        fg.fp_find_eval(h, pq, qs, fields=fq, out=found[:5], values=found[5])
+    torch.cuda.synchronize()
+    reps = 50
+    e0.record()
+    for _ in range(reps):
+        fg.fp_find_eval(h, pq, qs, fields=fq, out=found[:5], values=found[5])
+    e1.record()
+    torch.cuda.synchronize()
+    out["walsh_overset_N7"] = {"E": mesh.E, "points": q.P, "ms_per_call": e0.elapsed_time(e1) / reps,
+                               "note": "box 16x16 + annulus 16x3, tagged interface points, find + eval of u, v, p"}
+    return out
+
+
 # ---------------------------------------------------------------------------
 # served form: resident box + two rotated annular cylinders, Poisson requests
 # ---------------------------------------------------------------------------
@@ -629,6 +693,9 @@ def main():
 
     batched = None
     moving = None
+    planar = None
+    if rank == 0 and not args.no_planar:
+        planar = run_planar(args, fg, dev)
     if not args.no_moving:
         moving = run_moving(args, fg, dev, mesh, coords, sub, pts, fields)
     if not args.no_batched:
@@ -658,7 +725,7 @@ def main():
                               "newton_paths_per_step": v["newton_paths_per_step"]} for k, v in results.items()},
                 "roofline": roof, "roofline_other_forms": roof_other, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": R["gpu_launches"],
                 "clocks": R["clocks"], "batched": batched, "serving": served, "interface": interface,
-                "moving": moving}
+                "moving": moving, "planar": planar}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -307,10 +307,29 @@ __device__ __forceinline__ T box_step(const T (&r)[3], const T (&d)[3], T (&rn)[
 // the active-set step.  Converged when the next step is <= 1e-13 in every
 // coordinate (r is then kept with its own residual).  Returns true on
 // convergence; `res` is the residual norm at the returned r.
+// Threshold of the chord check: 1e-13 in r, raised to the rounding level of a
+// step where that is larger.  The residual x(r) - x* carries rounding errors
+// of a few units of |x*|, which a step J^-1 f turns into ||J^-1|| times as
+// much in r; on small elements far from the origin that exceeds 1e-13 and no
+// step could confirm convergence.  2 eps |x*| ||J^-1||_inf bounds the noise.
+__device__ __forceinline__ double chord_tol3(const double (&J)[9], const double (&xs)[3])
+{
+    const double C00 = J[4] * J[8] - J[5] * J[7], C01 = J[5] * J[6] - J[3] * J[8], C02 = J[3] * J[7] - J[4] * J[6];
+    const double det = J[0] * C00 + J[1] * C01 + J[2] * C02;
+    if (!(fabs(det) > 0.0) || !isfinite(det)) return Lim<double>::chord;
+    const double C10 = J[2] * J[7] - J[1] * J[8], C11 = J[0] * J[8] - J[2] * J[6], C12 = J[1] * J[6] - J[0] * J[7];
+    const double C20 = J[1] * J[5] - J[2] * J[4], C21 = J[2] * J[3] - J[0] * J[5], C22 = J[0] * J[4] - J[1] * J[3];
+    const double rows = fmax(fabs(C00) + fabs(C10) + fabs(C20),
+                             fmax(fabs(C01) + fabs(C11) + fabs(C21), fabs(C02) + fabs(C12) + fabs(C22)));
+    const double xm = fmax(fabs(xs[0]), fmax(fabs(xs[1]), fabs(xs[2])));
+    return fmax(Lim<double>::chord, 4.440892098500626e-16 * xm * rows / fabs(det));
+}
+
 template <int n>
 __device__ bool chord64(const ElemPtr<double>& el, const BasisTab& tab, const double (&xs)[3], double (&r)[3],
                         const double (&J)[9], double& res, int max_chord)
 {
+    const double tol = chord_tol3(J, xs);
     for (int it = 0; it < max_chord; ++it) {
         double f[3];
         eval_f<n, double>(el, tab, r, xs, f);
@@ -321,7 +340,7 @@ __device__ bool chord64(const ElemPtr<double>& el, const BasisTab& tab, const do
         double rn[3];
         box_step<double>(r, d, rn);
         const double sn = fmax(fabs(rn[0] - r[0]), fmax(fabs(rn[1] - r[1]), fabs(rn[2] - r[2])));
-        if (sn <= Lim<double>::chord) return true;
+        if (sn <= tol) return true;
         r[0] = rn[0]; r[1] = rn[1]; r[2] = rn[2];
     }
     return false;
@@ -340,6 +359,7 @@ __device__ T newton(const ElemPtr<T>& el, const BasisTab& tab, const T (&xs)[3],
     eval_fJ<n, T>(el, tab, r, xs, f, J);
     T phi = T(0.5) * (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
     T rho = T(1);
+    int chord_fail = 0;   // after two failed chord checks the trust-region rules alone finish the solve
     converged = true;
     for (int it = 0; it < max_it; ++it) {
         if (!(phi > T(0))) return T(0);
@@ -362,7 +382,7 @@ __device__ T newton(const ElemPtr<T>& el, const BasisTab& tab, const T (&xs)[3],
         const T sn = fmax(fabs(s[0]), fmax(fabs(s[1]), fabs(s[2])));
         if (!(sn > T(0))) return sqrt(T(2) * phi);
         // a small unconstrained Newton step: quadratic convergence from here
-        if (full && nfree == 3 && dn <= Lim<T>::quick) {
+        if (full && nfree == 3 && dn <= Lim<T>::quick && chord_fail < 2) {
             if constexpr (!FINAL) {
                 r[0] = rn[0]; r[1] = rn[1]; r[2] = rn[2];
                 return sqrt(T(2) * phi);
@@ -374,6 +394,7 @@ __device__ T newton(const ElemPtr<T>& el, const BasisTab& tab, const T (&xs)[3],
                     return res;
                 }
                 r[0] = rc[0]; r[1] = rc[1]; r[2] = rc[2];   // not yet converged: refresh J
+                ++chord_fail;
                 eval_fJ<n, T>(el, tab, r, xs, f, J);
                 phi = T(0.5) * (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
                 continue;

@@ -403,10 +403,23 @@ constexpr double kChord2 = 1e-13;   // chord correction that confirms convergenc
 constexpr double kStop2 = 1e-13;    // accepted step that ends a constrained solve
 constexpr double kRhoMin2 = 1e-15;
 
+// Threshold of the chord check: 1e-13 in r, raised to the rounding level of a
+// step (2 eps |x*| ||J^-1||_inf) where that is larger, as in the hexahedral
+// solver: on small elements far from the origin rounding alone exceeds 1e-13.
+__device__ __forceinline__ double chord_tol2(const double (&J)[4], const double (&xs)[2])
+{
+    const double det = J[0] * J[3] - J[1] * J[2];
+    if (!(fabs(det) > 0.0) || !isfinite(det)) return kChord2;
+    const double rows = fmax(fabs(J[3]) + fabs(J[1]), fabs(J[2]) + fabs(J[0]));
+    const double xm = fmax(fabs(xs[0]), fabs(xs[1]));
+    return fmax(kChord2, 4.440892098500626e-16 * xm * rows / fabs(det));
+}
+
 template <int n>
 __device__ bool chord2(const double* X0, const double* X1, const BasisTab& tab, const double (&xs)[2],
                        double (&r)[2], const double (&J)[4], double& res, int max_chord)
 {
+    const double tol = chord_tol2(J, xs);
     for (int it = 0; it < max_chord; ++it) {
         double f[2];
         eval_f2<n>(X0, X1, tab, r, xs, f);
@@ -417,7 +430,7 @@ __device__ bool chord2(const double* X0, const double* X1, const BasisTab& tab, 
         double rn[2];
         box_step2(r, d, rn);
         const double sn = fmax(fabs(rn[0] - r[0]), fabs(rn[1] - r[1]));
-        if (sn <= kChord2) return true;
+        if (sn <= tol) return true;
         r[0] = rn[0];
         r[1] = rn[1];
     }
@@ -434,6 +447,7 @@ __device__ double newton2(const double* X0, const double* X1, const BasisTab& ta
     eval_fJ2<n>(X0, X1, tab, r, xs, f, J);
     double phi = 0.5 * (f[0] * f[0] + f[1] * f[1]);
     double rho = 1.0;
+    int chord_fail = 0;   // after two failed chord checks the trust-region rules alone finish the solve
     for (int it = 0; it < max_it; ++it) {
         if (!(phi > 0.0)) return 0.0;
         double d[2];
@@ -453,7 +467,7 @@ __device__ double newton2(const double* X0, const double* X1, const BasisTab& ta
         const double s[2] = {rn[0] - r[0], rn[1] - r[1]};
         const double sn = fmax(fabs(s[0]), fabs(s[1]));
         if (!(sn > 0.0)) return sqrt(2.0 * phi);
-        if (full && nfree == 2 && dn <= kQuick2) {
+        if (full && nfree == 2 && dn <= kQuick2 && chord_fail < 2) {
             double rc[2] = {rn[0], rn[1]};
             double res;
             if (chord2<n>(X0, X1, tab, xs, rc, J, res, 3)) {
@@ -463,6 +477,7 @@ __device__ double newton2(const double* X0, const double* X1, const BasisTab& ta
             }
             r[0] = rc[0];
             r[1] = rc[1];
+            ++chord_fail;
             eval_fJ2<n>(X0, X1, tab, r, xs, f, J);
             phi = 0.5 * (f[0] * f[0] + f[1] * f[1]);
             continue;
