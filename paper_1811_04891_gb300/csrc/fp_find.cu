@@ -20,6 +20,8 @@
 //  6. k_rank<n,3>      per point: classify its pairs (INSIDE / BORDER), lowest
 //                      element id within a subdomain, owner = argmax of the
 //                      interpolated distance field D^k with lower-id tie band.
+#include <algorithm>
+
 #include "fp_common.cuh"
 #include "fp_internal.h"
 #include "fp_rank.cuh"
@@ -481,6 +483,9 @@ struct NewtonArgs {
                                 // [1] FP32 not converged, [2] FP64 step converged, [3] sent to the fallback
     const int32_t* warm_elem;   // optional [P]: each point's element at the previous mesh position
     const double* warm_rst;     // [3][P]: its reference coordinates there
+    int32_t* fb_count;          // mixed form: number of pairs sent to the FP64 fallback (zeroed before)
+    int32_t* fb_list;           // their slots, the first fb_cap of them
+    int64_t fb_cap;
 };
 
 // warm start (moving meshes): a pair whose element is the point's previous
@@ -518,6 +523,15 @@ __device__ __forceinline__ void solve_pair(const NewtonArgs& A, const BasisTab& 
     A.prst[q] = r[0];
     A.prst[A.cap + q] = r[1];
     A.prst[2 * A.cap + q] = r[2];
+}
+
+// FP32 value of a reference coordinate that is +-1 only when r is exactly +-1
+__device__ __forceinline__ float f32_inside(double v)
+{
+    float f = (float)v;
+    if (f >= 1.0f && v < 1.0) f = 0.99999994f;       // largest float below 1
+    if (f <= -1.0f && v > -1.0) f = -0.99999994f;
+    return f;
 }
 
 // ---- compensated FP32 residual for the refinement steps of the mixed form ----
@@ -651,7 +665,9 @@ __global__ void __launch_bounds__(256) k_newton_mixed(NewtonArgs A, BasisTab tab
                 for (int it = 0; it < 2; ++it) {
                     float f[3], d[3];
                     resid_df<n>(el32, lo32, tab, r, xd, f);
-                    const float rf[3] = {(float)r[0], (float)r[1], (float)r[2]};
+                    // the active set is decided on r itself: a coordinate just inside
+                    // a bound must not round onto it (it would be frozen off the bound)
+                    const float rf[3] = {f32_inside(r[0]), f32_inside(r[1]), f32_inside(r[2])};
                     if (gn_step<float>(J32, f, rf, d) == 0) break;
                     const double dd[3] = {(double)d[0], (double)d[1], (double)d[2]};
                     double rn[3];
@@ -675,47 +691,69 @@ __global__ void __launch_bounds__(256) k_newton_mixed(NewtonArgs A, BasisTab tab
         A.prst[A.cap + q] = r[1];
         A.prst[2 * A.cap + q] = r[2];
         A.pres[q] = res;
+        if (res < 0.0) {
+            const int32_t k = atomicAdd(A.fb_count, 1);
+            if (k < A.fb_cap) A.fb_list[k] = q;
+        }
     }
 }
 
 // pass 3 (FP64): full trust-region Newton for the pairs marked -1, from the
-// point the earlier passes reached.  These pairs are few and scattered, so
-// each block first gathers the marked pairs of a chunk of slots into shared
-// memory and then solves them with consecutive threads (dense warps).
+// point the earlier passes reached.  These pairs are few and scattered, and
+// each solve is a long dependent chain: the kernel is latency-bound.  The
+// mixed pass listed them (fb_list), so consecutive lanes take consecutive
+// list entries (dense warps) and blocks of one warp spread the warps over
+// the SMs.  If the list overflowed, blocks instead gather the marked pairs of
+// chunks of slots into shared memory and solve those.
+constexpr int kFullChunk = 8192;
+constexpr int kFullSub = 1024;
+
 template <int n>
-__global__ void __launch_bounds__(256) k_newton64_full(NewtonArgs A, BasisTab tab)
+__device__ __forceinline__ void solve_full64(const NewtonArgs& A, const BasisTab& tab, int32_t q)
 {
     constexpr int n3 = n * n * n;
-    constexpr int CH = 8192;                                    // slots gathered per round
-    __shared__ int32_t list[CH];
+    const int e = A.pair_elem[q];
+    const int64_t p = A.pair_pt[q];
+    const double xs[3] = {A.pts[p], A.pts[A.P + p], A.pts[2 * A.P + p]};
+    const ElemPtr<double> el64 = {A.coords + (int64_t)e * n3, A.coords + (A.E + e) * n3,
+                                  A.coords + (2 * A.E + e) * n3};
+    double r[3] = {A.prst[q], A.prst[A.cap + q], A.prst[2 * A.cap + q]}, J[9];
+    bool conv;
+    const double res = newton<n, double, true>(el64, tab, xs, r, J, A.max_newton, conv);
+    A.prst[q] = r[0];
+    A.prst[A.cap + q] = r[1];
+    A.prst[2 * A.cap + q] = r[2];
+    A.pres[q] = res;
+}
+
+template <int n>
+__global__ void __launch_bounds__(32) k_newton64_full(NewtonArgs A, BasisTab tab)
+{
+    const int64_t nfb = *A.fb_count;
+    if (nfb <= A.fb_cap) {
+        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nfb;
+             t += (int64_t)gridDim.x * blockDim.x)
+            solve_full64<n>(A, tab, A.fb_list[t]);
+        return;
+    }
+    __shared__ int32_t list[kFullSub];
     __shared__ int count;
     const int64_t npairs = live_pairs(A.dcount, A.cap);
-    for (int64_t base = (int64_t)blockIdx.x * CH; base < npairs; base += (int64_t)gridDim.x * CH) {
-        if (threadIdx.x == 0) count = 0;
-        __syncthreads();
-        const int64_t end = base + CH < npairs ? base + CH : npairs;
-        for (int64_t s = base + threadIdx.x; s < end; s += blockDim.x) {
-            const int32_t q = A.order[s];
-            if (A.pres[q] < 0.0) list[atomicAdd(&count, 1)] = q;
+    for (int64_t base = (int64_t)blockIdx.x * kFullChunk; base < npairs; base += (int64_t)gridDim.x * kFullChunk) {
+        const int64_t cend = base + kFullChunk < npairs ? base + kFullChunk : npairs;
+        for (int64_t sb = base; sb < cend; sb += kFullSub) {
+            if (threadIdx.x == 0) count = 0;
+            __syncthreads();
+            const int64_t end = sb + kFullSub < cend ? sb + kFullSub : cend;
+            for (int64_t s = sb + threadIdx.x; s < end; s += blockDim.x) {
+                const int32_t q = A.order[s];
+                if (A.pres[q] < 0.0) list[atomicAdd(&count, 1)] = q;
+            }
+            __syncthreads();
+            const int m = count;
+            for (int t = threadIdx.x; t < m; t += blockDim.x) solve_full64<n>(A, tab, list[t]);
+            __syncthreads();
         }
-        __syncthreads();
-        const int m = count;
-        for (int t = threadIdx.x; t < m; t += blockDim.x) {
-            const int32_t q = list[t];
-            const int e = A.pair_elem[q];
-            const int64_t p = A.pair_pt[q];
-            const double xs[3] = {A.pts[p], A.pts[A.P + p], A.pts[2 * A.P + p]};
-            const ElemPtr<double> el64 = {A.coords + (int64_t)e * n3, A.coords + (A.E + e) * n3,
-                                          A.coords + (2 * A.E + e) * n3};
-            double r[3] = {A.prst[q], A.prst[A.cap + q], A.prst[2 * A.cap + q]}, J[9];
-            bool conv;
-            const double res = newton<n, double, true>(el64, tab, xs, r, J, A.max_newton, conv);
-            A.prst[q] = r[0];
-            A.prst[A.cap + q] = r[1];
-            A.prst[2 * A.cap + q] = r[2];
-            A.pres[q] = res;
-        }
-        __syncthreads();
     }
 }
 
@@ -822,11 +860,25 @@ static cudaError_t solve_n(const FindArgs& a, int64_t npairs, const BasisTab& ta
         na.stats = a.stats;
         na.warm_elem = a.warm_elem;
         na.warm_rst = a.warm_rst;
+        na.fb_count = nullptr;
+        na.fb_list = nullptr;
+        na.fb_cap = 0;
         const unsigned grid = grid_for(npairs, block, a.persistent_blocks);
         if (a.ev[2]) cudaEventRecord(a.ev[2], s);
         if (fp.mixed) {
+            // fallback list: the per-point counts (free after the scan) hold
+            // the slots, the first scan scratch word (free after the sort) the count
+            na.fb_count = a.scan_tmp;
+            na.fb_list = a.cnt;
+            na.fb_cap = a.P;
+            cudaError_t e0 = cudaMemsetAsync(a.scan_tmp, 0, sizeof(int32_t), s);
+            if (e0 != cudaSuccess) return e0;
             k_newton_mixed<n><<<grid, block, 0, s>>>(na, tab);
-            k_newton64_full<n><<<grid, block, 0, s>>>(na, tab);
+            // blocks of one warp: enough for a list of up to 38,912 pairs in one
+            // pass, and for the chunked path over every slot if it overflowed
+            const unsigned gfull = (unsigned)std::max<int64_t>(
+                1216, a.persistent_blocks > 0 ? 0 : (npairs + kFullChunk - 1) / kFullChunk);
+            k_newton64_full<n><<<gfull, 32, 0, s>>>(na, tab);
             count_launch(2);
         } else {
             k_newton<n><<<grid, block, 0, s>>>(na, tab);
