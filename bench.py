@@ -53,7 +53,7 @@ P32_NOMINAL = 152 * 128 * 2 * 2.07e9
 SEED, ITER, RESID, RESID_DF, BASIS64, EVAL1 = 4.1e3, 8.4e3, 3.5e3, 19.3e3, 0.3e3, 1.17e3
 # DRAM bytes (read + written) per pair of the Newton stage, measured with ncu on the
 # 2.02M-point case of this workload (2.05M pairs) and scaled by the pairs of a launch.
-TRAFFIC_PER_PAIR = {"mixed": 1274.0, "fp64": 738.0}
+TRAFFIC_PER_PAIR = {"mixed": 1239.0, "fp64": 740.0}
 WORK = {"fp64": {"f64": SEED + 4 * ITER, "f32": 0.0},
         "mixed": {"f64": RESID + BASIS64, "f32": SEED + 4 * ITER + 2 * RESID_DF}}
 
