@@ -331,6 +331,26 @@ fp_status fp_find_warm(fp_handle *h, int64_t P, const double *pts, const int32_t
                        int32_t *sub, int32_t *elem, double *rst, double *dist2, double *out,
                        void *stream);
 
+/* fp_find_eval_host -- fp_find_eval (F == 0 and posted == NULL: fp_find) for
+ * points and results in HOST memory.  The points are cut into chunks of
+ * `chunk` points (<= 0: 2^22); while the device searches one chunk, a copy
+ * stream brings the next one in and another takes the results of the
+ * previous one out, so the copies overlap the search.  Two sets of device
+ * buffers alternate; they are kept in the handle for later calls (grown when
+ * a call asks for more) and freed with it.
+ *   pts [3][P], qsess [P] or NULL: host memory (pinned memory copies fastest)
+ *   fields / posted: device, as for fp_find_eval
+ *   code, sub, elem [P], rst [3][P], dist2 [P], out [F][P]: host memory
+ * Results are those of fp_find_eval on the same points.  The call waits for
+ * its work (work queued earlier on `stream` runs first) and returns with
+ * the host outputs complete.  Allocates on its first call and when it grows.
+ * Hexahedral handles only.  Errors: FP_ERR_NOT_SETUP, FP_ERR_INVALID_ARG,
+ * FP_ERR_OOM, FP_ERR_CUDA. */
+fp_status fp_find_eval_host(fp_handle *h, int64_t P, const double *pts, const int32_t *qsess, int F,
+                            const double *fields, const fp_fields *posted, int32_t *code,
+                            int32_t *sub, int32_t *elem, double *rst, double *dist2, double *out,
+                            int64_t chunk, void *stream);
+
 /* Mass-flux correction of interpolated interface velocity (Sec. 2.2,
  * Eqs. consv1, corr, consv2).
  * fp_bfaces_create: kind [E][6] int8 on the device marks faces of the

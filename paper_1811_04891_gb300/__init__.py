@@ -94,6 +94,8 @@ def _load():
     L.fp_eval_df.restype = ci
     L.fp_find_eval.argtypes = [vp, i64, vp, vp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.fp_find_eval.restype = ci
+    L.fp_find_eval_host.argtypes = [vp, i64, vp, vp, ci, vp, vp, vp, vp, vp, vp, vp, vp, i64, vp]
+    L.fp_find_eval_host.restype = ci
     L.fp_setup_2d.argtypes = list(L.fp_setup.argtypes)
     L.fp_setup_2d.restype = ci
     L.fp_find_warm.argtypes = [vp, i64, vp, vp, vp, vp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -492,6 +494,36 @@ def fp_find_eval_ws(h: Handle, ws: "Workspace", pts: torch.Tensor, qsess: Option
                                _ptr(elem), _ptr(rst), _ptr(dist2), _ptr(values), _stream(stream))
     _check(st, h.ptr)
     return code, sub, elem, rst, dist2, values
+
+
+def fp_find_eval_host(h: Handle, pts: torch.Tensor, qsess: Optional[torch.Tensor] = None, fields=None,
+                      posted: Optional["Fields"] = None, out=None, values: Optional[torch.Tensor] = None,
+                      chunk: int = 0, stream=None):
+    """find (+ eval when fields or posted are given) over points in HOST
+    memory (CPU tensor [3][P] float64, pinned for speed), streamed through
+    the device in chunks with the copies overlapping the search.  Returns
+    CPU tensors (code, sub, elem, rst [3][P], dist2[, values [F][P]])."""
+    if not isinstance(pts, torch.Tensor) or pts.is_cuda or pts.dtype != torch.float64 or not pts.is_contiguous():
+        raise TypeError("pts: expected a contiguous float64 CPU tensor")
+    if pts.ndim != 2 or pts.shape[0] != 3:
+        raise ValueError("pts must be [3][P]")
+    P = pts.shape[1]
+    if qsess is not None and (qsess.is_cuda or qsess.dtype != torch.int32 or not qsess.is_contiguous()):
+        raise TypeError("qsess: expected a contiguous int32 CPU tensor")
+    F, f64, fptr = (0, None, None) if fields is None and posted is None else _eval_args(fields, posted)
+    pin = pts.is_pinned()
+    if out is None:
+        out = (torch.empty(P, dtype=torch.int32, pin_memory=pin), torch.empty(P, dtype=torch.int32, pin_memory=pin),
+               torch.empty(P, dtype=torch.int32, pin_memory=pin), torch.empty((3, P), dtype=torch.float64, pin_memory=pin),
+               torch.empty(P, dtype=torch.float64, pin_memory=pin))
+    if F and values is None:
+        values = torch.empty((F, P), dtype=torch.float64, pin_memory=pin)
+    code, sub, elem, rst, dist2 = out
+    st = lib().fp_find_eval_host(h.ptr, P, _ptr(pts), _ptr(qsess), F, _ptr(f64), fptr, _ptr(code), _ptr(sub),
+                                 _ptr(elem), _ptr(rst), _ptr(dist2), _ptr(values if F else None), int(chunk),
+                                 _stream(stream))
+    _check(st, h.ptr)
+    return (code, sub, elem, rst, dist2, values) if F else (code, sub, elem, rst, dist2)
 
 
 UPDATE_DEFAULT_DIST = 1

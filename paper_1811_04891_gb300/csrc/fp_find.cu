@@ -327,14 +327,91 @@ __device__ __forceinline__ double chord_tol3(const double (&J)[9], const double 
     return fmax(Lim<double>::chord, 4.440892098500626e-16 * xm * rows / fabs(det));
 }
 
+// ---- one warp per pair: the n^2 rows of the contractions are split over the
+// lanes, partial sums reduced to lane 0 in a fixed order and broadcast, so
+// every lane holds the same bits and the Newton control flow stays uniform
+// across the warp.  Used for the few pairs of the mixed form's fallback, whose
+// cost is the latency of one long FP64 solve rather than throughput.
+__device__ __forceinline__ double warp_sum_bcast(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+
 template <int n>
+__device__ void eval_fJ_warp(const ElemPtr<double>& el, const BasisTab& tab, const double (&r)[3],
+                             const double (&xs)[3], double (&f)[3], double (&J)[9])
+{
+    double hr[n], dr[n], hs[n], ds[n], ht[n], dt[n];
+    lagrange_hd<n, double>(tab.xi, tab.ci, r[0], hr, dr);
+    lagrange_hd<n, double>(tab.xi, tab.ci, r[1], hs, ds);
+    lagrange_hd<n, double>(tab.xi, tab.ci, r[2], ht, dt);
+    double x[3] = {0, 0, 0}, xr[3] = {0, 0, 0}, xsd[3] = {0, 0, 0}, xt[3] = {0, 0, 0};
+    const int lane = threadIdx.x & 31;
+    for (int q = lane; q < n * n; q += 32) {              // row q = j + n k
+        const int j = q % n, k = q / n;
+        const double hsj = hs[j], dsj = ds[j], htk = ht[k], dtk = dt[k];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double v[n];
+            load_row<n>((a == 0 ? el.X0 : (a == 1 ? el.X1 : el.X2)) + n * q, v);
+            double u = 0.0, w = 0.0;
+#pragma unroll
+            for (int i = 0; i < n; ++i) {
+                u = fma(hr[i], v[i], u);
+                w = fma(dr[i], v[i], w);
+            }
+            x[a] = fma(htk, hsj * u, x[a]);
+            xr[a] = fma(htk, hsj * w, xr[a]);
+            xsd[a] = fma(htk, dsj * u, xsd[a]);
+            xt[a] = fma(dtk, hsj * u, xt[a]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        f[a] = warp_sum_bcast(x[a]) - xs[a];
+        J[3 * a + 0] = warp_sum_bcast(xr[a]);
+        J[3 * a + 1] = warp_sum_bcast(xsd[a]);
+        J[3 * a + 2] = warp_sum_bcast(xt[a]);
+    }
+}
+
+template <int n>
+__device__ void eval_f_warp(const ElemPtr<double>& el, const BasisTab& tab, const double (&r)[3],
+                            const double (&xs)[3], double (&f)[3])
+{
+    double hr[n], hs[n], ht[n];
+    lagrange_h<n, double>(tab.xi, tab.ci, r[0], hr);
+    lagrange_h<n, double>(tab.xi, tab.ci, r[1], hs);
+    lagrange_h<n, double>(tab.xi, tab.ci, r[2], ht);
+    double x[3] = {0, 0, 0};
+    const int lane = threadIdx.x & 31;
+    for (int q = lane; q < n * n; q += 32) {
+        const double c = ht[q / n] * hs[q % n];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double v[n];
+            load_row<n>((a == 0 ? el.X0 : (a == 1 ? el.X1 : el.X2)) + n * q, v);
+            double u = 0.0;
+#pragma unroll
+            for (int i = 0; i < n; ++i) u = fma(hr[i], v[i], u);
+            x[a] = fma(c, u, x[a]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) f[a] = warp_sum_bcast(x[a]) - xs[a];
+}
+
+template <int n, bool WARP = false>
 __device__ bool chord64(const ElemPtr<double>& el, const BasisTab& tab, const double (&xs)[3], double (&r)[3],
                         const double (&J)[9], double& res, int max_chord)
 {
     const double tol = chord_tol3(J, xs);
     for (int it = 0; it < max_chord; ++it) {
         double f[3];
-        eval_f<n, double>(el, tab, r, xs, f);
+        if constexpr (WARP) eval_f_warp<n>(el, tab, r, xs, f);
+        else eval_f<n, double>(el, tab, r, xs, f);
         res = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
         if (!(res > 0.0)) return true;
         double d[3];
@@ -353,12 +430,17 @@ __device__ bool chord64(const ElemPtr<double>& el, const BasisTab& tab, const do
 // residual norm ||x(r) - x*|| at the returned r.  With FINAL (FP64) a small
 // full Newton step hands over to chord iterations with the current Jacobian;
 // without it (FP32 phase of the mixed form) the loop stops after such a step.
-template <int n, typename T, bool FINAL>
+template <int n, typename T, bool FINAL, bool WARP = false>
 __device__ T newton(const ElemPtr<T>& el, const BasisTab& tab, const T (&xs)[3], T (&r)[3], T (&J)[9], int max_it,
                     bool& converged)
 {
+    static_assert(!WARP || (FINAL && sizeof(T) == 8), "the warp-cooperative solver is the FP64 one");
+    auto fJ = [&](const T (&rr)[3], T (&ff)[3], T (&JJ)[9]) {
+        if constexpr (WARP) eval_fJ_warp<n>(el, tab, rr, xs, ff, JJ);
+        else eval_fJ<n, T>(el, tab, rr, xs, ff, JJ);
+    };
     T f[3];
-    eval_fJ<n, T>(el, tab, r, xs, f, J);
+    fJ(r, f, J);
     T phi = T(0.5) * (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
     T rho = T(1);
     int chord_fail = 0;   // after two failed chord checks the trust-region rules alone finish the solve
@@ -391,13 +473,13 @@ __device__ T newton(const ElemPtr<T>& el, const BasisTab& tab, const T (&xs)[3],
             } else {
                 T rc[3] = {rn[0], rn[1], rn[2]};
                 T res;
-                if (chord64<n>(el, tab, xs, rc, J, res, 3)) {
+                if (chord64<n, WARP>(el, tab, xs, rc, J, res, 3)) {
                     r[0] = rc[0]; r[1] = rc[1]; r[2] = rc[2];
                     return res;
                 }
                 r[0] = rc[0]; r[1] = rc[1]; r[2] = rc[2];   // not yet converged: refresh J
                 ++chord_fail;
-                eval_fJ<n, T>(el, tab, r, xs, f, J);
+                fJ(r, f, J);
                 phi = T(0.5) * (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
                 continue;
             }
@@ -407,7 +489,7 @@ __device__ T newton(const ElemPtr<T>& el, const BasisTab& tab, const T (&xs)[3],
         for (int a = 0; a < 3; ++a) mf[a] = f[a] + J[3 * a] * s[0] + J[3 * a + 1] * s[1] + J[3 * a + 2] * s[2];
         const T pred = phi - T(0.5) * (mf[0] * mf[0] + mf[1] * mf[1] + mf[2] * mf[2]);
         T fn[3], Jn[9];
-        eval_fJ<n, T>(el, tab, rn, xs, fn, Jn);
+        fJ(rn, fn, Jn);
         const T phin = T(0.5) * (fn[0] * fn[0] + fn[1] * fn[1] + fn[2] * fn[2]);
         if (sn <= Lim<T>::stop) {
             if (phin <= phi) {
@@ -701,10 +783,11 @@ __global__ void __launch_bounds__(256) k_newton_mixed(NewtonArgs A, BasisTab tab
 // pass 3 (FP64): full trust-region Newton for the pairs marked -1, from the
 // point the earlier passes reached.  These pairs are few and scattered, and
 // each solve is a long dependent chain: the kernel is latency-bound.  The
-// mixed pass listed them (fb_list), so consecutive lanes take consecutive
-// list entries (dense warps) and blocks of one warp spread the warps over
-// the SMs.  If the list overflowed, blocks instead gather the marked pairs of
-// chunks of slots into shared memory and solve those.
+// mixed pass listed them (fb_list); each block is one warp and solves one
+// listed pair at a time with the warp-cooperative evaluators, which shortens
+// the chain about 16-fold.  If the list overflowed, blocks instead gather the
+// marked pairs of chunks of slots into shared memory and solve those one per
+// lane.
 constexpr int kFullChunk = 8192;
 constexpr int kFullSub = 1024;
 
@@ -731,9 +814,25 @@ __global__ void __launch_bounds__(32) k_newton64_full(NewtonArgs A, BasisTab tab
 {
     const int64_t nfb = *A.fb_count;
     if (nfb <= A.fb_cap) {
-        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nfb;
-             t += (int64_t)gridDim.x * blockDim.x)
-            solve_full64<n>(A, tab, A.fb_list[t]);
+        // one warp (this block) per listed pair
+        constexpr int n3 = n * n * n;
+        for (int64_t t = blockIdx.x; t < nfb; t += gridDim.x) {
+            const int32_t q = A.fb_list[t];
+            const int e = A.pair_elem[q];
+            const int64_t p = A.pair_pt[q];
+            const double xs[3] = {A.pts[p], A.pts[A.P + p], A.pts[2 * A.P + p]};
+            const ElemPtr<double> el64 = {A.coords + (int64_t)e * n3, A.coords + (A.E + e) * n3,
+                                          A.coords + (2 * A.E + e) * n3};
+            double r[3] = {A.prst[q], A.prst[A.cap + q], A.prst[2 * A.cap + q]}, J[9];
+            bool conv;
+            const double res = newton<n, double, true, true>(el64, tab, xs, r, J, A.max_newton, conv);
+            if (threadIdx.x == 0) {
+                A.prst[q] = r[0];
+                A.prst[A.cap + q] = r[1];
+                A.prst[2 * A.cap + q] = r[2];
+                A.pres[q] = res;
+            }
+        }
         return;
     }
     __shared__ int32_t list[kFullSub];

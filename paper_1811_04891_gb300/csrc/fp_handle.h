@@ -9,6 +9,8 @@
 
 #include "fp_common.cuh"
 
+struct fp_host_stream;   // fp_find_eval_host state (fp_stream.cu)
+
 enum { PROF_SCREEN = 0, PROF_SORT = 1, PROF_NEWTON = 2, PROF_RANK = 3, PROF_EVAL = 4, PROF_KINDS = 5 };
 
 struct fp_handle {
@@ -58,6 +60,7 @@ struct fp_handle {
     int64_t ncell_cap = 0, nnz_cap = 0;
     bool dist_default = false;     // dist was computed by the library (default field)
     bool stale = false;            // a failed fp_update_coords left the geometry inconsistent
+    fp_host_stream* host_stream = nullptr;   // buffers and streams of fp_find_eval_host
     int64_t last_pairs = 0;
     std::string err;
     // optional per-kernel timing with CUDA events on the launching stream

@@ -172,6 +172,10 @@ cudaEvent_t ev_get(fp_handle* h)
 
 void release(fp_handle* h)
 {
+    if (h->host_stream) {
+        host_stream_free(h->host_stream);
+        h->host_stream = nullptr;
+    }
     for (int k = 0; k < PROF_KINDS; ++k) {
         for (auto& pr : h->ev_pend[k]) {
             cudaEventDestroy(pr.first);

@@ -106,6 +106,12 @@ cudaError_t find_solve(const FindArgs& a, int64_t npairs, const BasisTab& tab, c
 cudaError_t find_solve_unsorted(const FindArgs& a, int64_t npairs, const BasisTab& tab, const FindParams& fp,
                                 int block, cudaStream_t s);
 
+// host streaming state of fp_find_eval_host (fp_stream.cu), freed with the handle
+}  // namespace fpg
+struct fp_host_stream;
+namespace fpg {
+void host_stream_free(fp_host_stream* hs);
+
 // counting sort of the pairs by element (fp_find.cu), shared by both dimensions
 cudaError_t find_sort(const FindArgs& a, int64_t npairs, cudaStream_t s);
 
