@@ -107,8 +107,10 @@ fp_status fp_setup(fp_handle **h, const double *coords, int64_t E, int N,
  * x^e(r,s) = sum_ij x_ij h_i(r) h_j(s).
  *   coords [2][E][n2] FP64 node coordinates x, y, node (i,j) at i + n*j,
  *          n2 = n^2
- *   dist   [E][n2] D^k, required when the mesh has more than one subdomain
- *          (there is no default field in 2D)
+ *   dist   [E][n2] D^k, or NULL: with more than one subdomain the library
+ *          computes the default (distance from each node to the nearest GLL
+ *          node of a boundary edge of its own subdomain; the same 2^37
+ *          node x boundary-node limit as fp_setup)
  *   opts   the FP64 form only (FP_PREC_MIXED gives FP_ERR_INVALID_ARG)
  * On a 2D handle fp_find, fp_find_eval, fp_find_warm and fp_eval take
  * points and reference coordinates as [2][P] and fields as [F][E][n2], with

@@ -180,6 +180,143 @@ cudaError_t launch_hull2(int n, int64_t E, const double* coords, const double* b
 }
 
 // ---------------------------------------------------------------------------
+// default distance field D^k in 2D: boundary edges of each subdomain (edges
+// whose two end points match no edge of another element of the same
+// subdomain), then the distance from every node to the nearest GLL node of a
+// boundary edge of its own subdomain.  Edge f = 0,1: r = -1,+1 (i = 0, N),
+// f = 2,3: s = -1,+1 (j = 0, N).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int edge_node2(int n, int f, int a)
+{
+    const int end = (f & 1) ? n - 1 : 0;
+    return (f >> 1) == 0 ? end + n * a : a + n * end;
+}
+
+// end points of every edge, sorted lexicographically: ec [4E][4]
+__global__ void k_edge_corners(int n, int64_t E, const double* __restrict__ coords, double* __restrict__ ec)
+{
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= 4 * E) return;
+    const int64_t e = f / 4;
+    const int k = (int)(f % 4), n2 = n * n;
+    const int i0 = edge_node2(n, k, 0), i1 = edge_node2(n, k, n - 1);
+    double a0 = coords[e * n2 + i0], a1 = coords[(E + e) * n2 + i0];
+    double b0 = coords[e * n2 + i1], b1 = coords[(E + e) * n2 + i1];
+    if (b0 < a0 || (b0 == a0 && b1 < a1)) {
+        double t = a0; a0 = b0; b0 = t;
+        t = a1; a1 = b1; b1 = t;
+    }
+    ec[4 * f + 0] = a0; ec[4 * f + 1] = a1; ec[4 * f + 2] = b0; ec[4 * f + 3] = b1;
+}
+
+// candidates from the hash cell of the edge midpoint (a neighbour's padded
+// box contains its whole edge, hence the midpoint of the chord)
+__global__ void k_edge_boundary(int64_t E, const double* __restrict__ ec, const int32_t* __restrict__ sub,
+                                HashGrid g, const int32_t* __restrict__ cstart, const int32_t* __restrict__ celems,
+                                int32_t* __restrict__ nbnd)
+{
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= 4 * E) return;
+    const int64_t e = f / 4;
+    const double* me = ec + 4 * f;
+    const double cx = 0.5 * (me[0] + me[2]), cy = 0.5 * (me[1] + me[3]);
+    const int ci = min(max((int)floor((cx - g.org[0]) * g.inv[0]), 0), g.dim[0] - 1);
+    const int cj = min(max((int)floor((cy - g.org[1]) * g.inv[1]), 0), g.dim[1] - 1);
+    const int64_t cidx = ci + (int64_t)g.dim[0] * cj;
+    int shared = 0;
+    for (int q = cstart[cidx]; q < cstart[cidx + 1] && !shared; ++q) {
+        const int e2 = celems[q];
+        if (e2 == e || sub[e2] != sub[e]) continue;
+        for (int k2 = 0; k2 < 4 && !shared; ++k2) {
+            const double* ot = ec + 4 * ((int64_t)e2 * 4 + k2);
+            shared = ot[0] == me[0] && ot[1] == me[1] && ot[2] == me[2] && ot[3] == me[3];
+        }
+    }
+    nbnd[f] = shared ? 0 : 1;
+}
+
+// the n GLL nodes of every boundary edge: positions [2][nb], subdomain [nb]
+__global__ void k_edge_gather(int n, int64_t E, const double* __restrict__ coords, const int32_t* __restrict__ sub,
+                              const int32_t* __restrict__ bnd_off, double* __restrict__ bx, int32_t* __restrict__ bs,
+                              int64_t nb)
+{
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= 4 * E) return;
+    const int o = bnd_off[f];
+    if (bnd_off[f + 1] == o) return;
+    const int64_t e = f / 4;
+    const int k = (int)(f % 4), n2 = n * n;
+    for (int a = 0; a < n; ++a) {
+        const int idx = edge_node2(n, k, a);
+        const int64_t m = (int64_t)o * n + a;
+        bx[m] = coords[e * n2 + idx];
+        bx[nb + m] = coords[(E + e) * n2 + idx];
+        bs[m] = sub[e];
+    }
+}
+
+__global__ void k_dist_default2(int n2, int64_t E, const double* __restrict__ coords, const int32_t* __restrict__ sub,
+                                const double* __restrict__ bx, const int32_t* __restrict__ bs, int64_t nb,
+                                double* __restrict__ D)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= E * n2) return;
+    const int64_t e = q / n2;
+    const double x = coords[q], y = coords[E * n2 + q];
+    const int s = sub[e];
+    double best = INFINITY;
+    for (int64_t b = 0; b < nb; ++b) {
+        if (bs[b] != s) continue;
+        const double dx = x - bx[b], dy = y - bx[nb + b];
+        best = fmin(best, __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+    }
+    D[q] = sqrt(best);
+}
+
+cudaError_t launch_dist_default2(int n, int64_t E, const double* coords, const int32_t* sub, const HashGrid& g,
+                                 const int32_t* cstart, const int32_t* celems, double* D, int64_t max_pairs,
+                                 bool* too_large, cudaStream_t s)
+{
+    *too_large = false;
+    const int64_t F = 4 * E;
+    double* ec = nullptr;
+    int32_t *nbnd = nullptr, *off = nullptr, *tmp = nullptr;
+    double* bx = nullptr;
+    int32_t* bs = nullptr;
+    int32_t total = 0;
+    cudaError_t e = cudaMalloc(&ec, sizeof(double) * 4 * F);
+    if (e == cudaSuccess) e = cudaMalloc(&nbnd, sizeof(int32_t) * F);
+    if (e == cudaSuccess) e = cudaMalloc(&off, sizeof(int32_t) * (F + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, sizeof(int32_t) * scan_tmp_elems(F));
+    if (e == cudaSuccess) {
+        const unsigned gf = (unsigned)((F + 127) / 128);
+        k_edge_corners<<<gf, 128, 0, s>>>(n, E, coords, ec);
+        k_edge_boundary<<<gf, 128, 0, s>>>(E, ec, sub, g, cstart, celems, nbnd);
+        count_launch(2);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = scan_exclusive(nbnd, off, F, tmp, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&total, off + F, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    const int64_t nb = (int64_t)total * n;
+    if (e == cudaSuccess && (double)E * n * n * (double)nb > (double)max_pairs) *too_large = true;
+    if (e == cudaSuccess && !*too_large) {
+        e = cudaMalloc(&bx, sizeof(double) * 2 * std::max<int64_t>(nb, 1));
+        if (e == cudaSuccess) e = cudaMalloc(&bs, sizeof(int32_t) * std::max<int64_t>(nb, 1));
+        if (e == cudaSuccess) {
+            const unsigned gf = (unsigned)((F + 127) / 128);
+            k_edge_gather<<<gf, 128, 0, s>>>(n, E, coords, sub, off, bx, bs, nb);
+            k_dist_default2<<<(unsigned)((E * n * n + 127) / 128), 128, 0, s>>>(n * n, E, coords, sub, bx, bs, nb, D);
+            count_launch(2);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    cudaFree(ec); cudaFree(nbnd); cudaFree(off); cudaFree(tmp); cudaFree(bx); cudaFree(bs);
+    return e;
+}
+
+// ---------------------------------------------------------------------------
 // screen
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool inside_boxes2(const ElemBox* __restrict__ bp, double x, double y)

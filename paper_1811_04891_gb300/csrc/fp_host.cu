@@ -354,9 +354,15 @@ fp_status build_geometry(fp_handle* h, cudaStream_t s, bool default_dist)
     GK(launch_hash_sort(ncell, h->cell_start, h->cell_elems, s), "hash sort");
 
     // default distance field for the owner rule
-    if (default_dist && h->dim == 2)
-        return fail(h, FP_ERR_INVALID_ARG, "2D meshes with more than one subdomain need dist");
-    if (default_dist) {
+    if (default_dist && h->dim == 2) {
+        GK(cudaStreamSynchronize(s), "sync hash fill");
+        if (!h->dist) GK(dalloc(&h->dist, (size_t)E * n3), "alloc dist");
+        bool too_large = false;
+        GK(launch_dist_default2(n, E, h->coords, h->sub, h->grid, h->cell_start, h->cell_elems, h->dist,
+                                int64_t(1) << 37, &too_large, s), "dist default 2d");
+        if (too_large) return fail(h, FP_ERR_INVALID_ARG, "mesh too large for the default distance field; pass dist");
+        h->dist_default = true;
+    } else if (default_dist) {
         double* fc = nullptr;
         int32_t *nb = nullptr, *nboff = nullptr, *tmp2 = nullptr;
         double* bx = nullptr;

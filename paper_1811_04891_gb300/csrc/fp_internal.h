@@ -118,6 +118,11 @@ cudaError_t find_sort(const FindArgs& a, int64_t npairs, cudaStream_t s);
 // 2D quadrilateral variant (fp_find2.cu): coords [2][E][n^2], pts / rst [2][P]
 cudaError_t launch_hull2(int n, int64_t E, const double* coords, const double* binv, double pad_border,
                          double pad_conv, ElemBox* boxes, double* nodebox, cudaStream_t s);
+// default D^k from the boundary edges of each subdomain; *too_large when the
+// node x boundary-node pairs exceed max_pairs (nothing computed then)
+cudaError_t launch_dist_default2(int n, int64_t E, const double* coords, const int32_t* sub, const HashGrid& g,
+                                 const int32_t* cstart, const int32_t* celems, double* D, int64_t max_pairs,
+                                 bool* too_large, cudaStream_t s);
 cudaError_t find_count2(const FindArgs& a, cudaStream_t s);
 cudaError_t find_emit2(const FindArgs& a, cudaStream_t s);
 cudaError_t find_solve2(const FindArgs& a, int64_t npairs, const BasisTab& tab, const FindParams& fp, int block,

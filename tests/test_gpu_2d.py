@@ -154,9 +154,6 @@ def test_2d_rejections(fg):
     ct = torch.from_numpy(coords).to(dev)
     with pytest.raises(fg.FindptsError):
         fg.fp_setup_2d(ct, 3, opts=fg.default_opts(precision=fg.PREC_MIXED))
-    two = torch.from_numpy(np.array([0, 0, 1, 1], np.int32)).to(dev)
-    with pytest.raises(fg.FindptsError):
-        fg.fp_setup_2d(ct, 3, two)                         # no default distance field in 2D
     h = fg.fp_setup_2d(ct, 3)
     with pytest.raises(Exception):
         fg.Workspace(h, 100)
@@ -165,3 +162,22 @@ def test_2d_rejections(fg):
         fg.fp_find_static(h, pts)
     with pytest.raises(Exception):
         fg.Fields(h, torch.zeros((1, E, 16), dtype=torch.float64, device=dev))
+
+
+@pytest.mark.parametrize("N", [3, 6])
+def test_2d_default_distance_owner(fg, N):
+    """No D passed: the library's default field (boundary edges of each
+    subdomain) decides the owner exactly as the oracle's default field does."""
+    mesh = synth.tiny_overlap_2d(N)                         # three overlapping rectangles
+    h = _setup(fg, mesh.coords, N, mesh.sub)                # dist = None
+    D = oracle.dist_default(mesh.coords, N, mesh.sub)
+    pts = synth.uniform_points_2d(4000, seed=N, lo=(0.0, 0.0), hi=(2.0, 1.0))
+    g = _run(fg, h, pts)
+    ref = oracle.find(mesh.coords, N, mesh.sub, pts, dist=D)
+    assert_parity(g, ref, 0)
+    assert len(np.unique(g["sub"][g["code"] == 0])) == 3
+    mesh, q = synth.walsh_2d(N=N, n_box=10, ring=(12, 2))
+    h = _setup(fg, mesh.coords, N, mesh.sub)
+    g = _run(fg, h, q.pts, q.qsess)
+    ref = oracle.find(mesh.coords, N, mesh.sub, q.pts, qsess=q.qsess, dist=oracle.dist_default(mesh.coords, N, mesh.sub))
+    assert_parity(g, ref, 0)
