@@ -42,20 +42,26 @@ UNIT = "points/s"
 # 1.25 TFLOP/s; FP32 = 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s.
 P64_NOMINAL = 1.25e12
 P32_NOMINAL = 152 * 128 * 2 * 2.07e9
-# Algorithmic work per (point, element) pair of the Newton stage at N=7 (n = 8):
-# nearest-node seed 4.1 kflop, one Newton iteration with Jacobian 8.4 kflop, a
-# value-only residual 3.5 kflop (3 coordinates x (n^3 + n^2 + n) FMA), a
-# compensated (double-float) FP32 residual 19.3 k FP32 operations (about 11 per
-# term), the FP64 basis values of three residuals 0.3 kflop.
-#   FP64 form:  seed + 4 iterations, all FP64.
-#   mixed form: FP32 seed + 4 FP32 iterations + 2 compensated FP32 residuals;
+# Algorithmic work per located point of the Newton stage at N=7 (n = 8),
+# counting the true element only: the nearest-node seed (4.1 kflop), the K
+# Newton iterations with Jacobian (8.4 kflop each) that the oracle needs from
+# that seed, a value-only residual 3.5 kflop (3 coordinates x (n^3 + n^2 + n)
+# FMA), a compensated (double-float) FP32 residual 19.3 k FP32 operations
+# (about 11 per term), the FP64 basis values of three residuals 0.3 kflop.
+# K = 3.43: the mean iteration count of the oracle's Newton on the true
+# element, measured on a 22,000-point sample of this workload (20,000 uniform
+# + 2,000 near-face points).
+#   FP64 form:  seed + K iterations, all FP64.
+#   mixed form: FP32 seed + K FP32 iterations + 2 compensated FP32 residuals;
 #               FP64: one residual + basis values (the final FP64 Newton step).
 SEED, ITER, RESID, RESID_DF, BASIS64, EVAL1 = 4.1e3, 8.4e3, 3.5e3, 19.3e3, 0.3e3, 1.17e3
-# DRAM bytes (read + written) per pair of the Newton stage, measured with ncu on the
-# 2.02M-point case of this workload (2.05M pairs) and scaled by the pairs of a launch.
+K_ORACLE = 3.43
+# DRAM bytes (read + written) per (point, candidate element) pair of the Newton
+# stage, measured with ncu on the 2.02M-point case of this workload (2.05M
+# pairs) and scaled by the pairs of a launch.
 TRAFFIC_PER_PAIR = {"mixed": 1239.0, "fp64": 740.0}
-WORK = {"fp64": {"f64": SEED + 4 * ITER, "f32": 0.0},
-        "mixed": {"f64": RESID + BASIS64, "f32": SEED + 4 * ITER + 2 * RESID_DF}}
+WORK = {"fp64": {"f64": SEED + K_ORACLE * ITER, "f32": 0.0},
+        "mixed": {"f64": RESID + BASIS64, "f32": SEED + K_ORACLE * ITER + 2 * RESID_DF}}
 
 
 def parse():
@@ -650,14 +656,15 @@ def main():
         kn = results[form]["kernel_ms"]["newton"] / 1e3
         pairs = results[form]["pairs_per_point"] * P
         w = WORK[form]
-        f64, f32 = w["f64"] * pairs, w["f32"] * pairs
+        f64, f32 = w["f64"] * P, w["f32"] * P          # per located point, true element only
         t_roof = f64 / P64_NOMINAL + f32 / P32_NOMINAL
         achieved = (f64 + f32 * P64_NOMINAL / P32_NOMINAL) / kn
         return {"bound": "alu", "achieved": achieved / 1e12, "peak": P64_NOMINAL / 1e12,
                 "unit": "TFLOP/s (FP64-equivalent: FP64 flops + FP32 flops x P64/P32)",
                 "frac": t_roof / kn, "traffic": TRAFFIC_PER_PAIR[form] * pairs,
                 "kernel": ("k_newton_mixed<8> + k_newton64_full<8>" if form == "mixed" else "k_newton<8>"),
-                "units_per_launch": pairs, "unit_work": w,
+                "units_per_launch": P, "work_unit": "located point (true element only)", "unit_work": w,
+                "pairs_per_launch": pairs,
                 "peak_source": "of nominal: GB300 FP64 1.25 TFLOP/s; FP32 152 SMs x 128 lanes x 2 x 2.07 GHz"}
 
     roof = roofline(head)
