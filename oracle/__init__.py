@@ -61,7 +61,9 @@ class Params:
 def lib():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
+        # FINDPTS_ORACLE_LIB: a separately built copy (the mutation tests load
+        # deliberately broken builds this way to show that the pins catch them)
+        _lib = ctypes.CDLL(os.environ.get("FINDPTS_ORACLE_LIB") or build())
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int32)
         i64 = ctypes.c_int64

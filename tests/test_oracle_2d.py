@@ -217,3 +217,27 @@ def test_walsh_workload_all_found():
     out = oracle.evaluate(mesh.N, res["code"], res["elem"], res["rst"], q.fields)
     exact = np.stack([-np.cos(q.pts[0]) * np.sin(q.pts[1]), np.sin(q.pts[0]) * np.cos(q.pts[1])])
     assert np.abs(out[:2] - exact).max() < 1e-3          # spectral interpolation of the eddy
+
+
+def test_border_projection_on_skewed_quad():
+    """2D analogue: a point just outside an edge of a skewed quad projects
+    orthogonally onto the edge line (r = 1, s of the foot point)."""
+    N = 3
+    xi = synth.reference_grid(N)
+    A = np.array([[0.5, 0.2], [0.3, 0.5]])                       # columns x_r, x_s
+    c = np.array([1.0, -2.0])
+    R, S = np.meshgrid(xi, xi, indexing="xy")                    # R[j][i] = xi_i, S[j][i] = xi_j
+    ref = np.stack([R.reshape(-1), S.reshape(-1)])               # node (i,j) at i + n j
+    coords = (c[:, None] + A @ ref)[:, None, :]
+    he = np.linalg.norm(coords[:, 0].max(axis=1) - coords[:, 0].min(axis=1))
+    t = A[:, 1] / np.linalg.norm(A[:, 1])
+    nrm = np.array([t[1], -t[0]])
+    if nrm @ A[:, 0] < 0:
+        nrm = -nrm
+    s0 = 0.35
+    foot = c + A @ np.array([1.0, s0])
+    d = 0.3e-6 * he
+    res = oracle.find(coords, N, _zeros(1), (foot + d * nrm)[:, None])
+    assert res["code"][0] == BORDER and res["elem"][0] == 0
+    np.testing.assert_allclose(res["rst"][:, 0], [1.0, s0], atol=1e-9)
+    np.testing.assert_allclose(np.sqrt(res["dist2"][0]), d, rtol=1e-6)

@@ -146,3 +146,33 @@ def test_spiral_element_robustness():
     res2 = oracle.find(coords, N, _zeros(1), pts[:, :100],
                        params=oracle.Params(tol_accept=1e-10, prefilter=False, n_restarts=8))
     np.testing.assert_allclose(res2["rst"], res["rst"][:, :100], atol=1e-12)
+
+
+def test_border_projection_on_skewed_element():
+    """A point just outside a face of a skewed (affine) element: the
+    constrained minimiser is its orthogonal projection onto the face plane
+    (reference r = 1 and the face coordinates of the foot point), and the
+    border distance is the distance to that plane -- the active set must
+    freeze r and keep minimising over (s, t)."""
+    N = 3
+    xi = synth.reference_grid(N)
+    A = np.array([[0.5, 0.0, 0.0], [0.25, 0.5, 0.0], [0.15, -0.1, 0.5]])   # columns: x_r, x_s, x_t
+    c = np.array([1.0, 2.0, 3.0])
+    R, S, T = np.meshgrid(xi, xi, xi, indexing="ij")
+    ref = np.stack([R, S, T]).reshape(3, -1)                     # node (i,j,k) with i slowest here
+    X = c[:, None] + A @ ref
+    n = N + 1
+    coords = X.reshape(3, n, n, n).transpose(0, 3, 2, 1).reshape(3, 1, n ** 3)   # i fastest
+    he = np.linalg.norm(coords[:, 0].max(axis=1) - coords[:, 0].min(axis=1))
+    nrm = np.cross(A[:, 1], A[:, 2])
+    nrm /= np.linalg.norm(nrm)
+    if nrm @ A[:, 0] < 0:
+        nrm = -nrm                                               # outward at r = +1
+    s0, t0 = 0.3, -0.4
+    foot = c + A @ np.array([1.0, s0, t0])
+    d = 0.3e-6 * he
+    pts = (foot + d * nrm)[:, None]
+    res = oracle.find(coords, N, _zeros(1), pts)
+    assert res["code"][0] == BORDER and res["elem"][0] == 0
+    np.testing.assert_allclose(res["rst"][:, 0], [1.0, s0, t0], atol=1e-9)
+    np.testing.assert_allclose(np.sqrt(res["dist2"][0]), d, rtol=1e-6)
