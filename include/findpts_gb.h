@@ -388,6 +388,17 @@ fp_status fp_flux_correct(const fp_bfaces *b, const double *u, double *u_out, do
  * fp_update_coords on a moving mesh); the face list, node kinds and the
  * interface numbering stay.  Allocates nothing; enqueued on `stream`. */
 fp_status fp_bfaces_refresh(fp_bfaces *b, void *stream);
+/* fp_bfaces_sort_iface: renumber the interface nodes so that nodes with the
+ * same donor element are consecutive.  elem [Mi] (device) holds each
+ * interface node's donor element in the current numbering (as found at the
+ * fp_bfaces_iface points; -1 = not found, placed last).  Afterwards
+ * fp_bfaces_iface lists the points in the new order and
+ * fp_flux_correct_iface reads u_iface in it.  Only the order changes: an
+ * evaluation at the reordered points reads each element's field rows from
+ * cache for neighbouring threads.  Nodes of one element keep an unspecified
+ * order among themselves (results do not depend on it).  Allocates and
+ * synchronises `stream`. */
+fp_status fp_bfaces_sort_iface(fp_bfaces *b, const int32_t *elem, void *stream);
 
 /* Interface-data pipeline helpers.
  * fp_bfaces_iface: number of interface nodes Mi and (if pts != NULL) their

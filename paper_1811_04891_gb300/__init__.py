@@ -120,6 +120,8 @@ def _load():
     L.fp_bfaces_iface.restype = ci
     L.fp_bfaces_refresh.argtypes = [vp, vp]
     L.fp_bfaces_refresh.restype = ci
+    L.fp_bfaces_sort_iface.argtypes = [vp, vp, vp]
+    L.fp_bfaces_sort_iface.restype = ci
     L.fp_extrapolate.argtypes = [ci, i64, ctypes.POINTER(vp), vp, vp]
     L.fp_extrapolate.restype = ci
     L.fp_eval.argtypes = [vp, i64, vp, vp, vp, ci, vp, vp, vp]
@@ -586,6 +588,16 @@ class BFaces:
         mi = ctypes.c_int64()
         lib().fp_bfaces_iface(self.ptr, ctypes.byref(mi), None, None)
         self.Mi = mi.value
+
+    def sort_iface(self, elem: torch.Tensor, stream=None):
+        """Renumber the interface nodes by donor element (elem [Mi] int32,
+        found at the current iface_points order)."""
+        elem = _dev(elem, torch.int32, "elem")
+        if elem.numel() != self.Mi:
+            raise ValueError("elem must hold one element id per interface node")
+        st = lib().fp_bfaces_sort_iface(self.ptr, _ptr(elem), _stream(stream))
+        if st != FP_OK:
+            raise FindptsError(st, "fp_bfaces_sort_iface failed")
 
     def refresh(self, stream=None):
         """Recompute node positions, normals and weights after fp_update_coords."""

@@ -19,34 +19,47 @@ struct EvalArgs {
     double* out;
 };
 
-template <int n>
+// One thread per point, or (SPLIT) one thread per (point, field): small
+// calls (an interface sub-iteration evaluates a few 10^4 points) are
+// latency-bound, and splitting the fields gives F times the threads; each
+// field's operations are the same either way.
+template <int n, bool SPLIT>
 __global__ void __launch_bounds__(128) k_eval(EvalArgs A, BasisTab tab)
 {
     constexpr int n3 = n * n * n;
-    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t p = SPLIT ? t / A.F : t;
     if (p >= A.P) return;
+    const int f0 = SPLIT ? (int)(t % A.F) : 0, f1 = SPLIT ? f0 + 1 : A.F;
     const int e = A.elem[p];
     if (A.code[p] == FP_CODE_NOT_FOUND || e < 0 || e >= A.E) {
-        for (int f = 0; f < A.F; ++f) A.out[(int64_t)f * A.P + p] = __longlong_as_double(0x7ff8000000000000ULL);
+        for (int f = f0; f < f1; ++f) A.out[(int64_t)f * A.P + p] = __longlong_as_double(0x7ff8000000000000ULL);
         return;
     }
     double hr[n], hs[n], ht[n];
     lagrange_h<n, double>(tab.xi, tab.ci, A.rst[p], hr);
     lagrange_h<n, double>(tab.xi, tab.ci, A.rst[A.P + p], hs);
     lagrange_h<n, double>(tab.xi, tab.ci, A.rst[2 * A.P + p], ht);
-    for (int f = 0; f < A.F; ++f)
+    for (int f = f0; f < f1; ++f)
         A.out[(int64_t)f * A.P + p] = contract<n, double>(A.fields + ((int64_t)f * A.E + e) * n3, hr, hs, ht);
 }
+
+// calls with at most this many (point, field) values take one thread each
+constexpr int64_t kSplitEval = int64_t(1) << 21;
 
 cudaError_t launch_eval(int n, int64_t E, int64_t P, const int32_t* code, const int32_t* elem, const double* rst,
                         int F, const double* fields, double* out, const BasisTab& tab, cudaStream_t s)
 {
     if (P == 0) return cudaSuccess;
     EvalArgs a{E, P, code, elem, rst, F, fields, out};
-    const unsigned grid = (unsigned)((P + 127) / 128);
+    const bool split = P * F <= kSplitEval;
+    const unsigned grid = (unsigned)(((split ? P * F : P) + 127) / 128);
     switch (n) {
-#define FP_CASE(NN) \
-    case NN: k_eval<NN><<<grid, 128, 0, s>>>(a, tab); break;
+#define FP_CASE(NN)                                                  \
+    case NN:                                                         \
+        if (split) k_eval<NN, true><<<grid, 128, 0, s>>>(a, tab);    \
+        else k_eval<NN, false><<<grid, 128, 0, s>>>(a, tab);         \
+        break;
         FP_CASE(2) FP_CASE(3) FP_CASE(4) FP_CASE(5) FP_CASE(6) FP_CASE(7) FP_CASE(8) FP_CASE(9)
         FP_CASE(10) FP_CASE(11) FP_CASE(12) FP_CASE(13) FP_CASE(14) FP_CASE(15) FP_CASE(16)
 #undef FP_CASE
@@ -112,15 +125,17 @@ struct Eval2Args {
     double* out;
 };
 
-template <int n>
+template <int n, bool SPLIT>
 __global__ void __launch_bounds__(128) k_eval_df(Eval2Args A, BasisTab tab)
 {
     constexpr int n3 = n * n * n;
-    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t p = SPLIT ? t / A.F : t;
     if (p >= A.P) return;
+    const int f0 = SPLIT ? (int)(t % A.F) : 0, f1 = SPLIT ? f0 + 1 : A.F;
     const int e = A.elem[p];
     if (A.code[p] == FP_CODE_NOT_FOUND || A.code[p] == FP_CODE_RETRY || e < 0 || e >= A.E) {
-        for (int f = 0; f < A.F; ++f) A.out[(int64_t)f * A.P + p] = __longlong_as_double(0x7ff8000000000000ULL);
+        for (int f = f0; f < f1; ++f) A.out[(int64_t)f * A.P + p] = __longlong_as_double(0x7ff8000000000000ULL);
         return;
     }
     double hr[n], hs[n], ht[n];
@@ -133,7 +148,7 @@ __global__ void __launch_bounds__(128) k_eval_df(Eval2Args A, BasisTab tab)
         df a = df_split(hr[i]), b = df_split(hs[i]), c = df_split(ht[i]);
         rh[i] = a.hi; rl[i] = a.lo; sh[i] = b.hi; sl[i] = b.lo; th[i] = c.hi; tl[i] = c.lo;
     }
-    for (int f = 0; f < A.F; ++f) {
+    for (int f = f0; f < f1; ++f) {
         const float2* Fe = A.fields + ((int64_t)f * A.E + e) * n3;
         df acc = {0.0f, 0.0f};
 #pragma unroll 1
@@ -199,10 +214,14 @@ cudaError_t launch_eval_df(int n, int64_t E, int64_t P, const int32_t* code, con
 {
     if (P == 0) return cudaSuccess;
     Eval2Args a{E, P, code, elem, rst, F, fields, out};
-    const unsigned grid = (unsigned)((P + 127) / 128);
+    const bool split = P * F <= kSplitEval;
+    const unsigned grid = (unsigned)(((split ? P * F : P) + 127) / 128);
     switch (n) {
-#define FP_CASE(NN) \
-    case NN: k_eval_df<NN><<<grid, 128, 0, s>>>(a, tab); break;
+#define FP_CASE(NN)                                                     \
+    case NN:                                                            \
+        if (split) k_eval_df<NN, true><<<grid, 128, 0, s>>>(a, tab);    \
+        else k_eval_df<NN, false><<<grid, 128, 0, s>>>(a, tab);         \
+        break;
         FP_CASE(2) FP_CASE(3) FP_CASE(4) FP_CASE(5) FP_CASE(6) FP_CASE(7) FP_CASE(8) FP_CASE(9)
         FP_CASE(10) FP_CASE(11) FP_CASE(12) FP_CASE(13) FP_CASE(14) FP_CASE(15) FP_CASE(16)
 #undef FP_CASE

@@ -196,6 +196,33 @@ __global__ void k_iface_pos(int64_t M, const int8_t* __restrict__ kind, const in
     if (m < M) ipos[m] = kind[m] == 2 ? off[m] : -1;
 }
 
+// interface numbering sorted by donor element (counting sort; points of one
+// element keep an arbitrary order among themselves)
+__global__ void k_key_hist(int64_t Mi, int64_t E, const int32_t* __restrict__ elem, int32_t* __restrict__ cnt)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= Mi) return;
+    const int32_t e = elem[k];
+    atomicAdd(cnt + ((e >= 0 && e < E) ? e : E), 1);
+}
+
+__global__ void k_key_scatter(int64_t Mi, int64_t E, const int32_t* __restrict__ elem,
+                              const int32_t* __restrict__ start, int32_t* __restrict__ cursor,
+                              int32_t* __restrict__ newpos)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= Mi) return;
+    const int32_t e = elem[k];
+    const int64_t key = (e >= 0 && e < E) ? e : E;
+    newpos[k] = start[key] + atomicAdd(cursor + key, 1);
+}
+
+__global__ void k_ipos_remap(int64_t M, const int32_t* __restrict__ newpos, int32_t* __restrict__ ipos)
+{
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m < M && ipos[m] >= 0) ipos[m] = newpos[ipos[m]];
+}
+
 __global__ void k_iface_flags(int64_t M, const int8_t* __restrict__ kind, int32_t* __restrict__ flag)
 {
     const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -296,7 +323,7 @@ extern "C" fp_status fp_bfaces_create(const fp_handle* h, const int8_t* kind, fp
     if (e == cudaSuccess) e = cudaMalloc(&b->nrm, sizeof(double) * 3 * std::max<int64_t>(b->M, 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->dA, sizeof(double) * std::max<int64_t>(b->M, 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->kind, std::max<int64_t>(b->M, 1));
-    b->nblk = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (b->M + 4095) / 4096));
+    b->nblk = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (b->M + 511) / 512));   // ~2 nodes per thread
     if (e == cudaSuccess) e = cudaMalloc(&b->partial, sizeof(double) * 2 * b->nblk);
     if (e == cudaSuccess) e = cudaMalloc(&b->result, sizeof(double) * 3);
     if (e == cudaSuccess && b->nf > 0) {
@@ -374,6 +401,37 @@ extern "C" void fp_bfaces_free(fp_bfaces* b)
     cudaDeviceSynchronize();
     bf_release(b);
     delete b;
+}
+
+extern "C" fp_status fp_bfaces_sort_iface(fp_bfaces* b, const int32_t* elem, void* stream)
+{
+    if (!b || !elem) return FP_ERR_INVALID_ARG;
+    if (!fp_live(b->owner)) return FP_ERR_NOT_SETUP;
+    const int64_t Mi = b->Mi, E = b->owner->E;
+    if (Mi == 0) return FP_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t *cnt = nullptr, *start = nullptr, *tmp = nullptr, *newpos = nullptr;
+    cudaError_t e = cudaMalloc(&cnt, sizeof(int32_t) * (E + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&start, sizeof(int32_t) * (E + 2));
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, sizeof(int32_t) * scan_tmp_elems(E + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&newpos, sizeof(int32_t) * Mi);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (E + 1), s);
+    if (e == cudaSuccess) {
+        k_key_hist<<<(unsigned)((Mi + 255) / 256), 256, 0, s>>>(Mi, E, elem, cnt);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = scan_exclusive(cnt, start, E + 1, tmp, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (E + 1), s);
+    if (e == cudaSuccess) {
+        k_key_scatter<<<(unsigned)((Mi + 255) / 256), 256, 0, s>>>(Mi, E, elem, start, cnt, newpos);
+        k_ipos_remap<<<(unsigned)((b->M + 255) / 256), 256, 0, s>>>(b->M, newpos, b->ipos);
+        count_launch(2);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(cnt); cudaFree(start); cudaFree(tmp); cudaFree(newpos);
+    return e == cudaSuccess ? FP_OK : (e == cudaErrorMemoryAllocation ? FP_ERR_OOM : FP_ERR_CUDA);
 }
 
 extern "C" fp_status fp_bfaces_refresh(fp_bfaces* b, void* stream)

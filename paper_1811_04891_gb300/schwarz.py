@@ -23,6 +23,8 @@ import paper_1811_04891_gb300 as fg
 class InterfaceExchange:
     def __init__(self, h, bfaces: "fg.BFaces", session: int, fields: torch.Tensor,
                  posted: Optional["fg.Fields"] = None, order: int = 1):
+        """`bfaces` belongs to this exchange: locate() renumbers its interface
+        nodes by donor element, so it must not be shared with another one."""
         if order not in (1, 2, 3):
             raise ValueError("order must be 1, 2 or 3")
         self.h, self.bf, self.fields, self.posted, self.order = h, bfaces, fields, posted, order
@@ -42,9 +44,15 @@ class InterfaceExchange:
         self.locate()
 
     def locate(self):
-        """(Re)locate the interface points in the donors (after mesh motion)."""
-        self.found = fg.fp_find_eval(self.h, self.pts, self.qs, fields=None if self.posted else self.fields,
-                                     posted=self.posted, values=self.vals)
+        """Locate the interface points in the donors, then renumber them by
+        donor element (neighbouring threads of the sub-iteration's eval then
+        share an element's field rows) and locate them in that order."""
+        f = None if self.posted else self.fields
+        self.found = fg.fp_find_eval(self.h, self.pts, self.qs, fields=f, posted=self.posted, values=self.vals)
+        self.bf.sort_iface(self.found[2])
+        self.bf.iface_points(out=self.pts)
+        self.found = fg.fp_find_eval(self.h, self.pts, self.qs, fields=f, posted=self.posted,
+                                     out=self.found[:5], values=self.vals)
         self.graph = None
 
     def move(self, coords: torch.Tensor, dist: Optional[torch.Tensor] = None):

@@ -66,12 +66,13 @@ def test_graph_replayed_subiterations_match_eager(fg):
     dev = torch.device("cuda:0")
     h = fg.fp_setup(torch.from_numpy(mesh.coords).to(dev), mesh.N, torch.from_numpy(mesh.sub).to(dev),
                     torch.from_numpy(mesh.dist).to(dev), opts=fg.default_opts(precision=fg.PREC_MIXED))
-    bf = fg.BFaces(h, torch.from_numpy(kind).to(dev))
     base = torch.from_numpy(q.fields[:3]).to(dev)
     fields_g = base.clone()
     fields_e = base.clone()
-    xg = InterfaceExchange(h, bf, 1, fields_g, order=2)
-    xe = InterfaceExchange(h, bf, 1, fields_e, order=2)
+    # each exchange renumbers the interface nodes of its own face set
+    xg = InterfaceExchange(h, fg.BFaces(h, torch.from_numpy(kind).to(dev)), 1, fields_g, order=2)
+    xe = InterfaceExchange(h, fg.BFaces(h, torch.from_numpy(kind).to(dev)), 1, fields_e, order=2)
+    bf = xg.bf
     for step in range(3):
         # the donors' solution changes between steps (a stand-in for the solver)
         fields_g.copy_(base * (1.0 + 0.1 * step))
@@ -87,3 +88,29 @@ def test_graph_replayed_subiterations_match_eager(fg):
         # the corrected flux vanishes
         x, nr, dA, nk = bf.nodes()
         assert abs(((ug * nr).sum(0) * dA).sum().item()) < 1e-10
+
+
+def test_sort_iface_renumbers_without_changing_results(fg):
+    N = 4
+    shp = (3, 3, 2)
+    coords = synth.box_mesh(shp, N, amp_frac=0.1)
+    kind = box_kind(shp, {(0, 0): 2, (0, 1): 2, (1, 0): 2, (1, 1): 1, (2, 0): 1, (2, 1): 2})
+    h, bf = _gpu_faces(fg, coords, N, kind)
+    pts0 = bf.iface_points()
+    found0 = fg.fp_find(h, pts0)
+    f = torch.from_numpy(np.stack([synth.field_u(coords), coords[0] * coords[1], coords[2] ** 2])).cuda()
+    up = torch.from_numpy(np.random.default_rng(2).uniform(-1, 1, (3, bf.M))).cuda()
+    u0 = fg.fp_eval(h, found0[0], found0[2], found0[3], f)
+    a = fg.fp_flux_correct_iface(bf, u0, up)
+    bf.sort_iface(found0[2])
+    pts1 = bf.iface_points()
+    found1 = fg.fp_find(h, pts1)
+    e1 = found1[2].cpu().numpy()
+    assert (np.diff(e1) >= 0).all()                                  # grouped by donor element
+    key0 = np.lexsort(pts0.cpu().numpy())
+    key1 = np.lexsort(pts1.cpu().numpy())
+    assert torch.equal(pts0[:, key0], pts1[:, key1])                 # the same points, reordered
+    u1 = fg.fp_eval(h, found1[0], found1[2], found1[3], f)
+    b = fg.fp_flux_correct_iface(bf, u1, up)
+    for p, q in zip(a, b):
+        assert torch.equal(p, q)
