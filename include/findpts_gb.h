@@ -353,6 +353,27 @@ fp_status fp_find_eval_host(fp_handle *h, int64_t P, const double *pts, const in
                             int32_t *sub, int32_t *elem, double *rst, double *dist2, double *out,
                             int64_t chunk, void *stream);
 
+/* Posted points: the split Lagrange basis values of P located points, for
+ * repeated evaluation at the same (e, r) -- the interface points of a
+ * Schwarz step are evaluated once per sub-iteration while the mesh stands
+ * still (Sec. 2: kappa sub-iterations per step).
+ * fp_points_create: room for P points of the handle's mesh (allocates;
+ *   hexahedral handles).  fp_points_free: release (NULL is a no-op).
+ * fp_points_set: compute and keep the basis values of the points
+ *   code/elem/rst (as written by fp_find, rst [3][P]); call again after the
+ *   points are found anew; the buffers stay where they are, so a graph that
+ *   captured fp_eval_points stays valid.  Enqueued on `stream`.
+ * fp_eval_points: out [F][P] = the posted double-float fields interpolated at
+ *   the posted points, bit-identical to fp_eval_df at the same (e, r); NaN for
+ *   points not found.  Allocates nothing, never waits. */
+typedef struct fp_points fp_points;
+fp_status fp_points_create(const fp_handle *h, int64_t P, fp_points **out);
+void fp_points_free(fp_points *q);
+fp_status fp_points_set(fp_handle *h, fp_points *q, const int32_t *code, const int32_t *elem,
+                        const double *rst, void *stream);
+fp_status fp_eval_points(fp_handle *h, const fp_fields *f, const fp_points *q, double *out,
+                         void *stream);
+
 /* Mass-flux correction of interpolated interface velocity (Sec. 2.2,
  * Eqs. consv1, corr, consv2).
  * fp_bfaces_create: kind [E][6] int8 on the device marks faces of the

@@ -96,6 +96,14 @@ def _load():
     L.fp_find_eval.restype = ci
     L.fp_find_eval_host.argtypes = [vp, i64, vp, vp, ci, vp, vp, vp, vp, vp, vp, vp, vp, i64, vp]
     L.fp_find_eval_host.restype = ci
+    L.fp_points_create.argtypes = [vp, i64, ctypes.POINTER(vp)]
+    L.fp_points_create.restype = ci
+    L.fp_points_free.argtypes = [vp]
+    L.fp_points_free.restype = None
+    L.fp_points_set.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.fp_points_set.restype = ci
+    L.fp_eval_points.argtypes = [vp, vp, vp, vp, vp]
+    L.fp_eval_points.restype = ci
     L.fp_setup_2d.argtypes = list(L.fp_setup.argtypes)
     L.fp_setup_2d.restype = ci
     L.fp_find_warm.argtypes = [vp, i64, vp, vp, vp, vp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -526,6 +534,41 @@ def fp_find_eval_host(h: Handle, pts: torch.Tensor, qsess: Optional[torch.Tensor
                                  _stream(stream))
     _check(st, h.ptr)
     return (code, sub, elem, rst, dist2, values) if F else (code, sub, elem, rst, dist2)
+
+
+class Points:
+    """Posted points (fp_points_*): split basis values of located points,
+    kept for repeated evaluation of posted fields at the same (e, r)."""
+
+    def __init__(self, h: Handle, P: int):
+        self.handle = h
+        self.P = int(P)
+        self.ptr = ctypes.c_void_p()
+        _check(lib().fp_points_create(h.ptr, self.P, ctypes.byref(self.ptr)), h.ptr)
+
+    def __del__(self):
+        if getattr(self, "ptr", None) is not None and self.ptr.value:
+            try:
+                lib().fp_points_free(self.ptr)
+            except Exception:
+                pass
+            self.ptr = ctypes.c_void_p(None)
+
+    def set(self, code: torch.Tensor, elem: torch.Tensor, rst: torch.Tensor, stream=None):
+        code = _dev(code, torch.int32, "code")
+        elem = _dev(elem, torch.int32, "elem")
+        rst = _dev(rst, torch.float64, "rst")
+        if code.numel() != self.P or elem.numel() != self.P or rst.shape != (3, self.P):
+            raise ValueError("code, elem [P] and rst [3][P] must match the posted point count")
+        _check(lib().fp_points_set(self.handle.ptr, self.ptr, _ptr(code), _ptr(elem), _ptr(rst), _stream(stream)),
+               self.handle.ptr)
+
+    def eval(self, posted: "Fields", out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((posted.F, self.P), dtype=torch.float64, device=torch.device("cuda"))
+        _check(lib().fp_eval_points(self.handle.ptr, posted.ptr, self.ptr, _ptr(out), _stream(stream)),
+               self.handle.ptr)
+        return out
 
 
 UPDATE_DEFAULT_DIST = 1

@@ -192,6 +192,96 @@ __global__ void __launch_bounds__(128) k_eval_df(Eval2Args A, BasisTab tab)
     }
 }
 
+// ---- posted points: the split basis values of located points, computed once
+// and reused by every evaluation at the same (e, r) (the interface points of
+// a Schwarz step are evaluated once per sub-iteration).  Layout [6n][P]:
+// rh, rl, sh, sl, th, tl, each n rows, so consecutive threads load
+// consecutive words; elem = -1 marks points without a value.
+template <int n>
+__global__ void k_points_basis(int64_t P, const int32_t* __restrict__ code, const int32_t* __restrict__ elem,
+                               const double* __restrict__ rst, float* __restrict__ basis, int32_t* __restrict__ pe,
+                               BasisTab tab)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const bool ok = !(code[p] == FP_CODE_NOT_FOUND || code[p] == FP_CODE_RETRY || elem[p] < 0);
+    pe[p] = ok ? elem[p] : -1;
+    if (!ok) return;
+    double h[n];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        lagrange_h<n, double>(tab.xi, tab.ci, rst[d * P + p], h);
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            const df v = df_split(h[i]);
+            basis[((int64_t)(2 * d) * n + i) * P + p] = v.hi;
+            basis[((int64_t)(2 * d + 1) * n + i) * P + p] = v.lo;
+        }
+    }
+}
+
+template <int n>
+__global__ void __launch_bounds__(128) k_eval_points_df(int64_t E, int64_t P, int F, const int32_t* __restrict__ pe,
+                                                        const float* __restrict__ basis,
+                                                        const float2* __restrict__ fields, double* __restrict__ out)
+{
+    constexpr int n3 = n * n * n;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t p = t / F;
+    if (p >= P) return;
+    const int f = (int)(t % F);
+    const int e = pe[p];
+    if (e < 0 || e >= E) {
+        out[(int64_t)f * P + p] = __longlong_as_double(0x7ff8000000000000ULL);
+        return;
+    }
+    float rh[n], rl[n], sh[n], sl[n], th[n], tl[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        rh[i] = __ldg(basis + (int64_t)(0 * n + i) * P + p);
+        rl[i] = __ldg(basis + (int64_t)(1 * n + i) * P + p);
+        sh[i] = __ldg(basis + (int64_t)(2 * n + i) * P + p);
+        sl[i] = __ldg(basis + (int64_t)(3 * n + i) * P + p);
+        th[i] = __ldg(basis + (int64_t)(4 * n + i) * P + p);
+        tl[i] = __ldg(basis + (int64_t)(5 * n + i) * P + p);
+    }
+    const float2* Fe = fields + ((int64_t)f * E + e) * n3;
+    df acc = {0.0f, 0.0f};
+#pragma unroll 1
+    for (int k = 0; k < n; ++k) {
+        df ck = {0.0f, 0.0f};
+#pragma unroll 1
+        for (int j = 0; j < n; ++j) {
+            df u = {0.0f, 0.0f};
+            if constexpr (n % 2 == 0) {
+                const float4* row = reinterpret_cast<const float4*>(Fe + n * (j + n * k));
+#pragma unroll
+                for (int i2 = 0; i2 < n / 2; ++i2) {
+                    const float4 v = __ldg(row + i2);
+                    df_fma_acc(u, v.x, v.y, rh[2 * i2], rl[2 * i2]);
+                    df_fma_acc(u, v.z, v.w, rh[2 * i2 + 1], rl[2 * i2 + 1]);
+                }
+            } else {
+                const float2* r2 = Fe + n * (j + n * k);
+#pragma unroll
+                for (int i = 0; i < n; ++i) {
+                    const float2 v = __ldg(r2 + i);
+                    df_fma_acc(u, v.x, v.y, rh[i], rl[i]);
+                }
+            }
+            const float tt = u.hi + u.lo;
+            u.lo = u.lo - (tt - u.hi);
+            u.hi = tt;
+            df_fma_acc(ck, u, sh[j], sl[j]);
+        }
+        const float tt = ck.hi + ck.lo;
+        ck.lo = ck.lo - (tt - ck.hi);
+        ck.hi = tt;
+        df_fma_acc(acc, ck, th[k], tl[k]);
+    }
+    out[(int64_t)f * P + p] = (double)acc.hi + (double)acc.lo;
+}
+
 __global__ void k_split_df(int64_t n, const double* __restrict__ src, float2* __restrict__ dst)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -205,6 +295,40 @@ cudaError_t launch_split_df(int64_t n, const double* src, float2* dst, cudaStrea
 {
     const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 32);
     k_split_df<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(n, src, dst);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_points_basis(int n, int64_t P, const int32_t* code, const int32_t* elem, const double* rst,
+                                float* basis, int32_t* pe, const BasisTab& tab, cudaStream_t s)
+{
+    if (P == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((P + 127) / 128);
+    switch (n) {
+#define FP_CASE(NN) \
+    case NN: k_points_basis<NN><<<grid, 128, 0, s>>>(P, code, elem, rst, basis, pe, tab); break;
+        FP_CASE(2) FP_CASE(3) FP_CASE(4) FP_CASE(5) FP_CASE(6) FP_CASE(7) FP_CASE(8) FP_CASE(9)
+        FP_CASE(10) FP_CASE(11) FP_CASE(12) FP_CASE(13) FP_CASE(14) FP_CASE(15) FP_CASE(16)
+#undef FP_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval_points_df(int n, int64_t E, int64_t P, int F, const int32_t* pe, const float* basis,
+                                  const float2* fields, double* out, cudaStream_t s)
+{
+    if (P == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((P * F + 127) / 128);
+    switch (n) {
+#define FP_CASE(NN) \
+    case NN: k_eval_points_df<NN><<<grid, 128, 0, s>>>(E, P, F, pe, basis, fields, out); break;
+        FP_CASE(2) FP_CASE(3) FP_CASE(4) FP_CASE(5) FP_CASE(6) FP_CASE(7) FP_CASE(8) FP_CASE(9)
+        FP_CASE(10) FP_CASE(11) FP_CASE(12) FP_CASE(13) FP_CASE(14) FP_CASE(15) FP_CASE(16)
+#undef FP_CASE
+        default: return cudaErrorInvalidValue;
+    }
     count_launch();
     return cudaGetLastError();
 }

@@ -919,6 +919,71 @@ fp_status fp_eval_df(fp_handle* h, const fp_fields* f, int64_t P, const int32_t*
     return FP_OK;
 }
 
+struct fp_points {
+    const fp_handle* owner = nullptr;
+    int64_t P = 0;
+    float* basis = nullptr;    // [6n][P]
+    int32_t* elem = nullptr;   // [P], -1 = no value
+};
+
+fp_status fp_points_create(const fp_handle* h, int64_t P, fp_points** out)
+{
+    if (!out) return FP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
+    if (P < 0 || P >= (int64_t(1) << 31) || h->dim != 3) return FP_ERR_INVALID_ARG;
+    fp_points* q = new fp_points();
+    q->owner = h;
+    q->P = P;
+    cudaError_t e = dalloc(&q->basis, (size_t)6 * h->n * std::max<int64_t>(P, 1));
+    if (e == cudaSuccess) e = dalloc(&q->elem, std::max<int64_t>(P, 1));
+    if (e != cudaSuccess) {
+        dfree(q->basis);
+        dfree(q->elem);
+        delete q;
+        return e == cudaErrorMemoryAllocation ? FP_ERR_OOM : FP_ERR_CUDA;
+    }
+    *out = q;
+    return FP_OK;
+}
+
+void fp_points_free(fp_points* q)
+{
+    if (!q) return;
+    cudaDeviceSynchronize();
+    dfree(q->basis);
+    dfree(q->elem);
+    delete q;
+}
+
+fp_status fp_points_set(fp_handle* h, fp_points* q, const int32_t* code, const int32_t* elem, const double* rst,
+                        void* stream)
+{
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
+    h->err.clear();
+    if (!q || q->owner != h) return fail(h, FP_ERR_INVALID_ARG, "fp_points_set: points made for another handle");
+    if (q->P == 0) return FP_OK;
+    if (!code || !elem || !rst) return fail(h, FP_ERR_INVALID_ARG, "fp_points_set: null pointer");
+    cudaError_t err = launch_points_basis(h->n, q->P, code, elem, rst, q->basis, q->elem, h->tab,
+                                          (cudaStream_t)stream);
+    if (err != cudaSuccess) return cuda_fail(h, err, "fp_points_set");
+    return FP_OK;
+}
+
+fp_status fp_eval_points(fp_handle* h, const fp_fields* f, const fp_points* q, double* out, void* stream)
+{
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
+    h->err.clear();
+    if (!f || f->owner != h) return fail(h, FP_ERR_INVALID_ARG, "fp_eval_points: fields posted for another handle");
+    if (!q || q->owner != h) return fail(h, FP_ERR_INVALID_ARG, "fp_eval_points: points made for another handle");
+    if (q->P == 0) return FP_OK;
+    if (!out) return fail(h, FP_ERR_INVALID_ARG, "fp_eval_points: null out");
+    cudaError_t err = launch_eval_points_df(h->n, h->E, q->P, f->F, q->elem, q->basis, f->data, out,
+                                            (cudaStream_t)stream);
+    if (err != cudaSuccess) return cuda_fail(h, err, "fp_eval_points");
+    return FP_OK;
+}
+
 fp_status fp_eval(fp_handle* h, int64_t P, const int32_t* code, const int32_t* elem, const double* rst, int F,
                   const double* fields, double* out, void* stream)
 {

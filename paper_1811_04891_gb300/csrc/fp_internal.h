@@ -137,6 +137,10 @@ cudaError_t launch_eval_pairs(int n, int64_t E, int64_t P, const int32_t* dcount
 cudaError_t launch_split_df(int64_t n, const double* src, float2* dst, cudaStream_t s);
 cudaError_t launch_eval_df(int n, int64_t E, int64_t P, const int32_t* code, const int32_t* elem, const double* rst,
                            int F, const float2* fields, double* out, const BasisTab& tab, cudaStream_t s);
+cudaError_t launch_points_basis(int n, int64_t P, const int32_t* code, const int32_t* elem, const double* rst,
+                                float* basis, int32_t* pe, const BasisTab& tab, cudaStream_t s);
+cudaError_t launch_eval_points_df(int n, int64_t E, int64_t P, int F, const int32_t* pe, const float* basis,
+                                  const float2* fields, double* out, cudaStream_t s);
 cudaError_t launch_eval(int n, int64_t E, int64_t P, const int32_t* code, const int32_t* elem, const double* rst,
                         int F, const double* fields, double* out, const BasisTab& tab, cudaStream_t s);
 

@@ -53,6 +53,9 @@ class InterfaceExchange:
         self.bf.iface_points(out=self.pts)
         self.found = fg.fp_find_eval(self.h, self.pts, self.qs, fields=f, posted=self.posted,
                                      out=self.found[:5], values=self.vals)
+        if self.posted is not None:     # basis values kept for the sub-iterations
+            self.ppts = fg.Points(self.h, self.pts.shape[1])
+            self.ppts.set(self.found[0], self.found[2], self.found[3])
         self.graph = None
 
     def move(self, coords: torch.Tensor, dist: Optional[torch.Tensor] = None):
@@ -66,11 +69,13 @@ class InterfaceExchange:
         self.bf.iface_points(out=self.pts)
         fg.fp_find_warm(self.h, self.pts, warm=(self.found[2], self.found[3]), qsess=self.qs, fields=self.fields,
                         posted=self.posted, out=self.found[:5], values=self.vals)
+        if self.posted is not None:     # same buffers: a captured sub-iteration stays valid
+            self.ppts.set(self.found[0], self.found[2], self.found[3])
 
     def _correct_eager(self):
         code, elem, rst = self.found[0], self.found[2], self.found[3]
         if self.posted is not None:
-            fg.fp_eval_df(self.h, self.posted, code, elem, rst, out=self.vals)
+            self.ppts.eval(self.posted, out=self.vals)
         else:
             fg.fp_eval(self.h, code, elem, rst, self.fields, out=self.vals)
         st = fg.lib().fp_flux_correct_iface(self.bf.ptr, fg._ptr(self.vals), fg._ptr(self.u_pres), fg._ptr(self.u),

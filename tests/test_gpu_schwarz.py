@@ -114,3 +114,24 @@ def test_sort_iface_renumbers_without_changing_results(fg):
     b = fg.fp_flux_correct_iface(bf, u1, up)
     for p, q in zip(a, b):
         assert torch.equal(p, q)
+
+
+def test_posted_points_equal_eval_df(fg):
+    """Posted points (cached basis values) evaluate posted fields exactly as
+    fp_eval_df does at the same located points, including NaN for points
+    not found; updating them in place tracks a new find."""
+    mesh, q = synth.config0()
+    dev = torch.device("cuda:0")
+    h = fg.fp_setup(torch.from_numpy(mesh.coords).to(dev), mesh.N, torch.from_numpy(mesh.sub).to(dev),
+                    opts=fg.default_opts(precision=fg.PREC_MIXED))
+    f = fg.Fields(h, torch.from_numpy(np.stack([q.fields[0], q.fields[0] ** 2])).to(dev))
+    pts = np.concatenate([q.pts[:, :3000], np.array([[1.5, 0.5, 0.5]]).T], axis=1)
+    r = fg.fp_find(h, torch.from_numpy(pts).to(dev))
+    pp = fg.Points(h, pts.shape[1])
+    for k in range(2):
+        pp.set(r[0], r[2], r[3])
+        a = pp.eval(f)
+        b = fg.fp_eval_df(h, f, r[0], r[2], r[3])
+        torch.testing.assert_close(a, b, rtol=0, atol=0, equal_nan=True)
+        assert torch.isnan(a[:, r[0] == fg.NOT_FOUND]).all() and (r[0] == fg.NOT_FOUND).sum() == 1
+        r = fg.fp_find(h, torch.from_numpy(np.ascontiguousarray(pts[:, ::-1])).to(dev))
