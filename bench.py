@@ -89,6 +89,29 @@ def parse():
     return ap.parse_args()
 
 
+def make_collectives(dist, world: int, device):
+    """barrier() and max_over_ranks(x) of the replica runs: every rank runs its
+    own copy of the workload (no collective on the data path); the job's time
+    is the slowest rank's."""
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return barrier, max_over_ranks
+
+
+def replica_rate(world: int, points_per_rank: int, steps: int, ms_slowest: float) -> float:
+    """Weak scaling: all ranks' points over the slowest rank's time (points/s)."""
+    return world * points_per_rank * steps / (ms_slowest / 1e3)
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -560,16 +583,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier, max_over_ranks = make_collectives(dist, world, dev)
 
     mesh, q = workload(args)
     P = q.P
@@ -641,7 +655,7 @@ def main():
         ms_max = max_over_ranks(ms)
         counts = torch.bincount(code.long(), minlength=3).tolist()
         npairs = fg.fp_last_find_stats(h)
-        results[form] = {"ms_per_step": ms_max / args.steps, "value": world * P * args.steps / (ms_max / 1e3),
+        results[form] = {"ms_per_step": ms_max / args.steps, "value": replica_rate(world, P, args.steps, ms_max),
                          "setup_ms": setup_ms, "gpu_launches": launches, "clocks": clk,
                          "kernel_ms": {k: (v[0] / max(v[1], 1)) for k, v in kt.items()},
                          "codes": {"inside": counts[0], "border": counts[1], "not_found": counts[2]},
@@ -696,7 +710,7 @@ def main():
             e2e_step()
         torch.cuda.synchronize()
         dt = max_over_ranks(time.perf_counter() - t0)
-        e2e = {"value": world * P * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(pts_h.numel() * 8),
+        e2e = {"value": replica_rate(world, P, args.steps, 1e3 * dt), "unit": UNIT, "h2d_bytes_per_step": int(pts_h.numel() * 8),
                "d2h_bytes_per_step": int(out_h.numel() * 8 + sum(t.numel() * t.element_size() for t in outs_h)),
                "api": "fp_find_eval_host (host buffers, chunks of 2^22 points, copies overlapped)"}
 
