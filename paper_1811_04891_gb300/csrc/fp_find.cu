@@ -12,7 +12,7 @@
 //                      point's previous (e, r) on a moving mesh), then
 //                      box-constrained trust-region Newton on
 //                      ||x^e(r) - x*||^2.  FP64 form: k_newton<n>.  Mixed
-//                      form: k_newton_mixed<n> runs the seed and the early
+//                      form: k_newton_mixed<n,CAP> runs the seed and the early
 //                      iterations in FP32 on element-local coordinates, a
 //                      compensated refinement and one FP64 step;
 //                      k_newton64_full<n> finishes the pairs that step did
@@ -706,8 +706,19 @@ __device__ __forceinline__ void resid_df(const ElemPtr<float>& hi, const ElemPtr
 
 // passes 1 and 2 in one kernel: the FP32 work of some warps overlaps the
 // FP64 work of others.
-template <int n>
-__global__ void __launch_bounds__(256) k_newton_mixed(NewtonArgs A, BasisTab tab)
+// Launch shape of the mixed Newton kernel.  CAP (one block per 128 pairs,
+// n <= 8): registers capped so that five blocks of 128 threads fit an SM --
+// more warps keep the FP64 pipe fed, at the price of a few spills to L1.
+// Otherwise (persistent grids of the workspace and batch paths, larger n)
+// the compiler is left free.
+template <int n, bool CAP> struct MixedLB {
+    static constexpr int threads = CAP ? 128 : 256;
+    static constexpr int blocks = CAP ? 5 : 1;
+};
+
+template <int n, bool CAP>
+__global__ void __launch_bounds__(MixedLB<n, CAP>::threads, MixedLB<n, CAP>::blocks)
+    k_newton_mixed(NewtonArgs A, BasisTab tab)
 {
     constexpr int n3 = n * n * n;
     const int64_t npairs = live_pairs(A.dcount, A.cap);
@@ -972,7 +983,14 @@ static cudaError_t solve_n(const FindArgs& a, int64_t npairs, const BasisTab& ta
             na.fb_cap = a.P;
             cudaError_t e0 = cudaMemsetAsync(a.scan_tmp, 0, sizeof(int32_t), s);
             if (e0 != cudaSuccess) return e0;
-            k_newton_mixed<n><<<grid, block, 0, s>>>(na, tab);
+            bool capped = false;
+            if constexpr (n <= 8) {
+                if (a.persistent_blocks == 0 && block <= 128) {
+                    k_newton_mixed<n, true><<<grid_for(npairs, block, 0), block, 0, s>>>(na, tab);
+                    capped = true;
+                }
+            }
+            if (!capped) k_newton_mixed<n, false><<<grid, block, 0, s>>>(na, tab);
             // blocks of one warp: enough for a list of up to 38,912 pairs in one
             // pass, and for the chunked path over every slot if it overflowed
             const unsigned gfull = (unsigned)std::max<int64_t>(
