@@ -59,7 +59,7 @@ K_ORACLE = 3.43
 # DRAM bytes (read + written) per (point, candidate element) pair of the Newton
 # stage, measured with ncu on the 2.02M-point case of this workload (2.05M
 # pairs) and scaled by the pairs of a launch.
-TRAFFIC_PER_PAIR = {"mixed": 1239.0, "fp64": 740.0}
+TRAFFIC_PER_PAIR = {"mixed": 1422.0, "fp64": 740.0}
 WORK = {"fp64": {"f64": SEED + K_ORACLE * ITER, "f32": 0.0},
         "mixed": {"f64": RESID + BASIS64, "f32": SEED + K_ORACLE * ITER + 2 * RESID_DF}}
 
