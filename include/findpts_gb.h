@@ -337,9 +337,13 @@ fp_status fp_find_warm(fp_handle *h, int64_t P, const double *pts, const int32_t
  * points and results in HOST memory.  The points are cut into chunks of
  * `chunk` points (<= 0: 2^22); while the device searches one chunk, a copy
  * stream brings the next one in and another takes the results of the
- * previous one out, so the copies overlap the search.  Two sets of device
- * buffers alternate; they are kept in the handle for later calls (grown when
- * a call asks for more) and freed with it.
+ * previous one out, so the copies overlap the search.  Two workspaces of
+ * `chunk` points and `max_pairs` candidate pairs (<= 0: 4 * chunk) and two
+ * sets of device buffers alternate; they are kept in the handle for later
+ * calls (grown when a call asks for more) and freed with it.  The searches
+ * never wait on the host; a chunk whose pairs overflowed its workspace has
+ * its RETRY points searched again with fp_find_eval before the call
+ * returns, so no FP_CODE_RETRY comes back.
  *   pts [3][P], qsess [P] or NULL: host memory (pinned memory copies fastest)
  *   fields / posted: device, as for fp_find_eval
  *   code, sub, elem [P], rst [3][P], dist2 [P], out [F][P]: host memory
@@ -351,7 +355,7 @@ fp_status fp_find_warm(fp_handle *h, int64_t P, const double *pts, const int32_t
 fp_status fp_find_eval_host(fp_handle *h, int64_t P, const double *pts, const int32_t *qsess, int F,
                             const double *fields, const fp_fields *posted, int32_t *code,
                             int32_t *sub, int32_t *elem, double *rst, double *dist2, double *out,
-                            int64_t chunk, void *stream);
+                            int64_t chunk, int64_t max_pairs, void *stream);
 
 /* Posted points: the split Lagrange basis values of P located points, for
  * repeated evaluation at the same (e, r) -- the interface points of a

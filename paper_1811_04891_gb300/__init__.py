@@ -94,7 +94,7 @@ def _load():
     L.fp_eval_df.restype = ci
     L.fp_find_eval.argtypes = [vp, i64, vp, vp, ci, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.fp_find_eval.restype = ci
-    L.fp_find_eval_host.argtypes = [vp, i64, vp, vp, ci, vp, vp, vp, vp, vp, vp, vp, vp, i64, vp]
+    L.fp_find_eval_host.argtypes = [vp, i64, vp, vp, ci, vp, vp, vp, vp, vp, vp, vp, vp, i64, i64, vp]
     L.fp_find_eval_host.restype = ci
     L.fp_points_create.argtypes = [vp, i64, ctypes.POINTER(vp)]
     L.fp_points_create.restype = ci
@@ -508,7 +508,7 @@ def fp_find_eval_ws(h: Handle, ws: "Workspace", pts: torch.Tensor, qsess: Option
 
 def fp_find_eval_host(h: Handle, pts: torch.Tensor, qsess: Optional[torch.Tensor] = None, fields=None,
                       posted: Optional["Fields"] = None, out=None, values: Optional[torch.Tensor] = None,
-                      chunk: int = 0, stream=None):
+                      chunk: int = 0, max_pairs: int = 0, stream=None):
     """find (+ eval when fields or posted are given) over points in HOST
     memory (CPU tensor [3][P] float64, pinned for speed), streamed through
     the device in chunks with the copies overlapping the search.  Returns
@@ -531,7 +531,7 @@ def fp_find_eval_host(h: Handle, pts: torch.Tensor, qsess: Optional[torch.Tensor
     code, sub, elem, rst, dist2 = out
     st = lib().fp_find_eval_host(h.ptr, P, _ptr(pts), _ptr(qsess), F, _ptr(f64), fptr, _ptr(code), _ptr(sub),
                                  _ptr(elem), _ptr(rst), _ptr(dist2), _ptr(values if F else None), int(chunk),
-                                 _stream(stream))
+                                 int(max_pairs), _stream(stream))
     _check(st, h.ptr)
     return (code, sub, elem, rst, dist2, values) if F else (code, sub, elem, rst, dist2)
 

@@ -794,6 +794,25 @@ void fp_workspace_free(fp_workspace* w)
     delete w;
 }
 
+}  // extern "C"
+
+// a workspace whose launches cover its whole pair capacity with one block per
+// 128 pairs (blocks past the device-side count exit at once) instead of a
+// persistent grid: no host wait, and the Newton work balances like a launch
+// sized on the host (used by the host-memory streaming path)
+void fpg::workspace_unpersist(fp_workspace* w)
+{
+    if (w) w->persistent_blocks = 0;
+}
+
+cudaError_t fpg::workspace_pair_count_async(fp_workspace* w, int32_t* host_dst, cudaStream_t s)
+{
+    if (!w || w->last_P <= 0) return cudaErrorInvalidValue;
+    return cudaMemcpyAsync(host_dst, w->off + w->last_P, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+}
+
+extern "C" {
+
 fp_status fp_workspace_last_pairs(fp_workspace* w, int64_t* npairs)
 {
     if (!w) return FP_ERR_INVALID_ARG;

@@ -109,8 +109,13 @@ cudaError_t find_solve_unsorted(const FindArgs& a, int64_t npairs, const BasisTa
 // host streaming state of fp_find_eval_host (fp_stream.cu), freed with the handle
 }  // namespace fpg
 struct fp_host_stream;
+struct fp_workspace;
 namespace fpg {
 void host_stream_free(fp_host_stream* hs);
+// workspace launches over its whole pair capacity instead of a persistent grid
+void workspace_unpersist(fp_workspace* w);
+// copy the workspace's device pair count of its latest find to *host_dst on s
+cudaError_t workspace_pair_count_async(fp_workspace* w, int32_t* host_dst, cudaStream_t s);
 
 // counting sort of the pairs by element (fp_find.cu), shared by both dimensions
 cudaError_t find_sort(const FindArgs& a, int64_t npairs, cudaStream_t s);

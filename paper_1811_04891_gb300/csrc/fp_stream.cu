@@ -6,18 +6,21 @@
 // pays for two copies per call besides the search.  This entry point hides
 // them: the points are cut into chunks; while the compute stream searches
 // chunk i, a copy stream brings chunk i+1 in and another takes the results
-// of chunk i-1 out.  Two sets of device buffers alternate between chunks, so
-// the copies of one chunk never touch the buffers the search of the other
-// is using; events order the three streams.  Each chunk runs the ordinary
-// find (+ fused eval) on the compute stream, which waits on the host only to
-// size its pair arrays, early in the chunk; the copy streams keep moving
-// meanwhile.  (The workspace path would avoid that wait, but its persistent
-// grids balance the Newton work of a chunk less well than one block per 128
-// pairs does.)
+// of chunk i-1 out.  Two sets of device buffers and two workspaces alternate
+// between chunks, so the copies of one chunk never touch the buffers the
+// search of the other is using; events order the three streams.  Each chunk
+// runs the workspace find (+ fused eval): the pair count stays on the device
+// and no call waits on the host, while the launches cover the workspace's
+// whole pair capacity with one block per 128 pairs (blocks past the count
+// exit at once), which balances the Newton work like a launch sized on the
+// host.  The pair count of every chunk comes back with its results; a chunk
+// whose pairs overflowed its workspace has its RETRY points searched again
+// with fp_find_eval before the call returns.
 #include <string.h>
 
 #include <algorithm>
 #include <string>
+#include <vector>
 
 #include "fp_common.cuh"
 #include "fp_handle.h"
@@ -26,6 +29,7 @@
 namespace {
 
 struct Slot {
+    fp_workspace* ws = nullptr;
     double* pts = nullptr;      // [3][chunk]
     int32_t* qs = nullptr;      // [chunk]
     int32_t* code = nullptr;
@@ -47,10 +51,12 @@ cudaError_t dmalloc(T** p, int64_t n)
 }  // namespace
 
 struct fp_host_stream {
-    int64_t chunk = 0;
+    int64_t chunk = 0, max_pairs = 0;
     int F = 0;
     Slot slot[2];
     cudaStream_t cin = nullptr, cout = nullptr;
+    int32_t* h_pairs = nullptr;   // pinned: device pair count of each chunk
+    int64_t h_pairs_cap = 0;
 };
 
 namespace fpg {
@@ -61,6 +67,7 @@ void host_stream_free(fp_host_stream* hs)
     if (hs->cin) cudaStreamSynchronize(hs->cin);
     if (hs->cout) cudaStreamSynchronize(hs->cout);
     for (Slot& S : hs->slot) {
+        if (S.ws) fp_workspace_free(S.ws);
         cudaFree(S.pts); cudaFree(S.qs); cudaFree(S.code); cudaFree(S.sub); cudaFree(S.elem);
         cudaFree(S.rst); cudaFree(S.dist2); cudaFree(S.out);
         if (S.in_done) cudaEventDestroy(S.in_done);
@@ -69,15 +76,17 @@ void host_stream_free(fp_host_stream* hs)
     }
     if (hs->cin) cudaStreamDestroy(hs->cin);
     if (hs->cout) cudaStreamDestroy(hs->cout);
+    if (hs->h_pairs) cudaFreeHost(hs->h_pairs);
     delete hs;
 }
 
 }  // namespace fpg
 
-static fp_status stream_state(fp_handle* h, int64_t chunk, int F, fp_host_stream** out)
+static fp_status stream_state(fp_handle* h, int64_t chunk, int64_t max_pairs, int F, int64_t nchunks,
+                              fp_host_stream** out)
 {
     fp_host_stream* hs = h->host_stream;
-    if (hs && (hs->chunk < chunk || hs->F < F)) {
+    if (hs && (hs->chunk < chunk || hs->max_pairs < max_pairs || hs->F < F)) {
         fpg::host_stream_free(hs);
         h->host_stream = hs = nullptr;
     }
@@ -85,10 +94,14 @@ static fp_status stream_state(fp_handle* h, int64_t chunk, int F, fp_host_stream
         cudaError_t e = cudaSuccess;
         hs = new fp_host_stream();
         hs->chunk = chunk;
+        hs->max_pairs = max_pairs;
         hs->F = F;
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hs->cin, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hs->cout, cudaStreamNonBlocking);
         for (Slot& S : hs->slot) {
+            if (e == cudaSuccess && fp_workspace_create(h, chunk, max_pairs, &S.ws) != FP_OK)
+                e = cudaErrorMemoryAllocation;
+            if (e == cudaSuccess) fpg::workspace_unpersist(S.ws);
             if (e == cudaSuccess) e = dmalloc(&S.pts, 3 * chunk);
             if (e == cudaSuccess) e = dmalloc(&S.qs, chunk);
             if (e == cudaSuccess) e = dmalloc(&S.code, chunk);
@@ -108,14 +121,86 @@ static fp_status stream_state(fp_handle* h, int64_t chunk, int F, fp_host_stream
         }
         h->host_stream = hs;
     }
+    if (hs->h_pairs_cap < nchunks) {
+        if (hs->h_pairs) cudaFreeHost(hs->h_pairs);
+        hs->h_pairs = nullptr;
+        hs->h_pairs_cap = 0;
+        if (cudaMallocHost((void**)&hs->h_pairs, sizeof(int32_t) * (size_t)nchunks) != cudaSuccess) {
+            h->err = "fp_find_eval_host: pinned pair counts";
+            return FP_ERR_OOM;
+        }
+        hs->h_pairs_cap = nchunks;
+    }
     *out = hs;
+    return FP_OK;
+}
+
+// search again, with the growing (synchronous) path, the RETRY points of one chunk
+static fp_status redo_retry(fp_handle* h, int64_t P, int64_t i0, int64_t c, const double* pts, const int32_t* qsess,
+                            bool eval, int F, const double* fields, const fp_fields* posted, int32_t* code,
+                            int32_t* sub, int32_t* elem, double* rst, double* dist2, double* out, cudaStream_t s)
+{
+    std::vector<int64_t> idx;
+    for (int64_t k = 0; k < c; ++k)
+        if (code[i0 + k] == FP_CODE_RETRY) idx.push_back(i0 + k);
+    const int64_t m = (int64_t)idx.size();
+    if (m == 0) return FP_OK;
+    std::vector<double> hp(3 * m), hr(3 * m), hd(m), ho((size_t)std::max(F, 1) * m);
+    std::vector<int32_t> hq(m), hc(m), hsb(m), he(m);
+    for (int64_t k = 0; k < m; ++k) {
+        for (int a = 0; a < 3; ++a) hp[a * m + k] = pts[a * P + idx[k]];
+        hq[k] = qsess ? qsess[idx[k]] : -1;
+    }
+    double *dp = nullptr, *dr = nullptr, *dd = nullptr, *dout = nullptr;
+    int32_t *dq = nullptr, *dc = nullptr, *dsu = nullptr, *de = nullptr;
+    cudaError_t e = dmalloc(&dp, 3 * m);
+    if (e == cudaSuccess) e = dmalloc(&dr, 3 * m);
+    if (e == cudaSuccess) e = dmalloc(&dd, m);
+    if (e == cudaSuccess) e = dmalloc(&dout, (int64_t)std::max(F, 1) * m);
+    if (e == cudaSuccess) e = dmalloc(&dq, m);
+    if (e == cudaSuccess) e = dmalloc(&dc, m);
+    if (e == cudaSuccess) e = dmalloc(&dsu, m);
+    if (e == cudaSuccess) e = dmalloc(&de, m);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dp, hp.data(), sizeof(double) * 3 * m, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dq, hq.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, s);
+    fp_status st = FP_ERR_CUDA;
+    if (e == cudaSuccess) {
+        st = eval ? fp_find_eval(h, m, dp, dq, F, fields, posted, dc, dsu, de, dr, dd, dout, s)
+                  : fp_find(h, m, dp, dq, dc, dsu, de, dr, dd, s);
+        if (st == FP_OK) {
+            e = cudaMemcpyAsync(hc.data(), dc, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hsb.data(), dsu, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(he.data(), de, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hr.data(), dr, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hd.data(), dd, sizeof(double) * m, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess && eval)
+                e = cudaMemcpyAsync(ho.data(), dout, sizeof(double) * F * m, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) st = FP_ERR_CUDA;
+        }
+    }
+    cudaFree(dp); cudaFree(dr); cudaFree(dd); cudaFree(dout); cudaFree(dq); cudaFree(dc); cudaFree(dsu); cudaFree(de);
+    if (st != FP_OK) {
+        if (h->err.empty()) h->err = "fp_find_eval_host: searching the RETRY points again failed";
+        return st;
+    }
+    for (int64_t k = 0; k < m; ++k) {
+        const int64_t p = idx[k];
+        code[p] = hc[k];
+        sub[p] = hsb[k];
+        elem[p] = he[k];
+        dist2[p] = hd[k];
+        for (int a = 0; a < 3; ++a) rst[a * P + p] = hr[a * m + k];
+        if (eval)
+            for (int f = 0; f < F; ++f) out[(int64_t)f * P + p] = ho[(size_t)f * m + k];
+    }
     return FP_OK;
 }
 
 extern "C" fp_status fp_find_eval_host(fp_handle* h, int64_t P, const double* pts, const int32_t* qsess, int F,
                                        const double* fields, const fp_fields* posted, int32_t* code, int32_t* sub,
                                        int32_t* elem, double* rst, double* dist2, double* out, int64_t chunk,
-                                       void* stream)
+                                       int64_t max_pairs, void* stream)
 {
     if (!fp_live(h)) return FP_ERR_NOT_SETUP;
     h->err.clear();
@@ -135,9 +220,14 @@ extern "C" fp_status fp_find_eval_host(fp_handle* h, int64_t P, const double* pt
     }
     if (chunk <= 0) chunk = int64_t(1) << 22;
     chunk = std::min(chunk, P);
+    if (max_pairs <= 0) max_pairs = 4 * chunk;
+    if (max_pairs >= (int64_t(1) << 31)) {
+        h->err = "fp_find_eval_host: max_pairs out of range";
+        return FP_ERR_INVALID_ARG;
+    }
     const int64_t nch = (P + chunk - 1) / chunk;
     fp_host_stream* hs = nullptr;
-    fp_status st = stream_state(h, chunk, eval ? F : 0, &hs);
+    fp_status st = stream_state(h, chunk, max_pairs, eval ? F : 0, nch, &hs);
     if (st != FP_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
@@ -156,15 +246,16 @@ extern "C" fp_status fp_find_eval_host(fp_handle* h, int64_t P, const double* pt
         if (e == cudaSuccess) e = cudaEventRecord(S.in_done, hs->cin);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, S.in_done, 0);
         if (e != cudaSuccess) break;
-        st = eval ? fp_find_eval(h, c, S.pts, qsess ? S.qs : nullptr, F, fields, posted, S.code, S.sub, S.elem,
-                                 S.rst, S.dist2, S.out, s)
-                  : fp_find(h, c, S.pts, qsess ? S.qs : nullptr, S.code, S.sub, S.elem, S.rst, S.dist2, s);
+        st = eval ? fp_find_eval_ws(h, S.ws, c, S.pts, qsess ? S.qs : nullptr, F, fields, posted, S.code, S.sub,
+                                    S.elem, S.rst, S.dist2, S.out, s)
+                  : fp_find_ws(h, S.ws, c, S.pts, qsess ? S.qs : nullptr, S.code, S.sub, S.elem, S.rst, S.dist2, s);
         if (st != FP_OK) {
             cudaStreamSynchronize(hs->cout);
             cudaStreamSynchronize(hs->cin);
             return st;
         }
-        e = cudaEventRecord(S.comp_done, s);
+        e = fpg::workspace_pair_count_async(S.ws, hs->h_pairs + i, s);
+        if (e == cudaSuccess) e = cudaEventRecord(S.comp_done, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(hs->cout, S.comp_done, 0);
         if (e == cudaSuccess) e = cudaMemcpyAsync(code + i0, S.code, sizeof(int32_t) * c, cudaMemcpyDeviceToHost, hs->cout);
         if (e == cudaSuccess) e = cudaMemcpyAsync(sub + i0, S.sub, sizeof(int32_t) * c, cudaMemcpyDeviceToHost, hs->cout);
@@ -186,6 +277,12 @@ extern "C" fp_status fp_find_eval_host(fp_handle* h, int64_t P, const double* pt
     if (e != cudaSuccess) {
         h->err = std::string("fp_find_eval_host: ") + cudaGetErrorString(e);
         return FP_ERR_CUDA;
+    }
+    for (int64_t i = 0; i < nch; ++i) {
+        if (hs->h_pairs[i] <= max_pairs) continue;               // every pair of the chunk fitted
+        const int64_t i0 = i * chunk, c = std::min(chunk, P - i0);
+        st = redo_retry(h, P, i0, c, pts, qsess, eval, F, fields, posted, code, sub, elem, rst, dist2, out, s);
+        if (st != FP_OK) return st;
     }
     return FP_OK;
 }

@@ -2,7 +2,8 @@
 streamed through the device in chunks): results identical to the device
 entry point for several chunk sizes with a ragged last chunk, with and
 without session tags and fields, in both forms, from pinned and pageable
-memory."""
+memory, and when a chunk's candidate pairs overflow the workspace (its RETRY
+points are searched again before the call returns)."""
 import numpy as np
 import pytest
 import torch
@@ -28,8 +29,8 @@ def _same(dev, host):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("chunk", [2500, 3000, 4096, 10 ** 6])
-def test_host_stream_equals_device(fg, prec, chunk):
+@pytest.mark.parametrize("chunk,max_pairs", [(2500, 0), (3000, 0), (4096, 0), (10 ** 6, 0), (2500, 300)])
+def test_host_stream_equals_device(fg, prec, chunk, max_pairs):
     mesh, q = synth.config0()
     dev = torch.device("cuda:0")
     h = fg.fp_setup(torch.from_numpy(mesh.coords).to(dev), mesh.N, torch.from_numpy(mesh.sub).to(dev),
@@ -41,7 +42,7 @@ def test_host_stream_equals_device(fg, prec, chunk):
     ref = fg.fp_find_eval(h, torch.from_numpy(np.ascontiguousarray(pts)).to(dev), fields=f, posted=posted)
     ph = torch.from_numpy(np.ascontiguousarray(pts)).pin_memory()
     for _ in range(2):                                   # state kept in the handle: a second call reuses it
-        got = fg.fp_find_eval_host(h, ph, fields=f, posted=posted, chunk=chunk)
+        got = fg.fp_find_eval_host(h, ph, fields=f, posted=posted, chunk=chunk, max_pairs=max_pairs)
         _same(ref, got)
     assert (got[0] != fg.RETRY).all()
 
