@@ -121,7 +121,7 @@ def dist_env():
 
 def workload(args):
     import synth
-    mesh, q = synth.config2(ne=args.ne, P_uniform=args.points, P_face=args.face_points)
+    mesh, q = synth.deformed_cube(ne=args.ne, P_uniform=args.points, P_face=args.face_points)
     return mesh, q
 
 
@@ -245,7 +245,7 @@ def run_batched(args, fg, dev, barrier, max_over_ranks, world):
     import torch
 
     import synth
-    insts = synth.config3()
+    insts = synth.instance_batch()
     out = {"instances": len(insts), "elements": int(sum(m.E for m, _ in insts)),
            "points_per_step": int(sum(q.P for _, q in insts)), "orders": sorted({m.N for m, _ in insts})}
     pts = torch.from_numpy(np.ascontiguousarray(np.concatenate([q.pts for _, q in insts], axis=1))).to(dev)
@@ -284,7 +284,7 @@ def run_batched(args, fg, dev, barrier, max_over_ranks, world):
 
 
 # ---------------------------------------------------------------------------
-# interface update of the box + annulus overlap (config 1): the cylinder's
+# interface update of the box + annulus overlap (box + annulus): the cylinder's
 # radial faces take velocity and pressure interpolated from the box, its end
 # walls keep prescribed data, and the interpolated velocity is flux-corrected
 # ---------------------------------------------------------------------------
@@ -292,7 +292,7 @@ def run_interface(args, fg, dev):
     import torch
 
     import synth
-    mesh, q = synth.config1()
+    mesh, q = synth.box_annulus()
     n_rad, n_az, n_ax = 4, 32, 8
     kind = np.zeros((mesh.E, 6), np.int8)
     for e in range(1024, mesh.E):
@@ -525,7 +525,7 @@ def run_served(args, fg, dev):
     sc = args.served_scale
     box = tuple(max(2, int(round(v * sc ** (1 / 3)))) for v in (80, 40, 40))
     cyl = tuple(max(2, int(round(v * sc ** (1 / 3)))) for v in (64, 8, 64))
-    mesh, iface = synth.config4_mesh(box_shape=box, cyl_shape=cyl)
+    mesh, iface = synth.box_two_annuli(box_shape=box, cyl_shape=cyl)
     F = 4
     coords_d = torch.from_numpy(mesh.coords).to(dev)
     x, y, z = coords_d[0], coords_d[1], coords_d[2]
@@ -539,7 +539,7 @@ def run_served(args, fg, dev):
     resident = (mesh.coords.nbytes * 1.5 + fields_d.numel() * 8 + mesh.dist.nbytes)
     del coords_d
     # capacity: a 1M-point mixed request stream served back to back
-    cal = synth.config4_requests(iface, 4, seed=40, size_range=(10 ** 6, 10 ** 6))
+    cal = synth.poisson_requests(iface, 4, seed=40, size_range=(10 ** 6, 10 ** 6))
     posted = fg.Fields(h, fields_d)
     srv = serve.Server(h, fields_d, slots=4, slot_points=1 << 19, budget_bytes=40e9, resident_bytes=resident,
                        posted=posted)
@@ -547,7 +547,7 @@ def run_served(args, fg, dev):
     capacity = sum(r.P for r in done) / span
     mean_size = (10 ** 6 - 10 ** 2) / np.log(10 ** 4)
     rate = args.served_load * capacity / mean_size
-    reqs = synth.config4_requests(iface, args.served_requests, seed=4, rate_hz=rate)
+    reqs = synth.poisson_requests(iface, args.served_requests, seed=4, rate_hz=rate)
     srv = serve.Server(h, fields_d, slots=4, slot_points=1 << 19, budget_bytes=40e9, resident_bytes=resident,
                        posted=posted)
     done, span = serve.run_stream(srv, [serve.Request(i, r["t_arrive"], r["pts"], r["qsess"])

@@ -31,7 +31,7 @@ __all__ = [
     "Mesh", "Queries", "reference_grid", "box_mesh", "annulus_mesh", "concat_meshes",
     "box_distance", "annulus_distance", "uniform_points", "near_face_points",
     "boundary_face_nodes", "field_u", "sine_product_field", "random_poly_field",
-    "config0", "config1", "config2", "config3", "config4_mesh", "config4_requests",
+    "cube4_small", "box_annulus", "deformed_cube", "instance_batch", "box_two_annuli", "poisson_requests",
     "tiny_overlap", "spiral_element", "reference_poly_field", "rigid_motion",
     "quad_mesh", "ring_mesh", "rect_distance", "uniform_points_2d", "edge_points_2d", "field_u_2d",
     "reference_poly_field_2d", "tiny_overlap_2d", "walsh_2d",
@@ -325,7 +325,7 @@ def reference_poly_field(N: int, E: int, seed: int):
 # ----------------------------------------------------------------------------
 # the five workloads
 # ----------------------------------------------------------------------------
-def config0():
+def cube4_small():
     """Unit cube 4x4x4 hex, N=7, interior nodes displaced by 0.05 h sin sin sin,
     1e4 uniform points (seed 0), field u = sin(pi x)cos(pi y)exp(z)."""
     N = 7
@@ -339,11 +339,11 @@ def config0():
 # the azimuthal direction of an annulus is periodic: only radial and axial faces bound it
 ANNULUS_FACES = [(0, 0), (0, 1), (2, 0), (2, 1)]
 
-BOX1 = dict(lo=(0.0, 0.0, 0.0), hi=(2.0, 1.0, 1.0))
-CYL1 = dict(r_in=0.15, r_out=0.35, z0=0.0, z1=1.0, center=(1.0, 0.5, 0.0))
+BOX_ANNULUS_BOX = dict(lo=(0.0, 0.0, 0.0), hi=(2.0, 1.0, 1.0))
+BOX_ANNULUS_CYL = dict(r_in=0.15, r_out=0.35, z0=0.0, z1=1.0, center=(1.0, 0.5, 0.0))
 
 
-def config1(n_az=32, n_rad=4, n_ax=8, box_shape=(16, 8, 8), N=7, margin=0.0):
+def box_annulus(n_az=32, n_rad=4, n_ax=8, box_shape=(16, 8, 8), N=7, margin=0.0):
     """Box [0,2]x[0,1]^2 (16x8x8, session 0) overlapped by the annular cylinder
     rho in [0.15,0.35] around (1,0.5), z in [0,1] (32 az x 4 rad x 8 ax,
     session 1), N=7.  Queries: the deduplicated boundary GLL nodes of each
@@ -351,16 +351,16 @@ def config1(n_az=32, n_rad=4, n_ax=8, box_shape=(16, 8, 8), N=7, margin=0.0):
     own session (every cylinder boundary node; box z-face nodes with
     r_in - margin <= rho <= r_out + margin).  Four fields u,v,w,p: random
     total-degree <= 5 polynomials (seed 1).  D^k in closed form."""
-    cb = box_mesh(box_shape, N, **BOX1)
-    cc, rho, zl = annulus_mesh(n_az, n_rad, n_ax, N, CYL1["r_in"], CYL1["r_out"],
-                               CYL1["z0"], CYL1["z1"], center=CYL1["center"])
-    db = box_distance(cb, BOX1["lo"], BOX1["hi"])
-    dc = annulus_distance(rho, zl, CYL1["r_in"], CYL1["r_out"], CYL1["z0"], CYL1["z1"])
+    cb = box_mesh(box_shape, N, **BOX_ANNULUS_BOX)
+    cc, rho, zl = annulus_mesh(n_az, n_rad, n_ax, N, BOX_ANNULUS_CYL["r_in"], BOX_ANNULUS_CYL["r_out"],
+                               BOX_ANNULUS_CYL["z0"], BOX_ANNULUS_CYL["z1"], center=BOX_ANNULUS_CYL["center"])
+    db = box_distance(cb, BOX_ANNULUS_BOX["lo"], BOX_ANNULUS_BOX["hi"])
+    dc = annulus_distance(rho, zl, BOX_ANNULUS_CYL["r_in"], BOX_ANNULUS_CYL["r_out"], BOX_ANNULUS_CYL["z0"], BOX_ANNULUS_CYL["z1"])
     mesh = concat_meshes([cb, cc], N, [0, 1], [db, dc], name="box+annulus-N7")
     qc = boundary_face_nodes(cc, N, (n_rad, n_az, n_ax), faces=ANNULUS_FACES)
     qb = boundary_face_nodes(cb, N, box_shape, faces=[(2, 0), (2, 1)])
     rb = np.hypot(qb[0] - 1.0, qb[1] - 0.5)
-    keep = (rb >= CYL1["r_in"] - margin) & (rb <= CYL1["r_out"] + margin)
+    keep = (rb >= BOX_ANNULUS_CYL["r_in"] - margin) & (rb <= BOX_ANNULUS_CYL["r_out"] + margin)
     qb = qb[:, keep]
     pts = np.ascontiguousarray(np.concatenate([qb, qc], axis=1))
     qsess = np.concatenate([np.zeros(qb.shape[1], np.int32), np.ones(qc.shape[1], np.int32)])
@@ -370,10 +370,10 @@ def config1(n_az=32, n_rad=4, n_ax=8, box_shape=(16, 8, 8), N=7, margin=0.0):
                          info={"P_box": int(qb.shape[1]), "P_cyl": int(qc.shape[1])})
 
 
-def config2(ne=32, P_uniform=10 ** 7, P_face=10 ** 5, N=7, with_fields=True):
+def deformed_cube(ne=32, P_uniform=10 ** 7, P_face=10 ** 5, N=7, with_fields=True):
     """ne^3 deformed hex (amplitude 0.1 h), N=7; P_uniform uniform points
     (seed 0) followed by P_face near-face points (seed 1); five fields
-    u (as config 0) and sine products with seeds 2-5."""
+    u (as in cube4_small) and sine products with seeds 2-5."""
     coords = box_mesh((ne, ne, ne), N, amp_frac=0.1)
     mesh = Mesh(coords=coords, N=N, sub=np.zeros(coords.shape[1], np.int32),
                 name=f"cube{ne}-N{N}")
@@ -389,7 +389,7 @@ def config2(ne=32, P_uniform=10 ** 7, P_face=10 ** 5, N=7, with_fields=True):
     return mesh, Queries(pts=pts, fields=fields, info={"P_uniform": P_uniform, "P_face": P_face})
 
 
-def config3(n_inst=64, seed=3, E_range=(64, 8192), P_range=(10 ** 3, 10 ** 6),
+def instance_batch(n_inst=64, seed=3, E_range=(64, 8192), P_range=(10 ** 3, 10 ** 6),
             Ns=(5, 7, 9), scale=1.0):
     """n_inst independent deformed unit-cube instances (amplitude 0.05 h):
     E ~ logU(E_range) rounded to near-cubic ex*ey*ez, N uniform in Ns,
@@ -414,22 +414,22 @@ def config3(n_inst=64, seed=3, E_range=(64, 8192), P_range=(10 ** 3, 10 ** 6),
     return out
 
 
-BOX4 = dict(lo=(0.0, 0.0, 0.0), hi=(2.0, 1.0, 1.0))
-CYL4 = [dict(center=(0.85, 0.5, 0.5), rot=(15.0, 0.0)),
+SERVED_BOX = dict(lo=(0.0, 0.0, 0.0), hi=(2.0, 1.0, 1.0))
+SERVED_CYLS = [dict(center=(0.85, 0.5, 0.5), rot=(15.0, 0.0)),
         dict(center=(1.15, 0.5, 0.5), rot=(0.0, -15.0))]
 
 
-def config4_mesh(box_shape=(80, 40, 40), cyl_shape=(64, 8, 64), N=7):
+def box_two_annuli(box_shape=(80, 40, 40), cyl_shape=(64, 8, 64), N=7):
     """Background box [0,2]x[0,1]^2 (session 0) + two annular cylinders
     rho in [0.15,0.35], length 0.6, (az,rad,ax) = cyl_shape, centred at
     (0.85,0.5,0.5) with axis rotated +15 deg about x (session 1) and at
     (1.15,0.5,0.5) rotated -15 deg about y (session 2).  D^k in closed form.
     Returns (Mesh, [interface node arrays [3][Q] per cylinder])."""
     parts, dists, iface = [], [], []
-    cb = box_mesh(box_shape, N, **BOX4)
+    cb = box_mesh(box_shape, N, **SERVED_BOX)
     parts.append(cb)
-    dists.append(box_distance(cb, BOX4["lo"], BOX4["hi"]))
-    for c in CYL4:
+    dists.append(box_distance(cb, SERVED_BOX["lo"], SERVED_BOX["hi"]))
+    for c in SERVED_CYLS:
         cc, rho, zl = annulus_mesh(cyl_shape[0], cyl_shape[1], cyl_shape[2], N, 0.15, 0.35,
                                    -0.3, 0.3, center=c["center"], rot=c["rot"])
         parts.append(cc)
@@ -440,7 +440,7 @@ def config4_mesh(box_shape=(80, 40, 40), cyl_shape=(64, 8, 64), N=7):
     return mesh, iface
 
 
-def config4_requests(iface, n_req: int, seed: int = 4, size_range=(10 ** 2, 10 ** 6),
+def poisson_requests(iface, n_req: int, seed: int = 4, size_range=(10 ** 2, 10 ** 6),
                      rate_hz: float = 100.0):
     """Poisson request stream: sizes logU(size_range); each request is 50%
     uniform points in the box (untagged, -1) and 50% cylinder interface nodes
@@ -454,7 +454,7 @@ def config4_requests(iface, n_req: int, seed: int = 4, size_range=(10 ** 2, 10 *
         P = int(round(math.exp(rng.uniform(math.log(size_range[0]), math.log(size_range[1])))))
         Pu = P // 2
         Pi = P - Pu
-        pu = (np.array(BOX4["lo"]) + (np.array(BOX4["hi"]) - np.array(BOX4["lo"])) *
+        pu = (np.array(SERVED_BOX["lo"]) + (np.array(SERVED_BOX["hi"]) - np.array(SERVED_BOX["lo"])) *
               rng.random((Pu, 3))).T
         which = rng.integers(0, len(iface), size=Pi)
         pi = np.empty((3, Pi))

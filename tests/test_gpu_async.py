@@ -32,7 +32,7 @@ def _np(t):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_ws_matches_fp_find(fg, prec):
-    mesh, q = synth.config2(ne=8, P_uniform=40000, P_face=4000, with_fields=False)
+    mesh, q = synth.deformed_cube(ne=8, P_uniform=40000, P_face=4000, with_fields=False)
     h = _setup(fg, mesh, prec)
     pts = torch.from_numpy(q.pts).cuda()
     ref = _np(fg.fp_find(h, pts))
@@ -45,7 +45,7 @@ def test_ws_matches_fp_find(fg, prec):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_ws_multisubdomain(fg, prec):
-    mesh, q = synth.config1()
+    mesh, q = synth.box_annulus()
     h = _setup(fg, mesh, prec)
     pts = torch.from_numpy(q.pts).cuda()
     qs = torch.from_numpy(q.qsess).cuda()
@@ -57,7 +57,7 @@ def test_ws_multisubdomain(fg, prec):
 
 
 def test_ws_overflow_marks_retry(fg):
-    mesh, q = synth.config2(ne=6, P_uniform=20000, P_face=0, with_fields=False)
+    mesh, q = synth.deformed_cube(ne=6, P_uniform=20000, P_face=0, with_fields=False)
     h = _setup(fg, mesh, 1)
     pts = torch.from_numpy(q.pts).cuda()
     ref = _np(fg.fp_find(h, pts))
@@ -76,7 +76,7 @@ def test_ws_overflow_marks_retry(fg):
 
 
 def test_graph_capture_and_replay(fg):
-    mesh, q = synth.config2(ne=6, P_uniform=30000, P_face=1000)
+    mesh, q = synth.deformed_cube(ne=6, P_uniform=30000, P_face=1000)
     h = _setup(fg, mesh, 1)
     dev = torch.device("cuda:0")
     P = q.P
@@ -111,7 +111,7 @@ def test_graph_capture_and_replay(fg):
 
 
 def test_two_workspaces_two_streams(fg):
-    mesh, q = synth.config2(ne=6, P_uniform=30000, P_face=2000, with_fields=False)
+    mesh, q = synth.deformed_cube(ne=6, P_uniform=30000, P_face=2000, with_fields=False)
     h = _setup(fg, mesh, 1)
     dev = torch.device("cuda:0")
     a = torch.from_numpy(q.pts[:, :16000].copy()).to(dev)

@@ -30,7 +30,7 @@ def h_mixed(fg, h):
 
 
 def _instances(n_inst, seed, prec, fg, with_empty=False):
-    insts = synth.config3(n_inst=n_inst, seed=seed, E_range=(8, 300), P_range=(50, 4000))
+    insts = synth.instance_batch(n_inst=n_inst, seed=seed, E_range=(8, 300), P_range=(50, 4000))
     dev = torch.device("cuda:0")
     handles, fields, pts = [], [], []
     for k, (mesh, q) in enumerate(insts):

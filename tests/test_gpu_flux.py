@@ -61,7 +61,7 @@ def test_interface_update_box_annulus(fg):
     """Cylinder (session 1) boundary: radial faces are interface faces whose
     velocity comes from the box (session 0); the end walls carry prescribed
     data.  Interpolate, then correct the flux -- against the oracle chain."""
-    mesh, q = synth.config1()
+    mesh, q = synth.box_annulus()
     n_rad, n_az, n_ax = 4, 32, 8
     E = mesh.E
     kind = np.zeros((E, 6), np.int8)
@@ -90,7 +90,7 @@ def test_interface_update_box_annulus(fg):
     # prescribed data on the end walls: the nodal values of the cylinder's own fields
     xn = x.cpu().numpy()
     rng = np.random.default_rng(1)
-    terms = [synth.random_poly_field(mesh.coords[:, :1], 5, rng)[1] for _ in range(4)]   # same draws as config1
+    terms = [synth.random_poly_field(mesh.coords[:, :1], 5, rng)[1] for _ in range(4)]   # same draws as box_annulus
     pres = np.stack([sum(c * xn[0] ** i * xn[1] ** j * xn[2] ** k for c, (i, j, k) in terms[f]) for f in range(3)])
     u.copy_(torch.from_numpy(pres))
     u[:, iface] = vals

@@ -23,7 +23,7 @@ def fg():
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("posted", [False, True])
 def test_fused_equals_separate(fg, prec, posted):
-    mesh, q = synth.config2(ne=6, P_uniform=25000, P_face=2500)
+    mesh, q = synth.deformed_cube(ne=6, P_uniform=25000, P_face=2500)
     dev = torch.device("cuda:0")
     h = fg.fp_setup(torch.from_numpy(mesh.coords).to(dev), mesh.N, torch.from_numpy(mesh.sub).to(dev),
                     opts=fg.default_opts(precision=prec))

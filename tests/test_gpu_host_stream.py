@@ -31,7 +31,7 @@ def _same(dev, host):
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("chunk,max_pairs", [(2500, 0), (3000, 0), (4096, 0), (10 ** 6, 0), (2500, 300)])
 def test_host_stream_equals_device(fg, prec, chunk, max_pairs):
-    mesh, q = synth.config0()
+    mesh, q = synth.cube4_small()
     dev = torch.device("cuda:0")
     h = fg.fp_setup(torch.from_numpy(mesh.coords).to(dev), mesh.N, torch.from_numpy(mesh.sub).to(dev),
                     opts=fg.default_opts(precision=prec))
@@ -48,7 +48,7 @@ def test_host_stream_equals_device(fg, prec, chunk, max_pairs):
 
 
 def test_host_stream_sessions_find_only_pageable(fg):
-    mesh, q = synth.config1(n_az=16, n_rad=2, n_ax=4, box_shape=(8, 4, 4), N=5)
+    mesh, q = synth.box_annulus(n_az=16, n_rad=2, n_ax=4, box_shape=(8, 4, 4), N=5)
     dev = torch.device("cuda:0")
     h = fg.fp_setup(torch.from_numpy(mesh.coords).to(dev), mesh.N, torch.from_numpy(mesh.sub).to(dev),
                     torch.from_numpy(mesh.dist).to(dev))

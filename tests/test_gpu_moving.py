@@ -78,14 +78,14 @@ def test_warm_find_moving_cylinder(fg, prec):
     nodes move with it, the box's stay.  Each step: update, then a warm find
     in place from the previous step's (e, r); parity with the oracle on the
     moved mesh and with a cold find on the same handle."""
-    mesh, q = synth.config1(n_az=16, n_rad=2, n_ax=4, box_shape=(8, 4, 4), N=5)
+    mesh, q = synth.box_annulus(n_az=16, n_rad=2, n_ax=4, box_shape=(8, 4, 4), N=5)
     h = _setup(fg, mesh.coords, mesh.N, mesh.sub, prec, mesh.dist)
     dev = torch.device("cuda:0")
     qs = torch.from_numpy(q.qsess).to(dev)
     ptsn = q.pts
     out = fg.fp_find(h, torch.from_numpy(ptsn).to(dev), qs)
     moving_pts = q.qsess == 1
-    center = synth.meshes.CYL1["center"]
+    center = synth.meshes.BOX_ANNULUS_CYL["center"]
     for k in range(1, 4):
         ang, sh = 4.0 * k, (0.01 * k, 0.005 * k, 0.0)
         ck = synth.rigid_motion(mesh.coords, mesh.sub, 1, ang, sh, center)
@@ -113,7 +113,7 @@ def test_warm_find_moving_cylinder(fg, prec):
 def test_warm_hints_do_not_change_results(fg, prec):
     """Wrong, out-of-range and non-finite hints only change where Newton
     starts: codes, subdomains and elements stay those of the cold find."""
-    mesh, q = synth.config0()
+    mesh, q = synth.cube4_small()
     h = _setup(fg, mesh.coords, mesh.N, mesh.sub, prec)
     pts = torch.from_numpy(np.concatenate([q.pts[:, :4000],
                                            synth.near_face_points(mesh.coords, mesh.N, 1000, seed=3)], 1)).cuda()
@@ -151,7 +151,7 @@ def test_interface_exchange_on_moving_annulus(fg):
     interface points in the buffers the graph reads."""
     from paper_1811_04891_gb300.schwarz import InterfaceExchange
     n_az, n_rad, n_ax, box = 16, 2, 4, (8, 4, 4)
-    mesh, q = synth.config1(n_az=n_az, n_rad=n_rad, n_ax=n_ax, box_shape=box, N=5)
+    mesh, q = synth.box_annulus(n_az=n_az, n_rad=n_rad, n_ax=n_ax, box_shape=box, N=5)
     nb = box[0] * box[1] * box[2]
     kind = np.zeros((mesh.E, 6), np.int8)
     for e in range(nb, mesh.E):
@@ -170,7 +170,7 @@ def test_interface_exchange_on_moving_annulus(fg):
         hs.append(h)
         xs.append(x)
     xg, xe = xs
-    center = synth.meshes.CYL1["center"]
+    center = synth.meshes.BOX_ANNULUS_CYL["center"]
     for k in range(4):
         if k:
             ck = torch.from_numpy(synth.rigid_motion(mesh.coords, mesh.sub, 1, 3.0 * k, (0.01 * k, 0.0, 0.0),

@@ -23,8 +23,8 @@ def _lib():
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_config0_full(prec):
-    mesh, q = synth.config0()
+def test_cube4_full(prec):
+    mesh, q = synth.cube4_small()
     g = gpu_find(mesh, q.pts, prec=prec, fields=q.fields)
     r = oracle_find(mesh, q.pts, fields=q.fields)
     assert (r["code"] == oracle.INSIDE).all()
@@ -32,8 +32,8 @@ def test_config0_full(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_config1_interface_points(prec):
-    mesh, q = synth.config1()
+def test_box_annulus_interface_points(prec):
+    mesh, q = synth.box_annulus()
     g = gpu_find(mesh, q.pts, q.qsess, prec=prec, fields=q.fields)
     r = oracle_find(mesh, q.pts, q.qsess, fields=q.fields)
     assert_parity(g, r, prec, fields=q.fields)
@@ -44,9 +44,9 @@ def test_config1_interface_points(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_config1_untagged_owner_rule(prec):
+def test_box_annulus_untagged_owner_rule(prec):
     """Untagged points in the box/cylinder overlap: owner = argmax delta^k."""
-    mesh, _ = synth.config1()
+    mesh, _ = synth.box_annulus()
     rng = np.random.default_rng(11)
     th = rng.uniform(0, 2 * np.pi, 4000)
     rho = rng.uniform(0.14, 0.36, 4000)
@@ -58,8 +58,8 @@ def test_config1_untagged_owner_rule(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_config2_reduced_with_near_face(prec):
-    mesh, q = synth.config2(ne=8, P_uniform=30011, P_face=5003)
+def test_deformed_cube_reduced_with_near_face(prec):
+    mesh, q = synth.deformed_cube(ne=8, P_uniform=30011, P_face=5003)
     g = gpu_find(mesh, q.pts, prec=prec, fields=q.fields)
     r = oracle_find(mesh, q.pts, fields=q.fields)
     assert_parity(g, r, prec, fields=q.fields)
@@ -166,7 +166,7 @@ def test_spiral_element_N15(prec):
 
 
 def test_invariance_hash_and_block():
-    mesh, q = synth.config2(ne=6, P_uniform=20000, P_face=2000)
+    mesh, q = synth.deformed_cube(ne=6, P_uniform=20000, P_face=2000)
     base = gpu_find(mesh, q.pts, prec=0)
     for kw in ({"hash_cells_per_elem": 0.2}, {"hash_cells_per_elem": 4.0}, {"points_per_block": 64},
                {"points_per_block": 256}):
@@ -216,19 +216,19 @@ def test_errors_are_reported():
                     torch.tensor([0, 70000], dtype=torch.int32, device=dev))
 
 
-@pytest.mark.parametrize("cfg", ["config0", "config1", "config2s", "N3", "N15"])
+@pytest.mark.parametrize("cfg", ["cube4_small", "box_annulus", "cube_small", "N3", "N15"])
 def test_eval_double_float_parity(cfg):
     """fp_eval_df (double-float on the FP32 pipes) against the oracle's FP64
     triple sums and the FP64 kernel, on located points."""
     import paper_1811_04891_gb300 as fg
-    if cfg == "config0":
-        mesh, q = synth.config0()
+    if cfg == "cube4_small":
+        mesh, q = synth.cube4_small()
         pts, fields = q.pts, q.fields
-    elif cfg == "config1":
-        mesh, q = synth.config1()
+    elif cfg == "box_annulus":
+        mesh, q = synth.box_annulus()
         pts, fields = q.pts, q.fields
-    elif cfg == "config2s":
-        mesh, q = synth.config2(ne=6, P_uniform=20000, P_face=3000)
+    elif cfg == "cube_small":
+        mesh, q = synth.deformed_cube(ne=6, P_uniform=20000, P_face=3000)
         pts, fields = q.pts, q.fields
     else:
         N = 3 if cfg == "N3" else 15

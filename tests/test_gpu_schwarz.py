@@ -53,7 +53,7 @@ def test_flux_correct_iface_equals_scattered(fg):
 
 def test_graph_replayed_subiterations_match_eager(fg):
     from paper_1811_04891_gb300.schwarz import InterfaceExchange
-    mesh, q = synth.config1()
+    mesh, q = synth.box_annulus()
     n_rad, n_az, n_ax = 4, 32, 8
     kind = np.zeros((mesh.E, 6), np.int8)
     for e in range(1024, mesh.E):
@@ -120,7 +120,7 @@ def test_posted_points_equal_eval_df(fg):
     """Posted points (cached basis values) evaluate posted fields exactly as
     fp_eval_df does at the same located points, including NaN for points
     not found; updating them in place tracks a new find."""
-    mesh, q = synth.config0()
+    mesh, q = synth.cube4_small()
     dev = torch.device("cuda:0")
     h = fg.fp_setup(torch.from_numpy(mesh.coords).to(dev), mesh.N, torch.from_numpy(mesh.sub).to(dev),
                     opts=fg.default_opts(precision=fg.PREC_MIXED))

@@ -19,14 +19,14 @@ def test_served_results_same_alone_and_in_mix():
         pytest.skip("no CUDA device")
     import paper_1811_04891_gb300 as fg
     from paper_1811_04891_gb300 import serve
-    mesh, iface = synth.config4_mesh(box_shape=(20, 10, 10), cyl_shape=(16, 3, 16))
+    mesh, iface = synth.box_two_annuli(box_shape=(20, 10, 10), cyl_shape=(16, 3, 16))
     rng = np.random.default_rng(0)
     fields = np.stack([synth.random_poly_field(mesh.coords, 3, rng)[0] for _ in range(4)])
     dev = torch.device("cuda:0")
     h = fg.fp_setup(torch.from_numpy(mesh.coords).to(dev), mesh.N, torch.from_numpy(mesh.sub).to(dev),
                     torch.from_numpy(mesh.dist).to(dev), opts=fg.default_opts(precision=fg.PREC_MIXED))
     fd = torch.from_numpy(fields).to(dev)
-    reqs = synth.config4_requests(iface, 40, seed=9, size_range=(10, 6000), rate_hz=2000.0)
+    reqs = synth.poisson_requests(iface, 40, seed=9, size_range=(10, 6000), rate_hz=2000.0)
 
     def make():
         return [serve.Request(rid=i, t_arrive=r["t_arrive"], pts=r["pts"], qsess=r["qsess"])

@@ -34,7 +34,7 @@ def test_static_find_matches_fp_find_on_two_calls(prec):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import paper_1811_04891_gb300 as fg
-    mesh, q = synth.config2(ne=6, P_uniform=12007, P_face=2003, with_fields=False)
+    mesh, q = synth.deformed_cube(ne=6, P_uniform=12007, P_face=2003, with_fields=False)
     dev = torch.device("cuda:0")
     h = fg.fp_setup(torch.from_numpy(mesh.coords).to(dev), mesh.N, torch.from_numpy(mesh.sub).to(dev),
                     opts=fg.default_opts(precision=prec))
