@@ -9,8 +9,9 @@ and quadrature exactness; the map against an independent Vandermonde
 evaluation; find against forward-mapped known (e, r) and affine closed forms;
 eval against exactly reproduced Q_N polynomials; ownership against tiny
 overlapping boxes with closed-form delta; the default distance field against
-closed forms on undeformed boxes.  The ownership rule on curved meshes with
-the default distance field is "parity unpinned" beyond those special cases.
+closed forms on undeformed boxes, annular cylinders (rotated too) and rings;
+ownership with that field on a curved box + annulus overlap against the exact
+boundary distances, away from ties.
 """
 from __future__ import annotations
 

@@ -568,6 +568,7 @@ def ring_mesh(n_az: int, n_rad: int, N: int, r_in: float, r_out: float, center=(
     n = N + 1
     rr = _axis_nodes(n_rad, r_in, r_out, xi)          # [n_rad][n]
     th = _axis_nodes(n_az, angle0, angle0 + 2 * np.pi, xi)
+    th[-1, -1] = angle0                                # wrap: last node is the first
     shp = (n_az, n_rad, n, n)                          # [ea][er][j][i]
     R = np.broadcast_to(rr[None, :, None, :], shp)
     T = np.broadcast_to(th[:, None, :, None], shp)

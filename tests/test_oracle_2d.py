@@ -241,3 +241,16 @@ def test_border_projection_on_skewed_quad():
     assert res["code"][0] == BORDER and res["elem"][0] == 0
     np.testing.assert_allclose(res["rst"][:, 0], [1.0, s0], atol=1e-9)
     np.testing.assert_allclose(np.sqrt(res["dist2"][0]), d, rtol=1e-6)
+
+
+@pytest.mark.parametrize("angle0", [0.0, 0.7])
+def test_default_distance_field_ring_closed_form(angle0):
+    """Curved edges: every node of a ring shares its angle with GLL nodes of
+    both circles and no point of a circle is nearer, so the distance to the
+    boundary-edge nodes is min(rho - r_in, r_out - rho); the periodic seam is
+    interior."""
+    N, r_in, r_out = 4, 0.2, 0.5
+    coords, rho = synth.meshes.ring_mesh(10, 3, N, r_in, r_out, center=(0.1, 0.3), angle0=angle0)
+    E = coords.shape[1]
+    D = oracle.dist_default(coords, N, np.zeros(E, np.int32))
+    np.testing.assert_allclose(D, np.minimum(rho - r_in, r_out - rho), atol=1e-13)

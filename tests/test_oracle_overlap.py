@@ -1,6 +1,7 @@
 """Pins for the oracle's multi-subdomain rules (Sec. 2.1, Fig. 4): session
 exclusion, owner = argmax_k delta^k(x*) with lower-id tie break, and the
-default nodal distance field against closed forms on undeformed boxes."""
+default nodal distance field against closed forms on undeformed boxes and
+curved annular cylinders, and ownership with that field on a curved overlap."""
 import numpy as np
 import pytest
 
@@ -69,3 +70,61 @@ def test_default_distance_field_two_subdomains_independent():
     D = oracle.dist_default(mesh.coords, N, mesh.sub)
     np.testing.assert_allclose(D[:2], synth.box_distance(a, (0, 0, 0), (1, 1, 1)), atol=1e-14)
     np.testing.assert_allclose(D[2:], synth.box_distance(b, (0.5, 0, 0), (1.5, 1, 1)), atol=1e-14)
+
+
+@pytest.mark.parametrize("rot", [(0.0, 0.0), (15.0, -20.0)])
+def test_default_distance_field_annulus_closed_form(rot):
+    """Curved boundaries: on an annular cylinder every node shares its (theta,
+    z) with GLL nodes of both cylindrical faces and its (rho, theta) with nodes
+    of both end faces, and no point of a face is nearer than those, so the
+    distance to the boundary-face nodes is exactly min(rho - r_in, r_out - rho,
+    z - z0, z1 - z).  The periodic seam in theta must not count as boundary."""
+    N, r_in, r_out, z0, z1 = 3, 0.2, 0.5, -0.25, 0.35
+    coords, rho, zl = synth.annulus_mesh(8, 2, 3, N, r_in, r_out, z0, z1, center=(0.3, -0.1, 0.2), rot=rot)
+    E = coords.shape[1]
+    D = oracle.dist_default(coords, N, np.zeros(E, np.int32))
+    ref = synth.annulus_distance(rho, zl, r_in, r_out, z0, z1)
+    np.testing.assert_allclose(D, ref, atol=1e-13)
+
+
+def test_default_distance_field_annulus_beside_box():
+    """Two subdomains, one curved: each node's distance is to its own
+    subdomain's boundary only (the cylinder inside the box changes neither)."""
+    N = 2
+    cb = synth.box_mesh((4, 2, 2), N, lo=(0.0, 0.0, 0.0), hi=(2.0, 1.0, 1.0))
+    cc, rho, zl = synth.annulus_mesh(8, 1, 2, N, 0.15, 0.35, 0.0, 1.0, center=(1.0, 0.5, 0.0))
+    mesh = synth.concat_meshes([cb, cc], N, [0, 1])
+    D = oracle.dist_default(mesh.coords, N, mesh.sub)
+    Eb = cb.shape[1]
+    np.testing.assert_allclose(D[:Eb], synth.box_distance(cb, (0, 0, 0), (2, 1, 1)), atol=1e-14)
+    np.testing.assert_allclose(D[Eb:], synth.annulus_distance(rho, zl, 0.15, 0.35, 0.0, 1.0), atol=1e-13)
+
+
+def test_owner_with_default_distance_on_curved_overlap():
+    """Ownership on a curved overlap with the default (computed) distance
+    field: for points in the annulus, which also lie in the box, the owner is
+    the subdomain whose exact boundary distance is larger (box: distance to
+    the six planes; annulus: min(rho - r_in, r_out - rho, z, 1 - z)) wherever
+    the two differ by more than the interpolation error of D near its kinks
+    (margin 0.01)."""
+    N = 5
+    cb = synth.box_mesh((8, 4, 4), N, lo=(0, 0, 0), hi=(2, 1, 1))
+    cc, _, _ = synth.annulus_mesh(16, 2, 4, N, 0.15, 0.35, 0.0, 1.0, center=(1.0, 0.5, 0.0))
+    mesh = synth.concat_meshes([cb, cc], N, [0, 1])
+    D = oracle.dist_default(mesh.coords, N, mesh.sub)
+    rng = np.random.default_rng(5)
+    P = 3000
+    r = np.sqrt(rng.uniform(0.15 ** 2, 0.35 ** 2, P))
+    th = rng.uniform(0, 2 * np.pi, P)
+    z = rng.uniform(0, 1, P)
+    pts = np.stack([1 + r * np.cos(th), 0.5 + r * np.sin(th), z])
+    d_box = np.minimum.reduce([pts[0], 2 - pts[0], pts[1], 1 - pts[1], pts[2], 1 - pts[2]])
+    d_cyl = np.minimum.reduce([r - 0.15, 0.35 - r, z, 1 - z])
+    res = oracle.find(mesh.coords, N, mesh.sub, pts, dist=D)
+    assert (res["code"] == INSIDE).all()
+    keep = np.abs(d_box - d_cyl) > 0.01
+    assert keep.sum() > 2000
+    np.testing.assert_array_equal(res["sub"][keep], np.where(d_cyl > d_box, 1, 0)[keep])
+    # a query tagged with the cylinder's session sees only the box
+    res_b = oracle.find(mesh.coords, N, mesh.sub, pts[:, :50], qsess=np.ones(50, np.int32), dist=D)
+    np.testing.assert_array_equal(res_b["sub"], 0)
