@@ -340,8 +340,9 @@ fp_status fp_find_warm(fp_handle *h, int64_t P, const double *pts, const int32_t
  * previous one out, so the copies overlap the search.  Two workspaces of
  * `chunk` points and `max_pairs` candidate pairs (<= 0: 4 * chunk) and two
  * sets of device buffers alternate; they are kept in the handle for later
- * calls (grown when a call asks for more) and freed with it.  The searches
- * never wait on the host; a chunk whose pairs overflowed its workspace has
+ * calls (grown when a call asks for more) and freed with it.  A call sizes
+ * its launches on the pairs per point of the previous call (any count is
+ * still solved completely).  The searches never wait on the host; a chunk whose pairs overflowed its workspace has
  * its RETRY points searched again with fp_find_eval before the call
  * returns, so no FP_CODE_RETRY comes back.
  *   pts [3][P], qsess [P] or NULL: host memory (pinned memory copies fastest)

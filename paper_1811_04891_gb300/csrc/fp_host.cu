@@ -742,6 +742,7 @@ struct fp_workspace {
     const fp_handle* owner = nullptr;
     int64_t max_points = 0, max_pairs = 0, last_P = 0;
     int persistent_blocks = 0;
+    int64_t grid_pairs = 0;     // without a persistent grid: pairs the launches cover (0: max_pairs)
     int32_t *cnt = nullptr, *off = nullptr, *scan_tmp = nullptr;
     int32_t *pair_elem = nullptr, *pair_pt = nullptr, *order = nullptr;
     int32_t *ecount = nullptr, *estart = nullptr;
@@ -805,6 +806,15 @@ void fpg::workspace_unpersist(fp_workspace* w)
     if (w) w->persistent_blocks = 0;
 }
 
+// the pairs one block per 128 covers in the next launches of a workspace
+// without a persistent grid (<= 0: the whole capacity).  The pair kernels loop
+// grid-stride over the device-side count, so a count above the hint is still
+// solved completely, with a second pass for the pairs beyond it.
+void fpg::workspace_grid_hint(fp_workspace* w, int64_t pairs)
+{
+    if (w) w->grid_pairs = pairs;
+}
+
 cudaError_t fpg::workspace_pair_count_async(fp_workspace* w, int32_t* host_dst, cudaStream_t s)
 {
     if (!w || w->last_P <= 0) return cudaErrorInvalidValue;
@@ -858,7 +868,9 @@ static fp_status find_ws_impl(fp_handle* h, fp_workspace* w, int64_t P, const do
     const int block = h->opts.points_per_block > 0 ? h->opts.points_per_block : 128;
     cudaError_t err = find_count(a, h->tab, fp, s);
     if (err == cudaSuccess) err = find_emit(a, s);
-    if (err == cudaSuccess) err = find_solve(a, w->max_pairs, h->tab, fp, block, s);
+    const int64_t grid_pairs = w->persistent_blocks == 0 && w->grid_pairs > 0 ? std::min(w->grid_pairs, w->max_pairs)
+                                                                              : w->max_pairs;
+    if (err == cudaSuccess) err = find_solve(a, grid_pairs, h->tab, fp, block, s);
     if (err != cudaSuccess) return cuda_fail(h, err, "fp_find_ws");
     w->last_P = P;
     return FP_OK;

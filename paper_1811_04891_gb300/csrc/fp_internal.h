@@ -114,6 +114,7 @@ namespace fpg {
 void host_stream_free(fp_host_stream* hs);
 // workspace launches over its whole pair capacity instead of a persistent grid
 void workspace_unpersist(fp_workspace* w);
+void workspace_grid_hint(fp_workspace* w, int64_t pairs);
 // copy the workspace's device pair count of its latest find to *host_dst on s
 cudaError_t workspace_pair_count_async(fp_workspace* w, int32_t* host_dst, cudaStream_t s);
 

@@ -10,10 +10,12 @@
 // between chunks, so the copies of one chunk never touch the buffers the
 // search of the other is using; events order the three streams.  Each chunk
 // runs the workspace find (+ fused eval): the pair count stays on the device
-// and no call waits on the host, while the launches cover the workspace's
-// whole pair capacity with one block per 128 pairs (blocks past the count
-// exit at once), which balances the Newton work like a launch sized on the
-// host.  The pair count of every chunk comes back with its results; a chunk
+// and no call waits on the host.  The launches give one block to 128 pairs,
+// which balances the Newton work like a launch sized on the host, over the
+// pairs the chunk is expected to have: the largest pairs per point of the
+// previous call's chunks, plus 1/8 and 4096 (the first call covers the whole
+// capacity).  The pair kernels loop grid-stride over the count on the device,
+// so a chunk with more pairs than expected is still solved completely.  The pair count of every chunk comes back with its results; a chunk
 // whose pairs overflowed its workspace has its RETRY points searched again
 // with fp_find_eval before the call returns.
 #include <string.h>
@@ -57,6 +59,7 @@ struct fp_host_stream {
     cudaStream_t cin = nullptr, cout = nullptr;
     int32_t* h_pairs = nullptr;   // pinned: device pair count of each chunk
     int64_t h_pairs_cap = 0;
+    double pairs_per_point = 0;   // largest of the previous call's chunks (0: none yet)
 };
 
 namespace fpg {
@@ -246,6 +249,8 @@ extern "C" fp_status fp_find_eval_host(fp_handle* h, int64_t P, const double* pt
         if (e == cudaSuccess) e = cudaEventRecord(S.in_done, hs->cin);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, S.in_done, 0);
         if (e != cudaSuccess) break;
+        fpg::workspace_grid_hint(S.ws, hs->pairs_per_point > 0
+                                           ? (int64_t)(1.125 * hs->pairs_per_point * (double)c) + 4096 : 0);
         st = eval ? fp_find_eval_ws(h, S.ws, c, S.pts, qsess ? S.qs : nullptr, F, fields, posted, S.code, S.sub,
                                     S.elem, S.rst, S.dist2, S.out, s)
                   : fp_find_ws(h, S.ws, c, S.pts, qsess ? S.qs : nullptr, S.code, S.sub, S.elem, S.rst, S.dist2, s);
@@ -278,6 +283,12 @@ extern "C" fp_status fp_find_eval_host(fp_handle* h, int64_t P, const double* pt
         h->err = std::string("fp_find_eval_host: ") + cudaGetErrorString(e);
         return FP_ERR_CUDA;
     }
+    double ppp = 0;
+    for (int64_t i = 0; i < nch; ++i) {
+        const int64_t c = std::min(chunk, P - i * chunk);
+        ppp = std::max(ppp, (double)hs->h_pairs[i] / (double)c);
+    }
+    hs->pairs_per_point = ppp;
     for (int64_t i = 0; i < nch; ++i) {
         if (hs->h_pairs[i] <= max_pairs) continue;               // every pair of the chunk fitted
         const int64_t i0 = i * chunk, c = std::min(chunk, P - i0);
