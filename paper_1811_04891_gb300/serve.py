@@ -50,6 +50,60 @@ class Request:
         return int(self.pts.shape[1])
 
 
+def slot_bytes(slot_points: int, F: int) -> int:
+    """Device + pinned-host bytes one slot holds for `slot_points` points and
+    F fields: points, tags, the five outputs and values on both sides, plus
+    the workspace's per-point scan arrays and 4 pairs per point of pair
+    records (element, point, order, residual, r)."""
+    return slot_points * (24 + 4 + 24 + 4 * 3 + 8 + 8 * F) + 2 * slot_points * (4 * 3 + 8 + 24) + \
+        slot_points * 12
+
+
+def slots_for_budget(slots: int, slot_points: int, F: int, budget_bytes: float, resident_bytes: float) -> int:
+    """Memory-budget admission: how many slots may hold work at once -- the
+    budget left after the resident mesh and fields, divided by the bytes of
+    one slot, at least one and at most `slots`."""
+    avail = max(0.0, budget_bytes - resident_bytes)
+    return max(1, min(slots, int(avail // slot_bytes(slot_points, F))))
+
+
+def pack_pending(pending: "collections.deque", capacity: int, copy_in) -> tuple:
+    """Continuous batching: take the oldest pending work into one slot of
+    `capacity` points -- whole requests while they fit, then the next chunk of
+    the request at the head.  copy_in(req, lo, slot_lo, n) copies points
+    [lo, lo + n) of req to slot positions [slot_lo, slot_lo + n).  Requests
+    whose last point is taken leave `pending`.  Returns (pieces, points used),
+    pieces = [(request, req_lo, slot_lo, n)]."""
+    n_used = 0
+    pieces = []
+    while pending and n_used < capacity:
+        req = pending[0]
+        take = min(req.P - req.next_pt, capacity - n_used)
+        lo = req.next_pt
+        copy_in(req, lo, n_used, take)
+        pieces.append((req, lo, n_used, take))
+        req.next_pt += take
+        n_used += take
+        if req.next_pt == req.P:
+            pending.popleft()
+    return pieces, n_used
+
+
+def scatter_results(pieces, code, elem, rst, values, now: float, completed: list):
+    """Copy one slot's results (code, elem [n], rst [3][n], values [F][n],
+    host arrays) back to the requests its pieces came from; a request whose
+    every point is back is stamped `now` and appended to `completed`."""
+    for req, lo, so, take in pieces:
+        req.code[lo:lo + take] = code[so:so + take]
+        req.elem[lo:lo + take] = elem[so:so + take]
+        req.rst[:, lo:lo + take] = rst[:, so:so + take]
+        req.values[:, lo:lo + take] = values[:, so:so + take]
+        req.done_pts += take
+        if req.done_pts == req.P:
+            req.t_done = now
+            completed.append(req)
+
+
 @dataclass
 class _Slot:
     stream: torch.cuda.Stream
@@ -77,11 +131,8 @@ class Server:
         self.posted = posted                  # fg.Fields (double-float) or None for FP64 eval
         self.F = int(fields.shape[0])
         self.dev = device or fields.device
-        per_slot = slot_points * (24 + 4 + 24 + 4 * 3 + 8 + 8 * self.F) + 2 * slot_points * (4 * 3 + 8 + 24) + \
-            slot_points * 12
-        self.slot_bytes = per_slot
-        avail = max(0.0, budget_bytes - resident_bytes)
-        self.max_slots = max(1, min(slots, int(avail // per_slot)))
+        self.slot_bytes = slot_bytes(slot_points, self.F)
+        self.max_slots = slots_for_budget(slots, slot_points, self.F, budget_bytes, resident_bytes)
         self.slot_points = slot_points
         self.slots: List[_Slot] = []
         for _ in range(self.max_slots):
@@ -117,19 +168,10 @@ class Server:
 
     # -- device side ------------------------------------------------------------
     def _fill(self, slot: _Slot) -> int:
-        n_used = 0
-        slot.pieces = []
-        while self.pending and n_used < self.slot_points:
-            req = self.pending[0]
-            take = min(req.P - req.next_pt, self.slot_points - n_used)
-            lo = req.next_pt
-            slot.pts_h[:, n_used:n_used + take].numpy()[...] = req.pts[:, lo:lo + take]
-            slot.qs_h[n_used:n_used + take].numpy()[...] = req.qsess[lo:lo + take]
-            slot.pieces.append((req, lo, n_used, take))
-            req.next_pt += take
-            n_used += take
-            if req.next_pt == req.P:
-                self.pending.popleft()
+        def copy_in(req, lo, so, take):
+            slot.pts_h[:, so:so + take].numpy()[...] = req.pts[:, lo:lo + take]
+            slot.qs_h[so:so + take].numpy()[...] = req.qsess[lo:lo + take]
+        slot.pieces, n_used = pack_pending(self.pending, self.slot_points, copy_in)
         return n_used
 
     def _launch(self, slot: _Slot, n: int):
@@ -159,17 +201,8 @@ class Server:
         n = slot.n
         rst_h = slot.rst_h.view(-1)[:3 * n].view(3, n).numpy()
         val_h = slot.val_h.view(-1)[:self.F * n].view(self.F, n).numpy()
-        code_h = slot.code_h[:n].numpy()
-        elem_h = slot.elem_h[:n].numpy()
-        for req, lo, so, take in slot.pieces:
-            req.code[lo:lo + take] = code_h[so:so + take]
-            req.elem[lo:lo + take] = elem_h[so:so + take]
-            req.rst[:, lo:lo + take] = rst_h[:, so:so + take]
-            req.values[:, lo:lo + take] = val_h[:, so:so + take]
-            req.done_pts += take
-            if req.done_pts == req.P:
-                req.t_done = now
-                self.completed.append(req)
+        scatter_results(slot.pieces, slot.code_h[:n].numpy(), slot.elem_h[:n].numpy(), rst_h, val_h, now,
+                        self.completed)
         slot.pieces = []
         slot.busy = False
 

@@ -1,0 +1,102 @@
+"""CPU tests of the serving loop's host logic: memory-budget admission, the
+continuous-batching packer and the scatter of slot results back to their
+requests.  A fake device computes each point's results from the point itself
+(in the slot buffer), slots finish out of order, and every request must get
+back exactly the results of its own points, once."""
+import collections
+
+import numpy as np
+import pytest
+
+from paper_1811_04891_gb300 import serve
+
+
+def test_slots_for_budget():
+    P, F = 1 << 20, 5
+    b = serve.slot_bytes(P, F)
+    assert b == P * (24 + 4 + 24 + 12 + 8 + 8 * F) + 2 * P * (12 + 8 + 24) + 12 * P
+    assert serve.slots_for_budget(4, P, F, 10 * b, 0) == 4                 # capped by the slots asked for
+    assert serve.slots_for_budget(8, P, F, 3.5 * b + 1e9, 1e9) == 3        # what the budget leaves
+    assert serve.slots_for_budget(4, P, F, 1e9, 2e9) == 1                  # never fewer than one
+    assert serve.slots_for_budget(4, P, F, 0.5 * b, 0) == 1
+
+
+def _request(rid, t, P, rng):
+    r = serve.Request(rid=rid, t_arrive=t, pts=rng.uniform(0, 1, (3, P)), qsess=rng.integers(-1, 3, P).astype(np.int32))
+    r.code = np.full(P, -7, np.int32)
+    r.elem = np.full(P, -7, np.int32)
+    r.rst = np.full((3, P), np.nan)
+    r.values = np.full((2, P), np.nan)
+    return r
+
+
+def _device(pts, qs):
+    """Stand-in for find + eval: results that depend on each point only."""
+    code = (np.floor(pts[0] * 3).astype(np.int32) + qs) % 3
+    elem = np.floor(pts[1] * 1000).astype(np.int32) + 7 * qs
+    rst = 2 * pts - 1
+    values = np.stack([pts.sum(0), pts[2] * qs])
+    return code, elem, rst, values
+
+
+@pytest.mark.parametrize("seed,capacity,nslots", [(0, 1000, 3), (1, 64, 1), (2, 4096, 4), (3, 1, 2)])
+def test_pack_and_scatter_return_each_point_its_own_results(seed, capacity, nslots):
+    rng = np.random.default_rng(seed)
+    sizes = list(rng.integers(1, 3 * capacity + 2, 40)) + [1, capacity, capacity + 1, 5 * capacity]
+    reqs = [_request(i, float(i), int(P), rng) for i, P in enumerate(sizes)]
+    pending = collections.deque()
+    completed = []
+    slots = [{"busy": False, "pts": np.zeros((3, capacity)), "qs": np.zeros(capacity, np.int32)}
+             for _ in range(nslots)]
+    first_packed = {}
+    arrivals = list(reqs)
+    tick = 0
+    while arrivals or pending or any(s["busy"] for s in slots):
+        tick += 1
+        for _ in range(int(rng.integers(0, 4))):            # requests arrive while slots are busy
+            if arrivals:
+                pending.append(arrivals.pop(0))
+        for s in slots:                                      # slots finish in random order
+            if s["busy"] and rng.random() < 0.5:
+                n = s["n"]
+                code, elem, rst, values = _device(s["pts"][:, :n], s["qs"][:n])
+                serve.scatter_results(s["pieces"], code, elem, rst, values, float(tick), completed)
+                s["busy"] = False
+        for s in slots:
+            if not s["busy"] and pending:
+                def copy_in(req, lo, so, take, s=s):
+                    s["pts"][:, so:so + take] = req.pts[:, lo:lo + take]
+                    s["qs"][so:so + take] = req.qsess[lo:lo + take]
+                pieces, n = serve.pack_pending(pending, capacity, copy_in)
+                assert 0 < n <= capacity and sum(p[3] for p in pieces) == n
+                slot_los = [p[2] for p in pieces]
+                assert slot_los == sorted(slot_los) and slot_los[0] == 0
+                for req, lo, so, take in pieces:
+                    first_packed.setdefault(req.rid, tick * 1000 + len(first_packed))
+                s.update(busy=True, pieces=pieces, n=n)
+        assert tick < 100000
+    # every request completed exactly once, with its own points' results
+    assert sorted(r.rid for r in completed) == list(range(len(reqs)))
+    for r in reqs:
+        assert r.done_pts == r.P and r.next_pt == r.P and r.t_done is not None
+        code, elem, rst, values = _device(r.pts, r.qsess)
+        np.testing.assert_array_equal(r.code, code)
+        np.testing.assert_array_equal(r.elem, elem)
+        np.testing.assert_array_equal(r.rst, rst)
+        np.testing.assert_array_equal(r.values, values)
+    # first-come first-served: a request starts no later than the ones after it
+    order = [first_packed[r.rid] for r in reqs]
+    assert order == sorted(order)
+
+
+def test_large_request_spans_slots_in_order():
+    rng = np.random.default_rng(5)
+    big = _request(0, 0.0, 2500, rng)
+    small = _request(1, 0.0, 10, rng)
+    pending = collections.deque([big, small])
+    got = []
+    for _ in range(3):
+        pieces, n = serve.pack_pending(pending, 1000, lambda *a: None)
+        got.append([(p[0].rid, p[1], p[2], p[3]) for p in pieces])
+    assert got == [[(0, 0, 0, 1000)], [(0, 1000, 0, 1000)], [(0, 2000, 0, 500), (1, 0, 500, 10)]]
+    assert not pending
