@@ -58,7 +58,11 @@ SEED, ITER, RESID, RESID_DF, BASIS64, EVAL1 = 4.1e3, 8.4e3, 3.5e3, 19.3e3, 0.3e3
 K_ORACLE = 3.43
 # DRAM bytes (read + written) per (point, candidate element) pair of the Newton
 # stage, measured with ncu on the 2.02M-point case of this workload (2.05M
-# pairs) and scaled by the pairs of a launch.
+# pairs over the same 32,768 elements) and scaled by the pairs of a launch.
+# The point gathers and scattered result writes grow with the pairs; the
+# element data (24 kB per element) does not, so at the full size, with five
+# times the pairs per element, the scaled figure is an upper bound (by up to
+# ~310 B per pair).
 TRAFFIC_PER_PAIR = {"mixed": 1422.0, "fp64": 740.0}
 WORK = {"fp64": {"f64": SEED + K_ORACLE * ITER, "f32": 0.0},
         "mixed": {"f64": RESID + BASIS64, "f32": SEED + K_ORACLE * ITER + 2 * RESID_DF}}
@@ -679,6 +683,8 @@ def main():
                 "kernel": ("k_newton_mixed<8> + k_newton64_full<8>" if form == "mixed" else "k_newton<8>"),
                 "units_per_launch": P, "work_unit": "located point (true element only)", "unit_work": w,
                 "pairs_per_launch": pairs,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per pair at 2.02e6 points, "
+                                  "x pairs per launch (an upper bound at full size)",
                 "peak_source": "of nominal: GB300 FP64 1.25 TFLOP/s; FP32 152 SMs x 128 lanes x 2 x 2.07 GHz"}
 
     roof = roofline(head)
