@@ -49,6 +49,17 @@ MUTATIONS = [
      "double g = area > 0.0 ? fl / area : 0.0;", 0),
     ("2D map: i and j node indices swapped", "double c = el->X[a][i + n * j];", "double c = el->X[a][j + n * i];", 0),
     ("2D eval: node index transposed", "v += f[i + n * j] * h[0][i] * h[1][j];", "v += f[j + n * i] * h[0][i] * h[1][j];", 0),
+    ("session discriminator ignored", "if (tag >= 0 && sub[e] == tag) continue;", "if (0) continue;", 0),
+    ("3D default distance: other subdomains' boundaries counted", "if (bs[b] != sub[e]) continue;",
+     "if (0) continue;", 1),
+    ("2D default distance: other subdomains' boundaries counted", "if (bs[b] != sub[e]) continue;",
+     "if (0) continue;", 2),
+    ("2D Jacobian: columns r and s swapped", "if (J) { J[3 * a + 0] = vr; J[3 * a + 1] = vs; }",
+     "if (J) { J[3 * a + 0] = vs; J[3 * a + 1] = vr; }", 0),
+    ("face quadrature: one GLL weight dropped", "dA[m] = wg[a] * wg[b] * len;", "dA[m] = wg[a] * len;", 0),
+    ("border: distance returned unsquared", "dist2[p] = b_d * b_d;", "dist2[p] = b_d;", 0),
+    ("prefilter: node box without its margin", "double g = 0.25 * (hi[a] - lo[a]) + prm->tol_border * he[e];",
+     "double g = 0.0;", 0),
 ]
 
 
@@ -78,4 +89,5 @@ def test_pins_catch_planted_mistake(tmp_path, name, old, new, which):
     env = dict(os.environ, FINDPTS_ORACLE_LIB=str(so))
     r = subprocess.run([sys.executable, "-m", "pytest", *PINS, "-x", "-q", "-p", "no:cacheprovider",
                         "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert r.returncode != 0, f"no pin caught the planted mistake: {name}\n{r.stdout[-2000:]}"
+    # exit code 1: tests ran and one failed (not a crash, a collection error or a usage error)
+    assert r.returncode == 1, f"no pin caught the planted mistake: {name} (exit {r.returncode})\n{r.stdout[-2000:]}"
