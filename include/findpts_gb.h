@@ -190,7 +190,12 @@ fp_status fp_find_static(fp_handle *h, int64_t P, const double *pts, const int32
  * of fp_find_ws for up to max_points points and max_pairs candidate pairs on
  * one handle's mesh; several workspaces let several finds run at once on
  * different streams (each workspace must be used by one call at a time).
- * fp_workspace_create allocates (max_pairs <= 0 picks 2 * max_points). */
+ * fp_workspace_create allocates (max_pairs <= 0 picks 2 * max_points) and
+ * writes the new workspace to *ws (NULL on failure); it serves hexahedral
+ * handles only.  Errors: FP_ERR_NOT_SETUP, FP_ERR_INVALID_ARG (ws NULL,
+ * max_points outside [1, 2^31), max_pairs >= 2^31, a 2D handle), FP_ERR_OOM,
+ * FP_ERR_CUDA.  fp_workspace_free synchronises the device, then frees (NULL
+ * is a no-op); the handle must outlive its workspaces. */
 typedef struct fp_workspace fp_workspace;
 fp_status fp_workspace_create(const fp_handle *h, int64_t max_points, int64_t max_pairs,
                               fp_workspace **ws);
