@@ -123,7 +123,9 @@ fp_status fp_setup_2d(fp_handle **h, const double *coords, int64_t E, int N,
 
 /* fp_reserve -- pre-size the find workspace for up to P points, so that
  * later fp_find calls with at most P points allocate nothing (required before
- * capturing fp_find into a CUDA graph).  Synchronises the device. */
+ * capturing fp_find into a CUDA graph).  Synchronises the device.
+ * Errors: FP_ERR_NOT_SETUP, FP_ERR_INVALID_ARG (P < 0), FP_ERR_OOM,
+ * FP_ERR_CUDA. */
 fp_status fp_reserve(fp_handle *h, int64_t P);
 
 /* fp_find -- locate P points (Sec. 2.1, findpts).
@@ -214,7 +216,8 @@ fp_status fp_find_ws(fp_handle *h, fp_workspace *ws, int64_t P, const double *pt
                      double *rst, double *dist2, void *stream);
 
 /* Number of candidate pairs of the workspace's most recent fp_find_ws
- * (synchronises the device; for diagnostics). */
+ * (synchronises the device; for diagnostics).  Errors: FP_ERR_INVALID_ARG
+ * (ws NULL), FP_ERR_CUDA. */
 fp_status fp_workspace_last_pairs(fp_workspace *ws, int64_t *npairs);
 
 /* Batches: many independent meshes (instances) of different E and N located
@@ -242,7 +245,17 @@ fp_status fp_workspace_last_pairs(fp_workspace *ws, int64_t *npairs);
  * the given data, keeps the fastest and returns its time (synchronises).
  * fp_batch_schedule reads (and, for positive inputs, sets) the schedule.
  * fp_batch_capture records one run on the given buffers into a CUDA graph;
- * fp_batch_launch replays it on `stream` (same buffers, new contents). */
+ * fp_batch_launch replays it on `stream` (same buffers, new contents).
+ * The batch copies what it needs at creation and owns it; fp_batch_free
+ * releases it (NULL is a no-op); fp_batch_last_error gives the text of the
+ * batch's last failure.  Errors: fp_batch_create FP_ERR_INVALID_ARG (b NULL,
+ * ninst < 1, NULL arrays, F < 0 or fields missing, a NULL, unset or 2D
+ * handle, npts < 0, handles whose precision, tolerances or max_newton
+ * differ, 2^31 points or more in total), FP_ERR_OOM, FP_ERR_CUDA;
+ * fp_batch_run / _tune / _capture FP_ERR_INVALID_ARG (NULL batch or
+ * pointer), FP_ERR_CUDA; fp_batch_schedule FP_ERR_INVALID_ARG (NULL batch,
+ * a block size that is not a multiple of 32 up to 256); fp_batch_launch
+ * FP_ERR_NOT_SETUP (nothing captured), FP_ERR_CUDA. */
 typedef struct fp_batch fp_batch;
 fp_status fp_batch_create(fp_batch **b, int ninst, fp_handle *const *handles, const int64_t *npts,
                           int F, const double *const *fields, double pairs_per_point);
@@ -375,7 +388,12 @@ fp_status fp_find_eval_host(fp_handle *h, int64_t P, const double *pts, const in
  *   captured fp_eval_points stays valid.  Enqueued on `stream`.
  * fp_eval_points: out [F][P] = the posted double-float fields interpolated at
  *   the posted points, bit-identical to fp_eval_df at the same (e, r); NaN for
- *   points not found.  Allocates nothing, never waits. */
+ *   points not found.  Allocates nothing, never waits.
+ * The points belong to the handle they were made for and must be freed
+ * before it.  Errors: fp_points_create FP_ERR_NOT_SETUP, FP_ERR_INVALID_ARG
+ * (out NULL, P outside [0, 2^31), a 2D handle), FP_ERR_OOM, FP_ERR_CUDA;
+ * fp_points_set and fp_eval_points FP_ERR_NOT_SETUP, FP_ERR_INVALID_ARG (NULL
+ * pointers, points or fields made for another handle), FP_ERR_CUDA. */
 typedef struct fp_points fp_points;
 fp_status fp_points_create(const fp_handle *h, int64_t P, fp_points **out);
 void fp_points_free(fp_points *q);
@@ -405,7 +423,13 @@ fp_status fp_eval_points(fp_handle *h, const fp_fields *f, const fp_points *q, d
  * through the listed faces vanishes.  gamma and flux (before correction) are
  * written to device scalars if non-NULL.  Deterministic fixed-order sums;
  * allocates nothing; enqueued on `stream`.  Edge and corner nodes appear once
- * per face, each with its own face's normal. */
+ * per face, each with its own face's normal.
+ * The face set keeps a pointer to its handle (which must outlive it) and
+ * owns its device arrays; fp_bfaces_free releases them (NULL is a no-op).
+ * Errors: fp_bfaces_create FP_ERR_NOT_SETUP, FP_ERR_INVALID_ARG (out or kind
+ * NULL, a 2D handle), FP_ERR_OOM, FP_ERR_CUDA; fp_bfaces_info,
+ * fp_bfaces_nodes and fp_flux_correct FP_ERR_INVALID_ARG (NULL face set, or
+ * u / u_out NULL), FP_ERR_CUDA. */
 typedef struct fp_bfaces fp_bfaces;
 fp_status fp_bfaces_create(const fp_handle *h, const int8_t *kind, fp_bfaces **out, void *stream);
 void fp_bfaces_free(fp_bfaces *b);
@@ -417,7 +441,9 @@ fp_status fp_flux_correct(const fp_bfaces *b, const double *u, double *u_out, do
 /* fp_bfaces_refresh: recompute positions, normals and weights of the listed
  * face nodes from the owner handle's current coordinates (after
  * fp_update_coords on a moving mesh); the face list, node kinds and the
- * interface numbering stay.  Allocates nothing; enqueued on `stream`. */
+ * interface numbering stay.  Allocates nothing; enqueued on `stream`.
+ * Errors: FP_ERR_INVALID_ARG (b NULL), FP_ERR_NOT_SETUP (its handle freed),
+ * FP_ERR_CUDA. */
 fp_status fp_bfaces_refresh(fp_bfaces *b, void *stream);
 /* fp_bfaces_sort_iface: renumber the interface nodes so that nodes with the
  * same donor element are consecutive.  elem [Mi] (device) holds each
@@ -428,7 +454,8 @@ fp_status fp_bfaces_refresh(fp_bfaces *b, void *stream);
  * evaluation at the reordered points reads each element's field rows from
  * cache for neighbouring threads.  Nodes of one element keep an unspecified
  * order among themselves (results do not depend on it).  Allocates and
- * synchronises `stream`. */
+ * synchronises `stream`.  Errors: FP_ERR_INVALID_ARG (b or elem NULL),
+ * FP_ERR_NOT_SETUP (its handle freed), FP_ERR_OOM, FP_ERR_CUDA. */
 fp_status fp_bfaces_sort_iface(fp_bfaces *b, const int32_t *elem, void *stream);
 
 /* Interface-data pipeline helpers.
@@ -445,7 +472,9 @@ fp_status fp_bfaces_sort_iface(fp_bfaces *b, const int32_t *elem, void *stream);
  * c = (1), (2,-1), (3,-3,1) for m = 1, 2, 3 (Sec. 2: lagged or extrapolated
  * boundary data, refined by kappa sub-iterations).  These calls allocate
  * nothing and never wait, so an eval + correction sub-iteration can be
- * captured in a CUDA graph and replayed kappa times. */
+ * captured in a CUDA graph and replayed kappa times.  Errors:
+ * FP_ERR_INVALID_ARG (NULL face set or arrays; for fp_extrapolate m outside
+ * 1..3, len < 0 or a NULL history pointer), FP_ERR_CUDA. */
 fp_status fp_bfaces_iface(const fp_bfaces *b, int64_t *n_iface, double *pts, void *stream);
 fp_status fp_flux_correct_iface(const fp_bfaces *b, const double *u_iface, const double *u_pres,
                                 double *u_out, double *gamma, double *flux, void *stream);
