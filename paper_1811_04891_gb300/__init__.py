@@ -763,3 +763,137 @@ def fp_debug_boxes(h: Handle):
     _check(lib().fp_debug_boxes(h.ptr, _ptr(aabb), _ptr(grid), _ptr(cs), _ptr(ce), _stream(None)), h.ptr)
     torch.cuda.synchronize()
     return aabb, grid, cs, ce
+
+
+# ---------------------------------------------------------------------------
+# The rest of the C ABI under its own names.  Objects the library creates come
+# back as the classes above (which free them when collected); the *_free calls
+# free them at once.  Argument marshalling only, as everywhere in this module.
+# ---------------------------------------------------------------------------
+def _release(obj, free_fn):
+    if obj is not None and getattr(obj, "ptr", None) is not None and obj.ptr.value:
+        free_fn(obj.ptr)
+        obj.ptr = ctypes.c_void_p(None)
+
+
+def fp_default_opts(**kw) -> fp_opts:
+    """fp_default_opts, with keyword overrides (see default_opts)."""
+    return default_opts(**kw)
+
+
+def fp_error_string(status: int) -> str:
+    return lib().fp_error_string(int(status)).decode()
+
+
+def fp_last_error(h: Optional[Handle] = None) -> str:
+    return lib().fp_last_error(None if h is None else h.ptr).decode()
+
+
+def fp_info(h: Handle) -> dict:
+    return h.info()
+
+
+def fp_free(h: Handle):
+    _release(h, lib().fp_free)
+
+
+def fp_workspace_create(h: Handle, max_points: int, max_pairs: int = 0) -> Workspace:
+    return Workspace(h, max_points, max_pairs)
+
+
+def fp_workspace_free(ws: Workspace):
+    _release(ws, lib().fp_workspace_free)
+
+
+def fp_workspace_last_pairs(ws: Workspace) -> int:
+    return ws.last_pairs()
+
+
+def fp_fields_create(h: Handle, fields: torch.Tensor, stream=None) -> Fields:
+    return Fields(h, fields, stream)
+
+
+def fp_fields_free(f: Fields):
+    _release(f, lib().fp_fields_free)
+
+
+def fp_points_create(h: Handle, P: int) -> Points:
+    return Points(h, P)
+
+
+def fp_points_free(q: Points):
+    _release(q, lib().fp_points_free)
+
+
+def fp_points_set(h: Handle, q: Points, code: torch.Tensor, elem: torch.Tensor, rst: torch.Tensor, stream=None):
+    if q.handle is not h:
+        raise ValueError("posted points belong to another handle")
+    q.set(code, elem, rst, stream)
+
+
+def fp_eval_points(h: Handle, f: Fields, q: Points, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    if q.handle is not h:
+        raise ValueError("posted points belong to another handle")
+    return q.eval(f, out, stream)
+
+
+def fp_batch_create(handles, npts, fields=None, pairs_per_point: float = 2.0) -> Batch:
+    return Batch(handles, npts, fields, pairs_per_point)
+
+
+def fp_batch_run(b: Batch, pts: torch.Tensor, outs, stream=None):
+    return b.run(pts, outs, stream)
+
+
+def fp_batch_tune(b: Batch, pts: torch.Tensor, outs, reps: int = 2, stream=None) -> float:
+    return b.tune(pts, outs, reps, stream)
+
+
+def fp_batch_schedule(b: Batch, block: int = 0, blocks_per_sm: int = 0):
+    return b.schedule(block, blocks_per_sm)
+
+
+def fp_batch_capture(b: Batch, pts: torch.Tensor, outs):
+    b.capture(pts, outs)
+
+
+def fp_batch_launch(b: Batch, stream=None):
+    b.launch(stream)
+
+
+def fp_batch_last_error(b: Batch) -> str:
+    return lib().fp_batch_last_error(b.ptr).decode()
+
+
+def fp_batch_free(b: Batch):
+    _release(b, lib().fp_batch_free)
+
+
+def fp_bfaces_create(h: Handle, kind: torch.Tensor, stream=None) -> BFaces:
+    return BFaces(h, kind, stream)
+
+
+def fp_bfaces_free(bf: BFaces):
+    _release(bf, lib().fp_bfaces_free)
+
+
+def fp_bfaces_info(bf: BFaces):
+    """(number of listed faces, number of face nodes M)."""
+    return bf.nfaces, bf.M
+
+
+def fp_bfaces_nodes(bf: BFaces, device=None):
+    return bf.nodes(device)
+
+
+def fp_bfaces_refresh(bf: BFaces, stream=None):
+    bf.refresh(stream)
+
+
+def fp_bfaces_sort_iface(bf: BFaces, elem: torch.Tensor, stream=None):
+    bf.sort_iface(elem, stream)
+
+
+def fp_bfaces_iface(bf: BFaces, device=None, out: Optional[torch.Tensor] = None):
+    """(Mi, interface node positions [3][Mi])."""
+    return bf.Mi, bf.iface_points(device, out)

@@ -45,3 +45,12 @@ def test_binding_rejects_cpu_tensors():
     import paper_1811_04891_gb300 as fg
     with pytest.raises(TypeError):
         fg.fp_setup(torch.zeros((3, 1, 8), dtype=torch.float64), 1)
+
+
+def test_binding_has_every_entry_point_by_name():
+    """The Python binding exposes each C entry point under its own name."""
+    import paper_1811_04891_gb300 as fg
+    missing = [n for n in declared_functions() if not callable(getattr(fg, n, None))]
+    assert not missing, missing
+    assert fg.fp_error_string(fg.FP_ERR_NOT_SETUP) == fg.lib().fp_error_string(fg.FP_ERR_NOT_SETUP).decode()
+    assert fg.fp_default_opts(precision=fg.PREC_MIXED).precision == fg.PREC_MIXED
