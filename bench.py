@@ -217,6 +217,20 @@ def oracle_rate(mesh, q, seconds: float, stride_seed: int = 0):
     return len(idx) / dt, len(idx), oracle.num_threads(), dt
 
 
+def oracle_rate_one_core(mesh, q, seconds: float):
+    """The oracle on one core (OpenMP threads set to 1, then restored) on a
+    strided sample sized to take about `seconds`; returns (points/s, sample
+    size, s)."""
+    import oracle
+    n0 = oracle.num_threads()
+    oracle.set_threads(1)
+    try:
+        rate, m, _, dt = oracle_rate(mesh, q, seconds, stride_seed=1)
+    finally:
+        oracle.set_threads(n0)
+    return rate, m, dt
+
+
 def run_reference(args):
     world, rank, local = dist_env()
     if rank != 0:
@@ -742,6 +756,8 @@ def main():
         rate, m, cores, dt = oracle_rate(mesh, q, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{m} of the {P} points (strided), find + eval, {dt:.1f} s"}
+        r1, m1, dt1 = oracle_rate_one_core(mesh, q, min(5.0, args.cpu_seconds))
+        cpu["one_core"] = {"value": r1, "unit": UNIT, "sample": f"{m1} strided points, {dt1:.1f} s"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": R["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -77,6 +77,8 @@ def lib():
         _lib.or_eval.argtypes = [ctypes.c_int, i64, i64, ip, ip, dp, ctypes.c_int, dp, dp]
         _lib.or_dist_default.argtypes = [ctypes.c_int, i64, dp, ip, dp]
         _lib.or_num_threads.restype = ctypes.c_int
+        _lib.or_set_threads.argtypes = [ctypes.c_int]
+        _lib.or_set_threads.restype = None
         i8p = ctypes.POINTER(ctypes.c_int8)
         _lib.or_bfaces.argtypes = [ctypes.c_int, i64, dp, i8p, dp, dp, dp, i8p]
         _lib.or_bfaces.restype = i64
@@ -107,6 +109,11 @@ def _i32(a):
 
 def num_threads() -> int:
     return int(lib().or_num_threads())
+
+
+def set_threads(n: int):
+    """Threads of the oracle's later OpenMP loops (n >= 1)."""
+    lib().or_set_threads(int(n))
 
 
 def gll(N: int):

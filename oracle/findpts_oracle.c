@@ -827,6 +827,18 @@ int or_num_threads(void)
 #endif
 }
 
+/* number of OpenMP threads the oracle's later loops use (n >= 1; for timing
+   it on one core beside all of them) */
+void or_set_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Mass-flux correction on a subdomain boundary (Sec. 2.2, Eqs. consv1,     */
 /* corr, consv2)                                                            */

@@ -62,3 +62,26 @@ def test_work_per_point_matches_its_parts():
     assert bench.P32_NOMINAL == pytest.approx(152 * 128 * 2 * 2.07e9)
     # the value-only FP64 residual: 3 coordinates x (n^3 + n^2 + n) FMA at n = 8, 2 flops each
     assert bench.RESID == pytest.approx(2 * 3 * (8 ** 3 + 8 ** 2 + 8), rel=0.01)
+
+
+def test_oracle_one_core_timing_restores_threads():
+    """The one-core oracle timing runs on one thread and gives the thread
+    count back; its results are the all-core oracle's (threads change only
+    the schedule)."""
+    import numpy as np
+
+    import oracle
+    import synth
+    mesh, q = synth.cube4_small()
+    n0 = oracle.num_threads()
+    rate, m, dt = bench.oracle_rate_one_core(mesh, q, 0.2)
+    assert rate > 0 and 1 <= m <= q.P and dt > 0
+    assert oracle.num_threads() == n0
+    oracle.set_threads(1)
+    try:
+        one = oracle.find(mesh.coords, mesh.N, mesh.sub, q.pts[:, :500])
+    finally:
+        oracle.set_threads(n0)
+    allc = oracle.find(mesh.coords, mesh.N, mesh.sub, q.pts[:, :500])
+    for k in ("code", "elem", "rst", "dist2"):
+        np.testing.assert_array_equal(one[k], allc[k])
