@@ -756,8 +756,11 @@ def main():
         rate, m, cores, dt = oracle_rate(mesh, q, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{m} of the {P} points (strided), find + eval, {dt:.1f} s"}
-        r1, m1, dt1 = oracle_rate_one_core(mesh, q, min(5.0, args.cpu_seconds))
-        cpu["one_core"] = {"value": r1, "unit": UNIT, "sample": f"{m1} strided points, {dt1:.1f} s"}
+        try:    # a side figure: its failure must not cost the measurement line
+            r1, m1, dt1 = oracle_rate_one_core(mesh, q, min(5.0, args.cpu_seconds))
+            cpu["one_core"] = {"value": r1, "unit": UNIT, "sample": f"{m1} strided points, {dt1:.1f} s"}
+        except Exception as ex:  # noqa: BLE001
+            cpu["one_core"] = {"error": str(ex)[:200]}
 
     if rank == 0:
         line = {"metric": METRIC, "value": R["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
