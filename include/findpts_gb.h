@@ -41,7 +41,8 @@ typedef enum {
     FP_ERR_INVALID_ARG = 1,   /* bad sizes, null required pointer, non-finite mesh  */
     FP_ERR_OOM = 2,           /* device allocation failed                            */
     FP_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed         */
-    FP_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up                  */
+    FP_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up (reserved: no
+                                 kernel of this library waits on another block)    */
     FP_ERR_NOT_SETUP = 5      /* null handle or handle without a mesh                */
 } fp_status;
 
