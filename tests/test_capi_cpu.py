@@ -54,3 +54,33 @@ def test_binding_has_every_entry_point_by_name():
     assert not missing, missing
     assert fg.fp_error_string(fg.FP_ERR_NOT_SETUP) == fg.lib().fp_error_string(fg.FP_ERR_NOT_SETUP).decode()
     assert fg.fp_default_opts(precision=fg.PREC_MIXED).precision == fg.PREC_MIXED
+
+
+def test_argument_checks_before_any_device_work():
+    """Bad arguments and missing handles are refused on the host, with the
+    status the header documents, before the library touches a device."""
+    import ctypes
+
+    import paper_1811_04891_gb300 as fg
+    L = fg.lib()
+    o = fg.default_opts()
+    h = ctypes.c_void_p()
+    out = ctypes.c_void_p()
+    INV, NOSET = fg.FP_ERR_INVALID_ARG, fg.FP_ERR_NOT_SETUP
+    assert L.fp_setup(ctypes.byref(h), None, 8, 0, None, None, ctypes.byref(o), None) == INV      # N < 1
+    assert L.fp_setup(ctypes.byref(h), None, 8, 16, None, None, ctypes.byref(o), None) == INV     # N > 15
+    assert L.fp_setup(ctypes.byref(h), None, 0, 3, None, None, ctypes.byref(o), None) == INV      # E < 1
+    assert L.fp_setup(ctypes.byref(h), None, 8, 3, None, None, ctypes.byref(o), None) == INV      # no coords
+    assert L.fp_setup(None, None, 8, 3, None, None, ctypes.byref(o), None) == INV
+    assert L.fp_last_error(None) == b"fp_setup: null handle pointer"
+    assert L.fp_workspace_create(None, 10, 0, ctypes.byref(out)) == NOSET
+    assert L.fp_points_create(None, 10, ctypes.byref(out)) == NOSET
+    assert L.fp_bfaces_create(None, None, ctypes.byref(out), None) == NOSET
+    assert L.fp_find_static(None, 1, None, None, None, None, None, None, None, None) == NOSET
+    assert L.fp_update_coords(None, None, None, 0, None) == NOSET
+    assert L.fp_find_eval_host(None, 1, None, None, 0, None, None, None, None, None, None, None, None, 0, 0,
+                               None) == NOSET
+    assert L.fp_extrapolate(0, 10, None, None, None) == INV                                       # m outside 1..3
+    assert L.fp_batch_create(ctypes.byref(out), 0, None, None, 0, None, 2.0) == INV               # no instances
+    assert L.fp_batch_schedule(None, None, None) == INV
+    assert L.fp_bfaces_info(None, None, None) == INV
