@@ -10,8 +10,9 @@ evaluation; find against forward-mapped known (e, r) and affine closed forms;
 eval against exactly reproduced Q_N polynomials; ownership against tiny
 overlapping boxes with closed-form delta; the default distance field against
 closed forms on undeformed boxes, annular cylinders (rotated too) and rings;
-ownership with that field on a curved box + annulus overlap against the exact
-boundary distances, away from ties.
+ownership with that field on curved overlaps (a cylinder or ring crossing a
+box face, both owners present) against the exact boundary distances, away
+from ties.
 """
 from __future__ import annotations
 

@@ -254,3 +254,30 @@ def test_default_distance_field_ring_closed_form(angle0):
     E = coords.shape[1]
     D = oracle.dist_default(coords, N, np.zeros(E, np.int32))
     np.testing.assert_allclose(D, np.minimum(rho - r_in, r_out - rho), atol=1e-13)
+
+
+def test_owner_with_default_distance_on_curved_overlap_2d():
+    """2D ownership with the default distance field: a ring that crosses the
+    top edge of a rectangle; for ring points inside the rectangle the owner
+    is the subdomain with the larger exact boundary distance (rectangle: the
+    four lines; ring: min(rho - r_in, r_out - rho)) wherever the two differ by
+    more than 0.01.  Both subdomains own some of them."""
+    N, C, R0, R1 = 5, (1.0, 0.8), 0.1, 0.3
+    cb = synth.quad_mesh((8, 4), N, lo=(0, 0), hi=(2, 1))
+    cr, _ = synth.meshes.ring_mesh(16, 2, N, R0, R1, center=C)
+    mesh = synth.concat_meshes([cb, cr], N, [0, 1])
+    D = oracle.dist_default(mesh.coords, N, mesh.sub)
+    rng = np.random.default_rng(6)
+    r = np.sqrt(rng.uniform(R0 ** 2, R1 ** 2, 4000))
+    th = rng.uniform(0, 2 * np.pi, 4000)
+    pts = np.stack([C[0] + r * np.cos(th), C[1] + r * np.sin(th)])
+    inside = pts[1] <= 1.0
+    pts, r = np.ascontiguousarray(pts[:, inside]), r[inside]
+    d_box = np.minimum.reduce([pts[0], 2 - pts[0], pts[1], 1 - pts[1]])
+    d_ring = np.minimum(r - R0, R1 - r)
+    res = oracle.find(mesh.coords, N, mesh.sub, pts, dist=D)
+    assert (res["code"] == INSIDE).all()
+    keep = np.abs(d_box - d_ring) > 0.01
+    want = np.where(d_ring > d_box, 1, 0)
+    np.testing.assert_array_equal(res["sub"][keep], want[keep])
+    assert 0.05 < want[keep].mean() < 0.95
