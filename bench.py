@@ -38,34 +38,47 @@ if ROOT not in sys.path:
 
 METRIC = "located+interpolated points/s (mixed vs FP64 form, N=7); serving p50/p99 ms"
 UNIT = "points/s"
-# Peaks for the ALU-bound Newton kernel, from the nominal GB300 figures: FP64
-# 1.25 TFLOP/s; FP32 = 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s.
-P64_NOMINAL = 1.25e12
-P32_NOMINAL = 152 * 128 * 2 * 2.07e9
-# Algorithmic work per located point of the Newton stage at N=7 (n = 8),
-# counting the true element only: the nearest-node seed (4.1 kflop), the K
-# Newton iterations with Jacobian (8.4 kflop each) that the oracle needs from
-# that seed, a value-only residual 3.5 kflop (3 coordinates x (n^3 + n^2 + n)
-# FMA), a compensated (double-float) FP32 residual 19.3 k FP32 operations
-# (about 11 per term), the FP64 basis values of three residuals 0.3 kflop.
+# Algorithmic work per located point at N=7 (n = 8), counting the true
+# element only: the nearest-node seed (512 nodes x 8 flops = 4.1 kflop), the
+# K Newton iterations with Jacobian (6n^3 + 9n^2 + 12n FMA + ~6n^2 basis, 8.4
+# kflop each) that the oracle needs from that seed, the final step (a
+# value-only residual 3 (n^3 + n^2 + n) FMA + basis values = 3.8 kflop), and
+# one field evaluation (n^3 + n^2 + n FMA = 1.17 kflop) per field.
 # K = 3.43: the mean iteration count of the oracle's Newton on the true
 # element, measured on a 22,000-point sample of this workload (20,000 uniform
 # + 2,000 near-face points).
-#   FP64 form:  seed + K iterations, all FP64.
-#   mixed form: FP32 seed + K FP32 iterations + 2 compensated FP32 residuals;
-#               FP64: one residual + basis values (the final FP64 Newton step).
-SEED, ITER, RESID, RESID_DF, BASIS64, EVAL1 = 4.1e3, 8.4e3, 3.5e3, 19.3e3, 0.3e3, 1.17e3
+SEED, ITER, FINAL, EVAL1 = 4.1e3, 8.4e3, 3.8e3, 1.17e3
 K_ORACLE = 3.43
+# Where each part of that work runs, and at which measured peak its
+# roofline time is taken:
+#   FP64 form:  seed + K iterations, all on the FP64 pipe              -> P64
+#   mixed form: seed + K iterations in FP32                            -> P32
+#               the final step at FP64 accuracy: on whichever of the
+#               FP64 pipe and double-float arithmetic on the FP32
+#               pipes this GPU runs faster                             -> max(P64, Pdf)
+#   eval:       FP64 form on the FP64 pipe; mixed form at FP64
+#               accuracy                                               -> P64 / max(P64, Pdf)
+# The refinement steps the mixed form adds between its FP32 iterations and
+# its final step are the implementation's precision technique, not the
+# method's work, and are not counted.
+WORK = {"fp64": {"f64": SEED + K_ORACLE * ITER, "f32": 0.0, "f64acc": 0.0},
+        "mixed": {"f64": 0.0, "f32": SEED + K_ORACLE * ITER, "f64acc": FINAL}}
 # DRAM bytes (read + written) per (point, candidate element) pair of the Newton
 # stage, measured with ncu on the 2.02M-point case of this workload (2.05M
 # pairs over the same 32,768 elements) and scaled by the pairs of a launch.
-# The point gathers and scattered result writes grow with the pairs; the
-# element data (24 kB per element) does not, so at the full size, with five
-# times the pairs per element, the scaled figure is an upper bound (by up to
-# ~310 B per pair).
+# None where the kernel changed after the capture.
 TRAFFIC_PER_PAIR = {"mixed": 1422.0, "fp64": 740.0}
-WORK = {"fp64": {"f64": SEED + K_ORACLE * ITER, "f32": 0.0},
-        "mixed": {"f64": RESID + BASIS64, "f32": SEED + K_ORACLE * ITER + 2 * RESID_DF}}
+HBM_FALLBACK_GBS = 6800.0
+
+
+def measured_hbm_gbs():
+    """Measured copy bandwidth (GB/s) of the GB300s, else the
+    fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except Exception:  # noqa: BLE001
+        return HBM_FALLBACK_GBS, "fallback"
 
 
 def parse():
@@ -86,6 +99,7 @@ def parse():
     ap.add_argument("--no-interface", action="store_true")
     ap.add_argument("--no-moving", action="store_true")
     ap.add_argument("--no-planar", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--served-requests", type=int, default=200)
     ap.add_argument("--served-load", type=float, default=0.7)
     ap.add_argument("--served-scale", type=float, default=1.0,
@@ -192,6 +206,96 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# measured arithmetic peaks (the roofline's denominators)
+# ---------------------------------------------------------------------------
+def measure_peaks(fg, dev, uuid, target_ms: float = 60.0, blocks_per_sm: int = 4):
+    """FP64, FP32 and double-float multiply-add rates of this GPU from the
+    library's chain probes (fp_fma_probe: 8 independent fma chains per thread,
+    blocks_per_sm blocks of 256 threads on every SM), each timed with CUDA
+    events on the launching stream, best of three launches of ~target_ms,
+    with the SM clock sampled meanwhile.  Returns TFLOP/s."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    sink = torch.empty(fg.fp_probe_threads(blocks_per_sm), dtype=torch.float64, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def once(kind, iters):
+        ev0.record(stream)
+        fl = fg.fp_fma_probe(kind, iters, sink, blocks_per_sm, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return fl, ev0.elapsed_time(ev1)
+
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.3)
+    rates, launches = {}, {}
+    for kind in ("f64", "f32", "df"):
+        iters = 256
+        fl, ms = once(kind, iters)
+        while ms < 5.0 and iters < (1 << 30):
+            iters *= 4
+            fl, ms = once(kind, iters)
+        iters = max(1, int(iters * target_ms / max(ms, 1e-3)))
+        best = 0.0
+        for _ in range(3):
+            fl, ms = once(kind, iters)
+            best = max(best, fl / (ms / 1e3))
+        rates[kind] = best / 1e12
+        launches[kind] = {"iters": iters, "flops": fl, "ms": ms}
+    clk = clocks.stop()
+    return {"p64": rates["f64"], "p32": rates["f32"], "pdf": rates["df"], "unit": "TFLOP/s",
+            "clocks": clk, "launches": launches,
+            "method": f"fp_fma_probe: {blocks_per_sm} x 256 threads per SM, 8 independent chains per thread, "
+                      "best of 3 launches (CUDA events); df = double-float multiply-add on the FP32 pipes "
+                      "(exact leading product + two-sum), counted as 2 FP64-class flops"}
+
+
+def roofline_form(form, P, F, kernel_ms, ms_per_step, peaks, hbm_gbs, pairs, coords_bytes, field_bytes):
+    """Roofline of one form from the algorithmic work (WORK, EVAL1) and the
+    measured peaks.  Dominant kernel: the Newton stage.  Whole step: find +
+    eval of F fields, with the step's compulsory HBM bytes beside it."""
+    p64, p32, pdf = peaks["p64"] * 1e12, peaks["p32"] * 1e12, peaks["pdf"] * 1e12
+    pacc = max(p64, pdf)                     # FP64-accuracy work of the mixed form
+    w = WORK[form]
+    kn = kernel_ms["newton"] / 1e3
+    if form == "fp64":
+        t_newton = P * w["f64"] / p64
+        achieved, peak, unit = P * w["f64"] / kn, p64, "TFLOP/s (FP64)"
+        t_eval = P * F * EVAL1 / p64
+    else:
+        t_newton = P * (w["f32"] / p32 + w["f64acc"] / pacc)
+        # FP32-equivalent flops: FP64-accuracy flops scaled by P32 / max(P64, Pdf)
+        achieved, peak = P * (w["f32"] + w["f64acc"] * p32 / pacc) / kn, p32
+        unit = "TFLOP/s (FP32-equivalent: FP32 flops + FP64-accuracy flops x P32/max(P64,Pdf))"
+        t_eval = P * F * EVAL1 / pacc
+    step_bytes = P * (24 + 44 + 8 * F) + coords_bytes + field_bytes
+    t_bytes = step_bytes / (hbm_gbs * 1e9)
+    t_step = max(t_newton + t_eval, t_bytes)
+    traffic = TRAFFIC_PER_PAIR.get(form)
+    fp64_view = P * (SEED + K_ORACLE * ITER + F * EVAL1) / p64
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": unit,
+            "frac": t_newton / kn, "traffic": None if traffic is None else traffic * pairs,
+            "kernel": "k_newton_mixed<8> + k_newton64_full<8>" if form == "mixed" else "k_newton<8>",
+            "kernel_ms": kernel_ms["newton"], "units_per_launch": P, "work_unit": "located point (true element only)",
+            "unit_work": w, "pairs_per_launch": pairs, "roofline_ms": 1e3 * t_newton,
+            "peaks_tflops": {"p64": peaks["p64"], "p32": peaks["p32"], "pdf": peaks["pdf"]},
+            "peak_source": "measured in this run (fp_fma_probe, CUDA events), SM clock "
+                           f"{peaks['clocks'].get('sm_mhz')} MHz",
+            "traffic_source": None if traffic is None else
+            "ncu dram__bytes_read.sum + dram__bytes_write.sum per pair at 2.02e6 points, x pairs per launch",
+            "step": {"frac": t_step / (ms_per_step / 1e3), "roofline_ms": 1e3 * t_step,
+                     "eval_roofline_ms": 1e3 * t_eval, "bytes": step_bytes, "bytes_ms": 1e3 * t_bytes,
+                     "note": f"find + eval of {F} fields: Newton roofline + eval roofline "
+                             f"({EVAL1:.0f} flop per field per point at "
+                             f"{'P64' if form == 'fp64' else 'max(P64, Pdf)'}), against the measured step"},
+            "fp64_roofline": {"ms": 1e3 * fp64_view, "frac": fp64_view / (ms_per_step / 1e3),
+                              "note": "the whole step's algorithmic work (seed + K iterations + evals) at the "
+                                      "FP64 peak, against the measured step: above 1 means faster than any "
+                                      "FP64-only implementation can be"}}
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle timing (baseline / reference arm)
 # ---------------------------------------------------------------------------
 def oracle_rate(mesh, q, seconds: float, stride_seed: int = 0):
@@ -240,20 +344,89 @@ def run_reference(args):
     per_step = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
     for s in range(args.warmup):
         oracle_rate(mesh, q, per_step, stride_seed=s)
-    samples = []
+    samples, times = [], []
     for s in range(args.steps):
         rate, m, cores, dt = oracle_rate(mesh, q, per_step, stride_seed=args.warmup + s)
         vals.append(rate)
         samples.append(m)
-    value = statistics.mean(vals)
+        times.append(dt)
+    value = sum(samples) / sum(times)
+    # one step of this arm is one bounded sample: its measured time, not the
+    # time the oracle would need for all of the workload's points
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * q.P / value,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "points_per_step": statistics.mean(samples),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(args, mesh, q),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"strided samples of {min(samples)}-{max(samples)} of the {q.P} points per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# configurations 0 and 1: small, latency-bound find + eval calls
+# ---------------------------------------------------------------------------
+def run_small_configs(args, fg, dev, peaks, with_oracle: bool):
+    """The plain single-subdomain cube (4^3 elements, 1e4 points, one field)
+    and the box + annulus overlap (2048 elements, its ~4e4 tagged interface
+    nodes, four fields, owner rule): one fp_find_eval call per step, both
+    forms, CUDA events over 50 calls after 5 warm-up calls.  The step
+    roofline uses the iteration count K of the 32^3 workload."""
+    import torch
+
+    import synth
+    out = {}
+    p64, p32 = peaks["p64"] * 1e12, peaks["p32"] * 1e12
+    pacc = max(p64, peaks["pdf"] * 1e12)
+    for name, (mesh, q) in (("cube4_small", synth.cube4_small()), ("box_annulus", synth.box_annulus())):
+        pts = torch.from_numpy(q.pts).to(dev)
+        qs = None if q.qsess is None else torch.from_numpy(q.qsess).to(dev)
+        fields = torch.from_numpy(q.fields).to(dev)
+        coords = torch.from_numpy(mesh.coords).to(dev)
+        sub = torch.from_numpy(mesh.sub).to(dev)
+        dist = None if mesh.dist is None else torch.from_numpy(mesh.dist).to(dev)
+        F, P = fields.shape[0], q.P
+        res = {"E": int(mesh.E), "N": int(mesh.N), "points": int(P), "fields": int(F)}
+        for form, prec in (("fp64", fg.PREC_FP64), ("mixed", fg.PREC_MIXED)):
+            h = fg.fp_setup(coords, mesh.N, sub, dist, opts=fg.default_opts(precision=prec))
+            fg.fp_reserve(h, P)
+            posted = fg.Fields(h, fields) if form == "mixed" else None
+            outs = fg._find_outs(P, dev)
+            vals = torch.empty((F, P), dtype=torch.float64, device=dev)
+            for _ in range(5):
+                fg.fp_find_eval(h, pts, qs, fields=fields, posted=posted, out=outs, values=vals)
+            torch.cuda.synchronize()
+            fg.fp_band_hits(h)
+            reps = 50
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fg.fp_find_eval(h, pts, qs, fields=fields, posted=posted, out=outs, values=vals)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            band = fg.fp_band_hits(h)
+            if form == "fp64":
+                t_roof = P * (SEED + K_ORACLE * ITER + F * EVAL1) / p64
+            else:
+                t_roof = P * ((SEED + K_ORACLE * ITER) / p32 + (FINAL + F * EVAL1) / pacc)
+            codes = torch.bincount(outs[0].long(), minlength=3).tolist()
+            res[form] = {"points_per_s": P / (ms / 1e3), "ms_per_call": ms, "step_roofline_frac": t_roof / (ms / 1e3),
+                         "band_hits_per_call": {k: v / reps for k, v in band.items()},
+                         "codes": {"inside": codes[0], "border": codes[1], "not_found": codes[2]}}
+            del posted, h
+        if with_oracle:
+            import oracle
+            t0 = time.perf_counter()
+            r = oracle.find(mesh.coords, mesh.N, mesh.sub, q.pts, qsess=q.qsess, dist=mesh.dist)
+            oracle.evaluate(mesh.N, r["code"], r["elem"], r["rst"], q.fields)
+            dt = time.perf_counter() - t0
+            res["oracle"] = {"points_per_s": P / dt, "cores": oracle.num_threads(), "sample": "all points"}
+        out[name] = res
+    out["note"] = ("latency-bound calls (few points): one fused find + eval call per step; step_roofline_frac = "
+                   "algorithmic work at the measured peaks over the call's time")
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -651,6 +824,7 @@ def main():
         fg.fp_profile(h, True)
         for k in fg.PROF_KINDS:
             fg.fp_profile_read(h, k)
+        fg.fp_band_hits(h)                      # reset: count the timed steps only
         clocks = ClockSampler(uuid)
         clocks.start()
         time.sleep(0.3)
@@ -667,6 +841,7 @@ def main():
         launches = fg.fp_launch_count() - l0
         ms = ev0.elapsed_time(ev1)
         clk = clocks.stop()
+        band = fg.fp_band_hits(h)
         paths = fg.fp_newton_paths(h) if form == "mixed" else None
         fg.fp_profile(h, False)
         kt = {k: fg.fp_profile_read(h, k) for k in fg.PROF_KINDS}
@@ -678,31 +853,19 @@ def main():
                          "kernel_ms": {k: (v[0] / max(v[1], 1)) for k, v in kt.items()},
                          "codes": {"inside": counts[0], "border": counts[1], "not_found": counts[2]},
                          "pairs_per_point": npairs / P, "newton_paths_per_step": None if paths is None else
-                         {k: v // max(1, args.steps) for k, v in paths.items()}}
+                         {k: v // max(1, args.steps) for k, v in paths.items()},
+                         "band_hits_per_step": {k: v / max(1, args.steps) for k, v in band.items()}}
 
     head = "mixed" if "mixed" in results else forms[0]
     R = results[head]
 
-    def roofline(form):
-        # the Newton stage (the dominant kernels), algorithmic flops per launch
-        kn = results[form]["kernel_ms"]["newton"] / 1e3
-        pairs = results[form]["pairs_per_point"] * P
-        w = WORK[form]
-        f64, f32 = w["f64"] * P, w["f32"] * P          # per located point, true element only
-        t_roof = f64 / P64_NOMINAL + f32 / P32_NOMINAL
-        achieved = (f64 + f32 * P64_NOMINAL / P32_NOMINAL) / kn
-        return {"bound": "alu", "achieved": achieved / 1e12, "peak": P64_NOMINAL / 1e12,
-                "unit": "TFLOP/s (FP64-equivalent: FP64 flops + FP32 flops x P64/P32)",
-                "frac": t_roof / kn, "traffic": TRAFFIC_PER_PAIR[form] * pairs,
-                "kernel": ("k_newton_mixed<8> + k_newton64_full<8>" if form == "mixed" else "k_newton<8>"),
-                "units_per_launch": P, "work_unit": "located point (true element only)", "unit_work": w,
-                "pairs_per_launch": pairs,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per pair at 2.02e6 points, "
-                                  "x pairs per launch (an upper bound at full size)",
-                "peak_source": "of nominal: GB300 FP64 1.25 TFLOP/s; FP32 152 SMs x 128 lanes x 2 x 2.07 GHz"}
-
-    roof = roofline(head)
-    roof_other = {f: roofline(f) for f in results if f != head}
+    peaks = measure_peaks(fg, dev, uuid)
+    hbm_gbs, hbm_src = measured_hbm_gbs()
+    coords_bytes, field_bytes = mesh.coords.nbytes, q.fields.nbytes
+    roofs = {f: roofline_form(f, P, F, results[f]["kernel_ms"], results[f]["ms_per_step"], peaks, hbm_gbs,
+                              results[f]["pairs_per_point"] * P, coords_bytes, field_bytes) for f in results}
+    roof = roofs[head]
+    roof_other = {f: v for f, v in roofs.items() if f != head}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -734,6 +897,9 @@ def main():
                "d2h_bytes_per_step": int(out_h.numel() * 8 + sum(t.numel() * t.element_size() for t in outs_h)),
                "api": "fp_find_eval_host (host buffers, chunks of 2^22 points, copies overlapped)"}
 
+    small = None
+    if rank == 0 and not args.no_small:
+        small = run_small_configs(args, fg, dev, peaks, with_oracle=not args.no_cpu_baseline)
     batched = None
     moving = None
     planar = None
@@ -770,9 +936,11 @@ def main():
                 "forms": {k: {"value": v["value"], "ms_per_step": v["ms_per_step"], "setup_ms": v["setup_ms"],
                               "kernel_ms": v["kernel_ms"], "codes": v["codes"],
                               "pairs_per_point": v["pairs_per_point"],
-                              "newton_paths_per_step": v["newton_paths_per_step"]} for k, v in results.items()},
-                "roofline": roof, "roofline_other_forms": roof_other, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": R["gpu_launches"],
-                "clocks": R["clocks"], "batched": batched, "serving": served, "interface": interface,
+                              "newton_paths_per_step": v["newton_paths_per_step"],
+                              "band_hits_per_step": v["band_hits_per_step"]} for k, v in results.items()},
+                "roofline": roof, "roofline_other_forms": roof_other, "peaks": peaks,
+                "hbm_peak": {"gbs": hbm_gbs, "source": hbm_src}, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": R["gpu_launches"],
+                "clocks": R["clocks"], "small_configs": small, "batched": batched, "serving": served, "interface": interface,
                 "moving": moving, "planar": planar}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -167,21 +167,27 @@ fp_status fp_eval(fp_handle *h, int64_t P, const int32_t *code, const int32_t *e
 
 /* fp_find_static -- fp_find for callers that cannot allocate device memory
  * at call time: a solver whose device memory is all handed to its own pool
- * allocator, code running under CUDA stream capture (where cudaMalloc and
- * cudaFree are not permitted), or a latency-bound loop that cannot afford
- * their implicit device synchronisation.  The paper has no counterpart; this
- * is a deployment variant of fp_find.
+ * allocator, or a latency-bound loop that cannot afford the implicit device
+ * synchronisation of cudaMalloc / cudaFree.  The paper has no counterpart;
+ * this is a deployment variant of fp_find.
  * Same arguments, outputs, rules and results as fp_find, for at most
  * FP_STATIC_MAX_POINTS points and FP_STATIC_MAX_PAIRS candidate pairs per
- * call (larger requests return FP_ERR_INVALID_ARG before any device work).
+ * call.  A request over the point limit returns FP_ERR_INVALID_ARG before any
+ * device work; the pair count is known only after the screen has counted the
+ * candidates, so a request over the pair limit returns FP_ERR_INVALID_ARG
+ * after that counting pass, with the outputs unwritten.
  * All per-call scratch lives in one file-scope device array of about 2.8 MB
  * that every GPU loading the library holds until exit; the call makes no
  * cudaMalloc / cudaFree or other allocating call.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress) and
- * should come before any stream capture.  All calls share the array and it
- * keeps the last call's contents (no part of it needs to start at zero);
- * calls that overlap on the GPU race on it and must be serialised.  Like
- * fp_find it waits for `stream` once, to read the number of pairs.
+ * should come before any stream capture.  The handle's device must be the
+ * current device (FP_ERR_INVALID_ARG otherwise).  All calls share the array
+ * and it keeps the last call's contents (no part of it needs to start at
+ * zero); calls that overlap on the GPU race on it and must be serialised.
+ * Like fp_find it waits for `stream` once, to read the number of pairs.
+ * Band hits and (while profiling) Newton path counts are counted as for
+ * fp_find; fp_profile does not time the kernels of static calls.
+ * fp_last_find_stats reports the pairs of the latest static call too.
  * Errors: FP_ERR_NOT_SETUP, FP_ERR_INVALID_ARG, FP_ERR_CUDA. */
 #define FP_STATIC_MAX_POINTS 16384
 #define FP_STATIC_MAX_PAIRS 65536
@@ -507,6 +513,39 @@ fp_status fp_profile_read(fp_handle *h, int kind, double *total_ms, int64_t *lau
  * confirmed by the single FP64 step, [3] sent to the full FP64 Newton.
  * Synchronises the device and resets the counters. */
 fp_status fp_newton_paths(fp_handle *h, int64_t *counts);
+
+/* Near-tie ("band") hits of the classification since the previous read
+ * (Sec. 2.1 decides INSIDE / BORDER by residual thresholds and the owner by
+ * comparing interpolated distances; where two of those numbers lie close
+ * together, ids could depend on rounding).  Counted on every find, workspace
+ * and static call of the handle, one count per point and kind:
+ *   counts[0]  a candidate's residual within a factor 2 of tol_accept*h_e
+ *   counts[1]  no INSIDE element, and a candidate's residual within a factor
+ *              2 of tol_border*h_e, or two BORDER candidates within
+ *              tie_band*L of the smallest residual
+ *   counts[2]  two subdomains' interpolated D^k within 2*tie_band*L of the
+ *              largest (the lower-id rule decided the owner, or nearly did)
+ * Synchronises the device and resets the counters.  Errors:
+ * FP_ERR_NOT_SETUP, FP_ERR_INVALID_ARG (counts NULL), FP_ERR_CUDA. */
+fp_status fp_band_hits(fp_handle *h, int64_t *counts);
+
+/* Arithmetic peak probes (measurement support; the paper has no
+ * counterpart).  The location stage is bound by arithmetic, so its roofline
+ * needs this GPU's multiply-add rates.  fp_fma_probe enqueues one launch of
+ * blocks_per_sm (1..8) blocks of 256 threads per SM; every thread runs 8
+ * independent chains of `iters` dependent steps:
+ *   kind 0  FP64 fma             kind 1  FP32 fma
+ *   kind 2  double-float multiply-add on the FP32 pipes (the operation the
+ *           mixed form uses for its FP64-accuracy residuals and eval)
+ * and stores one double per thread to `sink` (device, fp_probe_threads()
+ * doubles).  *flops (may be NULL) receives the launch's flop count (2 per
+ * step; a double-float step counts as one FP64-class multiply-add).  Time it
+ * with events on `stream`.  Errors: FP_ERR_INVALID_ARG (kind outside 0..2,
+ * iters < 1, blocks_per_sm outside 1..8, sink NULL), FP_ERR_CUDA.
+ * fp_probe_threads returns the threads of one launch (-1 on a CUDA error). */
+fp_status fp_fma_probe(int kind, int64_t iters, int blocks_per_sm, double *sink, double *flops,
+                       void *stream);
+int64_t fp_probe_threads(int blocks_per_sm);
 
 /* Number of kernels the library has launched in this process. */
 int64_t fp_launch_count(void);

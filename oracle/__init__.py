@@ -151,7 +151,7 @@ def map_points(coords, N: int, e: int, r):
 def find(coords, N: int, sub, pts, qsess=None, dist=None, params: Params | None = None):
     """Brute-force findpts on a hex (coords [3][E][n^3], pts [3][P]) or quad
     (coords [2][E][n^2], pts [2][P]) mesh.  Returns dict(code, sub, elem,
-    rst [d][P], dist2, bad_prefilter)."""
+    rst [d][P], dist2)."""
     prm = params or Params()
     coords = _f64(coords)
     dim = coords.shape[0]
@@ -175,8 +175,7 @@ def find(coords, N: int, sub, pts, qsess=None, dist=None, params: Params | None 
                         _i(code), _i(osub), _i(oel), _d(rst), _d(d2))
     if bad < 0:
         raise ValueError("oracle find: bad arguments")
-    return {"code": code, "sub": osub, "elem": oel, "rst": rst, "dist2": d2,
-            "bad_prefilter": int(bad)}
+    return {"code": code, "sub": osub, "elem": oel, "rst": rst, "dist2": d2}
 
 
 def evaluate(N: int, code, elem, rst, fields):

@@ -25,7 +25,8 @@
  *
  * Deliberately naive: the map and its Jacobian are full triple sums (no sum
  * factorisation), the Lagrange basis is the product formula, every element is
- * a candidate (a permissive, self-checked prefilter is optional).
+ * a candidate (a permissive prefilter is optional; a CPU test checks that it
+ * never changes a result against the same search without it).
  *
  * Readings where the paper is silent (stated once, used everywhere):
  *  - INSIDE:  ||x^e(r) - x*||_2 <= tol_accept * h_e, h_e = diagonal of the
@@ -467,8 +468,7 @@ typedef struct {
                               its extent per side, misses x*                  */
 } or_params;
 
-/* Returns the number of points for which the optional prefilter check found
-   a dropped answer (always 0 unless the prefilter is unsound for the mesh). */
+/* Returns 0, or -1 for bad arguments (dim not 2 or 3, N out of range). */
 int64_t or_find_d(int dim, int N, int64_t E, const double *coords, const int32_t *sub,
                   const double *dist, int64_t P, const double *pts, const int32_t *qsess,
                   const or_params *prm, int32_t *code, int32_t *osub, int32_t *oelem,
@@ -492,9 +492,7 @@ int64_t or_find_d(int dim, int N, int64_t E, const double *coords, const int32_t
     }
     double L = diag3(glo, ghi);
     double band = prm->tie_band * L;
-    int64_t bad_prefilter = 0;
-
-#pragma omp parallel for schedule(dynamic, 16) reduction(+ : bad_prefilter)
+#pragma omp parallel for schedule(dynamic, 16)
     for (int64_t p = 0; p < P; ++p) {
         double xs[3] = { pts[p], pts[P + p], dim == 3 ? pts[2 * P + p] : 0.0 };
         int32_t tag = qsess ? qsess[p] : -1;
@@ -597,18 +595,9 @@ int64_t or_find_d(int dim, int N, int64_t E, const double *coords, const int32_t
             dist2[p] = b_d * b_d;
         }
         free(bc_e); free(bc_d); free(bc_r);
-
-        /* self-check of the prefilter: the answer's element must pass it */
-        if (prm->prefilter && oelem[p] >= 0) {
-            int64_t e = oelem[p];
-            for (int a = 0; a < dim; ++a) {
-                double g = 0.25 * (ehi[3 * e + a] - elo[3 * e + a]);
-                if (xs[a] < elo[3 * e + a] - g || xs[a] > ehi[3 * e + a] + g) { ++bad_prefilter; break; }
-            }
-        }
     }
     free(elo); free(ehi); free(he);
-    return bad_prefilter;
+    return 0;
 }
 
 int64_t or_find(int N, int64_t E, const double *coords, const int32_t *sub,

@@ -155,6 +155,12 @@ def _load():
     L.fp_last_find_stats.restype = ci
     L.fp_newton_paths.argtypes = [vp, ctypes.POINTER(i64)]
     L.fp_newton_paths.restype = ci
+    L.fp_band_hits.argtypes = [vp, ctypes.POINTER(i64)]
+    L.fp_band_hits.restype = ci
+    L.fp_fma_probe.argtypes = [ci, i64, ci, vp, ctypes.POINTER(ctypes.c_double), vp]
+    L.fp_fma_probe.restype = ci
+    L.fp_probe_threads.argtypes = [ci]
+    L.fp_probe_threads.restype = i64
     _lib = L
     return L
 
@@ -389,6 +395,7 @@ class Batch:
 
 
 STATIC_MAX_POINTS = 16384
+STATIC_MAX_PAIRS = 65536
 
 
 def fp_find_static(h: Handle, pts: torch.Tensor, qsess: Optional[torch.Tensor] = None, out=None, stream=None):
@@ -746,6 +753,36 @@ def fp_newton_paths(h: Handle) -> dict:
     c = (ctypes.c_int64 * 4)()
     _check(lib().fp_newton_paths(h.ptr, c), h.ptr)
     return {"rejected_fp32": c[0], "fp32_not_converged": c[1], "fp64_step_converged": c[2], "fallback": c[3]}
+
+
+BAND_KINDS = ("accept", "border", "owner")
+
+
+def fp_band_hits(h: Handle) -> dict:
+    """Near-tie counts of the handle's classifications since the last read
+    (synchronises the device and resets them)."""
+    c = (ctypes.c_int64 * 3)()
+    _check(lib().fp_band_hits(h.ptr, c), h.ptr)
+    return {k: int(c[i]) for i, k in enumerate(BAND_KINDS)}
+
+
+PROBE_KINDS = {"f64": 0, "f32": 1, "df": 2}
+
+
+def fp_probe_threads(blocks_per_sm: int = 4) -> int:
+    return int(lib().fp_probe_threads(int(blocks_per_sm)))
+
+
+def fp_fma_probe(kind: str, iters: int, sink: torch.Tensor, blocks_per_sm: int = 4, stream=None) -> float:
+    """Enqueue one multiply-add chain probe launch (kind 'f64', 'f32' or 'df')
+    writing one double per thread to `sink`; returns the launch's flops."""
+    sink = _dev(sink, torch.float64, "sink")
+    if sink.numel() < fp_probe_threads(blocks_per_sm):
+        raise ValueError("sink smaller than fp_probe_threads(blocks_per_sm)")
+    fl = ctypes.c_double(0.0)
+    _check(lib().fp_fma_probe(PROBE_KINDS[kind], int(iters), int(blocks_per_sm), _ptr(sink), ctypes.byref(fl),
+                              _stream(stream)))
+    return fl.value
 
 
 def fp_launch_count() -> int:

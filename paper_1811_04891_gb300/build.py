@@ -16,7 +16,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfindpts_gb.so")
 SOURCES = ["fp_host.cu", "fp_setup.cu", "fp_scan.cu", "fp_find.cu", "fp_find2.cu", "fp_eval.cu", "fp_static.cu",
-           "fp_batch.cu", "fp_flux.cu", "fp_stream.cu"]
+           "fp_batch.cu", "fp_flux.cu", "fp_stream.cu", "fp_probe.cu"]
 HEADERS = ["fp_common.cuh", "fp_internal.h", "fp_handle.h", "fp_rank.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

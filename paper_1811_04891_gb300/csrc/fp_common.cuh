@@ -235,4 +235,50 @@ __device__ __forceinline__ T contract(const T* __restrict__ F, const T (&hr)[n],
     return acc;
 }
 
+// ---------------------------------------------------------------------------
+// Double-float arithmetic on the FP32 pipes (Dekker / Knuth error-free
+// transformations).  A value is carried as an unevaluated sum hi + lo of two
+// floats (about 48 significant bits).  df_fma_acc adds the product of two
+// double-floats to an accumulator: the leading product is formed exactly
+// (p = ah*bh, its rounding error by one fma), the cross terms ah*bl + al*bh
+// are added to that error, and the sum acc.hi + p is an error-free two-sum
+// whose error goes to the low part.  Used by the mixed form's residuals and
+// evaluation, and by the peak probe that measures its throughput.
+// ---------------------------------------------------------------------------
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_split(double v)
+{
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+
+// acc += (ah + al) * (bh + bl)
+__device__ __forceinline__ void df_fma_acc(df& acc, float ah, float al, float bh, float bl)
+{
+    const float p = ah * bh;
+    const float pe = fmaf(ah, bh, -p);
+    const float t = fmaf(ah, bl, fmaf(al, bh, pe));
+    const float s = acc.hi + p;
+    const float bb = s - acc.hi;
+    const float err = (acc.hi - (s - bb)) + (p - bb);
+    acc.hi = s;
+    acc.lo += err + t;
+}
+
+__device__ __forceinline__ void df_fma_acc(df& acc, const df& a, float bh, float bl)
+{
+    df_fma_acc(acc, a.hi, a.lo, bh, bl);
+}
+
+// renormalise (fast two-sum): |lo| below one unit in the last place of hi
+__device__ __forceinline__ void df_norm(df& a)
+{
+    const float t = a.hi + a.lo;
+    a.lo = a.lo - (t - a.hi);
+    a.hi = t;
+}
+
 }  // namespace fpg

@@ -85,35 +85,6 @@ cudaError_t launch_eval(int n, int64_t E, int64_t P, const int32_t* code, const 
 // ---------------------------------------------------------------------------
 namespace fpg {
 
-struct df {
-    float hi, lo;
-};
-
-__device__ __forceinline__ df df_split(double v)
-{
-    const float h = (float)v;
-    return {h, (float)(v - (double)h)};
-}
-
-// acc += a * b for double-floats a (value) and b (basis)
-__device__ __forceinline__ void df_fma_acc(df& acc, float ah, float al, float bh, float bl)
-{
-    const float p = ah * bh;
-    const float pe = fmaf(ah, bh, -p);
-    const float t = fmaf(ah, bl, fmaf(al, bh, pe));
-    const float s = acc.hi + p;
-    const float bb = s - acc.hi;
-    const float err = (acc.hi - (s - bb)) + (p - bb);
-    acc.hi = s;
-    acc.lo += err + t;
-}
-
-// acc += a * b where a is a double-float partial sum and b a double-float basis value
-__device__ __forceinline__ void df_fma_acc(df& acc, const df& a, float bh, float bl)
-{
-    df_fma_acc(acc, a.hi, a.lo, bh, bl);
-}
-
 struct Eval2Args {
     int64_t E;
     int64_t P;

@@ -621,29 +621,6 @@ __device__ __forceinline__ float f32_inside(double v)
 // basis values computed in FP64 and split, products formed exactly in their
 // leading part and summed with error-free two-sums (about 48 significant
 // bits in element-local units).  Runs on the FP32 pipes.
-struct df2 {
-    float hi, lo;
-};
-
-__device__ __forceinline__ void df2_acc(df2& acc, float ah, float al, float bh, float bl)
-{
-    const float p = ah * bh;
-    const float pe = fmaf(ah, bh, -p);
-    const float t = fmaf(ah, bl, fmaf(al, bh, pe));
-    const float s = acc.hi + p;
-    const float bb = s - acc.hi;
-    const float err = (acc.hi - (s - bb)) + (p - bb);
-    acc.hi = s;
-    acc.lo += err + t;
-}
-
-__device__ __forceinline__ void df2_norm(df2& a)
-{
-    const float t = a.hi + a.lo;
-    a.lo = a.lo - (t - a.hi);
-    a.hi = t;
-}
-
 template <int n>
 __device__ __forceinline__ void resid_df(const ElemPtr<float>& hi, const ElemPtr<float>& lo, const BasisTab& tab,
                                          const double (&r)[3], const double (&xl)[3], float (&f)[3])
@@ -659,14 +636,14 @@ __device__ __forceinline__ void resid_df(const ElemPtr<float>& hi, const ElemPtr
         sh[i] = (float)hs[i]; sl[i] = (float)(hs[i] - (double)sh[i]);
         th[i] = (float)ht[i]; tl[i] = (float)(ht[i] - (double)th[i]);
     }
-    df2 acc[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+    df acc[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
 #pragma unroll 1
     for (int k = 0; k < n; ++k) {
-        df2 ck[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+        df ck[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
 #pragma unroll 1
         for (int j = 0; j < n; ++j) {
             const int off = n * (j + n * k);
-            df2 u0[3], u1[3];
+            df u0[3], u1[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {             // three coordinates x two partial sums: six chains
                 const float* Xh = (a == 0 ? hi.X0 : (a == 1 ? hi.X1 : hi.X2)) + off;
@@ -678,22 +655,22 @@ __device__ __forceinline__ void resid_df(const ElemPtr<float>& hi, const ElemPtr
                 u1[a] = {0.0f, 0.0f};
 #pragma unroll
                 for (int i = 0; i < n; i += 2) {
-                    df2_acc(u0[a], vh[i], vl[i], rh[i], rl[i]);
-                    if (i + 1 < n) df2_acc(u1[a], vh[i + 1], vl[i + 1], rh[i + 1], rl[i + 1]);
+                    df_fma_acc(u0[a], vh[i], vl[i], rh[i], rl[i]);
+                    if (i + 1 < n) df_fma_acc(u1[a], vh[i + 1], vl[i + 1], rh[i + 1], rl[i + 1]);
                 }
             }
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                df2 u = u0[a];
-                df2_acc(u, u1[a].hi, u1[a].lo, 1.0f, 0.0f);
-                df2_norm(u);
-                df2_acc(ck[a], u.hi, u.lo, sh[j], sl[j]);
+                df u = u0[a];
+                df_fma_acc(u, u1[a].hi, u1[a].lo, 1.0f, 0.0f);
+                df_norm(u);
+                df_fma_acc(ck[a], u.hi, u.lo, sh[j], sl[j]);
             }
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            df2_norm(ck[a]);
-            df2_acc(acc[a], ck[a].hi, ck[a].lo, th[k], tl[k]);
+            df_norm(ck[a]);
+            df_fma_acc(acc[a], ck[a].hi, ck[a].lo, th[k], tl[k]);
         }
     }
 #pragma unroll
@@ -1024,6 +1001,7 @@ static cudaError_t solve_n(const FindArgs& a, int64_t npairs, const BasisTab& ta
     ra.pair_pt = a.pair_pt;
     ra.F = a.eval.F;
     ra.out = a.eval.out;
+    ra.band = a.band;
     if (a.ev[4]) cudaEventRecord(a.ev[4], s);
     k_rank<n, 3><<<(unsigned)((a.P + 127) / 128), 128, 0, s>>>(ra, fp, tab);
     count_launch();

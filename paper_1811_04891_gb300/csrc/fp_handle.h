@@ -14,6 +14,7 @@ struct fp_host_stream;   // fp_find_eval_host state (fp_stream.cu)
 enum { PROF_SCREEN = 0, PROF_SORT = 1, PROF_NEWTON = 2, PROF_RANK = 3, PROF_EVAL = 4, PROF_KINDS = 5 };
 
 struct fp_handle {
+    int device = -1;               // CUDA device the handle was set up on
     int dim = 3;                   // 3: hexahedra, coords [3][E][n^3]; 2: quadrilaterals, [2][E][n^2]
     int N = 0, n = 0;
     int64_t E = 0;
@@ -66,6 +67,7 @@ struct fp_handle {
     // optional per-kernel timing with CUDA events on the launching stream
     bool prof = false;
     unsigned long long* stats = nullptr;   // device [4] Newton path counters while profiling
+    unsigned long long* band = nullptr;    // device [3] near-tie counters of the classification (always on)
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pend[PROF_KINDS];
 };

@@ -186,6 +186,7 @@ void release(fp_handle* h)
     for (auto e : h->ev_free) cudaEventDestroy(e);
     h->ev_free.clear();
     dfree(h->stats);
+    dfree(h->band);
     dfree(h->coords); dfree(h->coords32); dfree(h->coords32lo); dfree(h->sub); dfree(h->dist); dfree(h->boxes); dfree(h->boxes32);
     dfree(h->cell_start); dfree(h->cell_elems); dfree(h->ecount); dfree(h->estart); dfree(h->escan_tmp);
     dfree(h->cnt); dfree(h->off); dfree(h->scan_tmp); dfree(h->pair_elem); dfree(h->pair_pt);
@@ -469,6 +470,7 @@ static fp_status setup_impl(fp_handle** hout, int dim, const double* coords, int
 
     fp_handle* h = new fp_handle();
     h->N = N; h->n = n; h->E = E; h->opts = o; h->dim = dim;
+    if (cudaGetDevice(&h->device) != cudaSuccess) h->device = -1;
     make_tab(N, &h->tab);
     cudaError_t err;
     const size_t ncoord = (size_t)dim * E * n3;
@@ -527,6 +529,8 @@ static fp_status setup_impl(fp_handle** hout, int dim, const double* coords, int
             return st;
         }
     }
+    CK(dalloc(&h->band, 3), "alloc band counters");
+    CK(cudaMemsetAsync(h->band, 0, 3 * sizeof(unsigned long long), s), "zero band counters");
     CK(dalloc(&h->ecount, E), "alloc ecount");
     CK(dalloc(&h->estart, E + 1), "alloc estart");
     CK(cudaStreamSynchronize(s), "sync setup");
@@ -579,6 +583,7 @@ static fp_status find_impl(fp_handle* h, int64_t P, const double* pts, const int
     a.code = code; a.osub = sub; a.oelem = elem; a.rst = rst; a.dist2 = dist2;
     a.eval = ev;
     a.stats = h->prof ? h->stats : nullptr;
+    a.band = h->band;
     a.warm_elem = warm_elem;
     a.warm_rst = warm_rst;
     cudaEvent_t scr0 = nullptr, scr1 = nullptr;
@@ -859,6 +864,7 @@ static fp_status find_ws_impl(fp_handle* h, fp_workspace* w, int64_t P, const do
     a.persistent_blocks = w->persistent_blocks;
     a.code = code; a.osub = sub; a.oelem = elem; a.rst = rst; a.dist2 = dist2;
     a.eval = ev;
+    a.band = h->band;
     FindParams fp;
     fp.tol_accept = h->opts.tol_accept;
     fp.tol_border = h->opts.tol_border;
@@ -1104,6 +1110,19 @@ fp_status fp_newton_paths(fp_handle* h, int64_t* counts)
         if (e != cudaSuccess) return cuda_fail(h, e, "fp_newton_paths");
     }
     for (int k = 0; k < 4; ++k) counts[k] = (int64_t)c[k];
+    return FP_OK;
+}
+
+fp_status fp_band_hits(fp_handle* h, int64_t* counts)
+{
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
+    if (!counts) return fail(h, FP_ERR_INVALID_ARG, "fp_band_hits: null counts");
+    unsigned long long c[3] = {0, 0, 0};
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(c, h->band, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(h->band, 0, sizeof(c));
+    if (e != cudaSuccess) return cuda_fail(h, e, "fp_band_hits");
+    for (int k = 0; k < 3; ++k) counts[k] = (int64_t)c[k];
     return FP_OK;
 }
 

@@ -89,6 +89,7 @@ struct FindArgs {
     cudaEvent_t ev[8];
     EvalSpec eval;                // eval.F == 0: find only
     unsigned long long* stats;    // optional Newton path counters (4 words), null = off
+    unsigned long long* band;     // optional near-tie counters (3 words, see fp_rank.cuh), null = off
     const int32_t* warm_elem;     // optional warm start: previous element [P] (null = off)
     const double* warm_rst;       // and previous reference coordinates [3][P]
     // outputs

@@ -29,7 +29,19 @@ struct RankArgs {
     int32_t* oelem;
     double* rst;
     double* dist2;
+    unsigned long long* band;   // optional [3] near-tie counters (see k_rank), null = off
 };
+
+// Near-tie ("band") hits of a point's decisions, counted so that a result
+// whose ids could depend on rounding is visible:
+//   BAND_ACCEPT  a candidate's residual within a factor 2 of tol_accept*h_e
+//                (INSIDE or not could differ between two FP64 evaluations)
+//   BAND_BORDER  no INSIDE winner and a candidate's residual within a factor
+//                2 of tol_border*h_e, or two BORDER candidates within the tie
+//                band of the smallest residual (the lowest id decided)
+//   BAND_OWNER   two subdomains' delta^k within twice the tie band of the
+//                largest (the lower-id rule decided, or nearly did)
+enum { BAND_ACCEPT = 0, BAND_BORDER = 1, BAND_OWNER = 2, BAND_KINDS = 3 };
 
 // D^k interpolated at (e, r) of a DIM-dimensional element (D: n^DIM values)
 template <int n, int DIM>
@@ -77,12 +89,16 @@ __global__ void __launch_bounds__(128) k_rank(RankArgs A, FindParams fp, BasisTa
         return;
     }
     // INSIDE winners: lowest element id per subdomain
+    unsigned hit = 0;
+    bool near_border = false;
     int best_q = -1, nwin = 0;
     double bmin = INFINITY;
     for (int q = b; q < en; ++q) {
         const int e = A.pair_elem[q];
         const double he = A.boxes[e].he;
         const double res = A.pres[q];
+        if (res >= 0.5 * fp.tol_accept * he && res <= 2.0 * fp.tol_accept * he) hit |= 1u << BAND_ACCEPT;
+        if (res >= 0.5 * fp.tol_border * he && res <= 2.0 * fp.tol_border * he) near_border = true;
         if (res <= fp.tol_accept * he) {
             const int s = A.sub[e];
             bool winner = true;
@@ -106,6 +122,7 @@ __global__ void __launch_bounds__(128) k_rank(RankArgs A, FindParams fp, BasisTa
     } else if (nwin > 1) {
         // owner = argmax delta^k(x*), ties within the band -> lower subdomain id
         double dmax = -INFINITY;
+        int nclose = 0;
         for (int pass = 0; pass < 2; ++pass) {
             int bs = 0x7fffffff;
             for (int q = b; q < en; ++q) {
@@ -122,25 +139,39 @@ __global__ void __launch_bounds__(128) k_rank(RankArgs A, FindParams fp, BasisTa
                 const double dl = A.dist ? interp_delta<n, DIM>(A.dist + (int64_t)e * n3, tab, A.prst, A.cap, q) : 0.0;
                 if (pass == 0) {
                     dmax = fmax(dmax, dl);
-                } else if (dl >= dmax - fp.band && s < bs) {
-                    bs = s;
-                    pick = q;
+                } else {
+                    if (dl >= dmax - 2.0 * fp.band) ++nclose;
+                    if (dl >= dmax - fp.band && s < bs) {
+                        bs = s;
+                        pick = q;
+                    }
                 }
             }
         }
+        if (nclose > 1) hit |= 1u << BAND_OWNER;
         code = 0;
     } else if (bmin < INFINITY) {
-        int be = 0x7fffffff;
+        int be = 0x7fffffff, ntie = 0;
         for (int q = b; q < en; ++q) {
             const int e = A.pair_elem[q];
             const double he = A.boxes[e].he;
             const double res = A.pres[q];
-            if (res > fp.tol_accept * he && res <= fp.tol_border * he && res <= bmin + fp.band && e < be) {
-                be = e;
-                pick = q;
+            if (res > fp.tol_accept * he && res <= fp.tol_border * he && res <= bmin + fp.band) {
+                ++ntie;
+                if (e < be) {
+                    be = e;
+                    pick = q;
+                }
             }
         }
+        if (ntie > 1) hit |= 1u << BAND_BORDER;
         code = 1;
+    }
+    if (nwin == 0 && near_border) hit |= 1u << BAND_BORDER;
+    if (hit && A.band) {
+#pragma unroll
+        for (int k = 0; k < BAND_KINDS; ++k)
+            if (hit & (1u << k)) atomicAdd(A.band + k, 1ULL);
     }
     for (int q = b; q < en; ++q)
         if (q != pick) A.pair_pt[q] = -1;

@@ -2,21 +2,23 @@
 //
 // Some callers cannot allocate device memory at the moment they need to
 // locate points: a solver that has handed all free device memory to its own
-// pool allocator (cudaMalloc would fail or fragment that pool), code running
-// while a stream is being captured into a CUDA graph (cudaMalloc / cudaFree
-// are not allowed there), or a latency-bound time-step loop that cannot take
-// the implicit device-wide synchronisation of cudaMalloc / cudaFree.  For
-// them this entry point runs the same screen / Newton / classification
-// kernels as fp_find, with all per-call scratch (pair offsets, pair lists,
-// per-pair results) carved out of one file-scope device array of fixed size,
-// g_fp_static_scratch.  The array exists on every GPU that loads the library
-// and is held until the process exits.
+// pool allocator (cudaMalloc would fail or fragment that pool), or a
+// latency-bound time-step loop that cannot take the implicit device-wide
+// synchronisation of cudaMalloc / cudaFree.  For them this entry point runs
+// the same screen / Newton / classification kernels as fp_find, with all
+// per-call scratch (pair offsets, pair lists, per-pair results) carved out of
+// one file-scope device array of fixed size, g_fp_static_scratch.  The array
+// exists on every GPU that loads the library and is held until the process
+// exits.  Like fp_find, the call waits once on its stream, to read the number
+// of candidate pairs back to the host.
 //
 // Limits: at most FP_STATIC_MAX_POINTS points and FP_STATIC_MAX_PAIRS
-// (point, candidate element) pairs per call; larger requests are rejected
-// with FP_ERR_INVALID_ARG before any device work.  Pairs are solved in point
-// order (no sort by element), which changes only the schedule, not the result
-// of any pair.
+// (point, candidate element) pairs per call.  The point limit is checked
+// before any device work; the pair count is only known after the screen has
+// counted the candidates, so a request over the pair limit is rejected with
+// FP_ERR_INVALID_ARG after that counting pass (its outputs are then left
+// unwritten).  Pairs are solved in point order (no sort by element), which
+// changes only the schedule, not the result of any pair.
 //
 // Sharing: every call on a device uses the same array and leaves the last
 // call's contents in it.  Nothing in it needs to start at zero (every word a
@@ -27,7 +29,9 @@
 // Set-up: the first call on each device, with that device current, looks up
 // the array's device address with cudaGetSymbolAddress (in host code the
 // symbol is only a host-side stand-in, not a device address).  Make that
-// first call before starting any stream capture.
+// first call before starting any stream capture.  A handle is used on the
+// device it was set up on; a call made while another device is current is
+// refused, since the scratch address would belong to the wrong GPU.
 #include <mutex>
 
 #include "fp_common.cuh"
@@ -106,6 +110,11 @@ extern "C" fp_status fp_find_static(fp_handle* h, int64_t P, const double* pts, 
         h->err = "fp_find_static: null pointer argument";
         return FP_ERR_INVALID_ARG;
     }
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != h->device) {
+        h->err = "fp_find_static: the current device is not the handle's device";
+        return FP_ERR_INVALID_ARG;
+    }
     if (scan_tmp_elems(P) > kScanTmp) {
         h->err = "fp_find_static: scan scratch too small";
         return FP_ERR_INVALID_ARG;
@@ -135,6 +144,8 @@ extern "C" fp_status fp_find_static(fp_handle* h, int64_t P, const double* pts, 
     a.prst = reinterpret_cast<double*>(b + kOffRst);
     a.cap = kMaxPairs;
     a.code = code; a.osub = sub; a.oelem = elem; a.rst = rst; a.dist2 = dist2;
+    a.stats = h->prof ? h->stats : nullptr;
+    a.band = h->band;
     FindParams fp;
     fp.tol_accept = h->opts.tol_accept;
     fp.tol_border = h->opts.tol_border;
@@ -150,6 +161,7 @@ extern "C" fp_status fp_find_static(fp_handle* h, int64_t P, const double* pts, 
         return FP_ERR_CUDA;
     }
     const int64_t npairs = h->h_total[0];
+    h->last_pairs = npairs;
     if (npairs < 0 || npairs > kMaxPairs) {
         h->err = "fp_find_static: more than FP_STATIC_MAX_PAIRS = 65536 candidate pairs";
         return FP_ERR_INVALID_ARG;

@@ -24,7 +24,7 @@ def gpu_find(mesh, pts, qsess=None, prec=0, dist="mesh", fields=None, **opt):
         out = fg.fp_eval(h, code, elem, rst, torch.from_numpy(np.ascontiguousarray(fields)).to(dev))
     torch.cuda.synchronize()
     res = {"code": code.cpu().numpy(), "sub": sub.cpu().numpy(), "elem": elem.cpu().numpy(),
-           "rst": rst.cpu().numpy(), "dist2": d2.cpu().numpy(), "handle": h}
+           "rst": rst.cpu().numpy(), "dist2": d2.cpu().numpy(), "handle": h, "band": fg.fp_band_hits(h)}
     if out is not None:
         res["eval"] = out.cpu().numpy()
     return res
@@ -38,7 +38,14 @@ def oracle_find(mesh, pts, qsess=None, dist="mesh", fields=None, **kw):
     return ref
 
 
-def assert_parity(g, r, prec=0, fields=None, he=None):
+NO_BAND = {"accept": 0, "border": 0, "owner": 0}
+
+
+def assert_parity(g, r, prec=0, fields=None, he=None, band=None):
+    """Element-by-element parity of a GPU result with the oracle's.  `band`,
+    when given, is the expected near-tie count per kind (fp_band_hits)."""
+    if band is not None:
+        assert g["band"] == band, g["band"]
     np.testing.assert_array_equal(g["code"], r["code"])
     np.testing.assert_array_equal(g["elem"], r["elem"])
     np.testing.assert_array_equal(g["sub"], r["sub"])

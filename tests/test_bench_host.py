@@ -52,16 +52,42 @@ def test_clock_record_without_samples(tmp_path):
 
 
 def test_work_per_point_matches_its_parts():
-    """Algorithmic work per located point (FP64 form: seed + K iterations;
-    mixed: FP64 residual + basis, FP32 seed + K iterations + two compensated
-    residuals) and the FP32 peak from the unit counts."""
-    assert bench.WORK["fp64"]["f64"] == pytest.approx(4.1e3 + 3.43 * 8.4e3)
-    assert bench.WORK["fp64"]["f32"] == 0.0
-    assert bench.WORK["mixed"]["f64"] == pytest.approx(3.5e3 + 0.3e3)
-    assert bench.WORK["mixed"]["f32"] == pytest.approx(4.1e3 + 3.43 * 8.4e3 + 2 * 19.3e3)
-    assert bench.P32_NOMINAL == pytest.approx(152 * 128 * 2 * 2.07e9)
-    # the value-only FP64 residual: 3 coordinates x (n^3 + n^2 + n) FMA at n = 8, 2 flops each
-    assert bench.RESID == pytest.approx(2 * 3 * (8 ** 3 + 8 ** 2 + 8), rel=0.01)
+    """Algorithmic work per located point at N=7 (n = 8): FP64 form seed + K
+    iterations on the FP64 pipe; mixed form seed + K iterations in FP32 and
+    the final FP64-accuracy step; no refinement steps counted."""
+    n = 8
+    assert bench.SEED == pytest.approx(n ** 3 * 8, rel=0.01)                 # 3 sub, 3 mul, 2 add per node
+    assert bench.ITER == pytest.approx(2 * (6 * n ** 3 + 9 * n ** 2 + 12 * n) + 6 * n ** 2 * 2, rel=0.02)
+    assert bench.FINAL == pytest.approx(2 * 3 * (n ** 3 + n ** 2 + n) + 0.3e3, rel=0.01)
+    assert bench.EVAL1 == pytest.approx(2 * (n ** 3 + n ** 2 + n), rel=0.01)
+    assert bench.WORK["fp64"] == {"f64": pytest.approx(4.1e3 + 3.43 * 8.4e3), "f32": 0.0, "f64acc": 0.0}
+    assert bench.WORK["mixed"] == {"f64": 0.0, "f32": pytest.approx(4.1e3 + 3.43 * 8.4e3), "f64acc": 3.8e3}
+
+
+def test_roofline_fraction_recomputes_from_its_parts():
+    """frac = algorithmic work x units / kernel time / measured peak, for
+    both forms; the step fraction adds the eval's work; the FP64 view puts
+    the whole step's work on the FP64 pipe."""
+    peaks = {"p64": 1.2, "p32": 70.0, "pdf": 6.0, "clocks": {"sm_mhz": 2070.0}}
+    P, F = 10_000_000, 5
+    for form in ("fp64", "mixed"):
+        km = {"newton": 40.0 if form == "mixed" else 300.0}
+        r = bench.roofline_form(form, P, F, km, 60.0 if form == "mixed" else 350.0, peaks, 6789.6, 1.0e7,
+                                4.0e8, 6.7e8)
+        w = bench.WORK[form]
+        if form == "fp64":
+            t = P * w["f64"] / 1.2e12
+            assert r["achieved"] == pytest.approx(P * w["f64"] / 0.300 / 1e12)
+            te = P * F * bench.EVAL1 / 1.2e12
+        else:
+            t = P * (w["f32"] / 70e12 + w["f64acc"] / 6e12)
+            te = P * F * bench.EVAL1 / 6e12
+        assert r["frac"] == pytest.approx(t / (km["newton"] / 1e3))
+        assert r["achieved"] / r["peak"] == pytest.approx(r["frac"])
+        step_ms = 60.0 if form == "mixed" else 350.0
+        assert r["step"]["frac"] == pytest.approx((t + te) / (step_ms / 1e3))
+        fp64 = P * (bench.SEED + bench.K_ORACLE * bench.ITER + F * bench.EVAL1) / 1.2e12
+        assert r["fp64_roofline"]["frac"] == pytest.approx(fp64 / (step_ms / 1e3))
 
 
 def test_oracle_one_core_timing_restores_threads():

@@ -84,3 +84,7 @@ def test_argument_checks_before_any_device_work():
     assert L.fp_batch_create(ctypes.byref(out), 0, None, None, 0, None, 2.0) == INV               # no instances
     assert L.fp_batch_schedule(None, None, None) == INV
     assert L.fp_bfaces_info(None, None, None) == INV
+    cnt = (ctypes.c_int64 * 3)()
+    assert L.fp_band_hits(None, cnt) == NOSET
+    assert L.fp_fma_probe(3, 10, 1, None, None, None) == INV                                      # kind outside 0..2
+    assert L.fp_fma_probe(0, 0, 1, None, None, None) == INV                                       # iters < 1

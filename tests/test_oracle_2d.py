@@ -61,7 +61,6 @@ def test_forward_map_recovery_2d(N):
     assert (res["code"] == INSIDE).all()
     np.testing.assert_array_equal(res["elem"], els)
     np.testing.assert_allclose(res["rst"], r, atol=1e-12)
-    assert res["bad_prefilter"] == 0
 
 
 def test_ring_recovery_2d():

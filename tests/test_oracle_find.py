@@ -28,7 +28,6 @@ def test_forward_map_recovery_deformed(N):
     assert (res["code"] == INSIDE).all()
     np.testing.assert_array_equal(res["elem"], els)
     np.testing.assert_allclose(res["rst"], r, atol=1e-12)
-    assert res["bad_prefilter"] == 0
 
 
 def test_affine_box_closed_form():
@@ -176,3 +175,42 @@ def test_border_projection_on_skewed_element():
     assert res["code"][0] == BORDER and res["elem"][0] == 0
     np.testing.assert_allclose(res["rst"][:, 0], [1.0, s0, t0], atol=1e-9)
     np.testing.assert_allclose(np.sqrt(res["dist2"][0]), d, rtol=1e-6)
+
+
+@pytest.mark.parametrize("case", ["deformed", "curved_border", "overlap_tags", "quad"])
+def test_prefilter_never_changes_a_result(case):
+    """The oracle's optional prefilter (node box grown by 25 % of its extent
+    plus the border tolerance) may only skip elements that cannot hold the
+    answer: with it and without it every output is identical, on strongly
+    deformed and curved elements, at border distances and with session tags."""
+    rng = np.random.default_rng(31)
+    qsess = None
+    if case == "deformed":
+        N = 5
+        coords = synth.box_mesh((3, 3, 2), N, amp_frac=0.45)
+        coords[0] += 0.04 * np.sin(5 * coords[1]) * np.cos(3 * coords[2])
+        mesh = synth.Mesh(coords=coords, N=N, sub=_zeros(coords.shape[1]))
+        pts = rng.uniform(-0.02, 1.02, (3, 1500))
+    elif case == "curved_border":
+        N = 6
+        mesh, _ = synth.box_annulus(n_az=12, n_rad=2, n_ax=2, box_shape=(4, 2, 2), N=N)
+        th = rng.uniform(0, 2 * np.pi, 1200)
+        # just outside and inside the annulus's curved faces, at border distances
+        rho = np.where(rng.random(1200) < 0.5, 0.15, 0.35) + rng.choice([-1, 1], 1200) * 10.0 ** rng.uniform(-9, -6, 1200)
+        pts = np.stack([1 + rho * np.cos(th), 0.5 + rho * np.sin(th), rng.uniform(0.0, 1.0, 1200)])
+        qsess = np.zeros(1200, np.int32)           # search the annulus only
+    elif case == "overlap_tags":
+        mesh = synth.tiny_overlap(N=4)
+        pts = np.stack([rng.uniform(-0.05, 2.05, 900), rng.uniform(-0.01, 1.01, 900), rng.uniform(0.0, 1.0, 900)])
+        qsess = rng.integers(-1, 3, 900).astype(np.int32)
+    else:
+        N = 7
+        mesh = synth.Mesh(coords=synth.quad_mesh((4, 3), N, amp_frac=0.4), N=N, sub=_zeros(12))
+        pts = rng.uniform(-0.02, 1.02, (2, 1500))
+    on = oracle.find(mesh.coords, mesh.N, mesh.sub, pts, qsess=qsess, dist=mesh.dist,
+                     params=oracle.Params(prefilter=True))
+    off = oracle.find(mesh.coords, mesh.N, mesh.sub, pts, qsess=qsess, dist=mesh.dist,
+                      params=oracle.Params(prefilter=False))
+    for k in ("code", "sub", "elem", "rst", "dist2"):
+        np.testing.assert_array_equal(on[k], off[k], err_msg=k)
+    assert (on["code"] == INSIDE).any() and (on["code"] != INSIDE).any()
