@@ -61,13 +61,22 @@ K_ORACLE = 3.43
 # The refinement steps the mixed form adds between its FP32 iterations and
 # its final step are the implementation's precision technique, not the
 # method's work, and are not counted.
+def work_for_order(n: int) -> dict:
+    """The per-point algorithmic work above for n = N + 1 GLL points per
+    direction, scaled from the N = 7 figures by each part's operation count
+    (seed n^3, iteration 6n^3 + 9n^2 + 12n, residual and eval n^3 + n^2 + n)."""
+    it = (6 * n ** 3 + 9 * n ** 2 + 12 * n) / (6 * 512 + 9 * 64 + 12 * 8)
+    ev = (n ** 3 + n ** 2 + n) / (512 + 64 + 8)
+    return {"seed": SEED * n ** 3 / 512, "iter": ITER * it, "final": FINAL * ev, "eval1": EVAL1 * ev}
+
+
 WORK = {"fp64": {"f64": SEED + K_ORACLE * ITER, "f32": 0.0, "f64acc": 0.0},
         "mixed": {"f64": 0.0, "f32": SEED + K_ORACLE * ITER, "f64acc": FINAL}}
 # DRAM bytes (read + written) per (point, candidate element) pair of the Newton
 # stage, measured with ncu on the 2.02M-point case of this workload (2.05M
 # pairs over the same 32,768 elements) and scaled by the pairs of a launch.
 # None where the kernel changed after the capture.
-TRAFFIC_PER_PAIR = {"mixed": 1422.0, "fp64": 740.0}
+TRAFFIC_PER_PAIR = {"fp64": 740.0}
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -100,8 +109,11 @@ def parse():
     ap.add_argument("--no-moving", action="store_true")
     ap.add_argument("--no-planar", action="store_true")
     ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip the peak probes (profiling runs); the line then has no roofline")
     ap.add_argument("--served-requests", type=int, default=200)
     ap.add_argument("--served-load", type=float, default=0.7)
+    ap.add_argument("--served-chunk", type=int, default=1 << 17)
     ap.add_argument("--served-scale", type=float, default=1.0,
                     help="element-count scale of the served mesh (1.0 = 193,536 elements)")
     return ap.parse_args()
@@ -432,7 +444,7 @@ def run_small_configs(args, fg, dev, peaks, with_oracle: bool):
 # ---------------------------------------------------------------------------
 # batched form: 64 deformed-box instances, E logU[64,8192], N in {5,7,9}
 # ---------------------------------------------------------------------------
-def run_batched(args, fg, dev, barrier, max_over_ranks, world):
+def run_batched(args, fg, dev, barrier, max_over_ranks, world, peaks):
     import torch
 
     import synth
@@ -447,12 +459,14 @@ def run_batched(args, fg, dev, barrier, max_over_ranks, world):
                                opts=fg.default_opts(precision=prec)) for m, _ in insts]
         b = fg.Batch(handles, [q.P for _, q in insts], fields)
         outs = b.outputs(dev)
+        t0 = time.perf_counter()
         tuned_ms = b.tune(pts, outs, reps=1)
-        block, bps = b.schedule()
+        tune_s = time.perf_counter() - t0
         b.capture(pts, outs)
         for _ in range(max(1, args.warmup)):
             b.launch()
         torch.cuda.synchronize()
+        b.band_hits()
         barrier()
         l0 = fg.fp_launch_count()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -463,14 +477,42 @@ def run_batched(args, fg, dev, barrier, max_over_ranks, world):
         torch.cuda.synchronize()
         barrier()
         ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+        launches = (fg.fp_launch_count() - l0) // max(1, args.steps)
+        band = b.band_hits()
         codes = torch.bincount(outs[0].long(), minlength=4).tolist()
-        out[form] = {"value": world * P / (ms / 1e3), "ms_per_step": ms, "tuned_ms": tuned_ms,
-                     "schedule": {"threads_per_block": block, "blocks_per_sm": bps},
-                     "gpu_launches": (fg.fp_launch_count() - l0) // max(1, args.steps),
+        # one profiled (eager) run: per-order Newton and eval times, the groups one after another
+        b.profile(True)
+        b.run(pts, outs)
+        torch.cuda.synchronize()
+        b.profile(False)
+        per_order = {}
+        for g in range(b.groups()):
+            gi = b.group_info(g)
+            n = gi["N"] + 1
+            w = work_for_order(n)
+            blk, bps, tile = b.schedule(g)
+            row = {"elements": gi["E"], "points": gi["P"], "pairs": gi["pairs"], "newton_ms": gi["newton_ms"],
+                   "eval_ms": gi["eval_ms"],
+                   "points_per_s_newton_eval": gi["P"] / max(1e-9, (gi["newton_ms"] + gi["eval_ms"]) / 1e3),
+                   "schedule": {"threads_per_block": blk, "blocks_per_sm": bps, "pairs_per_item": tile}}
+            if peaks is not None and gi["newton_ms"] > 0:
+                p64, p32 = peaks["p64"] * 1e12, peaks["p32"] * 1e12
+                pacc = max(p64, peaks["pdf"] * 1e12)
+                if form == "fp64":
+                    t = gi["P"] * (w["seed"] + K_ORACLE * w["iter"]) / p64
+                else:
+                    t = gi["P"] * ((w["seed"] + K_ORACLE * w["iter"]) / p32 + w["final"] / pacc)
+                row["newton_roofline_frac"] = t / (gi["newton_ms"] / 1e3)
+            per_order[f"N{gi['N']}"] = row
+        out[form] = {"value": world * P / (ms / 1e3), "ms_per_step": ms, "tuned_ms": tuned_ms, "tune_s": tune_s,
+                     "gpu_launches": launches, "per_order": per_order, "band_hits_per_step": band,
                      "codes": {"inside": codes[0], "border": codes[1], "not_found": codes[2], "retry": codes[3]}}
         del b, handles
     out["unit"] = UNIT
-    out["note"] = "one CUDA-graph launch per step over all instances; Newton schedule autotuned"
+    out["note"] = ("one CUDA-graph launch per step: batch-wide screen, scan, emit, pair sort and classification; "
+                   "per order N one persistent work-queue Newton launch (concurrent streams) and one eval launch; "
+                   "schedule autotuned per order; per-order times from one profiled eager run; roofline with the "
+                   "N=7 oracle iteration count K")
     return out
 
 
@@ -709,6 +751,13 @@ def run_planar(args, fg, dev):
 # served form: resident box + two rotated annular cylinders, Poisson requests
 # ---------------------------------------------------------------------------
 def run_served(args, fg, dev):
+    """Served form: the box + two rotated annular cylinders resident (config
+    4), a Poisson stream of requests served with continuous batching under a
+    40 GB device-memory budget, both forms.  Capacity = 1e6-point requests
+    served back to back; the stream runs at args.served_load of it.  Beside
+    them, fp_find_eval on the same resident mesh over 4e6 points of the same
+    mix in one device-resident call (what the loop's own overhead is measured
+    against)."""
     import torch
 
     import synth
@@ -725,35 +774,63 @@ def run_served(args, fg, dev):
                             -torch.cos(np.pi * x) * torch.sin(np.pi * y) * torch.exp(z),
                             torch.sin(np.pi * z) * x, x * x + y * y - z * z]).contiguous()
     del x, y, z
-    h = fg.fp_setup(coords_d, mesh.N, torch.from_numpy(mesh.sub).to(dev), torch.from_numpy(mesh.dist).to(dev),
-                    opts=fg.default_opts(precision=fg.PREC_MIXED))
-    resident = (mesh.coords.nbytes * 1.5 + fields_d.numel() * 8 + mesh.dist.nbytes)
-    del coords_d
-    # capacity: a 1M-point mixed request stream served back to back
+    sub_d = torch.from_numpy(mesh.sub).to(dev)
+    dist_d = torch.from_numpy(mesh.dist).to(dev)
+    out = {"elements": int(mesh.E), "N": mesh.N, "budget_bytes": 40e9, "chunk_points": args.served_chunk}
     cal = synth.poisson_requests(iface, 4, seed=40, size_range=(10 ** 6, 10 ** 6))
-    posted = fg.Fields(h, fields_d)
-    srv = serve.Server(h, fields_d, slots=4, slot_points=1 << 19, budget_bytes=40e9, resident_bytes=resident,
-                       posted=posted)
-    done, span = serve.run_stream(srv, [serve.Request(i, 0.0, r["pts"], r["qsess"]) for i, r in enumerate(cal)])
-    capacity = sum(r.P for r in done) / span
     mean_size = (10 ** 6 - 10 ** 2) / np.log(10 ** 4)
-    rate = args.served_load * capacity / mean_size
-    reqs = synth.poisson_requests(iface, args.served_requests, seed=4, rate_hz=rate)
-    srv = serve.Server(h, fields_d, slots=4, slot_points=1 << 19, budget_bytes=40e9, resident_bytes=resident,
-                       posted=posted)
-    done, span = serve.run_stream(srv, [serve.Request(i, r["t_arrive"], r["pts"], r["qsess"])
-                                        for i, r in enumerate(reqs)])
-    st = serve.latency_stats(done)
-    tot = sum(r.P for r in done)
-    codes = np.bincount(np.concatenate([r.code for r in done]), minlength=4).tolist()
-    return {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "requests": st["requests"],
-            "points": int(tot), "points_per_s": tot / span, "capacity_points_per_s": capacity,
-            "arrival_rate_hz": rate, "load": args.served_load, "slots": srv.max_slots,
-            "slot_points": srv.slot_points, "launches": srv.launches, "elements": int(mesh.E), "N": mesh.N,
-            "form": "mixed", "codes": {"inside": codes[0], "border": codes[1], "not_found": codes[2],
-                                       "retry": codes[3]},
-            "note": "Poisson arrivals, sizes logU[1e2,1e6], 50% uniform untagged + 50% cylinder interface "
-                    "nodes tagged with their session; latency = arrival to results in host memory"}
+    for form, prec in (("mixed", fg.PREC_MIXED), ("fp64", fg.PREC_FP64)):
+        h = fg.fp_setup(coords_d, mesh.N, sub_d, dist_d, opts=fg.default_opts(precision=prec))
+        posted = fg.Fields(h, fields_d) if form == "mixed" else None
+        resident = fields_d.numel() * 8 * (2 if posted is not None else 1)
+        # the same points through one fused device-resident call
+        allp = torch.from_numpy(np.ascontiguousarray(np.concatenate([r["pts"] for r in cal], axis=1))).to(dev)
+        allq = torch.from_numpy(np.concatenate([r["qsess"] for r in cal])).to(dev)
+        fg.fp_reserve(h, allp.shape[1])
+        o5 = fg._find_outs(allp.shape[1], dev)
+        vals = torch.empty((F, allp.shape[1]), dtype=torch.float64, device=dev)
+        for _ in range(2):
+            fg.fp_find_eval(h, allp, allq, fields=fields_d, posted=posted, out=o5, values=vals)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            fg.fp_find_eval(h, allp, allq, fields=fields_d, posted=posted, out=o5, values=vals)
+        e1.record()
+        torch.cuda.synchronize()
+        direct = 3 * allp.shape[1] / (e0.elapsed_time(e1) / 1e3)
+        del o5, vals, allp, allq
+        srv = serve.Server(h, fields_d, budget_bytes=40e9, resident_bytes=resident, chunk_points=args.served_chunk,
+                           streams=4, posted=posted)
+        # capacity: 1e6-point requests back to back (the first pass also fills the buffer pools)
+        for _ in range(2):
+            srv.completed = []
+            done, span = serve.run_stream(srv, [serve.Request(i, 0.0, r["pts"], r["qsess"])
+                                                for i, r in enumerate(cal)])
+        capacity = sum(r.P for r in done) / span
+        rate = args.served_load * capacity / mean_size
+        reqs = synth.poisson_requests(iface, args.served_requests, seed=4, rate_hz=rate)
+        srv.completed, srv.launches, srv.held_back, srv.peak_inflight_bytes = [], 0, 0, 0
+        srv.chunk_sizes = []
+        done, span = serve.run_stream(srv, [serve.Request(i, r["t_arrive"], r["pts"], r["qsess"])
+                                            for i, r in enumerate(reqs)])
+        st = serve.latency_stats(done)
+        tot = sum(r.P for r in done)
+        codes = np.bincount(np.concatenate([r.code for r in done]), minlength=4).tolist()
+        out[form] = {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+                     "requests": st["requests"], "points": int(tot), "points_per_s": tot / span,
+                     "capacity_points_per_s": capacity, "direct_fp_find_eval_points_per_s": direct,
+                     "capacity_over_direct": capacity / direct, "arrival_rate_hz": rate, "load": args.served_load,
+                     "chunks": srv.launches, "mean_chunk_points": float(np.mean(srv.chunk_sizes)),
+                     "held_back_passes": srv.held_back, "peak_inflight_bytes": srv.peak_inflight_bytes,
+                     "resident_bytes": srv.resident,
+                     "codes": {"inside": codes[0], "border": codes[1], "not_found": codes[2], "retry": codes[3]}}
+        del srv, posted, h
+    out["note"] = ("Poisson arrivals, sizes logU[1e2,1e6], 50% uniform untagged + 50% cylinder interface nodes "
+                   "tagged with their session; chunks of at most chunk_points admitted while their device bytes "
+                   "fit the 40 GB budget beside the resident state; 4 streams; latency = arrival to results in "
+                   "host memory; direct = one fp_find_eval over 4e6 device-resident points of the same mix")
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -859,12 +936,13 @@ def main():
     head = "mixed" if "mixed" in results else forms[0]
     R = results[head]
 
-    peaks = measure_peaks(fg, dev, uuid)
+    peaks = None if args.no_peaks else measure_peaks(fg, dev, uuid)
     hbm_gbs, hbm_src = measured_hbm_gbs()
     coords_bytes, field_bytes = mesh.coords.nbytes, q.fields.nbytes
-    roofs = {f: roofline_form(f, P, F, results[f]["kernel_ms"], results[f]["ms_per_step"], peaks, hbm_gbs,
-                              results[f]["pairs_per_point"] * P, coords_bytes, field_bytes) for f in results}
-    roof = roofs[head]
+    roofs = {} if peaks is None else {
+        f: roofline_form(f, P, F, results[f]["kernel_ms"], results[f]["ms_per_step"], peaks, hbm_gbs,
+                         results[f]["pairs_per_point"] * P, coords_bytes, field_bytes) for f in results}
+    roof = roofs.get(head)
     roof_other = {f: v for f, v in roofs.items() if f != head}
 
     # end to end through the public API with host buffers
@@ -898,7 +976,7 @@ def main():
                "api": "fp_find_eval_host (host buffers, chunks of 2^22 points, copies overlapped)"}
 
     small = None
-    if rank == 0 and not args.no_small:
+    if rank == 0 and not args.no_small and peaks is not None:
         small = run_small_configs(args, fg, dev, peaks, with_oracle=not args.no_cpu_baseline)
     batched = None
     moving = None
@@ -909,7 +987,7 @@ def main():
         moving = run_moving(args, fg, dev, mesh, coords, sub, pts, fields)
     if not args.no_batched:
         del handles
-        batched = run_batched(args, fg, dev, barrier, max_over_ranks, world)
+        batched = run_batched(args, fg, dev, barrier, max_over_ranks, world, peaks)
     served = None
     if rank == 0 and not args.no_served:
         served = run_served(args, fg, dev)

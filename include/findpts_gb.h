@@ -209,6 +209,13 @@ typedef struct fp_workspace fp_workspace;
 fp_status fp_workspace_create(const fp_handle *h, int64_t max_points, int64_t max_pairs,
                               fp_workspace **ws);
 void fp_workspace_free(fp_workspace *ws);
+/* Device bytes a workspace of max_points points and max_pairs pairs
+ * (<= 0: 2 * max_points) on this handle's mesh holds, for callers that
+ * budget device memory (the per-point, per-pair and per-element arrays;
+ * allocator rounding not included).  Errors: FP_ERR_NOT_SETUP,
+ * FP_ERR_INVALID_ARG (bytes NULL, sizes out of range). */
+fp_status fp_workspace_bytes(const fp_handle *h, int64_t max_points, int64_t max_pairs,
+                             int64_t *bytes);
 
 /* fp_find_ws -- fp_find with its scratch in `ws`.  Never waits on the host
  * and never allocates, so a sequence of fp_find_ws / fp_eval calls can be
@@ -230,39 +237,61 @@ fp_status fp_workspace_last_pairs(fp_workspace *ws, int64_t *npairs);
 /* Batches: many independent meshes (instances) of different E and N located
  * and interpolated in one launch sequence (the paper posts all meshes of all
  * sessions to one findpts_setup, Sec. 2.1; here independent problems share
- * the device).  Instances of the same N form a group whose geometry, boxes,
- * subdomain ids and fields are copied into group-resident arrays at creation;
- * each run screens every instance against its own hash grid, then solves all
- * candidate pairs of a group with one grid-stride Newton launch, classifies,
- * evaluates and scatters the results back to instance order.  A run never
- * waits on the host, so it can be captured into one CUDA graph.
- *   handles  [ninst] set-up handles (same precision, tolerances and
- *            max_newton); they must outlive the batch
+ * the device).  Instances of the same N form a group whose geometry, boxes
+ * and fields are copied into group-resident arrays at creation.  A run
+ * screens every point against its own instance's hash grid and boxes in one
+ * launch, sorts all candidate pairs by element in one pass, solves each
+ * group's pairs with one persistent Newton launch whose blocks draw work
+ * items (runs of `tile` element-sorted pairs) from a device counter, the
+ * groups' launches running concurrently, classifies every point (with its
+ * own instance's tie band, so each result equals fp_find on that instance
+ * alone) and evaluates the winning pairs, writing the results directly in
+ * instance order.  A run never waits on the host, so it can be captured into
+ * one CUDA graph.
+ *   handles  [ninst] set-up handles on the current device (same precision,
+ *            tolerances and max_newton); they must outlive the batch
  *   npts     [ninst] host array: points per instance (instance i owns points
  *            [sum_{k<i} npts_k, sum_{k<=i} npts_k) of every run)
  *   F        fields per instance (0 = find only)
  *   fields   [ninst] host array of device pointers, instance i's fields laid
  *            out [F][E_i][n_i^3] (NULL when F = 0); copied at creation
- *   pairs_per_point  pair capacity per point of each group (<= 0: 2.0);
+ *   pairs_per_point  pair capacity per point of the whole batch (<= 0: 2.0);
  *            points beyond it come back as FP_CODE_RETRY
- * The tie band of a group uses the largest L of its instances.
  * fp_batch_run: pts [3][Ptot], outputs as fp_find over Ptot points plus
- * out [F][Ptot] (may be NULL).  fp_batch_tune times every Newton schedule
- * (threads per block 64/128/256 x blocks per SM 1/2/4/8) with `reps` runs on
- * the given data, keeps the fastest and returns its time (synchronises).
- * fp_batch_schedule reads (and, for positive inputs, sets) the schedule.
+ * out [F][Ptot] (may be NULL); element ids are instance-local.
+ * fp_batch_tune: per group, times the Newton stage on the given data for
+ * every schedule -- threads per block 64/128/256 x blocks per SM 1/2/4/8
+ * (those that fit), then work items of 1, 4 or 16 blocks' worth of pairs --
+ * keeps the fastest, and caches it for the process by (form, N, log2 E,
+ * log2 pairs): a later batch or call whose group falls in a tuned bucket
+ * takes the cached schedule without timing.  Returns the time of a whole run
+ * with the chosen schedules (synchronises).
+ * fp_batch_schedule reads (and, for positive inputs, sets) one group's
+ * schedule; tile must be a multiple of block.  fp_batch_groups gives the
+ * number of groups; fp_batch_group_info a group's N, elements, points,
+ * candidate pairs of the latest run (synchronises) and the Newton and eval
+ * times (ms) of the latest profiled run (with fp_batch_profile(b, 1), runs
+ * record events around each group's Newton and eval launches and run the
+ * groups one after another on the caller's stream, so that each time is the
+ * group's own; graphs are captured without them) or, for the Newton stage,
+ * of the tuning.  fp_batch_band_hits reads and resets the
+ * batch's near-tie counts (as fp_band_hits).
  * fp_batch_capture records one run on the given buffers into a CUDA graph;
  * fp_batch_launch replays it on `stream` (same buffers, new contents).
  * The batch copies what it needs at creation and owns it; fp_batch_free
  * releases it (NULL is a no-op); fp_batch_last_error gives the text of the
  * batch's last failure.  Errors: fp_batch_create FP_ERR_INVALID_ARG (b NULL,
- * ninst < 1, NULL arrays, F < 0 or fields missing, a NULL, unset or 2D
- * handle, npts < 0, handles whose precision, tolerances or max_newton
- * differ, 2^31 points or more in total), FP_ERR_OOM, FP_ERR_CUDA;
- * fp_batch_run / _tune / _capture FP_ERR_INVALID_ARG (NULL batch or
- * pointer), FP_ERR_CUDA; fp_batch_schedule FP_ERR_INVALID_ARG (NULL batch,
- * a block size that is not a multiple of 32 up to 256); fp_batch_launch
- * FP_ERR_NOT_SETUP (nothing captured), FP_ERR_CUDA. */
+ * ninst < 1, NULL arrays, F < 0 or fields missing, a NULL, unset, 2D or
+ * other-device handle, npts < 0, handles whose precision, tolerances or
+ * max_newton differ, 2^31 points, elements or pairs or more), FP_ERR_OOM,
+ * FP_ERR_CUDA; fp_batch_run / _tune / _capture FP_ERR_INVALID_ARG (NULL batch
+ * or pointer), FP_ERR_CUDA; fp_batch_schedule FP_ERR_INVALID_ARG (NULL batch,
+ * group out of range, a block size that is not a multiple of 32 up to 256, a
+ * tile that is not a multiple of the block); fp_batch_groups /
+ * fp_batch_group_info / fp_batch_profile / fp_batch_band_hits
+ * FP_ERR_INVALID_ARG (NULL batch or pointer, group out of range),
+ * FP_ERR_CUDA; fp_batch_launch FP_ERR_NOT_SETUP (nothing captured),
+ * FP_ERR_CUDA. */
 typedef struct fp_batch fp_batch;
 fp_status fp_batch_create(fp_batch **b, int ninst, fp_handle *const *handles, const int64_t *npts,
                           int F, const double *const *fields, double pairs_per_point);
@@ -271,7 +300,12 @@ fp_status fp_batch_run(fp_batch *b, const double *pts, int32_t *code, int32_t *s
 fp_status fp_batch_tune(fp_batch *b, const double *pts, int32_t *code, int32_t *sub, int32_t *elem,
                         double *rst, double *dist2, double *out, void *stream, int reps,
                         double *best_ms);
-fp_status fp_batch_schedule(fp_batch *b, int *block, int *blocks_per_sm);
+fp_status fp_batch_schedule(fp_batch *b, int group, int *block, int *blocks_per_sm, int *tile);
+fp_status fp_batch_groups(const fp_batch *b, int *ngroups);
+fp_status fp_batch_group_info(fp_batch *b, int group, int *N, int64_t *E, int64_t *P, int64_t *pairs,
+                              double *newton_ms, double *eval_ms);
+fp_status fp_batch_profile(fp_batch *b, int enable);
+fp_status fp_batch_band_hits(fp_batch *b, int64_t *counts);
 fp_status fp_batch_capture(fp_batch *b, const double *pts, int32_t *code, int32_t *sub,
                            int32_t *elem, double *rst, double *dist2, double *out);
 fp_status fp_batch_launch(fp_batch *b, void *stream);
@@ -513,6 +547,13 @@ fp_status fp_profile_read(fp_handle *h, int kind, double *total_ms, int64_t *lau
  * confirmed by the single FP64 step, [3] sent to the full FP64 Newton.
  * Synchronises the device and resets the counters. */
 fp_status fp_newton_paths(fp_handle *h, int64_t *counts);
+
+/* Device bytes the handle holds: *resident = the posted mesh and its search
+ * structures (coordinates and their FP32 copies, boxes, hash grid, distance
+ * field, per-element sort arrays); *workspace = the handle's own fp_find
+ * workspace as grown so far (either pointer may be NULL; allocator rounding
+ * not included).  Errors: FP_ERR_NOT_SETUP. */
+fp_status fp_memory(const fp_handle *h, int64_t *resident, int64_t *workspace);
 
 /* Near-tie ("band") hits of the classification since the previous read
  * (Sec. 2.1 decides INSIDE / BORDER by residual thresholds and the owner by

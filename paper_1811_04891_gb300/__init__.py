@@ -76,8 +76,18 @@ def _load():
     L.fp_batch_run.restype = ci
     L.fp_batch_tune.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, ci, ctypes.POINTER(ctypes.c_double)]
     L.fp_batch_tune.restype = ci
-    L.fp_batch_schedule.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci)]
+    L.fp_batch_schedule.argtypes = [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci)]
     L.fp_batch_schedule.restype = ci
+    L.fp_batch_groups.argtypes = [vp, ctypes.POINTER(ci)]
+    L.fp_batch_groups.restype = ci
+    L.fp_batch_group_info.argtypes = [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                      ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]
+    L.fp_batch_group_info.restype = ci
+    L.fp_batch_profile.argtypes = [vp, ci]
+    L.fp_batch_profile.restype = ci
+    L.fp_batch_band_hits.argtypes = [vp, ctypes.POINTER(i64)]
+    L.fp_batch_band_hits.restype = ci
     L.fp_batch_capture.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     L.fp_batch_capture.restype = ci
     L.fp_batch_launch.argtypes = [vp, vp]
@@ -155,6 +165,10 @@ def _load():
     L.fp_last_find_stats.restype = ci
     L.fp_newton_paths.argtypes = [vp, ctypes.POINTER(i64)]
     L.fp_newton_paths.restype = ci
+    L.fp_workspace_bytes.argtypes = [vp, i64, i64, ctypes.POINTER(i64)]
+    L.fp_workspace_bytes.restype = ci
+    L.fp_memory.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.fp_memory.restype = ci
     L.fp_band_hits.argtypes = [vp, ctypes.POINTER(i64)]
     L.fp_band_hits.restype = ci
     L.fp_fma_probe.argtypes = [ci, i64, ci, vp, ctypes.POINTER(ctypes.c_double), vp]
@@ -381,10 +395,33 @@ class Batch:
         self._chk(lib().fp_batch_tune(self.ptr, *self._args(pts, outs), _stream(stream), int(reps), ctypes.byref(ms)))
         return ms.value
 
-    def schedule(self, block: int = 0, blocks_per_sm: int = 0):
-        b, s = ctypes.c_int(block), ctypes.c_int(blocks_per_sm)
-        self._chk(lib().fp_batch_schedule(self.ptr, ctypes.byref(b), ctypes.byref(s)))
-        return b.value, s.value
+    def schedule(self, group: int = 0, block: int = 0, blocks_per_sm: int = 0, tile: int = 0):
+        """(threads per block, blocks per SM, pairs per work item) of one
+        group's Newton stage; positive arguments set them."""
+        b, s, t = ctypes.c_int(block), ctypes.c_int(blocks_per_sm), ctypes.c_int(tile)
+        self._chk(lib().fp_batch_schedule(self.ptr, int(group), ctypes.byref(b), ctypes.byref(s), ctypes.byref(t)))
+        return b.value, s.value, t.value
+
+    def groups(self) -> int:
+        n = ctypes.c_int()
+        self._chk(lib().fp_batch_groups(self.ptr, ctypes.byref(n)))
+        return n.value
+
+    def group_info(self, group: int) -> dict:
+        N, E, P, pairs = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        tn, te = ctypes.c_double(), ctypes.c_double()
+        self._chk(lib().fp_batch_group_info(self.ptr, int(group), ctypes.byref(N), ctypes.byref(E), ctypes.byref(P),
+                                            ctypes.byref(pairs), ctypes.byref(tn), ctypes.byref(te)))
+        return {"N": N.value, "E": E.value, "P": P.value, "pairs": pairs.value, "newton_ms": tn.value,
+                "eval_ms": te.value}
+
+    def profile(self, enable: bool = True):
+        self._chk(lib().fp_batch_profile(self.ptr, 1 if enable else 0))
+
+    def band_hits(self) -> dict:
+        c = (ctypes.c_int64 * 3)()
+        self._chk(lib().fp_batch_band_hits(self.ptr, c))
+        return {k: int(c[i]) for i, k in enumerate(BAND_KINDS)}
 
     def capture(self, pts, outs):
         pts = _dev(pts, torch.float64, "pts")
@@ -755,6 +792,21 @@ def fp_newton_paths(h: Handle) -> dict:
     return {"rejected_fp32": c[0], "fp32_not_converged": c[1], "fp64_step_converged": c[2], "fallback": c[3]}
 
 
+def fp_workspace_bytes(h: Handle, max_points: int, max_pairs: int = 0) -> int:
+    """Device bytes a workspace of this size holds on the handle's mesh."""
+    b = ctypes.c_int64()
+    _check(lib().fp_workspace_bytes(h.ptr, int(max_points), int(max_pairs), ctypes.byref(b)), h.ptr)
+    return b.value
+
+
+def fp_memory(h: Handle) -> dict:
+    """Device bytes of the handle: the resident mesh and search structures,
+    and its own find workspace."""
+    r, w = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().fp_memory(h.ptr, ctypes.byref(r), ctypes.byref(w)), h.ptr)
+    return {"resident": r.value, "workspace": w.value}
+
+
 BAND_KINDS = ("accept", "border", "owner")
 
 
@@ -886,8 +938,24 @@ def fp_batch_tune(b: Batch, pts: torch.Tensor, outs, reps: int = 2, stream=None)
     return b.tune(pts, outs, reps, stream)
 
 
-def fp_batch_schedule(b: Batch, block: int = 0, blocks_per_sm: int = 0):
-    return b.schedule(block, blocks_per_sm)
+def fp_batch_schedule(b: Batch, group: int = 0, block: int = 0, blocks_per_sm: int = 0, tile: int = 0):
+    return b.schedule(group, block, blocks_per_sm, tile)
+
+
+def fp_batch_groups(b: Batch) -> int:
+    return b.groups()
+
+
+def fp_batch_group_info(b: Batch, group: int) -> dict:
+    return b.group_info(group)
+
+
+def fp_batch_profile(b: Batch, enable: bool = True):
+    b.profile(enable)
+
+
+def fp_batch_band_hits(b: Batch) -> dict:
+    return b.band_hits()
 
 
 def fp_batch_capture(b: Batch, pts: torch.Tensor, outs):

@@ -412,18 +412,27 @@ struct EvalPairsArgs {
     const int32_t* pair_pt;
     const double* prst;
     EvalSpec ev;
+    const int32_t* s_lo;      // batch groups: the group's sorted positions [*s_lo, *s_hi)
+    const int32_t* s_hi;
+    int32_t ebase;            // batch groups: subtracted from pair_elem
 };
 
 template <int n, bool DF>
 __global__ void __launch_bounds__(128) k_eval_pairs(EvalPairsArgs A, BasisTab tab)
 {
-    const int64_t t = *A.dcount;
-    const int64_t npairs = t < A.cap ? t : A.cap;
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < npairs; s += (int64_t)gridDim.x * blockDim.x) {
+    int64_t s0 = 0, s1;
+    if (A.s_lo) {
+        s0 = *A.s_lo;
+        s1 = *A.s_hi;
+    } else {
+        const int64_t t = *A.dcount;
+        s1 = t < A.cap ? t : A.cap;
+    }
+    for (int64_t s = s0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < s1; s += (int64_t)gridDim.x * blockDim.x) {
         const int32_t q = A.order[s];
         const int32_t p = A.pair_pt[q];
         if (p < 0) continue;                              // not the point's winning pair
-        const int e = A.pair_elem[q];
+        const int e = A.pair_elem[q] - A.ebase;
         const double r0 = A.prst[q], r1 = A.prst[A.cap + q], r2 = A.prst[2 * A.cap + q];
         if (DF)
             eval_point_df<n>(A.ev.fdf, A.E, A.ev.F, e, r0, r1, r2, tab, A.ev.out, A.P, p);
@@ -434,9 +443,10 @@ __global__ void __launch_bounds__(128) k_eval_pairs(EvalPairsArgs A, BasisTab ta
 
 cudaError_t launch_eval_pairs(int n, int64_t E, int64_t P, const int32_t* dcount, int64_t cap, const int32_t* order,
                               const int32_t* pair_elem, const int32_t* pair_pt, const double* prst,
-                              const EvalSpec& ev, const BasisTab& tab, unsigned grid, cudaStream_t s)
+                              const EvalSpec& ev, const BasisTab& tab, unsigned grid, cudaStream_t s,
+                              const int32_t* s_lo, const int32_t* s_hi, int32_t ebase)
 {
-    EvalPairsArgs a{E, P, cap, dcount, order, pair_elem, pair_pt, prst, ev};
+    EvalPairsArgs a{E, P, cap, dcount, order, pair_elem, pair_pt, prst, ev, s_lo, s_hi, ebase};
     const bool df = ev.fdf != nullptr;
     switch (n) {
 #define FP_CASE(NN)                                                   \

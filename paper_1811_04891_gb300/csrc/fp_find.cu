@@ -84,10 +84,8 @@ struct ScreenArgs {
 };
 
 template <bool EMIT, bool F32>
-__global__ void __launch_bounds__(256) k_screen(ScreenArgs A)
+__device__ __forceinline__ void screen_point(const ScreenArgs& A, int64_t p)
 {
-    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= A.P) return;
     const int64_t ld = A.stride ? A.stride : A.P;
     const double x = A.pts[p], y = A.pts[ld + p], z = A.pts[2 * ld + p];
     const int tag = A.qsess ? A.qsess[p] : -1;
@@ -128,6 +126,65 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs A)
         }
     }
     if (!EMIT) A.cnt[p] = c;
+}
+
+template <bool EMIT, bool F32>
+__global__ void __launch_bounds__(256) k_screen(ScreenArgs A)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= A.P) return;
+    screen_point<EMIT, F32>(A, p);
+}
+
+// Batches: one thread per point of all instances; the point's instance (the
+// last one whose first point is <= p) gives the hash grid, boxes and element
+// numbering it is screened against.
+template <bool EMIT, bool F32>
+__global__ void __launch_bounds__(256) k_bscreen(BScreenArgs B)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= B.P) return;
+    int lo = 0, hi = B.ninst;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(B.p0 + mid) <= p) lo = mid;
+        else hi = mid;
+    }
+    const BInst& I = B.inst[lo];
+    ScreenArgs A;
+    A.P = B.P;
+    A.pts = B.pts;
+    A.qsess = nullptr;
+    A.sub = I.sub;
+    A.boxes = I.boxes;
+    A.boxes32 = I.boxes32;
+    A.g = I.g;
+    A.cell_start = I.cell_start;
+    A.cell_elems = I.cell_elems;
+    A.cnt = B.cnt;
+    A.off = B.off;
+    A.pair_elem = B.pair_elem;
+    A.pair_pt = B.pair_pt;
+    A.cap = B.cap;
+    A.stride = B.P;
+    A.pt_base = 0;
+    A.elem_base = I.ebase;
+    screen_point<EMIT, F32>(A, p);
+}
+
+cudaError_t launch_bscreen(const BScreenArgs& b, bool emit, bool f32, cudaStream_t s)
+{
+    if (b.P == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((b.P + 255) / 256);
+    if (emit) {
+        if (f32) k_bscreen<true, true><<<grid, 256, 0, s>>>(b);
+        else k_bscreen<true, false><<<grid, 256, 0, s>>>(b);
+    } else {
+        if (f32) k_bscreen<false, true><<<grid, 256, 0, s>>>(b);
+        else k_bscreen<false, false><<<grid, 256, 0, s>>>(b);
+    }
+    count_launch();
+    return cudaGetLastError();
 }
 
 // number of pairs to process: the device-side total, capped by the capacity
@@ -527,15 +584,36 @@ __device__ __forceinline__ void seed_nearest(const ElemPtr<T>& el, const BasisTa
     constexpr int n3 = n * n * n;
     T best = T(INFINITY);
     int bq = 0;
+    if constexpr (sizeof(T) == 4 && n3 % 4 == 0) {
+        // four nodes per 16-byte load (every element's rows start 16-byte aligned)
+        const float4* X0 = reinterpret_cast<const float4*>(el.X0);
+        const float4* X1 = reinterpret_cast<const float4*>(el.X1);
+        const float4* X2 = reinterpret_cast<const float4*>(el.X2);
+#pragma unroll 2
+        for (int q4 = 0; q4 < n3 / 4; ++q4) {
+            const float4 a = __ldg(X0 + q4), b = __ldg(X1 + q4), c = __ldg(X2 + q4);
+            const float ax[4] = {a.x, a.y, a.z, a.w}, bx[4] = {b.x, b.y, b.z, b.w}, cx[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const T dx = ax[m] - xs[0], dy = bx[m] - xs[1], dz = cx[m] - xs[2];
+                const T d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 < best) {
+                    best = d2;
+                    bq = 4 * q4 + m;
+                }
+            }
+        }
+    } else {
 #pragma unroll 4
-    for (int q = 0; q < n3; ++q) {
-        const T dx = __ldg(el.X0 + q) - xs[0];
-        const T dy = __ldg(el.X1 + q) - xs[1];
-        const T dz = __ldg(el.X2 + q) - xs[2];
-        const T d2 = dx * dx + dy * dy + dz * dz;
-        if (d2 < best) {
-            best = d2;
-            bq = q;
+        for (int q = 0; q < n3; ++q) {
+            const T dx = __ldg(el.X0 + q) - xs[0];
+            const T dy = __ldg(el.X1 + q) - xs[1];
+            const T dz = __ldg(el.X2 + q) - xs[2];
+            const T d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 < best) {
+                best = d2;
+                bq = q;
+            }
         }
     }
     const int i = bq % n, j = (bq / n) % n, k = bq / (n * n);
@@ -566,9 +644,52 @@ struct NewtonArgs {
     const int32_t* warm_elem;   // optional [P]: each point's element at the previous mesh position
     const double* warm_rst;     // [3][P]: its reference coordinates there
     int32_t* fb_count;          // mixed form: number of pairs sent to the FP64 fallback (zeroed before)
-    int32_t* fb_list;           // their slots, the first fb_cap of them
-    int64_t fb_cap;
+    int32_t* fb_list;           // their slots, the first fb_cap of them (batch groups: from the group's
+    int64_t fb_cap;             //   first sorted position, capacity = the group's pairs)
+    // batch groups: the group's pairs are the sorted positions [*s_lo, *s_hi)
+    // (null: [0, live pairs)); pair_elem - ebase indexes the group's arrays
+    const int32_t* s_lo;
+    const int32_t* s_hi;
+    int32_t ebase;
+    int32_t* queue;             // work-queue counter (zeroed before the launch); null = grid-stride
+    int tile;                   // sorted positions per work item (a multiple of the block size)
 };
+
+struct PairRange {
+    int64_t s0, s1;
+};
+
+__device__ __forceinline__ PairRange pair_range(const NewtonArgs& A)
+{
+    if (A.s_lo) return {(int64_t)*A.s_lo, (int64_t)*A.s_hi};
+    return {0, live_pairs(A.dcount, A.cap)};
+}
+
+// Visit the sorted pair positions of the range: grid-stride over a fixed
+// grid, or (queue) work items of `tile` consecutive positions that whole
+// blocks draw from a device counter, so a block whose pairs converged fast
+// takes the next item instead of idling (pairs of one element stay together
+// in an item).  The counter only grows; no block waits on another.
+template <typename Fn>
+__device__ __forceinline__ void for_each_pair(const NewtonArgs& A, const PairRange& R, Fn&& fn)
+{
+    if (!A.queue) {
+        for (int64_t s = R.s0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < R.s1;
+             s += (int64_t)gridDim.x * blockDim.x)
+            fn(s);
+        return;
+    }
+    __shared__ int32_t item;
+    for (;;) {
+        if (threadIdx.x == 0) item = atomicAdd(A.queue, 1);
+        __syncthreads();
+        const int64_t t0 = R.s0 + (int64_t)item * A.tile;
+        __syncthreads();                                   // item read by all before it is redrawn
+        if (t0 >= R.s1) break;
+        const int64_t t1 = t0 + A.tile < R.s1 ? t0 + A.tile : R.s1;
+        for (int64_t s = t0 + threadIdx.x; s < t1; s += blockDim.x) fn(s);
+    }
+}
 
 // warm start (moving meshes): a pair whose element is the point's previous
 // element starts from the previous reference coordinates, clamped to the
@@ -592,8 +713,8 @@ __device__ __forceinline__ void solve_pair(const NewtonArgs& A, const BasisTab& 
 {
     constexpr int n3 = n * n * n;
     const int32_t q = A.order[s];
-    const int e = A.pair_elem[q];
-    const int64_t p = A.pair_pt[q];
+    const int e = A.pair_elem[q] - A.ebase;
+    const int64_t p = pair_point(A.pair_pt[q]);
     const double xs[3] = {A.pts[p], A.pts[A.P + p], A.pts[2 * A.P + p]};
     const ElemPtr<double> el64 = {A.coords + (int64_t)e * n3, A.coords + (A.E + e) * n3,
                                   A.coords + (2 * A.E + e) * n3};
@@ -681,6 +802,28 @@ __device__ __forceinline__ void resid_df(const ElemPtr<float>& hi, const ElemPtr
     }
 }
 
+// Threshold of the final step's convergence check on a double-float
+// residual: 1e-13 in r, raised to the rounding level of a step where that is
+// larger.  The residual is accurate to a few units of 2^-48 of the
+// element-local coordinates (|x - c_e| <= h_e), which a step J^-1 f turns
+// into ||J^-1|| times as much in r; 2^-46 h_e ||J^-1||_inf bounds that noise.
+__device__ __forceinline__ double chord_tol_df(const double (&J)[9], double he)
+{
+    const double C00 = J[4] * J[8] - J[5] * J[7], C01 = J[5] * J[6] - J[3] * J[8], C02 = J[3] * J[7] - J[4] * J[6];
+    const double det = J[0] * C00 + J[1] * C01 + J[2] * C02;
+    if (!(fabs(det) > 0.0) || !isfinite(det)) return Lim<double>::chord;
+    const double C10 = J[2] * J[7] - J[1] * J[8], C11 = J[0] * J[8] - J[2] * J[6], C12 = J[1] * J[6] - J[0] * J[7];
+    const double C20 = J[1] * J[5] - J[2] * J[4], C21 = J[2] * J[3] - J[0] * J[5], C22 = J[0] * J[4] - J[1] * J[3];
+    const double rows = fmax(fabs(C00) + fabs(C10) + fabs(C20),
+                             fmax(fabs(C01) + fabs(C11) + fabs(C21), fabs(C02) + fabs(C12) + fabs(C22)));
+    return fmax(Lim<double>::chord, 1.4210854715202004e-14 * he * rows / fabs(det));
+}
+
+// final steps of the mixed form: at most kRefine double-float residuals; a
+// step of at most kConfirm (computed in FP32) is re-solved in FP64
+constexpr int kRefine = 3;
+constexpr double kConfirm = 1e-10;
+
 // passes 1 and 2 in one kernel: the FP32 work of some warps overlaps the
 // FP64 work of others.
 // Launch shape of the mixed Newton kernel.  CAP (one block per 128 pairs,
@@ -693,16 +836,15 @@ template <int n, bool CAP> struct MixedLB {
     static constexpr int blocks = CAP ? 5 : 1;
 };
 
-template <int n, bool CAP>
-__global__ void __launch_bounds__(MixedLB<n, CAP>::threads, MixedLB<n, CAP>::blocks)
-    k_newton_mixed(NewtonArgs A, BasisTab tab)
+template <int n>
+__device__ __forceinline__ void solve_mixed(const NewtonArgs& A, const BasisTab& tab, int64_t s, int32_t* fbl,
+                                            int64_t fbc)
 {
     constexpr int n3 = n * n * n;
-    const int64_t npairs = live_pairs(A.dcount, A.cap);
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < npairs; s += (int64_t)gridDim.x * blockDim.x) {
+    {
         const int32_t q = A.order[s];
-        const int e = A.pair_elem[q];
-        const int64_t p = A.pair_pt[q];
+        const int e = A.pair_elem[q] - A.ebase;
+        const int64_t p = pair_point(A.pair_pt[q]);
         const double xs[3] = {A.pts[p], A.pts[A.P + p], A.pts[2 * A.P + p]};
         const double* c = A.boxes[e].c;
         const double xd[3] = {xs[0] - c[0], xs[1] - c[1], xs[2] - c[2]};
@@ -727,34 +869,56 @@ __global__ void __launch_bounds__(MixedLB<n, CAP>::threads, MixedLB<n, CAP>::blo
             else if ((double)res32 > A.reject32 * A.boxes[e].he) atomicAdd(A.stats + 0, 1ULL);
         }
         if (conv32 && (double)res32 <= A.reject32 * A.boxes[e].he) {
-            // refinement: compensated FP32 residuals, FP32 Jacobian, active-set
-            // step (constrained solutions on a face, edge or vertex too)
-            {
-                const ElemPtr<float> lo32 = {A.coords32lo + (int64_t)e * n3, A.coords32lo + (A.E + e) * n3,
-                                             A.coords32lo + (2 * A.E + e) * n3};
-                for (int it = 0; it < 2; ++it) {
-                    float f[3], d[3];
-                    resid_df<n>(el32, lo32, tab, r, xd, f);
-                    // the active set is decided on r itself: a coordinate just inside
-                    // a bound must not round onto it (it would be frozen off the bound)
-                    const float rf[3] = {f32_inside(r[0]), f32_inside(r[1]), f32_inside(r[2])};
-                    if (gn_step<float>(J32, f, rf, d) == 0) break;
-                    const double dd[3] = {(double)d[0], (double)d[1], (double)d[2]};
+            // Final Newton steps at FP64 accuracy: compensated (double-float)
+            // residuals on the split element-local coordinates, on the FP32
+            // pipes, with the FP32 Jacobian and the active-set step.  A step
+            // that is still large is taken as computed in FP32; once it is
+            // small, the 3x3 solve is repeated in FP64, and an FP64 step within
+            // the tolerance confirms convergence: r is kept with its own
+            // residual (as in chord64).  Unconfirmed after kRefine residuals:
+            // the pair goes to the full FP64 Newton.
+            const ElemPtr<float> lo32 = {A.coords32lo + (int64_t)e * n3, A.coords32lo + (A.E + e) * n3,
+                                         A.coords32lo + (2 * A.E + e) * n3};
+            res = -1.0;
+            for (int it = 0; it < kRefine; ++it) {
+                float f[3], d32[3];
+                resid_df<n>(el32, lo32, tab, r, xd, f);
+                const double fd[3] = {(double)f[0], (double)f[1], (double)f[2]};
+                if (f[0] == 0.0f && f[1] == 0.0f && f[2] == 0.0f) {   // exact hit
+                    res = 0.0;
+                    break;
+                }
+                // the active set is decided on r itself: a coordinate just inside
+                // a bound must not round onto it (it would be frozen off the bound)
+                const float rf[3] = {f32_inside(r[0]), f32_inside(r[1]), f32_inside(r[2])};
+                if (gn_step<float>(J32, f, rf, d32) == 0) {  // KKT point at a vertex
+                    res = sqrt(fd[0] * fd[0] + fd[1] * fd[1] + fd[2] * fd[2]);
+                    break;
+                }
+                double d[3] = {(double)d32[0], (double)d32[1], (double)d32[2]};
+                const bool small = fmaxf(fabsf(d32[0]), fmaxf(fabsf(d32[1]), fabsf(d32[2]))) <= (float)kConfirm;
+                if (small) {
+                    double J[9];
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) J[k] = (double)J32[k];
+                    if (gn_step<double>(J, fd, r, d) == 0) {
+                        res = sqrt(fd[0] * fd[0] + fd[1] * fd[1] + fd[2] * fd[2]);
+                        break;
+                    }
                     double rn[3];
-                    box_step<double>(r, dd, rn);
+                    box_step<double>(r, d, rn);
                     const double sn = fmax(fabs(rn[0] - r[0]), fmax(fabs(rn[1] - r[1]), fabs(rn[2] - r[2])));
+                    if (sn <= chord_tol_df(J, A.boxes[e].he)) {
+                        res = sqrt(fd[0] * fd[0] + fd[1] * fd[1] + fd[2] * fd[2]);
+                        break;
+                    }
                     r[0] = rn[0]; r[1] = rn[1]; r[2] = rn[2];
-                    if (sn <= 1e-14) break;
+                } else {
+                    double rn[3];
+                    box_step<double>(r, d, rn);
+                    r[0] = rn[0]; r[1] = rn[1]; r[2] = rn[2];
                 }
             }
-            // the final Newton step in FP64: FP64 residual, FP64 3x3 solve
-            const ElemPtr<double> el64 = {A.coords + (int64_t)e * n3, A.coords + (A.E + e) * n3,
-                                          A.coords + (2 * A.E + e) * n3};
-            double J[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) J[k] = (double)J32[k];
-            double r64res;
-            res = chord64<n>(el64, tab, xs, r, J, r64res, 1) ? r64res : -1.0;
             if (A.stats) atomicAdd(A.stats + (res < 0.0 ? 3 : 2), 1ULL);
         }
         A.prst[q] = r[0];
@@ -763,9 +927,19 @@ __global__ void __launch_bounds__(MixedLB<n, CAP>::threads, MixedLB<n, CAP>::blo
         A.pres[q] = res;
         if (res < 0.0) {
             const int32_t k = atomicAdd(A.fb_count, 1);
-            if (k < A.fb_cap) A.fb_list[k] = q;
+            if (k < fbc) fbl[k] = q;
         }
     }
+}
+
+template <int n, bool CAP>
+__global__ void __launch_bounds__(MixedLB<n, CAP>::threads, MixedLB<n, CAP>::blocks)
+    k_newton_mixed(NewtonArgs A, BasisTab tab)
+{
+    const PairRange R = pair_range(A);
+    int32_t* fbl = A.fb_list + (A.s_lo ? R.s0 : 0);
+    const int64_t fbc = A.s_lo ? R.s1 - R.s0 : A.fb_cap;
+    for_each_pair(A, R, [&](int64_t s) { solve_mixed<n>(A, tab, s, fbl, fbc); });
 }
 
 // pass 3 (FP64): full trust-region Newton for the pairs marked -1, from the
@@ -783,8 +957,8 @@ template <int n>
 __device__ __forceinline__ void solve_full64(const NewtonArgs& A, const BasisTab& tab, int32_t q)
 {
     constexpr int n3 = n * n * n;
-    const int e = A.pair_elem[q];
-    const int64_t p = A.pair_pt[q];
+    const int e = A.pair_elem[q] - A.ebase;
+    const int64_t p = pair_point(A.pair_pt[q]);
     const double xs[3] = {A.pts[p], A.pts[A.P + p], A.pts[2 * A.P + p]};
     const ElemPtr<double> el64 = {A.coords + (int64_t)e * n3, A.coords + (A.E + e) * n3,
                                   A.coords + (2 * A.E + e) * n3};
@@ -800,14 +974,17 @@ __device__ __forceinline__ void solve_full64(const NewtonArgs& A, const BasisTab
 template <int n>
 __global__ void __launch_bounds__(32) k_newton64_full(NewtonArgs A, BasisTab tab)
 {
+    const PairRange R = pair_range(A);
+    const int32_t* fbl = A.fb_list + (A.s_lo ? R.s0 : 0);
+    const int64_t fbc = A.s_lo ? R.s1 - R.s0 : A.fb_cap;
     const int64_t nfb = *A.fb_count;
-    if (nfb <= A.fb_cap) {
+    if (nfb <= fbc) {
         // one warp (this block) per listed pair
         constexpr int n3 = n * n * n;
         for (int64_t t = blockIdx.x; t < nfb; t += gridDim.x) {
-            const int32_t q = A.fb_list[t];
-            const int e = A.pair_elem[q];
-            const int64_t p = A.pair_pt[q];
+            const int32_t q = fbl[t];
+            const int e = A.pair_elem[q] - A.ebase;
+            const int64_t p = pair_point(A.pair_pt[q]);
             const double xs[3] = {A.pts[p], A.pts[A.P + p], A.pts[2 * A.P + p]};
             const ElemPtr<double> el64 = {A.coords + (int64_t)e * n3, A.coords + (A.E + e) * n3,
                                           A.coords + (2 * A.E + e) * n3};
@@ -825,9 +1002,8 @@ __global__ void __launch_bounds__(32) k_newton64_full(NewtonArgs A, BasisTab tab
     }
     __shared__ int32_t list[kFullSub];
     __shared__ int count;
-    const int64_t npairs = live_pairs(A.dcount, A.cap);
-    for (int64_t base = (int64_t)blockIdx.x * kFullChunk; base < npairs; base += (int64_t)gridDim.x * kFullChunk) {
-        const int64_t cend = base + kFullChunk < npairs ? base + kFullChunk : npairs;
+    for (int64_t base = R.s0 + (int64_t)blockIdx.x * kFullChunk; base < R.s1; base += (int64_t)gridDim.x * kFullChunk) {
+        const int64_t cend = base + kFullChunk < R.s1 ? base + kFullChunk : R.s1;
         for (int64_t sb = base; sb < cend; sb += kFullSub) {
             if (threadIdx.x == 0) count = 0;
             __syncthreads();
@@ -847,9 +1023,8 @@ __global__ void __launch_bounds__(32) k_newton64_full(NewtonArgs A, BasisTab tab
 template <int n>
 __global__ void __launch_bounds__(256) k_newton(NewtonArgs A, BasisTab tab)
 {
-    const int64_t npairs = live_pairs(A.dcount, A.cap);
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < npairs; s += (int64_t)gridDim.x * blockDim.x)
-        solve_pair<n>(A, tab, s);
+    const PairRange R = pair_range(A);
+    for_each_pair(A, R, [&](int64_t s) { solve_pair<n>(A, tab, s); });
 }
 
 // ---------------------------------------------------------------------------
@@ -922,63 +1097,106 @@ cudaError_t find_emit(const FindArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Newton stage (and the mixed form's FP64 fallback) over the pairs of a:
+// all live pairs, or (batch groups, a.s_lo set) the group's sorted range.
+// grid == 0: sized from npairs and the block (persistent when the caller
+// gave persistent_blocks).
 template <int n>
-static cudaError_t solve_n(const FindArgs& a, int64_t npairs, const BasisTab& tab, const FindParams& fp, int block,
-                           cudaStream_t s)
+static cudaError_t newton_n(const FindArgs& a, int64_t npairs, const BasisTab& tab, const FindParams& fp, int block,
+                            unsigned grid, cudaStream_t s)
 {
-    if (npairs > 0) {
-        NewtonArgs na;
-        na.dcount = a.off + a.P;
-        na.E = a.E;
-        na.order = a.order;
-        na.pair_elem = a.pair_elem;
-        na.pair_pt = a.pair_pt;
-        na.P = a.P;
-        na.pts = a.pts;
-        na.coords = a.coords;
-        na.coords32 = a.coords32;
-        na.coords32lo = a.coords32lo;
-        na.boxes = a.boxes;
-        na.pres = a.pres;
-        na.prst = a.prst;
-        na.cap = a.cap;
-        na.reject32 = 1e-4;
-        na.max_newton = fp.max_newton;
-        na.stats = a.stats;
-        na.warm_elem = a.warm_elem;
-        na.warm_rst = a.warm_rst;
-        na.fb_count = nullptr;
-        na.fb_list = nullptr;
-        na.fb_cap = 0;
-        const unsigned grid = grid_for(npairs, block, a.persistent_blocks);
-        if (a.ev[2]) cudaEventRecord(a.ev[2], s);
-        if (fp.mixed) {
+    NewtonArgs na;
+    na.dcount = a.off + a.P;
+    na.E = a.E;
+    na.order = a.order;
+    na.pair_elem = a.pair_elem;
+    na.pair_pt = a.pair_pt;
+    na.P = a.P;
+    na.pts = a.pts;
+    na.coords = a.coords;
+    na.coords32 = a.coords32;
+    na.coords32lo = a.coords32lo;
+    na.boxes = a.boxes;
+    na.pres = a.pres;
+    na.prst = a.prst;
+    na.cap = a.cap;
+    na.reject32 = 1e-4;
+    na.max_newton = fp.max_newton;
+    na.stats = a.stats;
+    na.warm_elem = a.warm_elem;
+    na.warm_rst = a.warm_rst;
+    na.fb_count = nullptr;
+    na.fb_list = nullptr;
+    na.fb_cap = 0;
+    na.s_lo = a.s_lo;
+    na.s_hi = a.s_hi;
+    na.ebase = a.ebase;
+    na.queue = a.queue;
+    na.tile = a.tile > 0 ? a.tile : block;
+    cudaError_t err;
+    if (a.queue && (err = cudaMemsetAsync(a.queue, 0, sizeof(int32_t), s)) != cudaSuccess) return err;
+    if (grid == 0) grid = grid_for(npairs, block, a.persistent_blocks);
+    if (fp.mixed) {
+        if (a.s_lo) {
+            // batch group: its own counter; its list from the group's first sorted position
+            na.fb_count = a.fb_count;
+            na.fb_list = a.fb_list;
+        } else {
             // fallback list: the per-point counts (free after the scan) hold
             // the slots, the first scan scratch word (free after the sort) the count
             na.fb_count = a.scan_tmp;
             na.fb_list = a.cnt;
             na.fb_cap = a.P;
-            cudaError_t e0 = cudaMemsetAsync(a.scan_tmp, 0, sizeof(int32_t), s);
-            if (e0 != cudaSuccess) return e0;
-            bool capped = false;
-            if constexpr (n <= 8) {
-                if (a.persistent_blocks == 0 && block <= 128) {
-                    k_newton_mixed<n, true><<<grid_for(npairs, block, 0), block, 0, s>>>(na, tab);
-                    capped = true;
-                }
-            }
-            if (!capped) k_newton_mixed<n, false><<<grid, block, 0, s>>>(na, tab);
-            // blocks of one warp: enough for a list of up to 38,912 pairs in one
-            // pass, and for the chunked path over every slot if it overflowed
-            const unsigned gfull = (unsigned)std::max<int64_t>(
-                1216, a.persistent_blocks > 0 ? 0 : (npairs + kFullChunk - 1) / kFullChunk);
-            k_newton64_full<n><<<gfull, 32, 0, s>>>(na, tab);
-            count_launch(2);
-        } else {
-            k_newton<n><<<grid, block, 0, s>>>(na, tab);
-            count_launch();
         }
-        cudaError_t err = cudaGetLastError();
+        if ((err = cudaMemsetAsync(na.fb_count, 0, sizeof(int32_t), s)) != cudaSuccess) return err;
+        bool capped = false;
+        if constexpr (n <= 8) {
+            if (block <= 128 && (a.persistent_blocks == 0 || a.queue)) {
+                const unsigned g = a.persistent_blocks == 0 && !a.queue ? grid_for(npairs, block, 0) : grid;
+                k_newton_mixed<n, true><<<g, block, 0, s>>>(na, tab);
+                capped = true;
+            }
+        }
+        if (!capped) k_newton_mixed<n, false><<<grid, block, 0, s>>>(na, tab);
+        // blocks of one warp: enough for a list of up to 38,912 pairs in one
+        // pass, and for the chunked path over every slot if it overflowed
+        const unsigned gfull = (unsigned)std::max<int64_t>(
+            1216, a.persistent_blocks > 0 || a.s_lo ? 0 : (npairs + kFullChunk - 1) / kFullChunk);
+        k_newton64_full<n><<<gfull, 32, 0, s>>>(na, tab);
+        count_launch(2);
+    } else {
+        k_newton<n><<<grid, block, 0, s>>>(na, tab);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+// Few pairs (a launch of fewer than two blocks per SM at `block` threads):
+// smaller blocks, down to one warp, so that every SM gets work.  The block
+// size changes only the schedule, not any pair's result.
+static int spread_block(int64_t npairs, int block)
+{
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0, k = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&k, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && k > 0)
+            nsm = k;
+        else
+            return block;
+    }
+    while (block > 32 && (npairs + block - 1) / block < 2 * nsm) block >>= 1;
+    return block;
+}
+
+template <int n>
+static cudaError_t solve_n(const FindArgs& a, int64_t npairs, const BasisTab& tab, const FindParams& fp, int block,
+                           cudaStream_t s)
+{
+    if (npairs > 0) {
+        if (a.ev[2]) cudaEventRecord(a.ev[2], s);
+        if (a.persistent_blocks == 0) block = spread_block(npairs, block);
+        cudaError_t err = newton_n<n>(a, npairs, tab, fp, block, 0, s);
         if (err != cudaSuccess) return err;
         if (a.ev[3]) cudaEventRecord(a.ev[3], s);
     }
@@ -1048,6 +1266,51 @@ cudaError_t find_solve(const FindArgs& a, int64_t npairs, const BasisTab& tab, c
         FP_CASE(10) FP_CASE(11) FP_CASE(12) FP_CASE(13) FP_CASE(14) FP_CASE(15) FP_CASE(16)
 #undef FP_CASE
         default: return cudaErrorInvalidValue;
+    }
+}
+
+// Newton stage of one order-n group of a batch (a.s_lo / a.s_hi / a.ebase
+// set), on `grid` blocks of `block` threads drawing work items of a.tile
+// sorted positions from the counter a.queue.
+cudaError_t find_newton_group(const FindArgs& a, const BasisTab& tab, const FindParams& fp, int block, unsigned grid,
+                              cudaStream_t s)
+{
+    switch (a.n) {
+#define FP_CASE(NN) \
+    case NN: return newton_n<NN>(a, a.cap, tab, fp, block, grid, s);
+        FP_CASE(2) FP_CASE(3) FP_CASE(4) FP_CASE(5) FP_CASE(6) FP_CASE(7) FP_CASE(8) FP_CASE(9)
+        FP_CASE(10) FP_CASE(11) FP_CASE(12) FP_CASE(13) FP_CASE(14) FP_CASE(15) FP_CASE(16)
+#undef FP_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Blocks of `block` threads of the Newton kernel a group of order n - 1
+// would launch (find_newton_group) that fit one SM at once.
+template <int n>
+static int newton_fit(bool mixed, int block)
+{
+    int k = 0;
+    cudaError_t e;
+    if (!mixed) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_newton<n>, block, 0);
+    } else if (n <= 8 && block <= 128) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_newton_mixed<n, true>, block, 0);
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_newton_mixed<n, false>, block, 0);
+    }
+    return e == cudaSuccess ? k : 1;
+}
+
+int newton_blocks_per_sm(int n, bool mixed, int block)
+{
+    switch (n) {
+#define FP_CASE(NN) \
+    case NN: return newton_fit<NN>(mixed, block);
+        FP_CASE(2) FP_CASE(3) FP_CASE(4) FP_CASE(5) FP_CASE(6) FP_CASE(7) FP_CASE(8) FP_CASE(9)
+        FP_CASE(10) FP_CASE(11) FP_CASE(12) FP_CASE(13) FP_CASE(14) FP_CASE(15) FP_CASE(16)
+#undef FP_CASE
+        default: return 1;
     }
 }
 

@@ -677,7 +677,7 @@ __global__ void __launch_bounds__(256) k_newton2(Newton2Args A, BasisTab tab)
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < npairs; s += (int64_t)gridDim.x * blockDim.x) {
         const int32_t q = A.order[s];
         const int e = A.pair_elem[q];
-        const int64_t p = A.pair_pt[q];
+        const int64_t p = pair_point(A.pair_pt[q]);
         const double xs[2] = {A.pts[p], A.pts[A.P + p]};
         const double* X0 = A.coords + (int64_t)e * n2;
         const double* X1 = A.coords + (A.E + e) * n2;

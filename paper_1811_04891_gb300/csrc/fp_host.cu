@@ -792,6 +792,17 @@ fp_status fp_workspace_create(const fp_handle* h, int64_t max_points, int64_t ma
     return FP_OK;
 }
 
+fp_status fp_workspace_bytes(const fp_handle* h, int64_t max_points, int64_t max_pairs, int64_t* bytes)
+{
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
+    if (!bytes || max_points < 1 || max_points >= (int64_t(1) << 31)) return FP_ERR_INVALID_ARG;
+    if (max_pairs <= 0) max_pairs = 2 * max_points;
+    if (max_pairs >= (int64_t(1) << 31)) return FP_ERR_INVALID_ARG;
+    *bytes = 4 * max_points + 4 * (max_points + 1) + 4 * std::max(scan_tmp_elems(max_points), scan_tmp_elems(h->E)) +
+             max_pairs * (4 + 4 + 4 + 8 + 24) + 4 * h->E + 4 * (h->E + 1);
+    return FP_OK;
+}
+
 void fp_workspace_free(fp_workspace* w)
 {
     if (!w) return;
@@ -1110,6 +1121,26 @@ fp_status fp_newton_paths(fp_handle* h, int64_t* counts)
         if (e != cudaSuccess) return cuda_fail(h, e, "fp_newton_paths");
     }
     for (int k = 0; k < 4; ++k) counts[k] = (int64_t)c[k];
+    return FP_OK;
+}
+
+fp_status fp_memory(const fp_handle* h, int64_t* resident, int64_t* workspace)
+{
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
+    const int64_t n3 = h->dim == 2 ? (int64_t)h->n * h->n : (int64_t)h->n * h->n * h->n;
+    const int64_t nc = h->dim * h->E * n3;
+    if (resident) {
+        int64_t b = 8 * nc + 4 * h->E + (int64_t)sizeof(ElemBox) * h->E + 48 * h->E + 4 * (h->ncell_cap + 1) +
+                    4 * h->ncell_cap + 4 * scan_tmp_elems(h->ncell_cap) + 4 * h->nnz_cap + 8 * (int64_t)h->n * h->n +
+                    96 * (int64_t)h->nred + 4 * h->E + 4 * (h->E + 1);
+        if (h->dist) b += 8 * h->E * n3;
+        if (h->coords32) b += 8 * nc + (int64_t)sizeof(ElemBox32) * h->E;
+        *resident = b;
+    }
+    if (workspace)
+        *workspace = 4 * h->cap_pts + 4 * (h->cap_pts + 1) +
+                     4 * (h->cap_pts > 0 ? std::max(scan_tmp_elems(h->cap_pts), scan_tmp_elems(h->E)) : 0) +
+                     h->cap_pairs * (4 + 4 + 4 + 8 + 24);
     return FP_OK;
 }
 

@@ -92,6 +92,15 @@ struct FindArgs {
     unsigned long long* band;     // optional near-tie counters (3 words, see fp_rank.cuh), null = off
     const int32_t* warm_elem;     // optional warm start: previous element [P] (null = off)
     const double* warm_rst;       // and previous reference coordinates [3][P]
+    // batch groups (fp_batch.cu): the group's pairs are the sorted positions
+    // [*s_lo, *s_hi); pair_elem - ebase indexes the group's arrays
+    const int32_t* s_lo;
+    const int32_t* s_hi;
+    int32_t ebase;
+    int32_t* queue;               // Newton work-queue counter (zeroed by the launcher), null = grid-stride
+    int tile;                     // sorted positions per work item (0: one block's worth)
+    int32_t* fb_count;            // mixed form, batch groups: fallback counter and list (group slice
+    int32_t* fb_list;             //   from the group's first sorted position)
     // outputs
     int32_t* code;
     int32_t* osub;
@@ -106,6 +115,11 @@ cudaError_t find_solve(const FindArgs& a, int64_t npairs, const BasisTab& tab, c
                        int block, cudaStream_t s);
 cudaError_t find_solve_unsorted(const FindArgs& a, int64_t npairs, const BasisTab& tab, const FindParams& fp,
                                 int block, cudaStream_t s);
+struct BScreenArgs;
+cudaError_t launch_bscreen(const BScreenArgs& b, bool emit, bool f32, cudaStream_t s);
+int newton_blocks_per_sm(int n, bool mixed, int block);
+cudaError_t find_newton_group(const FindArgs& a, const BasisTab& tab, const FindParams& fp, int block, unsigned grid,
+                              cudaStream_t s);
 
 // host streaming state of fp_find_eval_host (fp_stream.cu), freed with the handle
 }  // namespace fpg
@@ -138,9 +152,11 @@ cudaError_t launch_eval2(int n, int64_t E, int64_t P, const int32_t* code, const
                          int F, const double* fields, double* out, const BasisTab& tab, cudaStream_t s);
 
 // eval (fp_eval.cu)
+// s_lo / s_hi / ebase: batch groups, as in FindArgs (null: all live pairs)
 cudaError_t launch_eval_pairs(int n, int64_t E, int64_t P, const int32_t* dcount, int64_t cap, const int32_t* order,
                               const int32_t* pair_elem, const int32_t* pair_pt, const double* prst,
-                              const EvalSpec& ev, const BasisTab& tab, unsigned grid, cudaStream_t s);
+                              const EvalSpec& ev, const BasisTab& tab, unsigned grid, cudaStream_t s,
+                              const int32_t* s_lo = nullptr, const int32_t* s_hi = nullptr, int32_t ebase = 0);
 cudaError_t launch_split_df(int64_t n, const double* src, float2* dst, cudaStream_t s);
 cudaError_t launch_eval_df(int n, int64_t E, int64_t P, const int32_t* code, const int32_t* elem, const double* rst,
                            int F, const float2* fields, double* out, const BasisTab& tab, cudaStream_t s);

@@ -43,6 +43,13 @@ struct RankArgs {
 //                largest (the lower-id rule decided, or nearly did)
 enum { BAND_ACCEPT = 0, BAND_BORDER = 1, BAND_OWNER = 2, BAND_KINDS = 3 };
 
+// mark a pair that does not carry its point's result (see pair_point)
+__device__ __forceinline__ void mark_loser(int32_t* pp)
+{
+    const int32_t v = *pp;
+    if (v >= 0) *pp = ~v;
+}
+
 // D^k interpolated at (e, r) of a DIM-dimensional element (D: n^DIM values)
 template <int n, int DIM>
 __device__ __forceinline__ double interp_delta(const double* __restrict__ D, const BasisTab& tab, const double* prst,
@@ -70,16 +77,16 @@ __device__ __forceinline__ double interp_delta(const double* __restrict__ D, con
     }
 }
 
-// one thread per point; rst and prst hold DIM rows
-template <int n, int DIM>
-__global__ void __launch_bounds__(128) k_rank(RankArgs A, FindParams fp, BasisTab tab)
+// The decisions for point p (rst and prst hold DIM rows).  The context C
+// gives the per-element data: he(e) (h_e), sub(e), has_dist() and
+// delta(e, q) (D^k interpolated at pair q's r), and elem_out(e) (the element
+// id written out).
+template <int DIM, class Ctx>
+__device__ __forceinline__ void rank_point(const RankArgs& A, const FindParams& fp, const Ctx& C, int64_t p)
 {
-    constexpr int n3 = DIM == 2 ? n * n : n * n * n;
-    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= A.P) return;
     const int b = A.off[p], en = A.off[p + 1];
     if (en > A.cap) {                                  // pairs dropped: not searched
-        for (int q = b; q < A.cap; ++q) A.pair_pt[q] = -1;
+        for (int q = b; q < A.cap; ++q) mark_loser(A.pair_pt + q);
         for (int f = 0; f < A.F; ++f) A.out[(int64_t)f * A.P + p] = __longlong_as_double(0x7ff8000000000000ULL);
         A.code[p] = FP_CODE_RETRY;
         A.osub[p] = -1;
@@ -95,16 +102,16 @@ __global__ void __launch_bounds__(128) k_rank(RankArgs A, FindParams fp, BasisTa
     double bmin = INFINITY;
     for (int q = b; q < en; ++q) {
         const int e = A.pair_elem[q];
-        const double he = A.boxes[e].he;
+        const double he = C.he(e);
         const double res = A.pres[q];
         if (res >= 0.5 * fp.tol_accept * he && res <= 2.0 * fp.tol_accept * he) hit |= 1u << BAND_ACCEPT;
         if (res >= 0.5 * fp.tol_border * he && res <= 2.0 * fp.tol_border * he) near_border = true;
         if (res <= fp.tol_accept * he) {
-            const int s = A.sub[e];
+            const int s = C.sub(e);
             bool winner = true;
             for (int q2 = b; q2 < en && winner; ++q2) {
                 const int e2 = A.pair_elem[q2];
-                if (q2 != q && A.sub[e2] == s && e2 < e && A.pres[q2] <= fp.tol_accept * A.boxes[e2].he) winner = false;
+                if (q2 != q && C.sub(e2) == s && e2 < e && A.pres[q2] <= fp.tol_accept * C.he(e2)) winner = false;
             }
             if (winner) {
                 ++nwin;
@@ -127,16 +134,16 @@ __global__ void __launch_bounds__(128) k_rank(RankArgs A, FindParams fp, BasisTa
             int bs = 0x7fffffff;
             for (int q = b; q < en; ++q) {
                 const int e = A.pair_elem[q];
-                if (!(A.pres[q] <= fp.tol_accept * A.boxes[e].he)) continue;
-                const int s = A.sub[e];
+                if (!(A.pres[q] <= fp.tol_accept * C.he(e))) continue;
+                const int s = C.sub(e);
                 bool winner = true;
                 for (int q2 = b; q2 < en && winner; ++q2) {
                     const int e2 = A.pair_elem[q2];
-                    if (q2 != q && A.sub[e2] == s && e2 < e && A.pres[q2] <= fp.tol_accept * A.boxes[e2].he)
+                    if (q2 != q && C.sub(e2) == s && e2 < e && A.pres[q2] <= fp.tol_accept * C.he(e2))
                         winner = false;
                 }
                 if (!winner) continue;
-                const double dl = A.dist ? interp_delta<n, DIM>(A.dist + (int64_t)e * n3, tab, A.prst, A.cap, q) : 0.0;
+                const double dl = C.has_dist() ? C.delta(e, q) : 0.0;
                 if (pass == 0) {
                     dmax = fmax(dmax, dl);
                 } else {
@@ -154,7 +161,7 @@ __global__ void __launch_bounds__(128) k_rank(RankArgs A, FindParams fp, BasisTa
         int be = 0x7fffffff, ntie = 0;
         for (int q = b; q < en; ++q) {
             const int e = A.pair_elem[q];
-            const double he = A.boxes[e].he;
+            const double he = C.he(e);
             const double res = A.pres[q];
             if (res > fp.tol_accept * he && res <= fp.tol_border * he && res <= bmin + fp.band) {
                 ++ntie;
@@ -174,14 +181,14 @@ __global__ void __launch_bounds__(128) k_rank(RankArgs A, FindParams fp, BasisTa
             if (hit & (1u << k)) atomicAdd(A.band + k, 1ULL);
     }
     for (int q = b; q < en; ++q)
-        if (q != pick) A.pair_pt[q] = -1;
+        if (q != pick) mark_loser(A.pair_pt + q);
     if (pick < 0)
         for (int f = 0; f < A.F; ++f) A.out[(int64_t)f * A.P + p] = __longlong_as_double(0x7ff8000000000000ULL);
     if (pick >= 0) {
         const int e = A.pair_elem[pick];
         A.code[p] = code;
-        A.osub[p] = A.sub[e];
-        A.oelem[p] = e;
+        A.osub[p] = C.sub(e);
+        A.oelem[p] = C.elem_out(e);
         for (int a = 0; a < DIM; ++a) A.rst[a * A.P + p] = A.prst[a * A.cap + pick];
         const double res = A.pres[pick];
         A.dist2[p] = res * res;
@@ -192,6 +199,32 @@ __global__ void __launch_bounds__(128) k_rank(RankArgs A, FindParams fp, BasisTa
         for (int a = 0; a < DIM; ++a) A.rst[a * A.P + p] = 0.0;
         A.dist2[p] = INFINITY;
     }
+}
+
+// element data of one mesh (a handle)
+template <int n, int DIM>
+struct RankMesh {
+    static constexpr int n3 = DIM == 2 ? n * n : n * n * n;
+    const RankArgs& A;
+    const BasisTab& tab;
+    __device__ __forceinline__ double he(int e) const { return A.boxes[e].he; }
+    __device__ __forceinline__ int sub(int e) const { return A.sub[e]; }
+    __device__ __forceinline__ bool has_dist() const { return A.dist != nullptr; }
+    __device__ __forceinline__ double delta(int e, int64_t q) const
+    {
+        return interp_delta<n, DIM>(A.dist + (int64_t)e * n3, tab, A.prst, A.cap, q);
+    }
+    __device__ __forceinline__ int elem_out(int e) const { return e; }
+};
+
+// one thread per point
+template <int n, int DIM>
+__global__ void __launch_bounds__(128) k_rank(RankArgs A, FindParams fp, BasisTab tab)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= A.P) return;
+    const RankMesh<n, DIM> C{A, tab};
+    rank_point<DIM>(A, fp, C, p);
 }
 
 }  // namespace fpg

@@ -1,19 +1,27 @@
 """Serving loop: point-location / interpolation requests against resident meshes.
 
 The mesh, its hash grid and the fields stay resident on the device (one
-handle).  Requests of uneven size arrive over time.  The server keeps `slots`
-execution slots; each slot owns a CUDA stream, an fp_workspace and device /
-pinned-host buffers for up to `slot_points` points.  How many slots may hold
-work at once is set by the device-memory budget: budget minus the resident
-mesh and fields, divided by the bytes one slot holds.
+handle).  Requests of uneven size arrive over time and are served with
+continuous batching under a device-memory budget:
 
-Continuous batching: whenever a slot is free, the dispatcher packs the oldest
-pending work into it -- whole small requests, or the next chunk of a large
-one -- copies the points in from pinned memory, runs fp_find_ws + fp_eval on
-the slot's stream, and copies the codes and values back.  Requests that
-arrive while other slots are on the GPU are admitted as soon as a slot (and
-its memory) frees up, so their work overlaps on the device.  A request is
-complete when all its chunks are; its latency is completion minus arrival.
+* Work is cut into chunks of at most `chunk_points` points: whole small
+  requests packed together, or bounded pieces of a large one, taken in
+  arrival order.
+* A chunk holds device memory while it is in flight -- its points, tags,
+  outputs and values, and an fp_workspace for its candidate pairs (bytes from
+  chunk_bytes / fp_workspace_bytes).  It is admitted only when those bytes fit
+  in what is left of the budget: budget - resident mesh - chunks in flight.
+  With less room than a full chunk, a smaller chunk (never below
+  `min_chunk` points, or the whole head request if smaller) is admitted
+  instead; with less than that, the pending work waits until a chunk
+  completes and frees its memory ("held back").
+* Admitted chunks run on a pool of CUDA streams (copy in from pinned memory,
+  fp_find_eval_ws, copy out), so the work of requests that arrived at
+  different times overlaps on the device.  Buffers and workspaces are kept in
+  pools by capacity (a power of two) and reused; the pools never hold more
+  than the largest set of chunks the budget has let run at once.
+* A request completes when all its chunks are back; latency = completion -
+  arrival.
 
 Every point is located and interpolated independently of what else shares
 its launch, so a request's results are the same alone and in the mix.
@@ -23,7 +31,7 @@ from __future__ import annotations
 import collections
 import time
 from dataclasses import dataclass, field
-from typing import List, Optional
+from typing import Dict, List, Optional
 
 import numpy as np
 import torch
@@ -50,28 +58,46 @@ class Request:
         return int(self.pts.shape[1])
 
 
-def slot_bytes(slot_points: int, F: int) -> int:
-    """Device + pinned-host bytes one slot holds for `slot_points` points and
-    F fields: points, tags, the five outputs and values on both sides, plus
-    the workspace's per-point scan arrays and 4 pairs per point of pair
-    records (element, point, order, residual, r)."""
-    return slot_points * (24 + 4 + 24 + 4 * 3 + 8 + 8 * F) + 2 * slot_points * (4 * 3 + 8 + 24) + \
-        slot_points * 12
+def io_bytes(n: int, F: int) -> int:
+    """Device bytes of a chunk's own buffers for n points and F fields:
+    points (24), tags (4), code / sub / elem (12), r (24), dist^2 (8) and the
+    values (8 F) per point."""
+    return n * (24 + 4 + 12 + 24 + 8 + 8 * F)
 
 
-def slots_for_budget(slots: int, slot_points: int, F: int, budget_bytes: float, resident_bytes: float) -> int:
-    """Memory-budget admission: how many slots may hold work at once -- the
-    budget left after the resident mesh and fields, divided by the bytes of
-    one slot, at least one and at most `slots`."""
-    avail = max(0.0, budget_bytes - resident_bytes)
-    return max(1, min(slots, int(avail // slot_bytes(slot_points, F))))
+def chunk_capacity(n: int, chunk_points: int) -> int:
+    """Buffer class of a chunk of n points: the next power of two, at most
+    chunk_points (chunks are never larger)."""
+    c = 1
+    while c < n:
+        c <<= 1
+    return min(c, chunk_points)
+
+
+def admit(pending, chunk_points: int, min_chunk: int, avail: float, bytes_for) -> int:
+    """Memory-budget admission of the next chunk: the points to take now from
+    the head of `pending` -- a full chunk when its bytes fit in `avail`,
+    else the largest power-of-two capacity that fits (at least min_chunk
+    points, or the rest of the pending work if that is smaller), else 0 (the
+    work waits).  bytes_for(capacity) gives the device bytes a chunk of that
+    capacity holds."""
+    want = min(chunk_points, sum(r.P - r.next_pt for r in pending))
+    if want <= 0:
+        return 0
+    cap = chunk_capacity(want, chunk_points)
+    floor = min(want, min_chunk)
+    while cap > 1 and bytes_for(cap) > avail:
+        cap >>= 1
+    if bytes_for(cap) > avail or cap < floor:
+        return 0
+    return min(want, cap)
 
 
 def pack_pending(pending: "collections.deque", capacity: int, copy_in) -> tuple:
-    """Continuous batching: take the oldest pending work into one slot of
-    `capacity` points -- whole requests while they fit, then the next chunk of
-    the request at the head.  copy_in(req, lo, slot_lo, n) copies points
-    [lo, lo + n) of req to slot positions [slot_lo, slot_lo + n).  Requests
+    """Continuous batching: take the oldest pending work into one chunk of
+    `capacity` points -- whole requests while they fit, then the next piece
+    of the request at the head.  copy_in(req, lo, slot_lo, n) copies points
+    [lo, lo + n) of req to chunk positions [slot_lo, slot_lo + n).  Requests
     whose last point is taken leave `pending`.  Returns (pieces, points used),
     pieces = [(request, req_lo, slot_lo, n)]."""
     n_used = 0
@@ -90,7 +116,7 @@ def pack_pending(pending: "collections.deque", capacity: int, copy_in) -> tuple:
 
 
 def scatter_results(pieces, code, elem, rst, values, now: float, completed: list):
-    """Copy one slot's results (code, elem [n], rst [3][n], values [F][n],
+    """Copy one chunk's results (code, elem [n], rst [3][n], values [F][n],
     host arrays) back to the requests its pieces came from; a request whose
     every point is back is stamped `now` and appended to `completed`."""
     for req, lo, so, take in pieces:
@@ -105,8 +131,10 @@ def scatter_results(pieces, code, elem, rst, values, now: float, completed: list
 
 
 @dataclass
-class _Slot:
-    stream: torch.cuda.Stream
+class _Buffers:
+    """Device and pinned-host buffers and a workspace for chunks of up to
+    `cap` points."""
+    cap: int
     ws: "fg.Workspace"
     pts_h: torch.Tensor
     qs_h: torch.Tensor
@@ -118,44 +146,57 @@ class _Slot:
     elem_h: torch.Tensor
     rst_h: torch.Tensor
     val_h: torch.Tensor
+
+
+@dataclass
+class _Chunk:
+    buf: _Buffers
+    stream: torch.cuda.Stream
     event: torch.cuda.Event
+    n: int
+    nbytes: int
     pieces: list = field(default_factory=list)   # (request, req_lo, slot_lo, n)
-    busy: bool = False
 
 
 class Server:
-    def __init__(self, handle, fields: torch.Tensor, slots: int = 4, slot_points: int = 1 << 20,
-                 budget_bytes: float = 40e9, resident_bytes: float = 0.0, device=None, posted=None):
+    def __init__(self, handle, fields: torch.Tensor, budget_bytes: float = 40e9, resident_bytes: float = 0.0,
+                 chunk_points: int = 1 << 17, streams: int = 4, min_chunk: int = 1 << 12, pairs_per_point: int = 4,
+                 device=None, posted=None):
+        """handle: the resident mesh; fields [F][E][n^3] FP64 on the device
+        (or `posted` double-float fields for the mixed form);
+        budget_bytes: device memory the resident state and all chunks in
+        flight may hold together; resident_bytes: what the resident state
+        holds (fields, posted copies and anything else besides the handle's
+        own mesh, which fp_memory counts)."""
         self.h = handle
         self.fields = fields
         self.posted = posted                  # fg.Fields (double-float) or None for FP64 eval
         self.F = int(fields.shape[0])
         self.dev = device or fields.device
-        self.slot_bytes = slot_bytes(slot_points, self.F)
-        self.max_slots = slots_for_budget(slots, slot_points, self.F, budget_bytes, resident_bytes)
-        self.slot_points = slot_points
-        self.slots: List[_Slot] = []
-        for _ in range(self.max_slots):
-            P = slot_points
-            d = self.dev
-            outs = (torch.empty(P, dtype=torch.int32, device=d), torch.empty(P, dtype=torch.int32, device=d),
-                    torch.empty(P, dtype=torch.int32, device=d), torch.empty((3, P), dtype=torch.float64, device=d),
-                    torch.empty(P, dtype=torch.float64, device=d))
-            self.slots.append(_Slot(
-                stream=torch.cuda.Stream(device=d), ws=fg.Workspace(handle, P, 4 * P),
-                pts_h=torch.empty((3, P), dtype=torch.float64).pin_memory(),
-                qs_h=torch.empty(P, dtype=torch.int32).pin_memory(),
-                pts_d=torch.empty((3, P), dtype=torch.float64, device=d),
-                qs_d=torch.empty(P, dtype=torch.int32, device=d), outs=outs,
-                val_d=torch.empty((self.F, P), dtype=torch.float64, device=d),
-                code_h=torch.empty(P, dtype=torch.int32).pin_memory(),
-                elem_h=torch.empty(P, dtype=torch.int32).pin_memory(),
-                rst_h=torch.empty((3, P), dtype=torch.float64).pin_memory(),
-                val_h=torch.empty((self.F, P), dtype=torch.float64).pin_memory(),
-                event=torch.cuda.Event()))
+        self.chunk_points = int(chunk_points)
+        self.min_chunk = int(min_chunk)
+        self.pairs_per_point = int(pairs_per_point)
+        self.resident = float(resident_bytes) + fg.fp_memory(handle)["resident"]
+        self.budget = float(budget_bytes)
+        self.avail_total = self.budget - self.resident
+        if self.avail_total < self.bytes_for(min(self.min_chunk, self.chunk_points)):
+            raise ValueError("memory budget leaves no room for one chunk beside the resident state")
+        self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(max(1, int(streams)))]
+        self.free_streams = list(self.streams)
+        self.pool: Dict[int, List[_Buffers]] = collections.defaultdict(list)
+        self.inflight: List[_Chunk] = []
+        self.inflight_bytes = 0
+        self.peak_inflight_bytes = 0
+        self.held_back = 0                    # passes where work waited for memory with a stream free
         self.pending = collections.deque()
         self.completed: List[Request] = []
         self.launches = 0
+        self.chunk_sizes: List[int] = []
+
+    def bytes_for(self, cap: int) -> int:
+        """Device bytes a chunk of capacity `cap` holds: its buffers and its
+        workspace."""
+        return io_bytes(cap, self.F) + fg.fp_workspace_bytes(self.h, cap, self.pairs_per_point * cap)
 
     # -- request side ---------------------------------------------------------
     def submit(self, req: Request):
@@ -167,57 +208,90 @@ class Server:
         self.pending.append(req)
 
     # -- device side ------------------------------------------------------------
-    def _fill(self, slot: _Slot) -> int:
+    def _buffers(self, cap: int) -> _Buffers:
+        if self.pool[cap]:
+            return self.pool[cap].pop()
+        d, P, F = self.dev, cap, self.F
+        outs = (torch.empty(P, dtype=torch.int32, device=d), torch.empty(P, dtype=torch.int32, device=d),
+                torch.empty(P, dtype=torch.int32, device=d), torch.empty((3, P), dtype=torch.float64, device=d),
+                torch.empty(P, dtype=torch.float64, device=d))
+        return _Buffers(
+            cap=cap, ws=fg.Workspace(self.h, P, self.pairs_per_point * P),
+            pts_h=torch.empty((3, P), dtype=torch.float64).pin_memory(),
+            qs_h=torch.empty(P, dtype=torch.int32).pin_memory(),
+            pts_d=torch.empty((3, P), dtype=torch.float64, device=d),
+            qs_d=torch.empty(P, dtype=torch.int32, device=d), outs=outs,
+            val_d=torch.empty((F, P), dtype=torch.float64, device=d),
+            code_h=torch.empty(P, dtype=torch.int32).pin_memory(),
+            elem_h=torch.empty(P, dtype=torch.int32).pin_memory(),
+            rst_h=torch.empty((3, P), dtype=torch.float64).pin_memory(),
+            val_h=torch.empty((F, P), dtype=torch.float64).pin_memory())
+
+    def _launch(self, n: int):
+        cap = chunk_capacity(n, self.chunk_points)
+        buf = self._buffers(cap)
+        stream = self.free_streams.pop()
+
         def copy_in(req, lo, so, take):
-            slot.pts_h[:, so:so + take].numpy()[...] = req.pts[:, lo:lo + take]
-            slot.qs_h[so:so + take].numpy()[...] = req.qsess[lo:lo + take]
-        slot.pieces, n_used = pack_pending(self.pending, self.slot_points, copy_in)
-        return n_used
-
-    def _launch(self, slot: _Slot, n: int):
+            buf.pts_h[:, so:so + take].numpy()[...] = req.pts[:, lo:lo + take]
+            buf.qs_h[so:so + take].numpy()[...] = req.qsess[lo:lo + take]
+        pieces, n_used = pack_pending(self.pending, n, copy_in)
         F = self.F
-        with torch.cuda.stream(slot.stream):
-            # packed [3][n] / [F][n] views of the slot's buffers
-            pts_c = slot.pts_d.view(-1)[:3 * n].view(3, n)
-            rst_c = slot.outs[3].view(-1)[:3 * n].view(3, n)
-            val_c = slot.val_d.view(-1)[:F * n].view(F, n)
+        with torch.cuda.stream(stream):
+            # packed [3][n] / [F][n] views of the buffers
+            pts_c = buf.pts_d.view(-1)[:3 * n_used].view(3, n_used)
+            rst_c = buf.outs[3].view(-1)[:3 * n_used].view(3, n_used)
+            val_c = buf.val_d.view(-1)[:F * n_used].view(F, n_used)
             for a in range(3):
-                pts_c[a].copy_(slot.pts_h[a, :n], non_blocking=True)
-            qs_d = slot.qs_d[:n]
-            qs_d.copy_(slot.qs_h[:n], non_blocking=True)
-            code, osub, elem, d2 = slot.outs[0][:n], slot.outs[1][:n], slot.outs[2][:n], slot.outs[4][:n]
-            fg.fp_find_eval_ws(self.h, slot.ws, pts_c, qs_d, fields=self.fields, posted=self.posted,
-                               out=(code, osub, elem, rst_c, d2), values=val_c, stream=slot.stream)
-            slot.code_h[:n].copy_(code, non_blocking=True)
-            slot.elem_h[:n].copy_(elem, non_blocking=True)
-            slot.rst_h.view(-1)[:3 * n].copy_(rst_c.view(-1), non_blocking=True)
-            slot.val_h.view(-1)[:F * n].copy_(val_c.view(-1), non_blocking=True)
-            slot.event.record(slot.stream)
-        slot.busy = True
-        slot.n = n
+                pts_c[a].copy_(buf.pts_h[a, :n_used], non_blocking=True)
+            qs_d = buf.qs_d[:n_used]
+            qs_d.copy_(buf.qs_h[:n_used], non_blocking=True)
+            code, osub, elem, d2 = buf.outs[0][:n_used], buf.outs[1][:n_used], buf.outs[2][:n_used], \
+                buf.outs[4][:n_used]
+            fg.fp_find_eval_ws(self.h, buf.ws, pts_c, qs_d, fields=self.fields, posted=self.posted,
+                               out=(code, osub, elem, rst_c, d2), values=val_c, stream=stream)
+            buf.code_h[:n_used].copy_(code, non_blocking=True)
+            buf.elem_h[:n_used].copy_(elem, non_blocking=True)
+            buf.rst_h.view(-1)[:3 * n_used].copy_(rst_c.view(-1), non_blocking=True)
+            buf.val_h.view(-1)[:F * n_used].copy_(val_c.view(-1), non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        nbytes = self.bytes_for(cap)
+        self.inflight.append(_Chunk(buf=buf, stream=stream, event=ev, n=n_used, nbytes=nbytes, pieces=pieces))
+        self.inflight_bytes += nbytes
+        self.peak_inflight_bytes = max(self.peak_inflight_bytes, self.inflight_bytes)
         self.launches += 1
+        self.chunk_sizes.append(n_used)
 
-    def _harvest(self, slot: _Slot, now: float):
-        n = slot.n
-        rst_h = slot.rst_h.view(-1)[:3 * n].view(3, n).numpy()
-        val_h = slot.val_h.view(-1)[:self.F * n].view(self.F, n).numpy()
-        scatter_results(slot.pieces, slot.code_h[:n].numpy(), slot.elem_h[:n].numpy(), rst_h, val_h, now,
+    def _harvest(self, ch: _Chunk, now: float):
+        n = ch.n
+        rst_h = ch.buf.rst_h.view(-1)[:3 * n].view(3, n).numpy()
+        val_h = ch.buf.val_h.view(-1)[:self.F * n].view(self.F, n).numpy()
+        scatter_results(ch.pieces, ch.buf.code_h[:n].numpy(), ch.buf.elem_h[:n].numpy(), rst_h, val_h, now,
                         self.completed)
-        slot.pieces = []
-        slot.busy = False
+        self.pool[ch.buf.cap].append(ch.buf)
+        self.free_streams.append(ch.stream)
+        self.inflight_bytes -= ch.nbytes
 
     def step(self, now: float) -> bool:
-        """One dispatcher pass: harvest finished slots, refill free ones.
-        Returns True if any slot is busy or work is pending."""
-        for slot in self.slots:
-            if slot.busy and slot.event.query():
-                self._harvest(slot, now)
-        for slot in self.slots:
-            if not slot.busy and self.pending:
-                n = self._fill(slot)
-                if n:
-                    self._launch(slot, n)
-        return any(s.busy for s in self.slots) or bool(self.pending)
+        """One dispatcher pass: harvest finished chunks (freeing their memory
+        and streams), then admit chunks while a stream is free and the budget
+        has room.  Returns True if any chunk is in flight or work is pending."""
+        still = []
+        for ch in self.inflight:
+            if ch.event.query():
+                self._harvest(ch, now)
+            else:
+                still.append(ch)
+        self.inflight = still
+        while self.pending and self.free_streams:
+            n = admit(self.pending, self.chunk_points, self.min_chunk, self.avail_total - self.inflight_bytes,
+                      self.bytes_for)
+            if n == 0:
+                self.held_back += 1
+                break
+            self._launch(n)
+        return bool(self.inflight) or bool(self.pending)
 
 
 def run_stream(server: Server, requests: List[Request], time_scale: float = 1.0):

@@ -97,14 +97,26 @@ def test_batch_tune_and_graph_replay(fg):
     outs = batch.outputs()
     ms = batch.tune(allp, outs, reps=1)
     assert ms > 0
-    blk, bps = batch.schedule()
-    assert blk in (64, 128, 256) and bps in (1, 2, 4, 8)
+    scheds = []
+    for g in range(batch.groups()):
+        blk, bps, tile = batch.schedule(g)
+        assert blk in (64, 128, 256) and bps in (1, 2, 4, 8) and tile // blk in (1, 4, 16) and tile % blk == 0
+        scheds.append((blk, bps, tile))
+        info = batch.group_info(g)
+        assert info["N"] in (5, 7, 9) and info["pairs"] >= info["P"] > 0 and info["newton_ms"] > 0
+    # a second batch over the same instances takes the cached schedules
+    again = fg.Batch(handles, [p.shape[1] for p in pts], fields)
+    again.tune(allp, again.outputs(), reps=1)
+    assert [again.schedule(g) for g in range(again.groups())] == scheds
     ref = [x.clone() for x in batch.run(allp, batch.outputs())]
     batch.capture(allp, outs)
     for x in outs:
         x.zero_()
+    k0 = fg.fp_launch_count()
     batch.launch()
     torch.cuda.synchronize()
+    # one graph: screen, scan, emit, sort, per group Newton (+ fallback) and eval, classification
+    assert fg.fp_launch_count() - k0 <= 12 + 3 * batch.groups()
     for a, b in zip(ref, outs):
         assert torch.equal(a, b)
     # new contents in the captured input buffer
@@ -113,3 +125,42 @@ def test_batch_tune_and_graph_replay(fg):
     batch.launch()
     torch.cuda.synchronize()
     _check_against_single(fg, insts, handles, fields, pts2, outs)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_with_overlapping_subdomains(fg, prec):
+    """Instances with several subdomains (the owner rule, each instance with
+    its own tie band) beside single-subdomain ones: every result equals the
+    instance's own fp_find bit for bit and the oracle's at the tolerances."""
+    dev = torch.device("cuda:0")
+    overlap = synth.tiny_overlap(N=4)
+    annulus, _ = synth.box_annulus(n_az=12, n_rad=2, n_ax=3, box_shape=(6, 3, 3), N=5)
+    plain = synth.Mesh(coords=synth.box_mesh((3, 2, 2), 5, amp_frac=0.1), N=5, sub=np.zeros(12, np.int32))
+    meshes = [overlap, annulus, plain]
+    rng = np.random.default_rng(41)
+    xs = np.concatenate([rng.uniform(-0.05, 2.05, 700), [0.8, 0.8, 1.0]])
+    pts = [np.stack([xs, rng.uniform(0.02, 0.98, xs.size), rng.uniform(0.02, 0.98, xs.size)]),
+           np.stack([rng.uniform(0.0, 2.0, 900), rng.uniform(0.0, 1.0, 900), rng.uniform(0.0, 1.0, 900)]),
+           synth.uniform_points(500, seed=42)]
+    handles = [fg.fp_setup(torch.from_numpy(m.coords).to(dev), m.N, torch.from_numpy(m.sub).to(dev),
+                           None if m.dist is None else torch.from_numpy(m.dist).to(dev),
+                           opts=fg.default_opts(precision=prec)) for m in meshes]
+    batch = fg.Batch(handles, [p.shape[1] for p in pts])
+    allp = torch.from_numpy(np.ascontiguousarray(np.concatenate(pts, axis=1))).to(dev)
+    outs = [x.cpu().numpy() for x in batch.run(allp, batch.outputs())]
+    off = np.concatenate([[0], np.cumsum([p.shape[1] for p in pts])])
+    for k, (m, h) in enumerate(zip(meshes, handles)):
+        sl = slice(off[k], off[k + 1])
+        single = [x.cpu().numpy() for x in fg.fp_find(h, torch.from_numpy(np.ascontiguousarray(pts[k])).to(dev))]
+        for a, b in zip(outs[:4], single[:4]):
+            np.testing.assert_array_equal(a[..., sl], b)
+        np.testing.assert_array_equal(outs[4][sl], single[4])
+        ref = oracle.find(m.coords, m.N, m.sub, pts[k], dist=m.dist)
+        np.testing.assert_array_equal(outs[0][sl], ref["code"])
+        np.testing.assert_array_equal(outs[1][sl], ref["sub"])
+        np.testing.assert_array_equal(outs[2][sl], ref["elem"])
+        found = ref["code"] != oracle.NOT_FOUND
+        assert np.abs(outs[3][:, sl][:, found] - ref["rst"][:, found]).max() <= TOL_RST[prec]
+    assert set(np.unique(outs[1][off[1]:off[2]][outs[0][off[1]:off[2]] == 0])) == {0, 1}
+    # the two points at x = 0.8 tie between the first and second box (lower id wins)
+    assert batch.band_hits()["owner"] == 2

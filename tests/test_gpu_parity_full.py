@@ -79,6 +79,8 @@ def test_full_size_bench_configuration(full, prec):
     res = np.abs(x - q.pts).max()
     assert res <= TOL_MAP[prec], f"max |x(e, r) - x*| = {res:.3e}"
     assert np.isfinite(out).all()
+    # no decision of either call fell near a threshold or a tie band
+    assert fg.fp_band_hits(h) == {"accept": 0, "border": 0, "owner": 0}
     del h
 
 
@@ -129,4 +131,5 @@ def test_full_size_batched_configuration(batch_full, prec):
         x = oracle.evaluate(mesh.N, code[lo:hi], elem[lo:hi], rst[:, lo:hi], mesh.coords)
         worst_map = max(worst_map, float(np.abs(x - q.pts).max()))
     assert worst_map <= TOL_MAP_BATCH[prec], f"max |x(e, r) - x*| = {worst_map:.3e}"
+    assert b.band_hits() == {"accept": 0, "border": 0, "owner": 0}
     del b, handles

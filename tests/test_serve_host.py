@@ -11,14 +11,87 @@ import pytest
 from paper_1811_04891_gb300 import serve
 
 
-def test_slots_for_budget():
-    P, F = 1 << 20, 5
-    b = serve.slot_bytes(P, F)
-    assert b == P * (24 + 4 + 24 + 12 + 8 + 8 * F) + 2 * P * (12 + 8 + 24) + 12 * P
-    assert serve.slots_for_budget(4, P, F, 10 * b, 0) == 4                 # capped by the slots asked for
-    assert serve.slots_for_budget(8, P, F, 3.5 * b + 1e9, 1e9) == 3        # what the budget leaves
-    assert serve.slots_for_budget(4, P, F, 1e9, 2e9) == 1                  # never fewer than one
-    assert serve.slots_for_budget(4, P, F, 0.5 * b, 0) == 1
+def test_chunk_capacity_and_io_bytes():
+    assert [serve.chunk_capacity(n, 1 << 17) for n in (1, 2, 3, 4096, 4097, 1 << 17, 10 ** 6)] == \
+        [1, 2, 4, 4096, 8192, 1 << 17, 1 << 17]
+    assert serve.io_bytes(1000, 4) == 1000 * (24 + 4 + 12 + 24 + 8 + 32)
+
+
+class _Q:
+    def __init__(self, P, taken=0):
+        self.P, self.next_pt = P, taken
+
+
+def test_admit_by_memory():
+    per = 100                                   # bytes per point of capacity
+    bf = lambda cap: per * cap + 1000           # noqa: E731
+    big = collections.deque([_Q(10 ** 6)])
+    # room for a full chunk: a full chunk
+    assert serve.admit(big, 1 << 17, 1 << 12, bf(1 << 17), bf) == 1 << 17
+    # room for less: the largest power of two that fits, not below min_chunk
+    assert serve.admit(big, 1 << 17, 1 << 12, bf(1 << 15) + 5, bf) == 1 << 15
+    assert serve.admit(big, 1 << 17, 1 << 12, bf(1 << 12) - 1, bf) == 0        # held back
+    # a small head request is admitted whole when its capacity fits
+    small = collections.deque([_Q(300)])
+    assert serve.admit(small, 1 << 17, 1 << 12, bf(512), bf) == 300
+    assert serve.admit(small, 1 << 17, 1 << 12, bf(512) - 1, bf) == 0          # 256 < the request
+    # several requests: their total, up to a chunk
+    many = collections.deque([_Q(3000), _Q(5000, 1000), _Q(100)])
+    assert serve.admit(many, 1 << 17, 1 << 12, 1e12, bf) == 3000 + 4000 + 100
+    assert serve.admit(collections.deque(), 1 << 17, 1 << 12, 1e12, bf) == 0
+
+
+def test_budget_holds_work_back_and_every_request_gets_its_results():
+    """A fake device with memory accounting: chunks are admitted only while
+    their bytes fit the budget, requests that arrive while memory is taken
+    wait and are admitted when chunks complete, and every request gets back
+    exactly its own points' results."""
+    rng = np.random.default_rng(7)
+    per = 100
+    bf = lambda cap: per * cap                  # noqa: E731
+    chunk, min_chunk = 1 << 12, 1 << 8
+    avail = 2.5 * bf(chunk)                     # two full chunks, or one and smaller ones
+    reqs = [_request(i, float(i), int(P), rng) for i, P in enumerate(rng.integers(1, 3 * chunk, 60))]
+    pending, completed, inflight = collections.deque(), [], []
+    held = peak = 0
+    arrivals = list(reqs)
+    tick = 0
+    while arrivals or pending or inflight:
+        tick += 1
+        for _ in range(int(rng.integers(0, 4))):
+            if arrivals:
+                pending.append(arrivals.pop(0))
+        keep = []
+        for c in inflight:                       # chunks complete in random order
+            if rng.random() < 0.4:
+                code, elem, rst, values = _device(c["pts"][:, :c["n"]], c["qs"][:c["n"]])
+                serve.scatter_results(c["pieces"], code, elem, rst, values, float(tick), completed)
+            else:
+                keep.append(c)
+        inflight = keep
+        while pending and len(inflight) < 4:
+            used = sum(bf(c["cap"]) for c in inflight)
+            n = serve.admit(pending, chunk, min_chunk, avail - used, bf)
+            if n == 0:
+                held += 1
+                break
+            cap = serve.chunk_capacity(n, chunk)
+            c = {"cap": cap, "pts": np.zeros((3, cap)), "qs": np.zeros(cap, np.int32)}
+
+            def copy_in(req, lo, so, take, c=c):
+                c["pts"][:, so:so + take] = req.pts[:, lo:lo + take]
+                c["qs"][so:so + take] = req.qsess[lo:lo + take]
+            c["pieces"], c["n"] = serve.pack_pending(pending, n, copy_in)
+            assert c["n"] == n <= cap
+            inflight.append(c)
+            peak = max(peak, sum(bf(x["cap"]) for x in inflight))
+        assert tick < 100000
+    assert peak <= avail and held > 0
+    assert sorted(r.rid for r in completed) == list(range(len(reqs)))
+    for r in reqs:
+        code, elem, rst, values = _device(r.pts, r.qsess)
+        np.testing.assert_array_equal(r.code, code)
+        np.testing.assert_array_equal(r.values, values)
 
 
 def _request(rid, t, P, rng):
