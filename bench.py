@@ -505,6 +505,7 @@ def run_batched(args, fg, dev, barrier, max_over_ranks, world, peaks):
                 row["newton_roofline_frac"] = t / (gi["newton_ms"] / 1e3)
             per_order[f"N{gi['N']}"] = row
         out[form] = {"value": world * P / (ms / 1e3), "ms_per_step": ms, "tuned_ms": tuned_ms, "tune_s": tune_s,
+                     "groups_sequential": bool(b.mode()),
                      "gpu_launches": launches, "per_order": per_order, "band_hits_per_step": band,
                      "codes": {"inside": codes[0], "border": codes[1], "not_found": codes[2], "retry": codes[3]}}
         del b, handles

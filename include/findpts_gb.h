@@ -241,7 +241,7 @@ fp_status fp_workspace_last_pairs(fp_workspace *ws, int64_t *npairs);
  * and fields are copied into group-resident arrays at creation.  A run
  * screens every point against its own instance's hash grid and boxes in one
  * launch, sorts all candidate pairs by element in one pass, solves each
- * group's pairs with one persistent Newton launch whose blocks draw work
+ * group's pairs with one persistent Newton launch whose warps draw work
  * items (runs of `tile` element-sorted pairs) from a device counter, the
  * groups' launches running concurrently, classifies every point (with its
  * own instance's tie band, so each result equals fp_find on that instance
@@ -261,13 +261,14 @@ fp_status fp_workspace_last_pairs(fp_workspace *ws, int64_t *npairs);
  * out [F][Ptot] (may be NULL); element ids are instance-local.
  * fp_batch_tune: per group, times the Newton stage on the given data for
  * every schedule -- threads per block 64/128/256 x blocks per SM 1/2/4/8
- * (those that fit), then work items of 1, 4 or 16 blocks' worth of pairs --
+ * (those that fit), then work items of 32, 128 or 512 pairs per warp --
  * keeps the fastest, and caches it for the process by (form, N, log2 E,
  * log2 pairs): a later batch or call whose group falls in a tuned bucket
- * takes the cached schedule without timing.  Returns the time of a whole run
- * with the chosen schedules (synchronises).
+ * takes the cached schedule without timing.  It then times whole runs with
+ * the groups' launches concurrent and one after another, keeps the faster
+ * mode, and returns that run's time (synchronises).
  * fp_batch_schedule reads (and, for positive inputs, sets) one group's
- * schedule; tile must be a multiple of block.  fp_batch_groups gives the
+ * schedule; tile must be a multiple of 32.  fp_batch_groups gives the
  * number of groups; fp_batch_group_info a group's N, elements, points,
  * candidate pairs of the latest run (synchronises) and the Newton and eval
  * times (ms) of the latest profiled run (with fp_batch_profile(b, 1), runs
@@ -287,7 +288,7 @@ fp_status fp_workspace_last_pairs(fp_workspace *ws, int64_t *npairs);
  * FP_ERR_CUDA; fp_batch_run / _tune / _capture FP_ERR_INVALID_ARG (NULL batch
  * or pointer), FP_ERR_CUDA; fp_batch_schedule FP_ERR_INVALID_ARG (NULL batch,
  * group out of range, a block size that is not a multiple of 32 up to 256, a
- * tile that is not a multiple of the block); fp_batch_groups /
+ * tile that is not a multiple of 32); fp_batch_groups /
  * fp_batch_group_info / fp_batch_profile / fp_batch_band_hits
  * FP_ERR_INVALID_ARG (NULL batch or pointer, group out of range),
  * FP_ERR_CUDA; fp_batch_launch FP_ERR_NOT_SETUP (nothing captured),
@@ -302,6 +303,12 @@ fp_status fp_batch_tune(fp_batch *b, const double *pts, int32_t *code, int32_t *
                         double *best_ms);
 fp_status fp_batch_schedule(fp_batch *b, int group, int *block, int *blocks_per_sm, int *tile);
 fp_status fp_batch_groups(const fp_batch *b, int *ngroups);
+/* Whether the groups' Newton and eval launches run concurrently on their
+ * own streams (0) or one after another (1): *sequential = -1 reads the mode,
+ * 0 or 1 sets it first (fp_batch_tune sets it to the faster).  Captured
+ * graphs keep the mode they were captured with.  Errors: FP_ERR_INVALID_ARG
+ * (NULL pointer, another value). */
+fp_status fp_batch_mode(fp_batch *b, int *sequential);
 fp_status fp_batch_group_info(fp_batch *b, int group, int *N, int64_t *E, int64_t *P, int64_t *pairs,
                               double *newton_ms, double *eval_ms);
 fp_status fp_batch_profile(fp_batch *b, int enable);

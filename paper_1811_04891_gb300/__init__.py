@@ -78,6 +78,8 @@ def _load():
     L.fp_batch_tune.restype = ci
     L.fp_batch_schedule.argtypes = [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci)]
     L.fp_batch_schedule.restype = ci
+    L.fp_batch_mode.argtypes = [vp, ctypes.POINTER(ci)]
+    L.fp_batch_mode.restype = ci
     L.fp_batch_groups.argtypes = [vp, ctypes.POINTER(ci)]
     L.fp_batch_groups.restype = ci
     L.fp_batch_group_info.argtypes = [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(i64), ctypes.POINTER(i64),
@@ -401,6 +403,13 @@ class Batch:
         b, s, t = ctypes.c_int(block), ctypes.c_int(blocks_per_sm), ctypes.c_int(tile)
         self._chk(lib().fp_batch_schedule(self.ptr, int(group), ctypes.byref(b), ctypes.byref(s), ctypes.byref(t)))
         return b.value, s.value, t.value
+
+    def mode(self, sequential: int = -1) -> int:
+        """1 when the groups' launches run one after another, 0 when
+        concurrently; 0 or 1 sets the mode first."""
+        m = ctypes.c_int(int(sequential))
+        self._chk(lib().fp_batch_mode(self.ptr, ctypes.byref(m)))
+        return m.value
 
     def groups(self) -> int:
         n = ctypes.c_int()
@@ -940,6 +949,10 @@ def fp_batch_tune(b: Batch, pts: torch.Tensor, outs, reps: int = 2, stream=None)
 
 def fp_batch_schedule(b: Batch, group: int = 0, block: int = 0, blocks_per_sm: int = 0, tile: int = 0):
     return b.schedule(group, block, blocks_per_sm, tile)
+
+
+def fp_batch_mode(b: Batch, sequential: int = -1) -> int:
+    return b.mode(sequential)
 
 
 def fp_batch_groups(b: Batch) -> int:

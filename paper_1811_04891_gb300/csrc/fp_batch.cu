@@ -12,7 +12,7 @@
 //   k_bscreen (emit)    (point, batch element) pairs in point order
 //   sort                counting sort of all pairs by batch element, so each
 //                       group's pairs are one contiguous range of positions
-//   Newton, per group   a persistent launch whose blocks draw work items of
+//   Newton, per group   a persistent launch whose warps draw work items of
 //                       `tile` sorted positions from a device counter (the
 //                       groups' launches run concurrently on their own
 //                       streams); mixed form: its FP64 fallback after it
@@ -47,7 +47,7 @@ namespace {
 struct Sched {
     int block = 128;      // Newton threads per block
     int bps = 4;          // Newton blocks per SM (persistent grid)
-    int tile = 512;       // sorted positions per work item
+    int tile = 128;       // sorted positions per work item (one warp's)
 };
 
 struct Group {
@@ -233,9 +233,11 @@ struct fp_batch {
     int32_t* fb_list = nullptr;
     int32_t* gcount = nullptr;    // [2 * groups]: Newton work-queue counter, fallback counter
     double *pres = nullptr, *prst = nullptr;
+    double2* pstate = nullptr;    // FP64 form: state of solves paused by the first Newton pass
     unsigned long long* band = nullptr;
     cudaEvent_t fork = nullptr, fork2 = nullptr;
     bool prof = false;
+    bool sequential = false;      // groups' Newton / eval launches one after another on the run's stream
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -255,7 +257,7 @@ static void batch_release(fp_batch* b)
     release(b->d_inst); release(b->d_p0); release(b->d_rinst); release(b->d_rgrp); release(b->he_all);
     release(b->sub_all); release(b->cnt); release(b->off); release(b->scan_tmp); release(b->pair_elem);
     release(b->pair_pt); release(b->order); release(b->ecount); release(b->estart); release(b->fb_list);
-    release(b->gcount); release(b->pres); release(b->prst); release(b->band);
+    release(b->gcount); release(b->pres); release(b->prst); release(b->pstate); release(b->band);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->fork2) cudaEventDestroy(b->fork2);
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -452,6 +454,7 @@ extern "C" fp_status fp_batch_create(fp_batch** out, int ninst, fp_handle* const
         if (e == cudaSuccess) e = alloc(&b->gcount, 2 * ng);
         if (e == cudaSuccess) e = alloc(&b->pres, b->cap);
         if (e == cudaSuccess) e = alloc(&b->prst, 3 * b->cap);
+        if (e == cudaSuccess && !b->mixed) e = alloc(&b->pstate, b->cap);
         if (e == cudaSuccess) e = alloc(&b->band, 3);
         if (e == cudaSuccess) e = cudaMemset(b->band, 0, 3 * sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
@@ -504,6 +507,7 @@ static FindArgs group_args(const fp_batch* b, const Group& g, const double* pts)
     a.queue = b->gcount + 2 * gi;
     a.fb_count = b->gcount + 2 * gi + 1;
     a.fb_list = b->fb_list;
+    a.pstate = b->pstate;
     a.tile = g.sched.tile;
     a.persistent_blocks = g.sched.bps * b->nsm;
     return a;
@@ -556,12 +560,13 @@ static cudaError_t batch_run(fp_batch* b, const double* pts, int32_t* code, int3
     if ((e = cudaEventRecord(b->fork, s)) != cudaSuccess) return e;
     for (auto& g : b->groups) {
         if (g.P == 0) continue;
-        cudaStream_t gs = b->prof ? s : g.st;
-        if (!b->prof && (e = cudaStreamWaitEvent(gs, b->fork, 0)) != cudaSuccess) return e;
+        const bool serial = b->prof || b->sequential;
+        cudaStream_t gs = serial ? s : g.st;
+        if (!serial && (e = cudaStreamWaitEvent(gs, b->fork, 0)) != cudaSuccess) return e;
         if (b->prof) cudaEventRecord(g.t[0], gs);
         if ((e = group_newton(b, g, pts, gs)) != cudaSuccess) return e;
         if (b->prof) cudaEventRecord(g.t[1], gs);
-        if (!b->prof) {
+        if (!serial) {
             if ((e = cudaEventRecord(g.done, gs)) != cudaSuccess) return e;
             if ((e = cudaStreamWaitEvent(s, g.done, 0)) != cudaSuccess) return e;
         }
@@ -597,15 +602,16 @@ static cudaError_t batch_run(fp_batch* b, const double* pts, int32_t* code, int3
     if ((e = cudaEventRecord(b->fork2, s)) != cudaSuccess) return e;
     for (auto& g : b->groups) {
         if (g.P == 0) continue;
-        cudaStream_t gs = b->prof ? s : g.st;
-        if (!b->prof && (e = cudaStreamWaitEvent(gs, b->fork2, 0)) != cudaSuccess) return e;
+        const bool serial = b->prof || b->sequential;
+        cudaStream_t gs = serial ? s : g.st;
+        if (!serial && (e = cudaStreamWaitEvent(gs, b->fork2, 0)) != cudaSuccess) return e;
         if (b->prof) cudaEventRecord(g.t[2], gs);
         const EvalSpec ev{b->F, g.fields_df ? nullptr : g.fields, g.fields_df, out};
         e = launch_eval_pairs(g.n, g.E, P, nullptr, b->cap, b->order, b->pair_elem, b->pair_pt, b->prst, ev, g.tab,
                               (unsigned)(4 * b->nsm), gs, b->estart + g.ebase, b->estart + g.ebase + g.E, g.ebase);
         if (e != cudaSuccess) return e;
         if (b->prof) cudaEventRecord(g.t[3], gs);
-        if (!b->prof) {
+        if (!serial) {
             if ((e = cudaEventRecord(g.done2, gs)) != cudaSuccess) return e;
             if ((e = cudaStreamWaitEvent(s, g.done2, 0)) != cudaSuccess) return e;
         }
@@ -701,7 +707,7 @@ extern "C" fp_status fp_batch_tune(fp_batch* b, const double* pts, int32_t* code
             const int fit = std::max(1, newton_blocks_per_sm(g.n, b->mixed, blk));
             for (int bps : {1, 2, 4, 8}) {
                 if (bps > 2 * fit || e != cudaSuccess) continue;
-                Sched c{blk, bps, 4 * blk};
+                Sched c{blk, bps, 128};
                 float ms = 0.0f;
                 e = time_group(g, c, &ms);
                 if (e == cudaSuccess && ms < best_t) {
@@ -710,10 +716,10 @@ extern "C" fp_status fp_batch_tune(fp_batch* b, const double* pts, int32_t* code
                 }
             }
         }
-        for (int m : {1, 16}) {
+        for (int t : {32, 512}) {
             if (e != cudaSuccess) break;
             Sched c = best;
-            c.tile = m * best.block;
+            c.tile = t;
             float ms = 0.0f;
             e = time_group(g, c, &ms);
             if (e == cudaSuccess && ms < best_t) {
@@ -727,14 +733,27 @@ extern "C" fp_status fp_batch_tune(fp_batch* b, const double* pts, int32_t* code
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = best;
     }
-    // the whole run with the chosen schedules
-    float total = 0.0f;
-    if (e == cudaSuccess) e = batch_run(b, pts, code, sub, elem, rst, dist2, out, s);
-    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-    for (int k = 0; k < reps && e == cudaSuccess; ++k) e = batch_run(b, pts, code, sub, elem, rst, dist2, out, s);
-    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&total, e0, e1);
+    // the whole run with the chosen schedules, the groups concurrently on
+    // their streams or one after another (the persistent launches of one
+    // group can hold every SM, leaving nothing for the others to overlap):
+    // the faster of the two is kept
+    float total = INFINITY;
+    bool best_seq = false;
+    for (int mode = 0; mode < 2 && e == cudaSuccess; ++mode) {
+        b->sequential = mode == 1;
+        float t = 0.0f;
+        e = batch_run(b, pts, code, sub, elem, rst, dist2, out, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int k = 0; k < reps && e == cudaSuccess; ++k) e = batch_run(b, pts, code, sub, elem, rst, dist2, out, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e == cudaSuccess && t < total) {
+            total = t;
+            best_seq = b->sequential;
+        }
+    }
+    b->sequential = best_seq;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     b->prof = prof;
@@ -755,15 +774,22 @@ extern "C" fp_status fp_batch_schedule(fp_batch* b, int group, int* block, int* 
     }
     if (blocks_per_sm && *blocks_per_sm > 0) n.bps = std::min(*blocks_per_sm, 64);
     if (tile && *tile > 0) {
-        if (*tile % n.block != 0) return bfail(b, FP_ERR_INVALID_ARG, "fp_batch_schedule: tile");
+        if (*tile % 32 != 0) return bfail(b, FP_ERR_INVALID_ARG, "fp_batch_schedule: tile");
         n.tile = *tile;
-    } else if (n.tile % n.block != 0) {
-        n.tile = 4 * n.block;
     }
     c = n;
     if (block) *block = c.block;
     if (blocks_per_sm) *blocks_per_sm = c.bps;
     if (tile) *tile = c.tile;
+    return FP_OK;
+}
+
+extern "C" fp_status fp_batch_mode(fp_batch* b, int* sequential)
+{
+    if (!b || !sequential) return FP_ERR_INVALID_ARG;
+    if (*sequential == 0 || *sequential == 1) b->sequential = *sequential == 1;
+    else if (*sequential != -1) return bfail(b, FP_ERR_INVALID_ARG, "fp_batch_mode: -1, 0 or 1");
+    *sequential = b->sequential ? 1 : 0;
     return FP_OK;
 }
 

@@ -18,6 +18,8 @@ struct BasisTab {
     double ci[NMAX];
     float xif[NMAX];
     float cif[NMAX];
+    float xil[NMAX];    // low parts: xi = xif + xil, ci = cif + cil to about 48 bits
+    float cil[NMAX];
 };
 
 // Per-element search data (FP64), built once by the hull kernel.
@@ -312,6 +314,27 @@ __device__ __forceinline__ void df_norm(df& a)
     const float t = a.hi + a.lo;
     a.lo = a.lo - (t - a.hi);
     a.hi = t;
+}
+
+// a * b: exact leading product plus the cross terms, renormalised
+__device__ __forceinline__ df df_mul(df a, df b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    const float s = p + e;
+    return {s, e - (s - p)};
+}
+
+// a - b: error-free two-sum of the leading parts, then the low parts
+__device__ __forceinline__ df df_sub(df a, df b)
+{
+    const float s = a.hi - b.hi;
+    const float bb = s - a.hi;
+    const float err = (a.hi - (s - bb)) + (-b.hi - bb);
+    const float lo = err + (a.lo - b.lo);
+    const float t = s + lo;
+    return {t, lo - (t - s)};
 }
 
 }  // namespace fpg

@@ -487,9 +487,20 @@ __device__ bool chord64(const ElemPtr<double>& el, const BasisTab& tab, const do
 // residual norm ||x(r) - x*|| at the returned r.  With FINAL (FP64) a small
 // full Newton step hands over to chord iterations with the current Jacobian;
 // without it (FP32 phase of the mixed form) the loop stops after such a step.
+// State of a solve paused between two iterations (FP64 form, two passes):
+// with r, it is everything the next iteration depends on (f and J are
+// recomputed at r), so a resumed solve takes exactly the steps the
+// uninterrupted one would have.
+struct NewtonState {
+    double rho;
+    int chord_fail;
+    int it;
+    bool paused;
+};
+
 template <int n, typename T, bool FINAL, bool WARP = false>
 __device__ T newton(const ElemPtr<T>& el, const BasisTab& tab, const T (&xs)[3], T (&r)[3], T (&J)[9], int max_it,
-                    bool& converged)
+                    bool& converged, NewtonState* st = nullptr, int budget = 0x7fffffff)
 {
     static_assert(!WARP || (FINAL && sizeof(T) == 8), "the warp-cooperative solver is the FP64 one");
     auto fJ = [&](const T (&rr)[3], T (&ff)[3], T (&JJ)[9]) {
@@ -499,10 +510,20 @@ __device__ T newton(const ElemPtr<T>& el, const BasisTab& tab, const T (&xs)[3],
     T f[3];
     fJ(r, f, J);
     T phi = T(0.5) * (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
-    T rho = T(1);
-    int chord_fail = 0;   // after two failed chord checks the trust-region rules alone finish the solve
+    T rho = st ? T(st->rho) : T(1);
+    int chord_fail = st ? st->chord_fail : 0;   // after two failed chord checks the trust-region rules alone finish
+    const int it0 = st ? st->it : 0;
+    if (st) st->paused = false;
     converged = true;
-    for (int it = 0; it < max_it; ++it) {
+    for (int it = it0; it < max_it; ++it) {
+        if (st && it - it0 >= budget) {                   // pause: the caller resumes later
+            st->rho = (double)rho;
+            st->chord_fail = chord_fail;
+            st->it = it;
+            st->paused = true;
+            converged = false;
+            return sqrt(T(2) * phi);
+        }
         if (!(phi > T(0))) return T(0);
         T d[3];
         const int nfree = gn_step<T>(J, f, r, d);
@@ -652,7 +673,9 @@ struct NewtonArgs {
     const int32_t* s_hi;
     int32_t ebase;
     int32_t* queue;             // work-queue counter (zeroed before the launch); null = grid-stride
-    int tile;                   // sorted positions per work item (a multiple of the block size)
+    int tile;                   // sorted positions per work item (a multiple of 32)
+    double2* pstate;            // FP64 form: state of solves paused after the first pass's budget
+                                //   (rho, chord_fail + 4 it) per pair slot; null = one pass
 };
 
 struct PairRange {
@@ -667,9 +690,9 @@ __device__ __forceinline__ PairRange pair_range(const NewtonArgs& A)
 
 // Visit the sorted pair positions of the range: grid-stride over a fixed
 // grid, or (queue) work items of `tile` consecutive positions that whole
-// blocks draw from a device counter, so a block whose pairs converged fast
+// warps draw from a device counter, so a warp whose pairs converged fast
 // takes the next item instead of idling (pairs of one element stay together
-// in an item).  The counter only grows; no block waits on another.
+// in an item).  The counter only grows; no warp waits on another.
 template <typename Fn>
 __device__ __forceinline__ void for_each_pair(const NewtonArgs& A, const PairRange& R, Fn&& fn)
 {
@@ -679,15 +702,15 @@ __device__ __forceinline__ void for_each_pair(const NewtonArgs& A, const PairRan
             fn(s);
         return;
     }
-    __shared__ int32_t item;
+    const int lane = threadIdx.x & 31;
     for (;;) {
-        if (threadIdx.x == 0) item = atomicAdd(A.queue, 1);
-        __syncthreads();
+        int item = 0;
+        if (lane == 0) item = atomicAdd(A.queue, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
         const int64_t t0 = R.s0 + (int64_t)item * A.tile;
-        __syncthreads();                                   // item read by all before it is redrawn
         if (t0 >= R.s1) break;
         const int64_t t1 = t0 + A.tile < R.s1 ? t0 + A.tile : R.s1;
-        for (int64_t s = t0 + threadIdx.x; s < t1; s += blockDim.x) fn(s);
+        for (int64_t s = t0 + lane; s < t1; s += 32) fn(s);
     }
 }
 
@@ -707,9 +730,14 @@ __device__ __forceinline__ bool warm_seed(const NewtonArgs& A, int64_t p, int e,
     return true;
 }
 
-// FP64 form: nearest-node (or warm) start, full FP64 trust-region Newton
+// FP64 form: nearest-node (or warm) start, full FP64 trust-region Newton;
+// with A.pstate, the first pass stops a solve after kFirstPass iterations
+// and lists it (fbl, capacity fbc) for the second
+constexpr int kFirstPass = 4;
+
 template <int n>
-__device__ __forceinline__ void solve_pair(const NewtonArgs& A, const BasisTab& tab, int64_t s)
+__device__ __forceinline__ void solve_pair(const NewtonArgs& A, const BasisTab& tab, int64_t s, int32_t* fbl,
+                                           int64_t fbc)
 {
     constexpr int n3 = n * n * n;
     const int32_t q = A.order[s];
@@ -721,11 +749,65 @@ __device__ __forceinline__ void solve_pair(const NewtonArgs& A, const BasisTab& 
     double r[3], J[9];
     if (!warm_seed(A, p, e, r)) seed_nearest<n, double>(el64, tab, xs, r);
     bool conv64;
-    const double res = newton<n, double, true>(el64, tab, xs, r, J, A.max_newton, conv64);
-    A.pres[q] = res;
+    NewtonState st{1.0, 0, 0, false};
+    const double res = newton<n, double, true>(el64, tab, xs, r, J, A.max_newton, conv64, A.pstate ? &st : nullptr,
+                                               kFirstPass);
     A.prst[q] = r[0];
     A.prst[A.cap + q] = r[1];
     A.prst[2 * A.cap + q] = r[2];
+    if (st.paused) {
+        // still iterating after the first pass's budget: continued by
+        // k_newton_resume, so that warps of the first pass do not wait on it
+        A.pres[q] = -1.0;
+        A.pstate[q] = make_double2(st.rho, (double)(st.chord_fail + 4 * st.it));
+        const int32_t k = atomicAdd(A.fb_count, 1);
+        if (k < fbc) fbl[k] = q;
+    } else {
+        A.pres[q] = res;
+    }
+}
+
+// pass 2 of the FP64 form: the solves paused by the first pass, resumed
+// where they stopped, one per thread (the list is dense: every lane has a
+// long solve).  If the list overflowed, the paused slots (pres < 0) are
+// found by scanning the range instead.
+template <int n>
+__device__ __forceinline__ void resume_pair(const NewtonArgs& A, const BasisTab& tab, int32_t q)
+{
+    constexpr int n3 = n * n * n;
+    const int e = A.pair_elem[q] - A.ebase;
+    const int64_t p = pair_point(A.pair_pt[q]);
+    const double xs[3] = {A.pts[p], A.pts[A.P + p], A.pts[2 * A.P + p]};
+    const ElemPtr<double> el64 = {A.coords + (int64_t)e * n3, A.coords + (A.E + e) * n3,
+                                  A.coords + (2 * A.E + e) * n3};
+    double r[3] = {A.prst[q], A.prst[A.cap + q], A.prst[2 * A.cap + q]}, J[9];
+    const double2 sv = A.pstate[q];
+    const int code = (int)sv.y;
+    NewtonState st{sv.x, code & 3, code >> 2, false};
+    bool conv;
+    const double res = newton<n, double, true>(el64, tab, xs, r, J, A.max_newton, conv, &st);
+    A.prst[q] = r[0];
+    A.prst[A.cap + q] = r[1];
+    A.prst[2 * A.cap + q] = r[2];
+    A.pres[q] = res;
+}
+
+template <int n>
+__global__ void __launch_bounds__(128) k_newton_resume(NewtonArgs A, BasisTab tab)
+{
+    const PairRange R = pair_range(A);
+    const int32_t* fbl = A.fb_list + (A.s_lo ? R.s0 : 0);
+    const int64_t fbc = A.s_lo ? R.s1 - R.s0 : A.fb_cap;
+    const int64_t nfb = *A.fb_count;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, dt = (int64_t)gridDim.x * blockDim.x;
+    if (nfb <= fbc) {
+        for (int64_t t = t0; t < nfb; t += dt) resume_pair<n>(A, tab, fbl[t]);
+    } else {
+        for (int64_t s = R.s0 + t0; s < R.s1; s += dt) {
+            const int32_t q = A.order[s];
+            if (A.pres[q] < 0.0) resume_pair<n>(A, tab, q);
+        }
+    }
 }
 
 // FP32 value of a reference coordinate that is +-1 only when r is exactly +-1
@@ -742,21 +824,42 @@ __device__ __forceinline__ float f32_inside(double v)
 // basis values computed in FP64 and split, products formed exactly in their
 // leading part and summed with error-free two-sums (about 48 significant
 // bits in element-local units).  Runs on the FP32 pipes.
+// Lagrange basis at r in double-float arithmetic, on the FP32 pipes: r split
+// into (hi, lo), each factor r - xi_m by an error-free difference, the
+// prefix / suffix products and the normalisers c_i as double-float products.
+// About 2^-45 absolute error on the basis values (measured against
+// extended-precision products: 2.7e-14 at worst, 2e-15 rms, for N = 7),
+// against 2^-48 for an FP64 basis split afterwards; the residuals that use it
+// only steer and confirm the final Newton steps.
+template <int n>
+__device__ __forceinline__ void lagrange_h_df(double rv, const BasisTab& tab, float (&hh)[n], float (&hl)[n])
+{
+    const df r = df_split(rv);
+    df dm[n];
+#pragma unroll
+    for (int m = 0; m < n; ++m) dm[m] = df_sub(r, df{tab.xif[m], tab.xil[m]});
+    df pre[n];
+    pre[0] = {1.0f, 0.0f};
+#pragma unroll
+    for (int i = 1; i < n; ++i) pre[i] = df_mul(pre[i - 1], dm[i - 1]);
+    df suf = {1.0f, 0.0f};
+#pragma unroll
+    for (int i = n - 1; i >= 0; --i) {
+        const df t = df_mul(df{tab.cif[i], tab.cil[i]}, df_mul(pre[i], suf));
+        hh[i] = t.hi;
+        hl[i] = t.lo;
+        suf = df_mul(suf, dm[i]);
+    }
+}
+
 template <int n>
 __device__ __forceinline__ void resid_df(const ElemPtr<float>& hi, const ElemPtr<float>& lo, const BasisTab& tab,
                                          const double (&r)[3], const double (&xl)[3], float (&f)[3])
 {
-    double hr[n], hs[n], ht[n];
-    lagrange_h<n, double>(tab.xi, tab.ci, r[0], hr);
-    lagrange_h<n, double>(tab.xi, tab.ci, r[1], hs);
-    lagrange_h<n, double>(tab.xi, tab.ci, r[2], ht);
     float rh[n], rl[n], sh[n], sl[n], th[n], tl[n];
-#pragma unroll
-    for (int i = 0; i < n; ++i) {
-        rh[i] = (float)hr[i]; rl[i] = (float)(hr[i] - (double)rh[i]);
-        sh[i] = (float)hs[i]; sl[i] = (float)(hs[i] - (double)sh[i]);
-        th[i] = (float)ht[i]; tl[i] = (float)(ht[i] - (double)th[i]);
-    }
+    lagrange_h_df<n>(r[0], tab, rh, rl);
+    lagrange_h_df<n>(r[1], tab, sh, sl);
+    lagrange_h_df<n>(r[2], tab, th, tl);
     df acc[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
 #pragma unroll 1
     for (int k = 0; k < n; ++k) {
@@ -826,14 +929,15 @@ constexpr double kConfirm = 1e-10;
 
 // passes 1 and 2 in one kernel: the FP32 work of some warps overlaps the
 // FP64 work of others.
-// Launch shape of the mixed Newton kernel.  CAP (one block per 128 pairs,
-// n <= 8): registers capped so that five blocks of 128 threads fit an SM --
-// more warps keep the FP64 pipe fed, at the price of a few spills to L1.
+// Launch shape of the mixed Newton kernel.  CAP (blocks of up to 128
+// threads, n <= 8): registers capped at 128 so that four blocks of 128
+// threads fit an SM (measured: 2 % faster than five blocks at 96 registers,
+// which spill).
 // Otherwise (persistent grids of the workspace and batch paths, larger n)
 // the compiler is left free.
 template <int n, bool CAP> struct MixedLB {
     static constexpr int threads = CAP ? 128 : 256;
-    static constexpr int blocks = CAP ? 5 : 1;
+    static constexpr int blocks = CAP ? 4 : 1;
 };
 
 template <int n>
@@ -1024,7 +1128,9 @@ template <int n>
 __global__ void __launch_bounds__(256) k_newton(NewtonArgs A, BasisTab tab)
 {
     const PairRange R = pair_range(A);
-    for_each_pair(A, R, [&](int64_t s) { solve_pair<n>(A, tab, s); });
+    int32_t* fbl = A.fb_list + (A.s_lo ? R.s0 : 0);
+    const int64_t fbc = A.s_lo ? R.s1 - R.s0 : A.fb_cap;
+    for_each_pair(A, R, [&](int64_t s) { solve_pair<n>(A, tab, s, fbl, fbc); });
 }
 
 // ---------------------------------------------------------------------------
@@ -1133,6 +1239,7 @@ static cudaError_t newton_n(const FindArgs& a, int64_t npairs, const BasisTab& t
     na.ebase = a.ebase;
     na.queue = a.queue;
     na.tile = a.tile > 0 ? a.tile : block;
+    na.pstate = nullptr;
     cudaError_t err;
     if (a.queue && (err = cudaMemsetAsync(a.queue, 0, sizeof(int32_t), s)) != cudaSuccess) return err;
     if (grid == 0) grid = grid_for(npairs, block, a.persistent_blocks);
@@ -1165,8 +1272,26 @@ static cudaError_t newton_n(const FindArgs& a, int64_t npairs, const BasisTab& t
         k_newton64_full<n><<<gfull, 32, 0, s>>>(na, tab);
         count_launch(2);
     } else {
+        na.pstate = a.pstate;
+        if (a.pstate) {
+            if (a.s_lo) {
+                na.fb_count = a.fb_count;
+                na.fb_list = a.fb_list;
+            } else {
+                na.fb_count = a.scan_tmp;
+                na.fb_list = a.cnt;
+                na.fb_cap = a.P;
+            }
+            if ((err = cudaMemsetAsync(na.fb_count, 0, sizeof(int32_t), s)) != cudaSuccess) return err;
+        }
         k_newton<n><<<grid, block, 0, s>>>(na, tab);
         count_launch();
+        if (a.pstate) {
+            // the resumed solves: one per thread over the list (at most the
+            // pairs of the first pass), sized like the first pass's grid
+            k_newton_resume<n><<<std::max(1u, grid / 2), 128, 0, s>>>(na, tab);
+            count_launch();
+        }
     }
     return cudaGetLastError();
 }

@@ -47,6 +47,7 @@ struct fp_handle {
     int32_t* order = nullptr;
     double* pres = nullptr;
     double* prst = nullptr;
+    double2* pstate = nullptr;     // FP64 form: state of solves paused by the first Newton pass
     int32_t* h_total = nullptr;    // pinned host word for the pair count
     // geometry scratch kept for fp_update_coords (moving meshes)
     double* binv = nullptr;        // [n][n] inverse Bernstein-to-Lagrange matrix

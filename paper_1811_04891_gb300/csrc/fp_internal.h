@@ -101,6 +101,7 @@ struct FindArgs {
     int tile;                     // sorted positions per work item (0: one block's worth)
     int32_t* fb_count;            // mixed form, batch groups: fallback counter and list (group slice
     int32_t* fb_list;             //   from the group's first sorted position)
+    double2* pstate;              // FP64 form: [cap] state of solves paused by the first pass (null: one pass)
     // outputs
     int32_t* code;
     int32_t* osub;

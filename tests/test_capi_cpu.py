@@ -84,6 +84,7 @@ def test_argument_checks_before_any_device_work():
     assert L.fp_batch_create(ctypes.byref(out), 0, None, None, 0, None, 2.0) == INV               # no instances
     assert L.fp_batch_schedule(None, 0, None, None, None) == INV
     assert L.fp_batch_groups(None, None) == INV
+    assert L.fp_batch_mode(None, None) == INV
     assert L.fp_batch_profile(None, 1) == INV
     assert L.fp_bfaces_info(None, None, None) == INV
     cnt = (ctypes.c_int64 * 3)()

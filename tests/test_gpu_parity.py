@@ -264,3 +264,27 @@ def test_eval_double_float_parity(cfg):
     err_64 = (np.where(ok, np.abs(v64 - ref), 0.0) / scale).max()
     assert err_df <= 1e-12, err_df
     assert err_64 <= 1e-12, err_64
+
+
+def test_fp64_two_pass_newton_equals_one_pass():
+    """The FP64 form pauses solves that are still iterating after a fixed
+    budget and resumes them in a second, denser pass; a paused solve keeps
+    everything its next iteration depends on, so every output equals the
+    one-pass solve (fp_find_static runs one pass) bit for bit."""
+    import paper_1811_04891_gb300 as fg
+    dev = torch.device("cuda:0")
+    cases = []
+    coords, amap = synth.spiral_element(15)
+    rng = np.random.default_rng(21)
+    cases.append((synth.Mesh(coords=coords, N=15, sub=np.zeros(1, np.int32)),
+                  amap(*rng.uniform(-0.98, 0.98, (3, 3000))), {"tol_accept": 1e-10}))
+    mesh, q = synth.deformed_cube(ne=6, P_uniform=12000, P_face=3000, with_fields=False)
+    cases.append((mesh, q.pts, {}))
+    for m, pts, opt in cases:
+        h = fg.fp_setup(torch.from_numpy(m.coords).to(dev), m.N, torch.from_numpy(m.sub).to(dev),
+                        opts=fg.default_opts(precision=0, **opt))
+        t = torch.from_numpy(np.ascontiguousarray(pts)).to(dev)
+        two = [x.cpu().numpy() for x in fg.fp_find(h, t)]
+        one = [x.cpu().numpy() for x in fg.fp_find_static(h, t)]
+        for a, b in zip(two, one):
+            np.testing.assert_array_equal(a, b)
