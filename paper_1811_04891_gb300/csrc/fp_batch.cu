@@ -234,6 +234,7 @@ struct fp_batch {
     int32_t* gcount = nullptr;    // [2 * groups]: Newton work-queue counter, fallback counter
     double *pres = nullptr, *prst = nullptr;
     double2* pstate = nullptr;    // FP64 form: state of solves paused by the first Newton pass
+    int32_t* inv = nullptr;       // sorted position of each pair slot
     unsigned long long* band = nullptr;
     cudaEvent_t fork = nullptr, fork2 = nullptr;
     bool prof = false;
@@ -257,7 +258,7 @@ static void batch_release(fp_batch* b)
     release(b->d_inst); release(b->d_p0); release(b->d_rinst); release(b->d_rgrp); release(b->he_all);
     release(b->sub_all); release(b->cnt); release(b->off); release(b->scan_tmp); release(b->pair_elem);
     release(b->pair_pt); release(b->order); release(b->ecount); release(b->estart); release(b->fb_list);
-    release(b->gcount); release(b->pres); release(b->prst); release(b->pstate); release(b->band);
+    release(b->gcount); release(b->pres); release(b->prst); release(b->pstate); release(b->inv); release(b->band);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->fork2) cudaEventDestroy(b->fork2);
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -455,6 +456,7 @@ extern "C" fp_status fp_batch_create(fp_batch** out, int ninst, fp_handle* const
         if (e == cudaSuccess) e = alloc(&b->pres, b->cap);
         if (e == cudaSuccess) e = alloc(&b->prst, 3 * b->cap);
         if (e == cudaSuccess && !b->mixed) e = alloc(&b->pstate, b->cap);
+        if (e == cudaSuccess) e = alloc(&b->inv, b->cap);
         if (e == cudaSuccess) e = alloc(&b->band, 3);
         if (e == cudaSuccess) e = cudaMemset(b->band, 0, 3 * sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
@@ -508,6 +510,7 @@ static FindArgs group_args(const fp_batch* b, const Group& g, const double* pts)
     a.fb_count = b->gcount + 2 * gi + 1;
     a.fb_list = b->fb_list;
     a.pstate = b->pstate;
+    a.inv = b->inv;
     a.tile = g.sched.tile;
     a.persistent_blocks = g.sched.bps * b->nsm;
     return a;
@@ -548,6 +551,7 @@ static cudaError_t batch_run(fp_batch* b, const double* pts, int32_t* code, int3
         a.off = b->off;
         a.pair_elem = b->pair_elem;
         a.order = b->order;
+        a.inv = b->inv;
         a.ecount = b->ecount;
         a.estart = b->estart;
         a.scan_tmp = b->scan_tmp;
@@ -591,6 +595,7 @@ static cudaError_t batch_run(fp_batch* b, const double* pts, int32_t* code, int3
         ra.F = out ? b->F : 0;
         ra.out = out;
         ra.band = b->band;
+        ra.inv = b->inv;
         FindParams fp = b->groups[0].fp;
         k_rank_batch<<<(unsigned)((P + 127) / 128), 128, 0, s>>>(ra, fp, b->ninst, b->d_rinst, b->d_p0, b->he_all,
                                                                 b->sub_all, b->d_rgrp);
@@ -608,7 +613,8 @@ static cudaError_t batch_run(fp_batch* b, const double* pts, int32_t* code, int3
         if (b->prof) cudaEventRecord(g.t[2], gs);
         const EvalSpec ev{b->F, g.fields_df ? nullptr : g.fields, g.fields_df, out};
         e = launch_eval_pairs(g.n, g.E, P, nullptr, b->cap, b->order, b->pair_elem, b->pair_pt, b->prst, ev, g.tab,
-                              (unsigned)(4 * b->nsm), gs, b->estart + g.ebase, b->estart + g.ebase + g.E, g.ebase);
+                              (unsigned)(4 * b->nsm), gs, b->estart + g.ebase, b->estart + g.ebase + g.E, g.ebase,
+                              true);
         if (e != cudaSuccess) return e;
         if (b->prof) cudaEventRecord(g.t[3], gs);
         if (!serial) {

@@ -290,17 +290,21 @@ __device__ __forceinline__ df df_split(double v)
     return {h, (float)(v - (double)h)};
 }
 
+// The error-free transformations below need every sum and product rounded
+// on its own: the _rn intrinsics are never contracted into an fma by the
+// compiler.
+
 // acc += (ah + al) * (bh + bl)
 __device__ __forceinline__ void df_fma_acc(df& acc, float ah, float al, float bh, float bl)
 {
-    const float p = ah * bh;
+    const float p = __fmul_rn(ah, bh);
     const float pe = fmaf(ah, bh, -p);
     const float t = fmaf(ah, bl, fmaf(al, bh, pe));
-    const float s = acc.hi + p;
-    const float bb = s - acc.hi;
-    const float err = (acc.hi - (s - bb)) + (p - bb);
+    const float s = __fadd_rn(acc.hi, p);
+    const float bb = __fsub_rn(s, acc.hi);
+    const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
     acc.hi = s;
-    acc.lo += err + t;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, t));
 }
 
 __device__ __forceinline__ void df_fma_acc(df& acc, const df& a, float bh, float bl)
@@ -311,30 +315,81 @@ __device__ __forceinline__ void df_fma_acc(df& acc, const df& a, float bh, float
 // renormalise (fast two-sum): |lo| below one unit in the last place of hi
 __device__ __forceinline__ void df_norm(df& a)
 {
-    const float t = a.hi + a.lo;
-    a.lo = a.lo - (t - a.hi);
+    const float t = __fadd_rn(a.hi, a.lo);
+    a.lo = __fsub_rn(a.lo, __fsub_rn(t, a.hi));
     a.hi = t;
 }
 
 // a * b: exact leading product plus the cross terms, renormalised
 __device__ __forceinline__ df df_mul(df a, df b)
 {
-    const float p = a.hi * b.hi;
+    const float p = __fmul_rn(a.hi, b.hi);
     float e = fmaf(a.hi, b.hi, -p);
     e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
-    const float s = p + e;
-    return {s, e - (s - p)};
+    const float s = __fadd_rn(p, e);
+    return {s, __fsub_rn(e, __fsub_rn(s, p))};
 }
 
 // a - b: error-free two-sum of the leading parts, then the low parts
 __device__ __forceinline__ df df_sub(df a, df b)
 {
-    const float s = a.hi - b.hi;
-    const float bb = s - a.hi;
-    const float err = (a.hi - (s - bb)) + (-b.hi - bb);
-    const float lo = err + (a.lo - b.lo);
-    const float t = s + lo;
-    return {t, lo - (t - s)};
+    const float s = __fsub_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(-b.hi, bb));
+    const float lo = __fadd_rn(err, __fsub_rn(a.lo, b.lo));
+    const float t = __fadd_rn(s, lo);
+    return {t, __fsub_rn(lo, __fsub_rn(t, s))};
+}
+
+// One row of a double-float field contraction: sum_i v_i (rh_i + rl_i) for
+// the n values v (float2 pairs, 16-byte aligned rows for even n), one
+// accumulator in i order, renormalised.  Every double-float evaluation of
+// fields goes through this routine, so all of them round alike.  (Two
+// interleaved partial sums cost one more double-float addition per row,
+// which measured slower than the latency they hide.)
+template <int n>
+__device__ __forceinline__ df row_df(const float2* __restrict__ rowp, const float (&rh)[n], const float (&rl)[n])
+{
+    df u = {0.0f, 0.0f};
+    if constexpr (n % 2 == 0) {
+        const float4* row = reinterpret_cast<const float4*>(rowp);
+#pragma unroll
+        for (int i2 = 0; i2 < n / 2; ++i2) {
+            const float4 v = __ldg(row + i2);
+            df_fma_acc(u, v.x, v.y, rh[2 * i2], rl[2 * i2]);
+            df_fma_acc(u, v.z, v.w, rh[2 * i2 + 1], rl[2 * i2 + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            const float2 v = __ldg(rowp + i);
+            df_fma_acc(u, v.x, v.y, rh[i], rl[i]);
+        }
+    }
+    df_norm(u);
+    return u;
+}
+
+// sum_ijk F_ijk h_i h_j h_k for one element's double-float values Fe (n^3,
+// i fastest) and split basis values; rounded to FP64
+template <int n>
+__device__ __forceinline__ double contract_df(const float2* __restrict__ Fe, const float (&rh)[n],
+                                              const float (&rl)[n], const float (&sh)[n], const float (&sl)[n],
+                                              const float (&th)[n], const float (&tl)[n])
+{
+    df acc = {0.0f, 0.0f};
+#pragma unroll 1
+    for (int k = 0; k < n; ++k) {
+        df ck = {0.0f, 0.0f};
+#pragma unroll 1
+        for (int j = 0; j < n; ++j) {
+            const df u = row_df<n>(Fe + n * (j + n * k), rh, rl);
+            df_fma_acc(ck, u, sh[j], sl[j]);
+        }
+        df_norm(ck);
+        df_fma_acc(acc, ck, th[k], tl[k]);
+    }
+    return (double)acc.hi + (double)acc.lo;
 }
 
 }  // namespace fpg

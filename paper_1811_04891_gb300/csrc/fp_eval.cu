@@ -119,48 +119,8 @@ __global__ void __launch_bounds__(128) k_eval_df(Eval2Args A, BasisTab tab)
         df a = df_split(hr[i]), b = df_split(hs[i]), c = df_split(ht[i]);
         rh[i] = a.hi; rl[i] = a.lo; sh[i] = b.hi; sl[i] = b.lo; th[i] = c.hi; tl[i] = c.lo;
     }
-    for (int f = f0; f < f1; ++f) {
-        const float2* Fe = A.fields + ((int64_t)f * A.E + e) * n3;
-        df acc = {0.0f, 0.0f};
-#pragma unroll 1
-        for (int k = 0; k < n; ++k) {
-            df ck = {0.0f, 0.0f};
-#pragma unroll 1
-            for (int j = 0; j < n; ++j) {
-                const float4* row = reinterpret_cast<const float4*>(Fe + n * (j + n * k));
-                df u = {0.0f, 0.0f};
-                if constexpr (n % 2 == 0) {
-#pragma unroll
-                    for (int i2 = 0; i2 < n / 2; ++i2) {
-                        const float4 v = __ldg(row + i2);
-                        df_fma_acc(u, v.x, v.y, rh[2 * i2], rl[2 * i2]);
-                        df_fma_acc(u, v.z, v.w, rh[2 * i2 + 1], rl[2 * i2 + 1]);
-                    }
-                } else {
-                    const float2* r2 = Fe + n * (j + n * k);
-#pragma unroll
-                    for (int i = 0; i < n; ++i) {
-                        const float2 v = __ldg(r2 + i);
-                        df_fma_acc(u, v.x, v.y, rh[i], rl[i]);
-                    }
-                }
-                {   // renormalise (fast two-sum): keeps |lo| below one unit of hi
-                    const float t = u.hi + u.lo;
-                    u.lo = u.lo - (t - u.hi);
-                    u.hi = t;
-                }
-                df_fma_acc(ck, u, sh[j], sl[j]);
-            }
-            {
-                const float t = ck.hi + ck.lo;
-                ck.lo = ck.lo - (t - ck.hi);
-                ck.hi = t;
-            }
-            // t-basis by runtime index k: read from the split arrays
-            df_fma_acc(acc, ck, th[k], tl[k]);
-        }
-        A.out[(int64_t)f * A.P + p] = (double)acc.hi + (double)acc.lo;
-    }
+    for (int f = f0; f < f1; ++f)
+        A.out[(int64_t)f * A.P + p] = contract_df<n>(A.fields + ((int64_t)f * A.E + e) * n3, rh, rl, sh, sl, th, tl);
 }
 
 // ---- posted points: the split basis values of located points, computed once
@@ -216,41 +176,7 @@ __global__ void __launch_bounds__(128) k_eval_points_df(int64_t E, int64_t P, in
         th[i] = __ldg(basis + (int64_t)(4 * n + i) * P + p);
         tl[i] = __ldg(basis + (int64_t)(5 * n + i) * P + p);
     }
-    const float2* Fe = fields + ((int64_t)f * E + e) * n3;
-    df acc = {0.0f, 0.0f};
-#pragma unroll 1
-    for (int k = 0; k < n; ++k) {
-        df ck = {0.0f, 0.0f};
-#pragma unroll 1
-        for (int j = 0; j < n; ++j) {
-            df u = {0.0f, 0.0f};
-            if constexpr (n % 2 == 0) {
-                const float4* row = reinterpret_cast<const float4*>(Fe + n * (j + n * k));
-#pragma unroll
-                for (int i2 = 0; i2 < n / 2; ++i2) {
-                    const float4 v = __ldg(row + i2);
-                    df_fma_acc(u, v.x, v.y, rh[2 * i2], rl[2 * i2]);
-                    df_fma_acc(u, v.z, v.w, rh[2 * i2 + 1], rl[2 * i2 + 1]);
-                }
-            } else {
-                const float2* r2 = Fe + n * (j + n * k);
-#pragma unroll
-                for (int i = 0; i < n; ++i) {
-                    const float2 v = __ldg(r2 + i);
-                    df_fma_acc(u, v.x, v.y, rh[i], rl[i]);
-                }
-            }
-            const float tt = u.hi + u.lo;
-            u.lo = u.lo - (tt - u.hi);
-            u.hi = tt;
-            df_fma_acc(ck, u, sh[j], sl[j]);
-        }
-        const float tt = ck.hi + ck.lo;
-        ck.lo = ck.lo - (tt - ck.hi);
-        ck.hi = tt;
-        df_fma_acc(acc, ck, th[k], tl[k]);
-    }
-    out[(int64_t)f * P + p] = (double)acc.hi + (double)acc.lo;
+    out[(int64_t)f * P + p] = contract_df<n>(fields + ((int64_t)f * E + e) * n3, rh, rl, sh, sl, th, tl);
 }
 
 __global__ void k_split_df(int64_t n, const double* __restrict__ src, float2* __restrict__ dst)
@@ -365,43 +291,8 @@ __device__ __forceinline__ void eval_point_df(const float2* __restrict__ Fdf, in
         df a = df_split(hr[i]), b = df_split(hs[i]), c = df_split(ht[i]);
         rh[i] = a.hi; rl[i] = a.lo; sh[i] = b.hi; sl[i] = b.lo; th[i] = c.hi; tl[i] = c.lo;
     }
-    for (int f = 0; f < F; ++f) {
-        const float2* Fe = Fdf + ((int64_t)f * E + e) * n3;
-        df acc = {0.0f, 0.0f};
-#pragma unroll 1
-        for (int k = 0; k < n; ++k) {
-            df ck = {0.0f, 0.0f};
-#pragma unroll 1
-            for (int j = 0; j < n; ++j) {
-                df u = {0.0f, 0.0f};
-                if constexpr (n % 2 == 0) {
-                    const float4* row = reinterpret_cast<const float4*>(Fe + n * (j + n * k));
-#pragma unroll
-                    for (int i2 = 0; i2 < n / 2; ++i2) {
-                        const float4 v = __ldg(row + i2);
-                        df_fma_acc(u, v.x, v.y, rh[2 * i2], rl[2 * i2]);
-                        df_fma_acc(u, v.z, v.w, rh[2 * i2 + 1], rl[2 * i2 + 1]);
-                    }
-                } else {
-                    const float2* r2p = Fe + n * (j + n * k);
-#pragma unroll
-                    for (int i = 0; i < n; ++i) {
-                        const float2 v = __ldg(r2p + i);
-                        df_fma_acc(u, v.x, v.y, rh[i], rl[i]);
-                    }
-                }
-                const float t = u.hi + u.lo;
-                u.lo = u.lo - (t - u.hi);
-                u.hi = t;
-                df_fma_acc(ck, u, sh[j], sl[j]);
-            }
-            const float t = ck.hi + ck.lo;
-            ck.lo = ck.lo - (t - ck.hi);
-            ck.hi = t;
-            df_fma_acc(acc, ck, th[k], tl[k]);
-        }
-        out[(int64_t)f * P + p] = (double)acc.hi + (double)acc.lo;
-    }
+    for (int f = 0; f < F; ++f)
+        out[(int64_t)f * P + p] = contract_df<n>(Fdf + ((int64_t)f * E + e) * n3, rh, rl, sh, sl, th, tl);
 }
 
 struct EvalPairsArgs {
@@ -415,6 +306,7 @@ struct EvalPairsArgs {
     const int32_t* s_lo;      // batch groups: the group's sorted positions [*s_lo, *s_hi)
     const int32_t* s_hi;
     int32_t ebase;            // batch groups: subtracted from pair_elem
+    int walk;                 // pair results at sorted positions (else at pair slots)
 };
 
 template <int n, bool DF>
@@ -433,7 +325,8 @@ __global__ void __launch_bounds__(128) k_eval_pairs(EvalPairsArgs A, BasisTab ta
         const int32_t p = A.pair_pt[q];
         if (p < 0) continue;                              // not the point's winning pair
         const int e = A.pair_elem[q] - A.ebase;
-        const double r0 = A.prst[q], r1 = A.prst[A.cap + q], r2 = A.prst[2 * A.cap + q];
+        const int64_t w = A.walk ? s : q;
+        const double r0 = A.prst[w], r1 = A.prst[A.cap + w], r2 = A.prst[2 * A.cap + w];
         if (DF)
             eval_point_df<n>(A.ev.fdf, A.E, A.ev.F, e, r0, r1, r2, tab, A.ev.out, A.P, p);
         else
@@ -444,9 +337,9 @@ __global__ void __launch_bounds__(128) k_eval_pairs(EvalPairsArgs A, BasisTab ta
 cudaError_t launch_eval_pairs(int n, int64_t E, int64_t P, const int32_t* dcount, int64_t cap, const int32_t* order,
                               const int32_t* pair_elem, const int32_t* pair_pt, const double* prst,
                               const EvalSpec& ev, const BasisTab& tab, unsigned grid, cudaStream_t s,
-                              const int32_t* s_lo, const int32_t* s_hi, int32_t ebase)
+                              const int32_t* s_lo, const int32_t* s_hi, int32_t ebase, bool walk)
 {
-    EvalPairsArgs a{E, P, cap, dcount, order, pair_elem, pair_pt, prst, ev, s_lo, s_hi, ebase};
+    EvalPairsArgs a{E, P, cap, dcount, order, pair_elem, pair_pt, prst, ev, s_lo, s_hi, ebase, walk ? 1 : 0};
     const bool df = ev.fdf != nullptr;
     switch (n) {
 #define FP_CASE(NN)                                                   \

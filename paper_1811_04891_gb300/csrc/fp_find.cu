@@ -203,13 +203,15 @@ __global__ void k_ehist(const int32_t* __restrict__ dcount, int64_t cap, const i
 }
 
 __global__ void k_escatter(const int32_t* __restrict__ dcount, int64_t cap, const int32_t* __restrict__ pair_elem,
-                           const int32_t* __restrict__ estart, int32_t* __restrict__ cursor, int32_t* __restrict__ order)
+                           const int32_t* __restrict__ estart, int32_t* __restrict__ cursor, int32_t* __restrict__ order,
+                           int32_t* __restrict__ inv)
 {
     const int64_t npairs = live_pairs(dcount, cap);
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npairs; q += (int64_t)gridDim.x * blockDim.x) {
         const int e = pair_elem[q];
         const int pos = estart[e] + atomicAdd(cursor + e, 1);
         order[pos] = (int32_t)q;
+        if (inv) inv[q] = pos;
     }
 }
 
@@ -675,8 +677,14 @@ struct NewtonArgs {
     int32_t* queue;             // work-queue counter (zeroed before the launch); null = grid-stride
     int tile;                   // sorted positions per work item (a multiple of 32)
     double2* pstate;            // FP64 form: state of solves paused after the first pass's budget
-                                //   (rho, chord_fail + 4 it) per pair slot; null = one pass
+                                //   (rho, chord_fail + 4 it) per pair; null = one pass
+    bool walk;                  // pair results (pres, prst, pstate) at sorted positions s (coalesced);
+                                //   otherwise at pair slots q.  Fallback lists hold the same index.
 };
+
+// where pair s / q keeps its results, and the pair of a listed index
+__device__ __forceinline__ int64_t result_slot(const NewtonArgs& A, int64_t s, int32_t q) { return A.walk ? s : q; }
+__device__ __forceinline__ int32_t listed_pair(const NewtonArgs& A, int64_t t) { return A.walk ? A.order[t] : (int32_t)t; }
 
 struct PairRange {
     int64_t s0, s1;
@@ -752,18 +760,19 @@ __device__ __forceinline__ void solve_pair(const NewtonArgs& A, const BasisTab& 
     NewtonState st{1.0, 0, 0, false};
     const double res = newton<n, double, true>(el64, tab, xs, r, J, A.max_newton, conv64, A.pstate ? &st : nullptr,
                                                kFirstPass);
-    A.prst[q] = r[0];
-    A.prst[A.cap + q] = r[1];
-    A.prst[2 * A.cap + q] = r[2];
+    const int64_t w = result_slot(A, s, q);
+    A.prst[w] = r[0];
+    A.prst[A.cap + w] = r[1];
+    A.prst[2 * A.cap + w] = r[2];
     if (st.paused) {
         // still iterating after the first pass's budget: continued by
         // k_newton_resume, so that warps of the first pass do not wait on it
-        A.pres[q] = -1.0;
-        A.pstate[q] = make_double2(st.rho, (double)(st.chord_fail + 4 * st.it));
+        A.pres[w] = -1.0;
+        A.pstate[w] = make_double2(st.rho, (double)(st.chord_fail + 4 * st.it));
         const int32_t k = atomicAdd(A.fb_count, 1);
-        if (k < fbc) fbl[k] = q;
+        if (k < fbc) fbl[k] = (int32_t)w;
     } else {
-        A.pres[q] = res;
+        A.pres[w] = res;
     }
 }
 
@@ -772,24 +781,25 @@ __device__ __forceinline__ void solve_pair(const NewtonArgs& A, const BasisTab& 
 // long solve).  If the list overflowed, the paused slots (pres < 0) are
 // found by scanning the range instead.
 template <int n>
-__device__ __forceinline__ void resume_pair(const NewtonArgs& A, const BasisTab& tab, int32_t q)
+__device__ __forceinline__ void resume_pair(const NewtonArgs& A, const BasisTab& tab, int64_t w)
 {
     constexpr int n3 = n * n * n;
+    const int32_t q = listed_pair(A, w);
     const int e = A.pair_elem[q] - A.ebase;
     const int64_t p = pair_point(A.pair_pt[q]);
     const double xs[3] = {A.pts[p], A.pts[A.P + p], A.pts[2 * A.P + p]};
     const ElemPtr<double> el64 = {A.coords + (int64_t)e * n3, A.coords + (A.E + e) * n3,
                                   A.coords + (2 * A.E + e) * n3};
-    double r[3] = {A.prst[q], A.prst[A.cap + q], A.prst[2 * A.cap + q]}, J[9];
-    const double2 sv = A.pstate[q];
+    double r[3] = {A.prst[w], A.prst[A.cap + w], A.prst[2 * A.cap + w]}, J[9];
+    const double2 sv = A.pstate[w];
     const int code = (int)sv.y;
     NewtonState st{sv.x, code & 3, code >> 2, false};
     bool conv;
     const double res = newton<n, double, true>(el64, tab, xs, r, J, A.max_newton, conv, &st);
-    A.prst[q] = r[0];
-    A.prst[A.cap + q] = r[1];
-    A.prst[2 * A.cap + q] = r[2];
-    A.pres[q] = res;
+    A.prst[w] = r[0];
+    A.prst[A.cap + w] = r[1];
+    A.prst[2 * A.cap + w] = r[2];
+    A.pres[w] = res;
 }
 
 template <int n>
@@ -804,8 +814,8 @@ __global__ void __launch_bounds__(128) k_newton_resume(NewtonArgs A, BasisTab ta
         for (int64_t t = t0; t < nfb; t += dt) resume_pair<n>(A, tab, fbl[t]);
     } else {
         for (int64_t s = R.s0 + t0; s < R.s1; s += dt) {
-            const int32_t q = A.order[s];
-            if (A.pres[q] < 0.0) resume_pair<n>(A, tab, q);
+            const int64_t w = result_slot(A, s, A.order[s]);
+            if (A.pres[w] < 0.0) resume_pair<n>(A, tab, w);
         }
     }
 }
@@ -867,28 +877,22 @@ __device__ __forceinline__ void resid_df(const ElemPtr<float>& hi, const ElemPtr
 #pragma unroll 1
         for (int j = 0; j < n; ++j) {
             const int off = n * (j + n * k);
-            df u0[3], u1[3];
+            df u[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {             // three coordinates x two partial sums: six chains
+            for (int a = 0; a < 3; ++a) {             // three coordinates: three independent chains
                 const float* Xh = (a == 0 ? hi.X0 : (a == 1 ? hi.X1 : hi.X2)) + off;
                 const float* Xl = (a == 0 ? lo.X0 : (a == 1 ? lo.X1 : lo.X2)) + off;
                 float vh[n], vl[n];
                 load_row<n>(Xh, vh);
                 load_row<n>(Xl, vl);
-                u0[a] = {0.0f, 0.0f};
-                u1[a] = {0.0f, 0.0f};
+                u[a] = {0.0f, 0.0f};
 #pragma unroll
-                for (int i = 0; i < n; i += 2) {
-                    df_fma_acc(u0[a], vh[i], vl[i], rh[i], rl[i]);
-                    if (i + 1 < n) df_fma_acc(u1[a], vh[i + 1], vl[i + 1], rh[i + 1], rl[i + 1]);
-                }
+                for (int i = 0; i < n; ++i) df_fma_acc(u[a], vh[i], vl[i], rh[i], rl[i]);
             }
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                df u = u0[a];
-                df_fma_acc(u, u1[a].hi, u1[a].lo, 1.0f, 0.0f);
-                df_norm(u);
-                df_fma_acc(ck[a], u.hi, u.lo, sh[j], sl[j]);
+                df_norm(u[a]);
+                df_fma_acc(ck[a], u[a].hi, u[a].lo, sh[j], sl[j]);
             }
         }
 #pragma unroll
@@ -930,9 +934,9 @@ constexpr double kConfirm = 1e-10;
 // passes 1 and 2 in one kernel: the FP32 work of some warps overlaps the
 // FP64 work of others.
 // Launch shape of the mixed Newton kernel.  CAP (blocks of up to 128
-// threads, n <= 8): registers capped at 128 so that four blocks of 128
-// threads fit an SM (measured: 2 % faster than five blocks at 96 registers,
-// which spill).
+// threads, n <= 10, where 128 registers need no spills): registers capped so
+// that four blocks of 128 threads fit an SM (measured at n = 8: 2 % faster
+// than five blocks at 96 registers, which spill).
 // Otherwise (persistent grids of the workspace and batch paths, larger n)
 // the compiler is left free.
 template <int n, bool CAP> struct MixedLB {
@@ -1025,13 +1029,14 @@ __device__ __forceinline__ void solve_mixed(const NewtonArgs& A, const BasisTab&
             }
             if (A.stats) atomicAdd(A.stats + (res < 0.0 ? 3 : 2), 1ULL);
         }
-        A.prst[q] = r[0];
-        A.prst[A.cap + q] = r[1];
-        A.prst[2 * A.cap + q] = r[2];
-        A.pres[q] = res;
+        const int64_t w = result_slot(A, s, q);
+        A.prst[w] = r[0];
+        A.prst[A.cap + w] = r[1];
+        A.prst[2 * A.cap + w] = r[2];
+        A.pres[w] = res;
         if (res < 0.0) {
             const int32_t k = atomicAdd(A.fb_count, 1);
-            if (k < fbc) fbl[k] = q;
+            if (k < fbc) fbl[k] = (int32_t)w;
         }
     }
 }
@@ -1058,21 +1063,22 @@ constexpr int kFullChunk = 8192;
 constexpr int kFullSub = 1024;
 
 template <int n>
-__device__ __forceinline__ void solve_full64(const NewtonArgs& A, const BasisTab& tab, int32_t q)
+__device__ __forceinline__ void solve_full64(const NewtonArgs& A, const BasisTab& tab, int64_t w)
 {
     constexpr int n3 = n * n * n;
+    const int32_t q = listed_pair(A, w);
     const int e = A.pair_elem[q] - A.ebase;
     const int64_t p = pair_point(A.pair_pt[q]);
     const double xs[3] = {A.pts[p], A.pts[A.P + p], A.pts[2 * A.P + p]};
     const ElemPtr<double> el64 = {A.coords + (int64_t)e * n3, A.coords + (A.E + e) * n3,
                                   A.coords + (2 * A.E + e) * n3};
-    double r[3] = {A.prst[q], A.prst[A.cap + q], A.prst[2 * A.cap + q]}, J[9];
+    double r[3] = {A.prst[w], A.prst[A.cap + w], A.prst[2 * A.cap + w]}, J[9];
     bool conv;
     const double res = newton<n, double, true>(el64, tab, xs, r, J, A.max_newton, conv);
-    A.prst[q] = r[0];
-    A.prst[A.cap + q] = r[1];
-    A.prst[2 * A.cap + q] = r[2];
-    A.pres[q] = res;
+    A.prst[w] = r[0];
+    A.prst[A.cap + w] = r[1];
+    A.prst[2 * A.cap + w] = r[2];
+    A.pres[w] = res;
 }
 
 template <int n>
@@ -1086,20 +1092,21 @@ __global__ void __launch_bounds__(32) k_newton64_full(NewtonArgs A, BasisTab tab
         // one warp (this block) per listed pair
         constexpr int n3 = n * n * n;
         for (int64_t t = blockIdx.x; t < nfb; t += gridDim.x) {
-            const int32_t q = fbl[t];
+            const int64_t w = fbl[t];
+            const int32_t q = listed_pair(A, w);
             const int e = A.pair_elem[q] - A.ebase;
             const int64_t p = pair_point(A.pair_pt[q]);
             const double xs[3] = {A.pts[p], A.pts[A.P + p], A.pts[2 * A.P + p]};
             const ElemPtr<double> el64 = {A.coords + (int64_t)e * n3, A.coords + (A.E + e) * n3,
                                           A.coords + (2 * A.E + e) * n3};
-            double r[3] = {A.prst[q], A.prst[A.cap + q], A.prst[2 * A.cap + q]}, J[9];
+            double r[3] = {A.prst[w], A.prst[A.cap + w], A.prst[2 * A.cap + w]}, J[9];
             bool conv;
             const double res = newton<n, double, true, true>(el64, tab, xs, r, J, A.max_newton, conv);
             if (threadIdx.x == 0) {
-                A.prst[q] = r[0];
-                A.prst[A.cap + q] = r[1];
-                A.prst[2 * A.cap + q] = r[2];
-                A.pres[q] = res;
+                A.prst[w] = r[0];
+                A.prst[A.cap + w] = r[1];
+                A.prst[2 * A.cap + w] = r[2];
+                A.pres[w] = res;
             }
         }
         return;
@@ -1113,8 +1120,8 @@ __global__ void __launch_bounds__(32) k_newton64_full(NewtonArgs A, BasisTab tab
             __syncthreads();
             const int64_t end = sb + kFullSub < cend ? sb + kFullSub : cend;
             for (int64_t s = sb + threadIdx.x; s < end; s += blockDim.x) {
-                const int32_t q = A.order[s];
-                if (A.pres[q] < 0.0) list[atomicAdd(&count, 1)] = q;
+                const int64_t w = result_slot(A, s, A.order[s]);
+                if (A.pres[w] < 0.0) list[atomicAdd(&count, 1)] = (int32_t)w;
             }
             __syncthreads();
             const int m = count;
@@ -1240,6 +1247,7 @@ static cudaError_t newton_n(const FindArgs& a, int64_t npairs, const BasisTab& t
     na.queue = a.queue;
     na.tile = a.tile > 0 ? a.tile : block;
     na.pstate = nullptr;
+    na.walk = a.inv != nullptr;
     cudaError_t err;
     if (a.queue && (err = cudaMemsetAsync(a.queue, 0, sizeof(int32_t), s)) != cudaSuccess) return err;
     if (grid == 0) grid = grid_for(npairs, block, a.persistent_blocks);
@@ -1257,7 +1265,7 @@ static cudaError_t newton_n(const FindArgs& a, int64_t npairs, const BasisTab& t
         }
         if ((err = cudaMemsetAsync(na.fb_count, 0, sizeof(int32_t), s)) != cudaSuccess) return err;
         bool capped = false;
-        if constexpr (n <= 8) {
+        if constexpr (n <= 10) {
             if (block <= 128 && (a.persistent_blocks == 0 || a.queue)) {
                 const unsigned g = a.persistent_blocks == 0 && !a.queue ? grid_for(npairs, block, 0) : grid;
                 k_newton_mixed<n, true><<<g, block, 0, s>>>(na, tab);
@@ -1345,6 +1353,7 @@ static cudaError_t solve_n(const FindArgs& a, int64_t npairs, const BasisTab& ta
     ra.F = a.eval.F;
     ra.out = a.eval.out;
     ra.band = a.band;
+    ra.inv = a.inv;
     if (a.ev[4]) cudaEventRecord(a.ev[4], s);
     k_rank<n, 3><<<(unsigned)((a.P + 127) / 128), 128, 0, s>>>(ra, fp, tab);
     count_launch();
@@ -1353,7 +1362,8 @@ static cudaError_t solve_n(const FindArgs& a, int64_t npairs, const BasisTab& ta
     if (err != cudaSuccess || a.eval.F == 0 || npairs == 0) return err;
     if (a.ev[6]) cudaEventRecord(a.ev[6], s);
     err = launch_eval_pairs(n, a.E, a.P, a.off + a.P, a.cap, a.order, a.pair_elem, a.pair_pt, a.prst, a.eval, tab,
-                            grid_for(npairs, 128, a.persistent_blocks ? 4 * a.persistent_blocks : 0), s);
+                            grid_for(npairs, 128, a.persistent_blocks ? 4 * a.persistent_blocks : 0), s, nullptr,
+                            nullptr, 0, a.inv != nullptr);
     if (a.ev[7]) cudaEventRecord(a.ev[7], s);
     return err;
 }
@@ -1371,7 +1381,7 @@ cudaError_t find_sort(const FindArgs& a, int64_t npairs, cudaStream_t s)
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         if ((err = scan_exclusive(a.ecount, a.estart, a.E, a.scan_tmp, s)) != cudaSuccess) return err;
         if ((err = cudaMemsetAsync(a.ecount, 0, sizeof(int32_t) * a.E, s)) != cudaSuccess) return err;
-        k_escatter<<<g256, 256, 0, s>>>(a.off + a.P, a.cap, a.pair_elem, a.estart, a.ecount, a.order);
+        k_escatter<<<g256, 256, 0, s>>>(a.off + a.P, a.cap, a.pair_elem, a.estart, a.ecount, a.order, a.inv);
         count_launch();
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         if (a.ev[1]) cudaEventRecord(a.ev[1], s);
@@ -1419,7 +1429,7 @@ static int newton_fit(bool mixed, int block)
     cudaError_t e;
     if (!mixed) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_newton<n>, block, 0);
-    } else if (n <= 8 && block <= 128) {
+    } else if (n <= 10 && block <= 128) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_newton_mixed<n, true>, block, 0);
     } else {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, k_newton_mixed<n, false>, block, 0);

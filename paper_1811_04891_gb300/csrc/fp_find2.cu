@@ -833,7 +833,7 @@ static cudaError_t solve2_n(const FindArgs& a, int64_t npairs, const BasisTab& t
     ra.P = a.P; ra.E = a.E; ra.off = a.off; ra.pair_elem = a.pair_elem; ra.pres = a.pres; ra.prst = a.prst;
     ra.cap = a.cap; ra.sub = a.sub; ra.boxes = a.boxes; ra.dist = a.dist; ra.code = a.code; ra.osub = a.osub;
     ra.oelem = a.oelem; ra.rst = a.rst; ra.dist2 = a.dist2; ra.pair_pt = a.pair_pt; ra.F = a.eval.F;
-    ra.out = a.eval.out; ra.band = a.band;
+    ra.out = a.eval.out; ra.band = a.band; ra.inv = nullptr;   // 2D: pair results stay at their slots
     if (a.ev[4]) cudaEventRecord(a.ev[4], s);
     k_rank<n, 2><<<(unsigned)((a.P + 127) / 128), 128, 0, s>>>(ra, fp, tab);
     count_launch();

@@ -48,6 +48,7 @@ struct fp_handle {
     double* pres = nullptr;
     double* prst = nullptr;
     double2* pstate = nullptr;     // FP64 form: state of solves paused by the first Newton pass
+    int32_t* inv = nullptr;        // [cap] sorted position of each pair slot (hexahedral handles)
     int32_t* h_total = nullptr;    // pinned host word for the pair count
     // geometry scratch kept for fp_update_coords (moving meshes)
     double* binv = nullptr;        // [n][n] inverse Bernstein-to-Lagrange matrix

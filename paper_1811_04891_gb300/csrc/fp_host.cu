@@ -192,7 +192,7 @@ void release(fp_handle* h)
     dfree(h->coords); dfree(h->coords32); dfree(h->coords32lo); dfree(h->sub); dfree(h->dist); dfree(h->boxes); dfree(h->boxes32);
     dfree(h->cell_start); dfree(h->cell_elems); dfree(h->ecount); dfree(h->estart); dfree(h->escan_tmp);
     dfree(h->cnt); dfree(h->off); dfree(h->scan_tmp); dfree(h->pair_elem); dfree(h->pair_pt);
-    dfree(h->order); dfree(h->pres); dfree(h->prst); dfree(h->pstate);
+    dfree(h->order); dfree(h->pres); dfree(h->prst); dfree(h->pstate); dfree(h->inv);
     dfree(h->binv); dfree(h->nodebox); dfree(h->red); dfree(h->hcnt); dfree(h->htmp); dfree(h->flag);
     if (h->h_total) cudaFreeHost(h->h_total);
     h->h_total = nullptr;
@@ -221,11 +221,13 @@ fp_status grow_pairs(fp_handle* h, int64_t np)
     int64_t cap = std::max<int64_t>(np + np / 4, 2048);
     cudaDeviceSynchronize();
     dfree(h->pair_elem); dfree(h->pair_pt); dfree(h->order); dfree(h->pres); dfree(h->prst); dfree(h->pstate);
+    dfree(h->inv);
     const bool two_pass = h->dim == 3 && h->opts.precision == FP_PREC_FP64;
     cudaError_t e;
     if ((e = dalloc(&h->pair_elem, cap)) != cudaSuccess || (e = dalloc(&h->pair_pt, cap)) != cudaSuccess ||
         (e = dalloc(&h->order, cap)) != cudaSuccess || (e = dalloc(&h->pres, cap)) != cudaSuccess ||
         (e = dalloc(&h->prst, 3 * cap)) != cudaSuccess ||
+        (h->dim == 3 && (e = dalloc(&h->inv, cap)) != cudaSuccess) ||
         (two_pass && (e = dalloc(&h->pstate, cap)) != cudaSuccess)) {
         h->cap_pairs = 0;
         return cuda_fail(h, e, "workspace (pairs)");
@@ -616,6 +618,7 @@ static fp_status find_impl(fp_handle* h, int64_t P, const double* pts, const int
     if (st != FP_OK) return st;
     a.pair_elem = h->pair_elem; a.pair_pt = h->pair_pt; a.order = h->order;
     a.pres = h->pres; a.prst = h->prst; a.cap = h->cap_pairs; a.pstate = h->pstate;
+    a.inv = d2 ? nullptr : h->inv;
     if (npairs > 0) {
         err = d2 ? find_emit2(a, s) : find_emit(a, s);
         if (err != cudaSuccess) return cuda_fail(h, err, "fp_find emit");
@@ -757,12 +760,14 @@ struct fp_workspace {
     int32_t *ecount = nullptr, *estart = nullptr;
     double *pres = nullptr, *prst = nullptr;
     double2* pstate = nullptr;  // FP64 form: state of solves paused by the first Newton pass
+    int32_t* inv = nullptr;     // sorted position of each pair slot
 };
 
 static void ws_release(fp_workspace* w)
 {
     dfree(w->cnt); dfree(w->off); dfree(w->scan_tmp); dfree(w->pair_elem); dfree(w->pair_pt);
     dfree(w->order); dfree(w->ecount); dfree(w->estart); dfree(w->pres); dfree(w->prst); dfree(w->pstate);
+    dfree(w->inv);
 }
 
 fp_status fp_workspace_create(const fp_handle* h, int64_t max_points, int64_t max_pairs, fp_workspace** out)
@@ -788,7 +793,7 @@ fp_status fp_workspace_create(const fp_handle* h, int64_t max_points, int64_t ma
         (e = dalloc(&w->pair_elem, max_pairs)) != cudaSuccess || (e = dalloc(&w->pair_pt, max_pairs)) != cudaSuccess ||
         (e = dalloc(&w->order, max_pairs)) != cudaSuccess || (e = dalloc(&w->ecount, h->E)) != cudaSuccess ||
         (e = dalloc(&w->estart, h->E + 1)) != cudaSuccess || (e = dalloc(&w->pres, max_pairs)) != cudaSuccess ||
-        (e = dalloc(&w->prst, 3 * max_pairs)) != cudaSuccess ||
+        (e = dalloc(&w->prst, 3 * max_pairs)) != cudaSuccess || (e = dalloc(&w->inv, max_pairs)) != cudaSuccess ||
         (h->opts.precision == FP_PREC_FP64 && (e = dalloc(&w->pstate, max_pairs)) != cudaSuccess)) {
         ws_release(w);
         delete w;
@@ -805,7 +810,7 @@ fp_status fp_workspace_bytes(const fp_handle* h, int64_t max_points, int64_t max
     if (max_pairs <= 0) max_pairs = 2 * max_points;
     if (max_pairs >= (int64_t(1) << 31)) return FP_ERR_INVALID_ARG;
     *bytes = 4 * max_points + 4 * (max_points + 1) + 4 * std::max(scan_tmp_elems(max_points), scan_tmp_elems(h->E)) +
-             max_pairs * (4 + 4 + 4 + 8 + 24 + (h->opts.precision == FP_PREC_FP64 ? 16 : 0)) + 4 * h->E +
+             max_pairs * (4 + 4 + 4 + 4 + 8 + 24 + (h->opts.precision == FP_PREC_FP64 ? 16 : 0)) + 4 * h->E +
              4 * (h->E + 1);
     return FP_OK;
 }
@@ -879,6 +884,7 @@ static fp_status find_ws_impl(fp_handle* h, fp_workspace* w, int64_t P, const do
     a.cnt = w->cnt; a.off = w->off; a.scan_tmp = w->scan_tmp; a.ecount = w->ecount; a.estart = w->estart;
     a.pair_elem = w->pair_elem; a.pair_pt = w->pair_pt; a.order = w->order; a.pres = w->pres; a.prst = w->prst;
     a.pstate = w->pstate;
+    a.inv = w->inv;
     a.cap = w->max_pairs;
     a.persistent_blocks = w->persistent_blocks;
     a.code = code; a.osub = sub; a.oelem = elem; a.rst = rst; a.dist2 = dist2;
@@ -1148,7 +1154,7 @@ fp_status fp_memory(const fp_handle* h, int64_t* resident, int64_t* workspace)
     if (workspace)
         *workspace = 4 * h->cap_pts + 4 * (h->cap_pts + 1) +
                      4 * (h->cap_pts > 0 ? std::max(scan_tmp_elems(h->cap_pts), scan_tmp_elems(h->E)) : 0) +
-                     h->cap_pairs * (4 + 4 + 4 + 8 + 24 + (h->pstate ? 16 : 0));
+                     h->cap_pairs * (4 + 4 + 4 + 8 + 24 + (h->pstate ? 16 : 0) + (h->inv ? 4 : 0));
     return FP_OK;
 }
 

@@ -77,6 +77,8 @@ struct FindArgs {
     int32_t* ecount;              // [E]  (zeroed by the launcher)
     int32_t* estart;              // [E+1]
     int32_t* order;               // [cap]
+    int32_t* inv;                 // [cap] sorted position of each pair slot; set (3D): the Newton stage keeps
+                                  //   pair results in sorted order (coalesced), null (2D): in slot order
     double* pres;                 // [cap]
     double* prst;                 // [3][cap]
     int32_t* scan_tmp;
@@ -157,7 +159,8 @@ cudaError_t launch_eval2(int n, int64_t E, int64_t P, const int32_t* code, const
 cudaError_t launch_eval_pairs(int n, int64_t E, int64_t P, const int32_t* dcount, int64_t cap, const int32_t* order,
                               const int32_t* pair_elem, const int32_t* pair_pt, const double* prst,
                               const EvalSpec& ev, const BasisTab& tab, unsigned grid, cudaStream_t s,
-                              const int32_t* s_lo = nullptr, const int32_t* s_hi = nullptr, int32_t ebase = 0);
+                              const int32_t* s_lo = nullptr, const int32_t* s_hi = nullptr, int32_t ebase = 0,
+                              bool walk = false);
 cudaError_t launch_split_df(int64_t n, const double* src, float2* dst, cudaStream_t s);
 cudaError_t launch_eval_df(int n, int64_t E, int64_t P, const int32_t* code, const int32_t* elem, const double* rst,
                            int F, const float2* fields, double* out, const BasisTab& tab, cudaStream_t s);

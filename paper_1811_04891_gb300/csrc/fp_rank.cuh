@@ -30,6 +30,7 @@ struct RankArgs {
     double* rst;
     double* dist2;
     unsigned long long* band;   // optional [3] near-tie counters (see k_rank), null = off
+    const int32_t* inv;         // pair results at sorted positions inv[q] (3D), null: at slots q (2D)
 };
 
 // Near-tie ("band") hits of a point's decisions, counted so that a result
@@ -85,6 +86,8 @@ template <int DIM, class Ctx>
 __device__ __forceinline__ void rank_point(const RankArgs& A, const FindParams& fp, const Ctx& C, int64_t p)
 {
     const int b = A.off[p], en = A.off[p + 1];
+    // where pair q's results are kept
+    auto W = [&](int q) -> int64_t { return A.inv ? (int64_t)A.inv[q] : (int64_t)q; };
     if (en > A.cap) {                                  // pairs dropped: not searched
         for (int q = b; q < A.cap; ++q) mark_loser(A.pair_pt + q);
         for (int f = 0; f < A.F; ++f) A.out[(int64_t)f * A.P + p] = __longlong_as_double(0x7ff8000000000000ULL);
@@ -103,7 +106,7 @@ __device__ __forceinline__ void rank_point(const RankArgs& A, const FindParams& 
     for (int q = b; q < en; ++q) {
         const int e = A.pair_elem[q];
         const double he = C.he(e);
-        const double res = A.pres[q];
+        const double res = A.pres[W(q)];
         if (res >= 0.5 * fp.tol_accept * he && res <= 2.0 * fp.tol_accept * he) hit |= 1u << BAND_ACCEPT;
         if (res >= 0.5 * fp.tol_border * he && res <= 2.0 * fp.tol_border * he) near_border = true;
         if (res <= fp.tol_accept * he) {
@@ -111,7 +114,7 @@ __device__ __forceinline__ void rank_point(const RankArgs& A, const FindParams& 
             bool winner = true;
             for (int q2 = b; q2 < en && winner; ++q2) {
                 const int e2 = A.pair_elem[q2];
-                if (q2 != q && C.sub(e2) == s && e2 < e && A.pres[q2] <= fp.tol_accept * C.he(e2)) winner = false;
+                if (q2 != q && C.sub(e2) == s && e2 < e && A.pres[W(q2)] <= fp.tol_accept * C.he(e2)) winner = false;
             }
             if (winner) {
                 ++nwin;
@@ -134,16 +137,16 @@ __device__ __forceinline__ void rank_point(const RankArgs& A, const FindParams& 
             int bs = 0x7fffffff;
             for (int q = b; q < en; ++q) {
                 const int e = A.pair_elem[q];
-                if (!(A.pres[q] <= fp.tol_accept * C.he(e))) continue;
+                if (!(A.pres[W(q)] <= fp.tol_accept * C.he(e))) continue;
                 const int s = C.sub(e);
                 bool winner = true;
                 for (int q2 = b; q2 < en && winner; ++q2) {
                     const int e2 = A.pair_elem[q2];
-                    if (q2 != q && C.sub(e2) == s && e2 < e && A.pres[q2] <= fp.tol_accept * C.he(e2))
+                    if (q2 != q && C.sub(e2) == s && e2 < e && A.pres[W(q2)] <= fp.tol_accept * C.he(e2))
                         winner = false;
                 }
                 if (!winner) continue;
-                const double dl = C.has_dist() ? C.delta(e, q) : 0.0;
+                const double dl = C.has_dist() ? C.delta(e, W(q)) : 0.0;
                 if (pass == 0) {
                     dmax = fmax(dmax, dl);
                 } else {
@@ -162,7 +165,7 @@ __device__ __forceinline__ void rank_point(const RankArgs& A, const FindParams& 
         for (int q = b; q < en; ++q) {
             const int e = A.pair_elem[q];
             const double he = C.he(e);
-            const double res = A.pres[q];
+            const double res = A.pres[W(q)];
             if (res > fp.tol_accept * he && res <= fp.tol_border * he && res <= bmin + fp.band) {
                 ++ntie;
                 if (e < be) {
@@ -189,8 +192,8 @@ __device__ __forceinline__ void rank_point(const RankArgs& A, const FindParams& 
         A.code[p] = code;
         A.osub[p] = C.sub(e);
         A.oelem[p] = C.elem_out(e);
-        for (int a = 0; a < DIM; ++a) A.rst[a * A.P + p] = A.prst[a * A.cap + pick];
-        const double res = A.pres[pick];
+        for (int a = 0; a < DIM; ++a) A.rst[a * A.P + p] = A.prst[a * A.cap + W(pick)];
+        const double res = A.pres[W(pick)];
         A.dist2[p] = res * res;
     } else {
         A.code[p] = 2;

@@ -146,6 +146,7 @@ extern "C" fp_status fp_find_static(fp_handle* h, int64_t P, const double* pts, 
     a.code = code; a.osub = sub; a.oelem = elem; a.rst = rst; a.dist2 = dist2;
     a.stats = h->prof ? h->stats : nullptr;
     a.band = h->band;
+    a.inv = a.order;    // pairs stay in point order: order and its inverse are both the identity
     FindParams fp;
     fp.tol_accept = h->opts.tol_accept;
     fp.tol_border = h->opts.tol_border;
