@@ -73,10 +73,10 @@ def work_for_order(n: int) -> dict:
 WORK = {"fp64": {"f64": SEED + K_ORACLE * ITER, "f32": 0.0, "f64acc": 0.0},
         "mixed": {"f64": 0.0, "f32": SEED + K_ORACLE * ITER, "f64acc": FINAL}}
 # DRAM bytes (read + written) per (point, candidate element) pair of the Newton
-# stage, measured with ncu on the 2.02M-point case of this workload (2.05M
-# pairs over the same 32,768 elements) and scaled by the pairs of a launch.
-# None where the kernel changed after the capture.
-TRAFFIC_PER_PAIR = {"fp64": 740.0}
+# stage, from one-pass ncu captures of the stage at this full size
+# (dram__bytes_read.sum + dram__bytes_write.sum of k_newton_mixed, and of
+# k_newton + k_newton_resume, over the 10.24 M pairs of one launch).
+TRAFFIC_PER_PAIR = {"mixed": 604.0, "fp64": 620.0}
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -295,12 +295,14 @@ def roofline_form(form, P, F, kernel_ms, ms_per_step, peaks, hbm_gbs, pairs, coo
             "peak_source": "measured in this run (fp_fma_probe, CUDA events), SM clock "
                            f"{peaks['clocks'].get('sm_mhz')} MHz",
             "traffic_source": None if traffic is None else
-            "ncu dram__bytes_read.sum + dram__bytes_write.sum per pair at 2.02e6 points, x pairs per launch",
+            "ncu dram__bytes_read.sum + dram__bytes_write.sum per pair, full-size one-pass capture, x pairs",
             "step": {"frac": t_step / (ms_per_step / 1e3), "roofline_ms": 1e3 * t_step,
                      "eval_roofline_ms": 1e3 * t_eval, "bytes": step_bytes, "bytes_ms": 1e3 * t_bytes,
                      "note": f"find + eval of {F} fields: Newton roofline + eval roofline "
                              f"({EVAL1:.0f} flop per field per point at "
                              f"{'P64' if form == 'fp64' else 'max(P64, Pdf)'}), against the measured step"},
+            "frac_final_step_on_fp64_pipe": (None if form == "fp64" else
+                                             P * (w["f32"] / p32 + w["f64acc"] / p64) / kn),
             "fp64_roofline": {"ms": 1e3 * fp64_view, "frac": fp64_view / (ms_per_step / 1e3),
                               "note": "the whole step's algorithmic work (seed + K iterations + evals) at the "
                                       "FP64 peak, against the measured step: above 1 means faster than any "
