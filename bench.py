@@ -804,7 +804,7 @@ def run_served(args, fg, dev):
         direct = 3 * allp.shape[1] / (e0.elapsed_time(e1) / 1e3)
         del o5, vals, allp, allq
         srv = serve.Server(h, fields_d, budget_bytes=40e9, resident_bytes=resident, chunk_points=args.served_chunk,
-                           streams=4, posted=posted)
+                           streams=4, posted=posted, copy_threads=4)
         # capacity: 1e6-point requests back to back (the first pass also fills the buffer pools)
         for _ in range(2):
             srv.completed = []
@@ -826,12 +826,15 @@ def run_served(args, fg, dev):
                      "capacity_over_direct": capacity / direct, "arrival_rate_hz": rate, "load": args.served_load,
                      "chunks": srv.launches, "mean_chunk_points": float(np.mean(srv.chunk_sizes)),
                      "held_back_passes": srv.held_back, "peak_inflight_bytes": srv.peak_inflight_bytes,
+                     "copy_threads": srv.copy_threads,
                      "resident_bytes": srv.resident,
                      "codes": {"inside": codes[0], "border": codes[1], "not_found": codes[2], "retry": codes[3]}}
+        srv.close()
         del srv, posted, h
     out["note"] = ("Poisson arrivals, sizes logU[1e2,1e6], 50% uniform untagged + 50% cylinder interface nodes "
                    "tagged with their session; chunks of at most chunk_points admitted while their device bytes "
-                   "fit the 40 GB budget beside the resident state; 4 streams; latency = arrival to results in "
+                   "fit the 40 GB budget beside the resident state; 4 streams; results copied into the requests "
+                   "on 4 host threads; latency = arrival to results in "
                    "host memory; direct = one fp_find_eval over 4e6 device-resident points of the same mix")
     return out
 

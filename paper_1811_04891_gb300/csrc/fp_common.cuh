@@ -312,6 +312,15 @@ __device__ __forceinline__ void df_fma_acc(df& acc, const df& a, float bh, float
     df_fma_acc(acc, a.hi, a.lo, bh, bl);
 }
 
+// the first term of a sum: df_fma_acc into a zero accumulator without the
+// two-sum (the same value, up to the sign of a zero)
+__device__ __forceinline__ df df_prod(float ah, float al, float bh, float bl)
+{
+    const float p = __fmul_rn(ah, bh);
+    const float pe = fmaf(ah, bh, -p);
+    return {p, fmaf(ah, bl, fmaf(al, bh, pe))};
+}
+
 // renormalise (fast two-sum): |lo| below one unit in the last place of hi
 __device__ __forceinline__ void df_norm(df& a)
 {
@@ -350,18 +359,23 @@ __device__ __forceinline__ df df_sub(df a, df b)
 template <int n>
 __device__ __forceinline__ df row_df(const float2* __restrict__ rowp, const float (&rh)[n], const float (&rl)[n])
 {
-    df u = {0.0f, 0.0f};
+    df u;
     if constexpr (n % 2 == 0) {
         const float4* row = reinterpret_cast<const float4*>(rowp);
+        const float4 v0 = __ldg(row);
+        u = df_prod(v0.x, v0.y, rh[0], rl[0]);
+        df_fma_acc(u, v0.z, v0.w, rh[1], rl[1]);
 #pragma unroll
-        for (int i2 = 0; i2 < n / 2; ++i2) {
+        for (int i2 = 1; i2 < n / 2; ++i2) {
             const float4 v = __ldg(row + i2);
             df_fma_acc(u, v.x, v.y, rh[2 * i2], rl[2 * i2]);
             df_fma_acc(u, v.z, v.w, rh[2 * i2 + 1], rl[2 * i2 + 1]);
         }
     } else {
+        const float2 v0 = __ldg(rowp);
+        u = df_prod(v0.x, v0.y, rh[0], rl[0]);
 #pragma unroll
-        for (int i = 0; i < n; ++i) {
+        for (int i = 1; i < n; ++i) {
             const float2 v = __ldg(rowp + i);
             df_fma_acc(u, v.x, v.y, rh[i], rl[i]);
         }

@@ -885,9 +885,9 @@ __device__ __forceinline__ void resid_df(const ElemPtr<float>& hi, const ElemPtr
                 float vh[n], vl[n];
                 load_row<n>(Xh, vh);
                 load_row<n>(Xl, vl);
-                u[a] = {0.0f, 0.0f};
+                u[a] = df_prod(vh[0], vl[0], rh[0], rl[0]);
 #pragma unroll
-                for (int i = 0; i < n; ++i) df_fma_acc(u[a], vh[i], vl[i], rh[i], rl[i]);
+                for (int i = 1; i < n; ++i) df_fma_acc(u[a], vh[i], vl[i], rh[i], rl[i]);
             }
 #pragma unroll
             for (int a = 0; a < 3; ++a) {

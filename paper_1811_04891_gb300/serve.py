@@ -20,6 +20,11 @@ continuous batching under a device-memory budget:
   different times overlaps on the device.  Buffers and workspaces are kept in
   pools by capacity (a power of two) and reused; the pools never hold more
   than the largest set of chunks the budget has let run at once.
+* A finished chunk's results are copied from its pinned buffers into the
+  requests on a few host threads (`copy_threads`; numpy copies release the
+  GIL), so the dispatcher keeps admitting and launching meanwhile.  The
+  chunk's buffers, and the device bytes they count for, go back to the pool
+  when that copy is done.
 * A request completes when all its chunks are back; latency = completion -
   arrival.
 
@@ -30,6 +35,7 @@ from __future__ import annotations
 
 import collections
 import time
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 from typing import Dict, List, Optional
 
@@ -51,6 +57,7 @@ class Request:
     values: np.ndarray = None             # [F][P]
     done_pts: int = 0
     next_pt: int = 0
+    t_last: Optional[float] = None
     t_done: Optional[float] = None
 
     @property
@@ -115,19 +122,33 @@ def pack_pending(pending: "collections.deque", capacity: int, copy_in) -> tuple:
     return pieces, n_used
 
 
-def scatter_results(pieces, code, elem, rst, values, now: float, completed: list):
+def copy_results(pieces, code, elem, rst, values):
     """Copy one chunk's results (code, elem [n], rst [3][n], values [F][n],
-    host arrays) back to the requests its pieces came from; a request whose
-    every point is back is stamped `now` and appended to `completed`."""
+    host arrays) back to the requests its pieces came from.  Pieces write
+    disjoint slices, so chunks may be copied concurrently."""
     for req, lo, so, take in pieces:
         req.code[lo:lo + take] = code[so:so + take]
         req.elem[lo:lo + take] = elem[so:so + take]
         req.rst[:, lo:lo + take] = rst[:, so:so + take]
         req.values[:, lo:lo + take] = values[:, so:so + take]
+
+
+def account(pieces, t: float, completed: list):
+    """Count one chunk's copied pieces against their requests; a request
+    whose every point is back is stamped with the latest time one of its
+    chunks was copied (t for this one) and appended to `completed`."""
+    for req, lo, so, take in pieces:
         req.done_pts += take
+        req.t_last = t if req.t_last is None else max(req.t_last, t)
         if req.done_pts == req.P:
-            req.t_done = now
+            req.t_done = req.t_last
             completed.append(req)
+
+
+def scatter_results(pieces, code, elem, rst, values, now: float, completed: list):
+    """copy_results then account, in the calling thread, stamped `now`."""
+    copy_results(pieces, code, elem, rst, values)
+    account(pieces, now, completed)
 
 
 @dataclass
@@ -161,13 +182,15 @@ class _Chunk:
 class Server:
     def __init__(self, handle, fields: torch.Tensor, budget_bytes: float = 40e9, resident_bytes: float = 0.0,
                  chunk_points: int = 1 << 17, streams: int = 4, min_chunk: int = 1 << 12, pairs_per_point: int = 4,
-                 device=None, posted=None):
+                 device=None, posted=None, copy_threads: int = 4):
         """handle: the resident mesh; fields [F][E][n^3] FP64 on the device
         (or `posted` double-float fields for the mixed form);
         budget_bytes: device memory the resident state and all chunks in
         flight may hold together; resident_bytes: what the resident state
         holds (fields, posted copies and anything else besides the handle's
-        own mesh, which fp_memory counts)."""
+        own mesh, which fp_memory counts); copy_threads: host threads that
+        copy finished chunks' results into the requests (0: the dispatcher
+        copies them itself)."""
         self.h = handle
         self.fields = fields
         self.posted = posted                  # fg.Fields (double-float) or None for FP64 eval
@@ -192,6 +215,16 @@ class Server:
         self.completed: List[Request] = []
         self.launches = 0
         self.chunk_sizes: List[int] = []
+        self.copy_threads = max(0, int(copy_threads))
+        self.copiers = ThreadPoolExecutor(self.copy_threads) if self.copy_threads else None
+        self.copying: List[tuple] = []        # (future, chunk) of results being copied out
+        self.t0 = time.perf_counter()         # origin of the times requests are stamped with
+        self.idle = False                     # the last pass moved nothing
+
+    def close(self):
+        if self.copiers is not None:
+            self.copiers.shutdown(wait=True)
+            self.copiers = None
 
     def bytes_for(self, cap: int) -> int:
         """Device bytes a chunk of capacity `cap` holds: its buffers and its
@@ -263,27 +296,51 @@ class Server:
         self.launches += 1
         self.chunk_sizes.append(n_used)
 
-    def _harvest(self, ch: _Chunk, now: float):
+    def _copy_out(self, ch: _Chunk) -> float:
         n = ch.n
         rst_h = ch.buf.rst_h.view(-1)[:3 * n].view(3, n).numpy()
         val_h = ch.buf.val_h.view(-1)[:self.F * n].view(self.F, n).numpy()
-        scatter_results(ch.pieces, ch.buf.code_h[:n].numpy(), ch.buf.elem_h[:n].numpy(), rst_h, val_h, now,
-                        self.completed)
+        copy_results(ch.pieces, ch.buf.code_h[:n].numpy(), ch.buf.elem_h[:n].numpy(), rst_h, val_h)
+        return time.perf_counter() - self.t0
+
+    def _release(self, ch: _Chunk, t: float):
+        account(ch.pieces, t, self.completed)
         self.pool[ch.buf.cap].append(ch.buf)
-        self.free_streams.append(ch.stream)
         self.inflight_bytes -= ch.nbytes
 
+    def _harvest(self, ch: _Chunk, now: float):
+        """A chunk whose device work and copies are done gives its stream back
+        at once; its results are copied into the requests (on a copier
+        thread if there are any) before its buffers are released."""
+        self.free_streams.append(ch.stream)
+        if self.copiers is None:
+            self._release(ch, self._copy_out(ch))
+        else:
+            self.copying.append((self.copiers.submit(self._copy_out, ch), ch))
+
     def step(self, now: float) -> bool:
-        """One dispatcher pass: harvest finished chunks (freeing their memory
-        and streams), then admit chunks while a stream is free and the budget
-        has room.  Returns True if any chunk is in flight or work is pending."""
+        """One dispatcher pass: harvest finished chunks (freeing their
+        streams), release chunks whose results are copied out (their memory),
+        then admit chunks while a stream is free and the budget has room.
+        Returns True if any chunk is in flight or being copied out, or work
+        is pending."""
         still = []
         for ch in self.inflight:
             if ch.event.query():
                 self._harvest(ch, now)
             else:
                 still.append(ch)
+        moved = len(still) < len(self.inflight)
         self.inflight = still
+        left = []
+        for fut, ch in self.copying:
+            if fut.done():
+                self._release(ch, fut.result())
+            else:
+                left.append((fut, ch))
+        moved = moved or len(left) < len(self.copying)
+        self.copying = left
+        launched = self.launches
         while self.pending and self.free_streams:
             n = admit(self.pending, self.chunk_points, self.min_chunk, self.avail_total - self.inflight_bytes,
                       self.bytes_for)
@@ -291,7 +348,8 @@ class Server:
                 self.held_back += 1
                 break
             self._launch(n)
-        return bool(self.inflight) or bool(self.pending)
+        self.idle = not moved and self.launches == launched
+        return bool(self.inflight) or bool(self.copying) or bool(self.pending)
 
 
 def run_stream(server: Server, requests: List[Request], time_scale: float = 1.0):
@@ -300,6 +358,7 @@ def run_stream(server: Server, requests: List[Request], time_scale: float = 1.0)
     order = sorted(requests, key=lambda r: r.t_arrive)
     i = 0
     t0 = time.perf_counter()
+    server.t0 = t0
     while True:
         now = time.perf_counter() - t0
         while i < len(order) and order[i].t_arrive * time_scale <= now:
@@ -309,6 +368,8 @@ def run_stream(server: Server, requests: List[Request], time_scale: float = 1.0)
         busy = server.step(now)
         if i == len(order) and not busy:
             break
+        if busy and server.idle:
+            time.sleep(5e-5)          # let the copier threads take the interpreter
         if not busy and i < len(order):
             wait = order[i].t_arrive * time_scale - (time.perf_counter() - t0)
             if wait > 0:

@@ -173,3 +173,36 @@ def test_large_request_spans_slots_in_order():
         got.append([(p[0].rid, p[1], p[2], p[3]) for p in pieces])
     assert got == [[(0, 0, 0, 1000)], [(0, 1000, 0, 1000)], [(0, 2000, 0, 500), (1, 0, 500, 10)]]
     assert not pending
+
+
+def test_copied_chunks_complete_requests_at_their_latest_copy():
+    """Results copied on several threads: chunks of one request copied out
+    of order, concurrently; the request completes once, stamped with the
+    latest copy's time, with every point's results in place."""
+    from concurrent.futures import ThreadPoolExecutor
+    P, n = 10_000, 1024
+    req = serve.Request(0, 0.0, np.zeros((3, P)), np.zeros(P, np.int32))
+    req.code, req.elem = np.empty(P, np.int32), np.empty(P, np.int32)
+    req.rst, req.values = np.empty((3, P)), np.empty((2, P))
+    chunks = []
+    for lo in range(0, P, n):
+        take = min(n, P - lo)
+        ids = np.arange(lo, lo + take)
+        chunks.append(([(req, lo, 0, take)], ids.astype(np.int32), -ids.astype(np.int32),
+                       np.stack([ids * 1.0, ids * 2.0, ids * 3.0]), np.stack([ids + 0.5, ids - 0.5])))
+    order = list(np.random.default_rng(3).permutation(len(chunks)))
+    with ThreadPoolExecutor(4) as ex:
+        futs = [ex.submit(serve.copy_results, *chunks[k]) for k in order]
+        for f in futs:
+            f.result()
+    completed = []
+    times = [7.0, 2.0, 9.5] + [1.0] * (len(chunks) - 3)
+    for k, t in zip(order, times):
+        assert req.t_done is None
+        serve.account(chunks[k][0], t, completed)
+    assert completed == [req] and req.t_done == 9.5 and req.done_pts == P
+    ids = np.arange(P)
+    np.testing.assert_array_equal(req.code, ids)
+    np.testing.assert_array_equal(req.elem, -ids)
+    np.testing.assert_array_equal(req.rst, np.stack([ids * 1.0, ids * 2.0, ids * 3.0]))
+    np.testing.assert_array_equal(req.values, np.stack([ids + 0.5, ids - 0.5]))
