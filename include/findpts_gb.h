@@ -551,9 +551,19 @@ fp_status fp_profile_read(fp_handle *h, int kind, double *total_ms, int64_t *lau
 /* Mixed form, while profiling is enabled: how many pairs took each Newton
  * path since the previous read -- counts[0] rejected after the FP32 phase
  * (converged away from the element), [1] FP32 phase not converged, [2]
- * confirmed by the single FP64 step, [3] sent to the full FP64 Newton.
- * Synchronises the device and resets the counters. */
+ * finished by the compensated final steps, [3] sent to the full FP64
+ * Newton.  Synchronises the device and resets the counters. */
 fp_status fp_newton_paths(fp_handle *h, int64_t *counts);
+
+/* Mixed form (Sec. 2.1 Newton solve, final steps at FP64 accuracy): the
+ * number of compensated (double-float) residuals a pair may use in its final
+ * steps before it is handed to the full FP64 Newton, 0..8 (3 after
+ * fp_setup).  0 sends every pair whose FP32 phase converged near its element
+ * to the full FP64 Newton: slower, with results within the same tolerance.
+ * Applies to later fp_find / fp_find_eval / fp_find_static calls and to
+ * batches created afterwards (all handles of a batch must agree).
+ * Errors: FP_ERR_NOT_SETUP, FP_ERR_INVALID_ARG (out of range). */
+fp_status fp_set_mixed_refine(fp_handle *h, int max_residuals);
 
 /* Device bytes the handle holds: *resident = the posted mesh and its search
  * structures (coordinates and their FP32 copies, boxes, hash grid, distance

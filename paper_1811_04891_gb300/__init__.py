@@ -159,6 +159,8 @@ def _load():
     L.fp_debug_boxes.restype = ci
     L.fp_profile.argtypes = [vp, ci]
     L.fp_profile.restype = ci
+    L.fp_set_mixed_refine.argtypes = [vp, ci]
+    L.fp_set_mixed_refine.restype = ci
     L.fp_profile_read.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
     L.fp_profile_read.restype = ci
     L.fp_launch_count.argtypes = []
@@ -778,6 +780,12 @@ PROF_KINDS = {"screen": 0, "sort": 1, "newton": 2, "rank": 3, "eval": 4}
 
 def fp_profile(h: Handle, enable: bool = True):
     _check(lib().fp_profile(h.ptr, int(bool(enable))), h.ptr)
+
+
+def fp_set_mixed_refine(h: Handle, max_residuals: int):
+    """Mixed form: compensated residuals per pair before the full FP64
+    Newton (0..8, default 3; 0 sends every pair to the full FP64 Newton)."""
+    _check(lib().fp_set_mixed_refine(h.ptr, int(max_residuals)), h.ptr)
 
 
 def fp_profile_read(h: Handle, kind: str):

@@ -295,7 +295,7 @@ extern "C" fp_status fp_batch_create(fp_batch** out, int ninst, fp_handle* const
         const fp_opts& o0 = handles[0]->opts;
         if (h->opts.precision != o0.precision || h->opts.tol_accept != o0.tol_accept ||
             h->opts.tol_border != o0.tol_border || h->opts.max_newton != o0.max_newton ||
-            h->opts.tie_band != o0.tie_band) {
+            h->opts.tie_band != o0.tie_band || h->refine != handles[0]->refine) {
             delete b;
             return FP_ERR_INVALID_ARG;
         }
@@ -350,6 +350,7 @@ extern "C" fp_status fp_batch_create(fp_batch** out, int ninst, fp_handle* const
         g.fp.band = 0.0;                  // per instance, in the classification
         g.fp.max_newton = o.max_newton;
         g.fp.mixed = b->mixed;
+        g.fp.refine = handles[0]->refine;
         e = alloc(&g.coords, 3 * g.E * n3);
         if (e == cudaSuccess && b->mixed) e = alloc(&g.coords32, 3 * g.E * n3);
         if (e == cudaSuccess && b->mixed) e = alloc(&g.coords32lo, 3 * g.E * n3);

@@ -89,6 +89,7 @@ struct FindParams {
     double band;        // absolute tie band = tie_band * L
     int max_newton;
     int mixed;
+    int refine;         // mixed form: compensated residuals per pair before the FP64 fallback
 };
 
 // ---------------------------------------------------------------------------
@@ -395,7 +396,8 @@ __device__ __forceinline__ double contract_df(const float2* __restrict__ Fe, con
 #pragma unroll 1
     for (int k = 0; k < n; ++k) {
         df ck = {0.0f, 0.0f};
-#pragma unroll 1
+        // two rows in flight: their loads and two-sums overlap
+#pragma unroll 2
         for (int j = 0; j < n; ++j) {
             const df u = row_df<n>(Fe + n * (j + n * k), rh, rl);
             df_fma_acc(ck, u, sh[j], sl[j]);

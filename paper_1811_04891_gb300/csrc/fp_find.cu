@@ -662,6 +662,7 @@ struct NewtonArgs {
     int64_t cap;
     double reject32;      // mixed: reject after FP32 when residual > reject32 * h_e
     int max_newton;
+    int refine;           // mixed: compensated residuals per pair before the FP64 fallback
     unsigned long long* stats;  // optional path counters (profiling): [0] rejected after FP32,
                                 // [1] FP32 not converged, [2] FP64 step converged, [3] sent to the fallback
     const int32_t* warm_elem;   // optional [P]: each point's element at the previous mesh position
@@ -926,10 +927,12 @@ __device__ __forceinline__ double chord_tol_df(const double (&J)[9], double he)
     return fmax(Lim<double>::chord, 1.4210854715202004e-14 * he * rows / fabs(det));
 }
 
-// final steps of the mixed form: at most kRefine double-float residuals; a
-// step of at most kConfirm (computed in FP32) is re-solved in FP64
-constexpr int kRefine = 3;
+// final steps of the mixed form: at most NewtonArgs::refine double-float
+// residuals (3 by default); a step of at most kConfirm (computed in FP32) is
+// re-solved in FP64; an FP64 step of at most kTake chord tolerances is taken
+// without another residual (see solve_mixed)
 constexpr double kConfirm = 1e-10;
+constexpr double kTake = 1e3;
 
 // passes 1 and 2 in one kernel: the FP32 work of some warps overlaps the
 // FP64 work of others.
@@ -983,12 +986,18 @@ __device__ __forceinline__ void solve_mixed(const NewtonArgs& A, const BasisTab&
             // that is still large is taken as computed in FP32; once it is
             // small, the 3x3 solve is repeated in FP64, and an FP64 step within
             // the tolerance confirms convergence: r is kept with its own
-            // residual (as in chord64).  Unconfirmed after kRefine residuals:
+            // residual (as in chord64).  An FP64 step s above the tolerance ct
+            // but at most kTake * ct is taken, and the residual at r + s is
+            // the linear model f + J s: the Jacobian (FP32, from the last FP32
+            // iterate) has a relative error eps of at most ~1e-4, so r + s is
+            // within eps |s| <= 0.1 ct of the solution and f + J s within
+            // eps |J s| of its residual -- a further compensated residual
+            // would only confirm this.  Unconfirmed after A.refine residuals:
             // the pair goes to the full FP64 Newton.
             const ElemPtr<float> lo32 = {A.coords32lo + (int64_t)e * n3, A.coords32lo + (A.E + e) * n3,
                                          A.coords32lo + (2 * A.E + e) * n3};
             res = -1.0;
-            for (int it = 0; it < kRefine; ++it) {
+            for (int it = 0; it < A.refine; ++it) {
                 float f[3], d32[3];
                 resid_df<n>(el32, lo32, tab, r, xd, f);
                 const double fd[3] = {(double)f[0], (double)f[1], (double)f[2]};
@@ -1016,8 +1025,19 @@ __device__ __forceinline__ void solve_mixed(const NewtonArgs& A, const BasisTab&
                     double rn[3];
                     box_step<double>(r, d, rn);
                     const double sn = fmax(fabs(rn[0] - r[0]), fmax(fabs(rn[1] - r[1]), fabs(rn[2] - r[2])));
-                    if (sn <= chord_tol_df(J, A.boxes[e].he)) {
+                    const double ct = chord_tol_df(J, A.boxes[e].he);
+                    if (sn <= ct) {
                         res = sqrt(fd[0] * fd[0] + fd[1] * fd[1] + fd[2] * fd[2]);
+                        break;
+                    }
+                    if (sn <= kTake * ct) {
+                        double g[3];
+#pragma unroll
+                        for (int a = 0; a < 3; ++a)
+                            g[a] = fd[a] + J[3 * a] * (rn[0] - r[0]) + J[3 * a + 1] * (rn[1] - r[1]) +
+                                   J[3 * a + 2] * (rn[2] - r[2]);
+                        r[0] = rn[0]; r[1] = rn[1]; r[2] = rn[2];
+                        res = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
                         break;
                     }
                     r[0] = rn[0]; r[1] = rn[1]; r[2] = rn[2];
@@ -1235,6 +1255,7 @@ static cudaError_t newton_n(const FindArgs& a, int64_t npairs, const BasisTab& t
     na.cap = a.cap;
     na.reject32 = 1e-4;
     na.max_newton = fp.max_newton;
+    na.refine = fp.refine;
     na.stats = a.stats;
     na.warm_elem = a.warm_elem;
     na.warm_rst = a.warm_rst;

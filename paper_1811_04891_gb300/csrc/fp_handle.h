@@ -20,6 +20,7 @@ struct fp_handle {
     int64_t E = 0;
     int nsub = 0;
     fp_opts opts{};
+    int refine = 3;                // mixed form: compensated residuals per pair (fp_set_mixed_refine)
     fpg::BasisTab tab{};
     fpg::HashGrid grid{};
     int64_t nnz = 0;

@@ -605,6 +605,7 @@ static fp_status find_impl(fp_handle* h, int64_t P, const double* pts, const int
     fp.band = h->opts.tie_band * h->L;
     fp.max_newton = h->opts.max_newton;
     fp.mixed = h->opts.precision == FP_PREC_MIXED;
+    fp.refine = h->refine;
     const bool d2 = h->dim == 2;
     cudaError_t err = d2 ? find_count2(a, s) : find_count(a, h->tab, fp, s);
     if (err != cudaSuccess) return cuda_fail(h, err, "fp_find count");
@@ -896,6 +897,7 @@ static fp_status find_ws_impl(fp_handle* h, fp_workspace* w, int64_t P, const do
     fp.band = h->opts.tie_band * h->L;
     fp.max_newton = h->opts.max_newton;
     fp.mixed = h->opts.precision == FP_PREC_MIXED;
+    fp.refine = h->refine;
     const int block = h->opts.points_per_block > 0 ? h->opts.points_per_block : 128;
     cudaError_t err = find_count(a, h->tab, fp, s);
     if (err == cudaSuccess) err = find_emit(a, s);
@@ -1090,6 +1092,14 @@ fp_status fp_profile(fp_handle* h, int enable)
         if (e == cudaSuccess) e = cudaMemset(h->stats, 0, 4 * sizeof(unsigned long long));
         if (e != cudaSuccess) return cuda_fail(h, e, "fp_profile");
     }
+    return FP_OK;
+}
+
+fp_status fp_set_mixed_refine(fp_handle* h, int max_residuals)
+{
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
+    if (max_residuals < 0 || max_residuals > 8) return FP_ERR_INVALID_ARG;
+    h->refine = max_residuals;
     return FP_OK;
 }
 

@@ -153,6 +153,7 @@ extern "C" fp_status fp_find_static(fp_handle* h, int64_t P, const double* pts, 
     fp.band = h->opts.tie_band * h->L;
     fp.max_newton = h->opts.max_newton;
     fp.mixed = h->opts.precision == FP_PREC_MIXED;
+    fp.refine = h->refine;
 
     err = find_count(a, h->tab, fp, s);
     if (err == cudaSuccess) err = cudaMemcpyAsync(h->h_total, a.off + P, sizeof(int32_t), cudaMemcpyDeviceToHost, s);

@@ -9,7 +9,9 @@ TOL_RST = {0: 1e-12, 1: 1e-10}       # FP64 form / mixed form (|delta r| bound)
 TOL_EVAL_REL = 1e-12                 # eval, relative to the field's max |nodal value|
 
 
-def gpu_find(mesh, pts, qsess=None, prec=0, dist="mesh", fields=None, **opt):
+def gpu_find(mesh, pts, qsess=None, prec=0, dist="mesh", fields=None, refine=None, paths=False, **opt):
+    """refine: fp_set_mixed_refine before the find; paths: return the mixed
+    form's Newton path counts (fp_newton_paths) under "paths"."""
     import paper_1811_04891_gb300 as fg
     dev = torch.device("cuda:0")
     d = mesh.dist if isinstance(dist, str) and dist == "mesh" else dist
@@ -17,6 +19,10 @@ def gpu_find(mesh, pts, qsess=None, prec=0, dist="mesh", fields=None, **opt):
                     torch.from_numpy(mesh.sub).to(dev),
                     None if d is None else torch.from_numpy(np.ascontiguousarray(d)).to(dev),
                     opts=fg.default_opts(precision=prec, **opt))
+    if refine is not None:
+        fg.fp_set_mixed_refine(h, refine)
+    if paths:
+        fg.fp_profile(h, True)
     qs = None if qsess is None else torch.from_numpy(np.ascontiguousarray(qsess, dtype=np.int32)).to(dev)
     code, sub, elem, rst, d2 = fg.fp_find(h, torch.from_numpy(np.ascontiguousarray(pts)).to(dev), qs)
     out = None
@@ -27,6 +33,8 @@ def gpu_find(mesh, pts, qsess=None, prec=0, dist="mesh", fields=None, **opt):
            "rst": rst.cpu().numpy(), "dist2": d2.cpu().numpy(), "handle": h, "band": fg.fp_band_hits(h)}
     if out is not None:
         res["eval"] = out.cpu().numpy()
+    if paths:
+        res["paths"] = fg.fp_newton_paths(h)
     return res
 
 

@@ -57,6 +57,40 @@ def test_box_annulus_untagged_owner_rule(prec):
     assert set(np.unique(r["sub"][r["code"] == 0])) == {0, 1}
 
 
+@pytest.mark.parametrize("refine", [0, 1, 2, 3])
+def test_mixed_final_steps_and_full_fp64_fallback(refine):
+    """Every route out of the mixed form's FP32 phase gives the oracle's
+    results: refine = 0 sends every pair that converged near its element to
+    the full FP64 Newton; with 1 the first compensated residual's step is
+    too large to finish most pairs (they fall back); 2 finishes most of
+    them; 3 is the default."""
+    mesh, q = synth.deformed_cube(ne=8, P_uniform=30011, P_face=5003)
+    g = gpu_find(mesh, q.pts, prec=1, fields=q.fields, refine=refine, paths=True)
+    r = oracle_find(mesh, q.pts, fields=q.fields)
+    assert_parity(g, r, 1, fields=q.fields, band=NO_BAND)
+    p = g["paths"]
+    near = p["fp64_step_converged"] + p["fallback"] - p["fp32_not_converged"]
+    assert near > 0.9 * q.pts.shape[1]
+    if refine == 0:
+        assert p["fp64_step_converged"] == 0 and p["fallback"] >= near
+    if refine == 1:
+        assert p["fallback"] > 0.5 * near
+    if refine >= 2:
+        assert p["fp64_step_converged"] > 0.5 * near
+    if refine == 3:
+        assert p["fallback"] <= 1e-3 * near
+
+
+def test_mixed_full_fp64_fallback_sessions_and_borders():
+    """The full FP64 Newton behind the mixed form on tagged interface points
+    of the box + annulus mesh (session exclusion, border points, owner rule)."""
+    mesh, q = synth.box_annulus()
+    g = gpu_find(mesh, q.pts, q.qsess, prec=1, fields=q.fields, refine=0, paths=True)
+    r = oracle_find(mesh, q.pts, q.qsess, fields=q.fields)
+    assert_parity(g, r, 1, fields=q.fields, band=NO_BAND)
+    assert g["paths"]["fp64_step_converged"] == 0 and g["paths"]["fallback"] > 0
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_deformed_cube_reduced_with_near_face(prec):
     mesh, q = synth.deformed_cube(ne=8, P_uniform=30011, P_face=5003)
