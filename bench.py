@@ -242,7 +242,7 @@ def measure_peaks(fg, dev, uuid, target_ms: float = 60.0, blocks_per_sm: int = 4
     clocks.start()
     time.sleep(0.3)
     rates, launches = {}, {}
-    for kind in ("f64", "f32", "df"):
+    for kind in ("f64", "f32", "df", "f32x2", "df2"):
         iters = 256
         fl, ms = once(kind, iters)
         while ms < 5.0 and iters < (1 << 30):
@@ -256,11 +256,12 @@ def measure_peaks(fg, dev, uuid, target_ms: float = 60.0, blocks_per_sm: int = 4
         rates[kind] = best / 1e12
         launches[kind] = {"iters": iters, "flops": fl, "ms": ms}
     clk = clocks.stop()
-    return {"p64": rates["f64"], "p32": rates["f32"], "pdf": rates["df"], "unit": "TFLOP/s",
-            "clocks": clk, "launches": launches,
+    return {"p64": rates["f64"], "p32": max(rates["f32"], rates["f32x2"]), "pdf": max(rates["df"], rates["df2"]),
+            "unit": "TFLOP/s", "clocks": clk, "launches": launches, "by_kind": rates,
             "method": f"fp_fma_probe: {blocks_per_sm} x 256 threads per SM, 8 independent chains per thread, "
                       "best of 3 launches (CUDA events); df = double-float multiply-add on the FP32 pipes "
-                      "(exact leading product + two-sum), counted as 2 FP64-class flops"}
+                      "(exact leading product + two-sum), counted as 2 FP64-class flops; p32 and pdf are the "
+                      "faster of the scalar and the packed-pair (float2) instruction forms"}
 
 
 def roofline_form(form, P, F, kernel_ms, ms_per_step, peaks, hbm_gbs, pairs, coords_bytes, field_bytes):
@@ -291,7 +292,8 @@ def roofline_form(form, P, F, kernel_ms, ms_per_step, peaks, hbm_gbs, pairs, coo
             "kernel": "k_newton_mixed<8> + k_newton64_full<8>" if form == "mixed" else "k_newton<8>",
             "kernel_ms": kernel_ms["newton"], "units_per_launch": P, "work_unit": "located point (true element only)",
             "unit_work": w, "pairs_per_launch": pairs, "roofline_ms": 1e3 * t_newton,
-            "peaks_tflops": {"p64": peaks["p64"], "p32": peaks["p32"], "pdf": peaks["pdf"]},
+            "peaks_tflops": {"p64": peaks["p64"], "p32": peaks["p32"], "pdf": peaks["pdf"],
+                             "by_instruction_form": peaks.get("by_kind")},
             "peak_source": "measured in this run (fp_fma_probe, CUDA events), SM clock "
                            f"{peaks['clocks'].get('sm_mhz')} MHz",
             "traffic_source": None if traffic is None else

@@ -595,10 +595,13 @@ fp_status fp_band_hits(fp_handle *h, int64_t *counts);
  *   kind 0  FP64 fma             kind 1  FP32 fma
  *   kind 2  double-float multiply-add on the FP32 pipes (the operation the
  *           mixed form uses for its FP64-accuracy residuals and eval)
+ *   kind 3  packed FP32 pair fma (two lanes of a float2 per instruction)
+ *   kind 4  two double-float multiply-adds in packed FP32 pairs
  * and stores one double per thread to `sink` (device, fp_probe_threads()
  * doubles).  *flops (may be NULL) receives the launch's flop count (2 per
- * step; a double-float step counts as one FP64-class multiply-add).  Time it
- * with events on `stream`.  Errors: FP_ERR_INVALID_ARG (kind outside 0..2,
+ * fma, 4 per packed pair fma; a double-float step counts as one FP64-class
+ * multiply-add).  Time it with events on `stream`.  Errors:
+ * FP_ERR_INVALID_ARG (kind outside 0..4,
  * iters < 1, blocks_per_sm outside 1..8, sink NULL), FP_ERR_CUDA.
  * fp_probe_threads returns the threads of one launch (-1 on a CUDA error). */
 fp_status fp_fma_probe(int kind, int64_t iters, int blocks_per_sm, double *sink, double *flops,

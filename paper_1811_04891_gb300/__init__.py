@@ -835,7 +835,7 @@ def fp_band_hits(h: Handle) -> dict:
     return {k: int(c[i]) for i, k in enumerate(BAND_KINDS)}
 
 
-PROBE_KINDS = {"f64": 0, "f32": 1, "df": 2}
+PROBE_KINDS = {"f64": 0, "f32": 1, "df": 2, "f32x2": 3, "df2": 4}
 
 
 def fp_probe_threads(blocks_per_sm: int = 4) -> int:

@@ -396,7 +396,7 @@ extern "C" fp_status fp_batch_create(fp_batch** out, int ninst, fp_handle* const
         if (e == cudaSuccess && F > 0 && b->mixed) {
             const int64_t nv = (int64_t)F * g.E * n3;
             e = alloc(&g.fields_df, nv);
-            if (e == cudaSuccess) e = launch_split_df(nv, g.fields, g.fields_df, 0);
+            if (e == cudaSuccess) e = launch_split_df(nv, g.n, g.fields, g.fields_df, 0);
         }
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);

@@ -207,6 +207,8 @@ __device__ __forceinline__ void map_jac(const T* __restrict__ X0, const T* __res
 {
     // The j and k loops stay rolled: unrolled, the contraction is inlined
     // eight times over in the Newton kernels and runs ~1.8x slower (measured).
+    // (Packed FP32 pairs for the i sums, as the double-float rows use them,
+    // measured slower here: 26.4 against 25.8 ms for the mixed Newton stage.)
     T xa[3] = {0, 0, 0}, xr[3] = {0, 0, 0}, xs[3] = {0, 0, 0}, xt[3] = {0, 0, 0};
 #pragma unroll 1
     for (int k = 0; k < n; ++k) {
@@ -322,6 +324,45 @@ __device__ __forceinline__ df df_prod(float ah, float al, float bh, float bl)
     return {p, fmaf(ah, bl, fmaf(al, bh, pe))};
 }
 
+// Two double-floats side by side in packed FP32 pairs (x and y lanes of a
+// float2): every packed operation is the scalar one on each lane, rounded
+// the same way, so df2_fma_acc gives exactly two df_fma_acc results.
+struct df2 {
+    float2 hi, lo;
+};
+
+__device__ __forceinline__ float2 f2_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ void df2_fma_acc(df2& acc, float2 ah, float2 al, float2 bh, float2 bl)
+{
+    const float2 p = __fmul2_rn(ah, bh);
+    const float2 pe = __ffma2_rn(ah, bh, f2_neg(p));
+    const float2 t = __ffma2_rn(ah, bl, __ffma2_rn(al, bh, pe));
+    const float2 s = __fadd2_rn(acc.hi, p);
+    const float2 bb = __fadd2_rn(s, f2_neg(acc.hi));
+    const float2 err = __fadd2_rn(__fadd2_rn(acc.hi, f2_neg(__fadd2_rn(s, f2_neg(bb)))), __fadd2_rn(p, f2_neg(bb)));
+    acc.hi = s;
+    acc.lo = __fadd2_rn(acc.lo, __fadd2_rn(err, t));
+}
+
+// the first term of a packed pair of sums (df_prod on both lanes)
+__device__ __forceinline__ df2 df2_prod(float2 ah, float2 al, float2 bh, float2 bl)
+{
+    const float2 p = __fmul2_rn(ah, bh);
+    const float2 pe = __ffma2_rn(ah, bh, f2_neg(p));
+    return {p, __ffma2_rn(ah, bl, __ffma2_rn(al, bh, pe))};
+}
+
+// the sum of a packed pair's two lanes: error-free two-sum of the leading
+// parts, the low parts and the error added to the low part
+__device__ __forceinline__ df df2_join(const df2& a)
+{
+    const float s = __fadd_rn(a.hi.x, a.hi.y);
+    const float bb = __fsub_rn(s, a.hi.x);
+    const float err = __fadd_rn(__fsub_rn(a.hi.x, __fsub_rn(s, bb)), __fsub_rn(a.hi.y, bb));
+    return {s, __fadd_rn(__fadd_rn(a.lo.x, a.lo.y), err)};
+}
+
 // renormalise (fast two-sum): |lo| below one unit in the last place of hi
 __device__ __forceinline__ void df_norm(df& a)
 {
@@ -351,38 +392,38 @@ __device__ __forceinline__ df df_sub(df a, df b)
     return {t, __fsub_rn(lo, __fsub_rn(t, s))};
 }
 
-// One row of a double-float field contraction: sum_i v_i (rh_i + rl_i) for
-// the n values v (float2 pairs, 16-byte aligned rows for even n), one
-// accumulator in i order, renormalised.  Every double-float evaluation of
-// fields goes through this routine, so all of them round alike.  (Two
-// interleaved partial sums cost one more double-float addition per row,
-// which measured slower than the latency they hide.)
+// One row of a double-float contraction: sum_i (vh_i + vl_i)(rh_i + rl_i),
+// even i in the x lanes and odd i in the y lanes of packed FP32 pairs (one
+// instruction does both), the lanes joined by an error-free two-sum and the
+// result renormalised.  Every double-float contraction (Newton residuals and
+// field evaluation) goes through this routine, so all of them round alike.
+template <int n>
+__device__ __forceinline__ df row_df(const float (&vh)[n], const float (&vl)[n], const float (&rh)[n],
+                                     const float (&rl)[n])
+{
+    df2 u = df2_prod(make_float2(vh[0], vh[1]), make_float2(vl[0], vl[1]), make_float2(rh[0], rh[1]),
+                     make_float2(rl[0], rl[1]));
+#pragma unroll
+    for (int m = 1; m < n / 2; ++m)
+        df2_fma_acc(u, make_float2(vh[2 * m], vh[2 * m + 1]), make_float2(vl[2 * m], vl[2 * m + 1]),
+                    make_float2(rh[2 * m], rh[2 * m + 1]), make_float2(rl[2 * m], rl[2 * m + 1]));
+    df r = df2_join(u);
+    if constexpr (n % 2 == 1) df_fma_acc(r, vh[n - 1], vl[n - 1], rh[n - 1], rl[n - 1]);
+    df_norm(r);
+    return r;
+}
+
+// Posted (double-float) fields keep each row of n nodes as its n high parts
+// followed by its n low parts (n float2 slots), so both halves load as
+// aligned vectors for even n.
 template <int n>
 __device__ __forceinline__ df row_df(const float2* __restrict__ rowp, const float (&rh)[n], const float (&rl)[n])
 {
-    df u;
-    if constexpr (n % 2 == 0) {
-        const float4* row = reinterpret_cast<const float4*>(rowp);
-        const float4 v0 = __ldg(row);
-        u = df_prod(v0.x, v0.y, rh[0], rl[0]);
-        df_fma_acc(u, v0.z, v0.w, rh[1], rl[1]);
-#pragma unroll
-        for (int i2 = 1; i2 < n / 2; ++i2) {
-            const float4 v = __ldg(row + i2);
-            df_fma_acc(u, v.x, v.y, rh[2 * i2], rl[2 * i2]);
-            df_fma_acc(u, v.z, v.w, rh[2 * i2 + 1], rl[2 * i2 + 1]);
-        }
-    } else {
-        const float2 v0 = __ldg(rowp);
-        u = df_prod(v0.x, v0.y, rh[0], rl[0]);
-#pragma unroll
-        for (int i = 1; i < n; ++i) {
-            const float2 v = __ldg(rowp + i);
-            df_fma_acc(u, v.x, v.y, rh[i], rl[i]);
-        }
-    }
-    df_norm(u);
-    return u;
+    const float* row = reinterpret_cast<const float*>(rowp);
+    float vh[n], vl[n];
+    load_row<n>(row, vh);
+    load_row<n>(row + n, vl);
+    return row_df<n>(vh, vl, rh, rl);
 }
 
 // sum_ijk F_ijk h_i h_j h_k for one element's double-float values Fe (n^3,

@@ -92,7 +92,7 @@ struct Eval2Args {
     const int32_t* elem;
     const double* rst;
     int F;
-    const float2* fields;     // [F][E][n3] (hi, lo)
+    const float2* fields;     // [F][E][n3] posted: per row n high parts, then n low parts
     double* out;
 };
 
@@ -179,19 +179,24 @@ __global__ void __launch_bounds__(128) k_eval_points_df(int64_t E, int64_t P, in
     out[(int64_t)f * P + p] = contract_df<n>(fields + ((int64_t)f * E + e) * n3, rh, rl, sh, sl, th, tl);
 }
 
-__global__ void k_split_df(int64_t n, const double* __restrict__ src, float2* __restrict__ dst)
+// posted fields: value v -> (hi, lo) = (fl32(v), fl32(v - hi)), each row of
+// n nodes stored as its n high parts then its n low parts (see row_df)
+__global__ void k_split_df(int64_t count, int n, const double* __restrict__ src, float2* __restrict__ dst)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float* d = reinterpret_cast<float*>(dst);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / n, c = i - row * n;
         const double v = src[i];
         const float h = (float)v;
-        dst[i] = make_float2(h, (float)(v - (double)h));
+        d[2 * n * row + c] = h;
+        d[2 * n * row + n + c] = (float)(v - (double)h);
     }
 }
 
-cudaError_t launch_split_df(int64_t n, const double* src, float2* dst, cudaStream_t s)
+cudaError_t launch_split_df(int64_t count, int n, const double* src, float2* dst, cudaStream_t s)
 {
-    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 32);
-    k_split_df<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(n, src, dst);
+    const int64_t blocks = std::min<int64_t>((count + 255) / 256, 152 * 32);
+    k_split_df<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(count, n, src, dst);
     count_launch();
     return cudaGetLastError();
 }

@@ -886,15 +886,10 @@ __device__ __forceinline__ void resid_df(const ElemPtr<float>& hi, const ElemPtr
                 float vh[n], vl[n];
                 load_row<n>(Xh, vh);
                 load_row<n>(Xl, vl);
-                u[a] = df_prod(vh[0], vl[0], rh[0], rl[0]);
-#pragma unroll
-                for (int i = 1; i < n; ++i) df_fma_acc(u[a], vh[i], vl[i], rh[i], rl[i]);
+                u[a] = row_df<n>(vh, vl, rh, rl);
             }
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                df_norm(u[a]);
-                df_fma_acc(ck[a], u[a].hi, u[a].lo, sh[j], sl[j]);
-            }
+            for (int a = 0; a < 3; ++a) df_fma_acc(ck[a], u[a].hi, u[a].lo, sh[j], sl[j]);
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {

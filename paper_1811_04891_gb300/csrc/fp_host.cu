@@ -941,7 +941,7 @@ fp_status fp_fields_create(const fp_handle* h, int F, const double* fields, fp_f
     f->owner = h;
     f->F = F;
     cudaError_t e = dalloc(&f->data, n);
-    if (e == cudaSuccess) e = launch_split_df(n, fields, f->data, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = launch_split_df(n, h->n, fields, f->data, (cudaStream_t)stream);
     if (e != cudaSuccess) {
         dfree(f->data);
         delete f;

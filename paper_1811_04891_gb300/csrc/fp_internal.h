@@ -161,7 +161,7 @@ cudaError_t launch_eval_pairs(int n, int64_t E, int64_t P, const int32_t* dcount
                               const EvalSpec& ev, const BasisTab& tab, unsigned grid, cudaStream_t s,
                               const int32_t* s_lo = nullptr, const int32_t* s_hi = nullptr, int32_t ebase = 0,
                               bool walk = false);
-cudaError_t launch_split_df(int64_t n, const double* src, float2* dst, cudaStream_t s);
+cudaError_t launch_split_df(int64_t count, int n, const double* src, float2* dst, cudaStream_t s);
 cudaError_t launch_eval_df(int n, int64_t E, int64_t P, const int32_t* code, const int32_t* elem, const double* rst,
                            int F, const float2* fields, double* out, const BasisTab& tab, cudaStream_t s);
 cudaError_t launch_points_basis(int n, int64_t P, const int32_t* code, const int32_t* elem, const double* rst,
