@@ -76,7 +76,7 @@ WORK = {"fp64": {"f64": SEED + K_ORACLE * ITER, "f32": 0.0, "f64acc": 0.0},
 # stage, from one-pass ncu captures of the stage at this full size
 # (dram__bytes_read.sum + dram__bytes_write.sum of k_newton_mixed, and of
 # k_newton + k_newton_resume, over the 10.24 M pairs of one launch).
-TRAFFIC_PER_PAIR = {"mixed": 604.0, "fp64": 620.0}
+TRAFFIC_PER_PAIR = {"mixed": 622.0, "fp64": 620.0}
 HBM_FALLBACK_GBS = 6800.0
 
 
