@@ -15,7 +15,13 @@
 //   DFx2:  two DF steps in packed pairs (df2_fma_acc, 4 FP64-class flops)
 // The multiplier a is just below 1 and the addend small, so no chain
 // overflows or underflows.  Each thread stores the sum of its chains, so no
-// step can be optimised away.
+// step can be optimised away.  Each probe uses the operand form that
+// measured fastest: the FP64 probe takes a and the addend as per-thread
+// register values (perturbed by the thread index below their last bit) --
+// straight from the kernel parameters, as operands common to the warp, it
+// measured 16 % slower (1.06 against 1.26 TFLOP/s); the FP32 and
+// double-float probes take them from the parameters (with register operands
+// they measured 3-13 % slower).
 #include "fp_common.cuh"
 #include "fp_internal.h"
 
@@ -24,8 +30,9 @@ namespace fpg {
 constexpr int kChains = 8;
 constexpr int kProbeThreads = 256;
 
-__global__ void __launch_bounds__(kProbeThreads) k_probe_f64(int64_t iters, double a, double b, double* sink)
+__global__ void __launch_bounds__(kProbeThreads) k_probe_f64(int64_t iters, double a0, double b0, double* sink)
 {
+    const double a = a0 + (double)(threadIdx.x & 7) * 1e-17, b = b0 + (double)(threadIdx.x & 3) * 1e-19;
     double x[kChains];
 #pragma unroll
     for (int c = 0; c < kChains; ++c) x[c] = (double)(threadIdx.x + c);
