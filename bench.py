@@ -109,6 +109,8 @@ def parse():
     ap.add_argument("--no-moving", action="store_true")
     ap.add_argument("--no-planar", action="store_true")
     ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--stage-eval", action="store_true",
+                    help="mixed form: time the eval with element fields staged in shared memory")
     ap.add_argument("--no-peaks", action="store_true",
                     help="skip the peak probes (profiling runs); the line then has no roofline")
     ap.add_argument("--served-requests", type=int, default=200)
@@ -898,6 +900,8 @@ def main():
         # mixed form: fields posted once as double-float pairs, evaluated on the FP32 pipes
         posted = fg.Fields(h, fields) if form == "mixed" else None
         handles[form + "_fields"] = posted
+        if posted is not None and args.stage_eval:
+            fg.fp_set_eval_staging(h, True)
 
         def step(h=h, posted=posted):
             # one fused call: find, then eval in the element-sorted pair order
@@ -940,6 +944,24 @@ def main():
                          "pairs_per_point": npairs / P, "newton_paths_per_step": None if paths is None else
                          {k: v // max(1, args.steps) for k, v in paths.items()},
                          "band_hits_per_step": {k: v / max(1, args.steps) for k, v in band.items()}}
+        if posted is not None:
+            # the other eval design beside the timed one: element fields staged
+            # in shared memory per block, or read through L1 (same values)
+            fg.fp_set_eval_staging(h, not args.stage_eval)
+            for _ in range(2):
+                step()
+            torch.cuda.synchronize()
+            fg.fp_profile(h, True)
+            fg.fp_profile_read(h, "eval")
+            for _ in range(args.steps):
+                step()
+            other = fg.fp_profile_read(h, "eval")
+            fg.fp_profile(h, False)
+            fg.fp_set_eval_staging(h, args.stage_eval)
+            results[form]["eval_staging"] = {
+                "timed_design": "staged in shared memory" if args.stage_eval else "L1 (rows shared by an element's threads)",
+                "eval_ms_staged": other[0] / max(other[1], 1) if not args.stage_eval else results[form]["kernel_ms"]["eval"],
+                "eval_ms_l1": results[form]["kernel_ms"]["eval"] if not args.stage_eval else other[0] / max(other[1], 1)}
 
     head = "mixed" if "mixed" in results else forms[0]
     R = results[head]
@@ -1023,7 +1045,8 @@ def main():
                               "kernel_ms": v["kernel_ms"], "codes": v["codes"],
                               "pairs_per_point": v["pairs_per_point"],
                               "newton_paths_per_step": v["newton_paths_per_step"],
-                              "band_hits_per_step": v["band_hits_per_step"]} for k, v in results.items()},
+                              "band_hits_per_step": v["band_hits_per_step"],
+                              "eval_staging": v.get("eval_staging")} for k, v in results.items()},
                 "roofline": roof, "roofline_other_forms": roof_other, "peaks": peaks,
                 "hbm_peak": {"gbs": hbm_gbs, "source": hbm_src}, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": R["gpu_launches"],
                 "clocks": R["clocks"], "small_configs": small, "batched": batched, "serving": served, "interface": interface,

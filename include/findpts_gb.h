@@ -565,6 +565,16 @@ fp_status fp_newton_paths(fp_handle *h, int64_t *counts);
  * Errors: FP_ERR_NOT_SETUP, FP_ERR_INVALID_ARG (out of range). */
 fp_status fp_set_mixed_refine(fp_handle *h, int max_residuals);
 
+/* Fused evaluation of posted (double-float) fields (Sec. 2.1 findpts_eval):
+ * with enable != 0, each block copies the fields of every element its 128
+ * sorted (point, element) pairs touch into shared memory once and reads the
+ * rows from there; with 0 (after fp_setup) the rows are read through L1,
+ * where the threads of one element share them.  Results are identical either
+ * way; elements whose F fields exceed 48 KB are always read through L1.
+ * Applies to later fp_find_eval / fp_find_eval_ws / fp_find_warm calls with
+ * posted fields.  Errors: FP_ERR_NOT_SETUP. */
+fp_status fp_set_eval_staging(fp_handle *h, int enable);
+
 /* Device bytes the handle holds: *resident = the posted mesh and its search
  * structures (coordinates and their FP32 copies, boxes, hash grid, distance
  * field, per-element sort arrays); *workspace = the handle's own fp_find

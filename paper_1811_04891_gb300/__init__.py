@@ -161,6 +161,8 @@ def _load():
     L.fp_profile.restype = ci
     L.fp_set_mixed_refine.argtypes = [vp, ci]
     L.fp_set_mixed_refine.restype = ci
+    L.fp_set_eval_staging.argtypes = [vp, ci]
+    L.fp_set_eval_staging.restype = ci
     L.fp_profile_read.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
     L.fp_profile_read.restype = ci
     L.fp_launch_count.argtypes = []
@@ -780,6 +782,11 @@ PROF_KINDS = {"screen": 0, "sort": 1, "newton": 2, "rank": 3, "eval": 4}
 
 def fp_profile(h: Handle, enable: bool = True):
     _check(lib().fp_profile(h.ptr, int(bool(enable))), h.ptr)
+
+
+def fp_set_eval_staging(h: Handle, enable: bool = True):
+    """Fused eval of posted fields from shared memory (same results)."""
+    _check(lib().fp_set_eval_staging(h.ptr, int(bool(enable))), h.ptr)
 
 
 def fp_set_mixed_refine(h: Handle, max_residuals: int):

@@ -413,22 +413,52 @@ __device__ __forceinline__ df row_df(const float (&vh)[n], const float (&vl)[n],
     return r;
 }
 
+// n floats of a row held in shared memory (plain loads, vectors for even n)
+template <int n>
+__device__ __forceinline__ void load_row_sm(const float* p, float (&v)[n])
+{
+    if constexpr (n % 4 == 0) {
+        const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+        for (int i = 0; i < n / 4; ++i) {
+            const float4 t = q[i];
+            v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+        }
+    } else if constexpr (n % 2 == 0) {
+        const float2* q = reinterpret_cast<const float2*>(p);
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i) {
+            const float2 t = q[i];
+            v[2 * i] = t.x; v[2 * i + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < n; ++i) v[i] = p[i];
+    }
+}
+
 // Posted (double-float) fields keep each row of n nodes as its n high parts
 // followed by its n low parts (n float2 slots), so both halves load as
-// aligned vectors for even n.
-template <int n>
+// aligned vectors for even n.  SM: the row is in shared memory.
+template <int n, bool SM = false>
 __device__ __forceinline__ df row_df(const float2* __restrict__ rowp, const float (&rh)[n], const float (&rl)[n])
 {
     const float* row = reinterpret_cast<const float*>(rowp);
     float vh[n], vl[n];
-    load_row<n>(row, vh);
-    load_row<n>(row + n, vl);
+    if constexpr (SM) {
+        load_row_sm<n>(row, vh);
+        load_row_sm<n>(row + n, vl);
+    } else {
+        load_row<n>(row, vh);
+        load_row<n>(row + n, vl);
+    }
     return row_df<n>(vh, vl, rh, rl);
 }
 
 // sum_ijk F_ijk h_i h_j h_k for one element's double-float values Fe (n^3,
-// i fastest) and split basis values; rounded to FP64
-template <int n>
+// i fastest) and split basis values; rounded to FP64.  SM: Fe is in shared
+// memory.
+template <int n, bool SM = false>
 __device__ __forceinline__ double contract_df(const float2* __restrict__ Fe, const float (&rh)[n],
                                               const float (&rl)[n], const float (&sh)[n], const float (&sl)[n],
                                               const float (&th)[n], const float (&tl)[n])
@@ -440,7 +470,7 @@ __device__ __forceinline__ double contract_df(const float2* __restrict__ Fe, con
         // two rows in flight: their loads and two-sums overlap
 #pragma unroll 2
         for (int j = 0; j < n; ++j) {
-            const df u = row_df<n>(Fe + n * (j + n * k), rh, rl);
+            const df u = row_df<n, SM>(Fe + n * (j + n * k), rh, rl);
             df_fma_acc(ck, u, sh[j], sl[j]);
         }
         df_norm(ck);

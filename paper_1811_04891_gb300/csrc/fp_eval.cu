@@ -2,6 +2,7 @@
 // points by sum factorisation, out[f][p] = sum_ijk F_ijk h_i(r) h_j(s) h_k(t),
 // in FP64; quiet NaN for points that were not found.
 #include <algorithm>
+#include <climits>
 
 #include "fp_common.cuh"
 #include "fp_internal.h"
@@ -339,6 +340,85 @@ __global__ void __launch_bounds__(128) k_eval_pairs(EvalPairsArgs A, BasisTab ta
     }
 }
 
+// Fused double-float evaluation with each element's posted fields staged in
+// shared memory: a block takes kStageTile consecutive sorted pairs (the pairs
+// of one element are consecutive), copies the fields of each element the
+// tile touches into shared memory once, in ascending element order, and the
+// threads whose pairs lie in that element read their rows from there.
+constexpr int kStageTile = 128;
+
+template <int n>
+__global__ void __launch_bounds__(kStageTile) k_eval_pairs_staged(EvalPairsArgs A, BasisTab tab)
+{
+    constexpr int n3 = n * n * n;
+    extern __shared__ float4 stage4[];               // F * n3 float2: the current element's fields
+    float2* stage = reinterpret_cast<float2*>(stage4);
+    __shared__ int ecur;
+    int64_t s0 = 0, s1;
+    if (A.s_lo) {
+        s0 = *A.s_lo;
+        s1 = *A.s_hi;
+    } else {
+        const int64_t t = *A.dcount;
+        s1 = t < A.cap ? t : A.cap;
+    }
+    const int F = A.ev.F;
+    for (int64_t base = s0 + (int64_t)blockIdx.x * kStageTile; base < s1;
+         base += (int64_t)gridDim.x * kStageTile) {
+        const int64_t s = base + threadIdx.x;
+        int32_t p = -1;
+        int e = -1;
+        float rh[n], rl[n], sh[n], sl[n], th[n], tl[n];
+        if (s < s1) {
+            const int32_t q = A.order[s];
+            p = A.pair_pt[q];
+            e = A.pair_elem[q] - A.ebase;
+            if (p >= 0) {
+                const int64_t w = A.walk ? s : q;
+                double hr[n], hs[n], ht[n];
+                lagrange_h<n, double>(tab.xi, tab.ci, A.prst[w], hr);
+                lagrange_h<n, double>(tab.xi, tab.ci, A.prst[A.cap + w], hs);
+                lagrange_h<n, double>(tab.xi, tab.ci, A.prst[2 * A.cap + w], ht);
+#pragma unroll
+                for (int i = 0; i < n; ++i) {
+                    const df a = df_split(hr[i]), b = df_split(hs[i]), c = df_split(ht[i]);
+                    rh[i] = a.hi; rl[i] = a.lo; sh[i] = b.hi; sl[i] = b.lo; th[i] = c.hi; tl[i] = c.lo;
+                }
+            }
+        }
+        bool done = p < 0;                           // losers and threads past the end have nothing to do
+        for (;;) {
+            if (threadIdx.x == 0) ecur = INT_MAX;
+            __syncthreads();
+            if (!done) atomicMin(&ecur, e);
+            __syncthreads();
+            const int ec = ecur;
+            if (ec == INT_MAX) break;                // uniform: every thread read the same value
+            for (int f = 0; f < F; ++f) {
+                const float2* src = A.ev.fdf + ((int64_t)f * A.E + ec) * n3;
+                if constexpr (n3 % 2 == 0) {
+                    const float4* s4 = reinterpret_cast<const float4*>(src);
+                    float4* d4 = stage4 + f * (n3 / 2);
+                    for (int v = threadIdx.x; v < n3 / 2; v += kStageTile) d4[v] = __ldg(s4 + v);
+                } else {
+                    for (int v = threadIdx.x; v < n3; v += kStageTile) stage[f * n3 + v] = __ldg(src + v);
+                }
+            }
+            __syncthreads();
+            if (!done && e == ec) {
+                for (int f = 0; f < F; ++f)
+                    A.ev.out[(int64_t)f * A.P + p] = contract_df<n, true>(stage + f * n3, rh, rl, sh, sl, th, tl);
+                done = true;
+            }
+            __syncthreads();                         // the next element overwrites the stage
+        }
+    }
+}
+
+// staging is used when one element's posted fields fit in this much shared
+// memory (larger ones are evaluated from L1 / L2 as without staging)
+constexpr int64_t kStageMaxBytes = 48 * 1024;
+
 cudaError_t launch_eval_pairs(int n, int64_t E, int64_t P, const int32_t* dcount, int64_t cap, const int32_t* order,
                               const int32_t* pair_elem, const int32_t* pair_pt, const double* prst,
                               const EvalSpec& ev, const BasisTab& tab, unsigned grid, cudaStream_t s,
@@ -346,11 +426,14 @@ cudaError_t launch_eval_pairs(int n, int64_t E, int64_t P, const int32_t* dcount
 {
     EvalPairsArgs a{E, P, cap, dcount, order, pair_elem, pair_pt, prst, ev, s_lo, s_hi, ebase, walk ? 1 : 0};
     const bool df = ev.fdf != nullptr;
+    const int64_t stage_bytes = (int64_t)ev.F * n * n * n * (int64_t)sizeof(float2);
+    const bool staged = df && ev.staged && stage_bytes <= kStageMaxBytes;
     switch (n) {
-#define FP_CASE(NN)                                                   \
-    case NN:                                                          \
-        if (df) k_eval_pairs<NN, true><<<grid, 128, 0, s>>>(a, tab);  \
-        else k_eval_pairs<NN, false><<<grid, 128, 0, s>>>(a, tab);    \
+#define FP_CASE(NN)                                                                       \
+    case NN:                                                                              \
+        if (staged) k_eval_pairs_staged<NN><<<grid, kStageTile, stage_bytes, s>>>(a, tab); \
+        else if (df) k_eval_pairs<NN, true><<<grid, 128, 0, s>>>(a, tab);                 \
+        else k_eval_pairs<NN, false><<<grid, 128, 0, s>>>(a, tab);                        \
         break;
         FP_CASE(2) FP_CASE(3) FP_CASE(4) FP_CASE(5) FP_CASE(6) FP_CASE(7) FP_CASE(8) FP_CASE(9)
         FP_CASE(10) FP_CASE(11) FP_CASE(12) FP_CASE(13) FP_CASE(14) FP_CASE(15) FP_CASE(16)

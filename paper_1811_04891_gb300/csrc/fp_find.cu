@@ -741,8 +741,10 @@ __device__ __forceinline__ bool warm_seed(const NewtonArgs& A, int64_t p, int e,
 
 // FP64 form: nearest-node (or warm) start, full FP64 trust-region Newton;
 // with A.pstate, the first pass stops a solve after kFirstPass iterations
-// and lists it (fbl, capacity fbc) for the second
-constexpr int kFirstPass = 4;
+// and lists it (fbl, capacity fbc) for the second.  Measured on the 32^3
+// N=7 workload: budgets 1 / 2 / 3 / 4 / 5 / 6 gave 387 / 300 / 311 / 319 /
+// 323 / 326 ms for the two passes together.
+constexpr int kFirstPass = 2;
 
 template <int n>
 __device__ __forceinline__ void solve_pair(const NewtonArgs& A, const BasisTab& tab, int64_t s, int32_t* fbl,

@@ -21,6 +21,7 @@ struct fp_handle {
     int nsub = 0;
     fp_opts opts{};
     int refine = 3;                // mixed form: compensated residuals per pair (fp_set_mixed_refine)
+    int stage_eval = 0;            // fused eval of posted fields from shared memory (fp_set_eval_staging)
     fpg::BasisTab tab{};
     fpg::HashGrid grid{};
     int64_t nnz = 0;

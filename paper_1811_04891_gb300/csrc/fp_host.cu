@@ -668,7 +668,7 @@ static fp_status eval_spec(fp_handle* h, int F, const double* fields, const fp_f
     if (posted) {
         if (posted->owner != h) return fail(h, FP_ERR_INVALID_ARG, "fp_find_eval: fields posted for another handle");
         if (F != posted->F) return fail(h, FP_ERR_INVALID_ARG, "fp_find_eval: F differs from the posted fields");
-        *ev = EvalSpec{posted->F, nullptr, posted->data, out};
+        *ev = EvalSpec{posted->F, nullptr, posted->data, out, h->stage_eval};
         return FP_OK;
     }
     if (!fields || F < 1) return fail(h, FP_ERR_INVALID_ARG, "fp_find_eval: no fields");
@@ -1092,6 +1092,13 @@ fp_status fp_profile(fp_handle* h, int enable)
         if (e == cudaSuccess) e = cudaMemset(h->stats, 0, 4 * sizeof(unsigned long long));
         if (e != cudaSuccess) return cuda_fail(h, e, "fp_profile");
     }
+    return FP_OK;
+}
+
+fp_status fp_set_eval_staging(fp_handle* h, int enable)
+{
+    if (!fp_live(h)) return FP_ERR_NOT_SETUP;
+    h->stage_eval = enable != 0;
     return FP_OK;
 }
 

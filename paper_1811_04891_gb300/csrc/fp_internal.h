@@ -51,6 +51,7 @@ struct EvalSpec {
     const double* f64;
     const float2* fdf;
     double* out;
+    int staged = 0;     // posted fields: stage each element's fields in shared memory (fp_set_eval_staging)
 };
 
 struct FindArgs {

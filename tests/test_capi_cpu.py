@@ -90,5 +90,6 @@ def test_argument_checks_before_any_device_work():
     cnt = (ctypes.c_int64 * 3)()
     assert L.fp_band_hits(None, cnt) == NOSET
     assert L.fp_set_mixed_refine(None, 3) == NOSET
+    assert L.fp_set_eval_staging(None, 1) == NOSET
     assert L.fp_fma_probe(5, 10, 1, None, None, None) == INV                                      # kind outside 0..4
     assert L.fp_fma_probe(0, 0, 1, None, None, None) == INV                                       # iters < 1
