@@ -81,7 +81,37 @@ struct ScreenArgs {
     int64_t stride;       // row stride of pts (and offset of y, z rows); 0 means P
     int32_t pt_base;      // added to the point index written into pair_pt
     int32_t elem_base;    // added to the element index written into pair_elem
+    uint32_t* mask;       // optional [P]: the count pass records which entries of the point's cell list
+                          //   passed (bit q - start), so the emit pass need not test them again;
+                          //   kMaskOverflow marks lists longer than 31 entries (tested again)
 };
+
+constexpr uint32_t kMaskOverflow = 0x80000000u;
+
+// the hash cell of a point (-1: not finite or outside the grid); the FP32
+// screen hashes in FP32
+template <bool F32>
+__device__ __forceinline__ int64_t hash_cell(const HashGrid& g, double x, double y, double z)
+{
+    if (!(isfinite(x) && isfinite(y) && isfinite(z))) return -1;
+    double u0, u1, u2;
+    if (F32) {
+        u0 = (double)(((float)x - (float)g.org[0]) * (float)g.inv[0]);
+        u1 = (double)(((float)y - (float)g.org[1]) * (float)g.inv[1]);
+        u2 = (double)(((float)z - (float)g.org[2]) * (float)g.inv[2]);
+    } else {
+        u0 = (x - g.org[0]) * g.inv[0];
+        u1 = (y - g.org[1]) * g.inv[1];
+        u2 = (z - g.org[2]) * g.inv[2];
+    }
+    if (!(u0 >= 0.0 && u1 >= 0.0 && u2 >= 0.0 && u0 <= (double)g.dim[0] && u1 <= (double)g.dim[1] &&
+          u2 <= (double)g.dim[2]))
+        return -1;
+    const int i = min((int)u0, g.dim[0] - 1);
+    const int j = min((int)u1, g.dim[1] - 1);
+    const int k = min((int)u2, g.dim[2] - 1);
+    return i + (int64_t)g.dim[0] * (j + (int64_t)g.dim[1] * k);
+}
 
 template <bool EMIT, bool F32>
 __device__ __forceinline__ void screen_point(const ScreenArgs& A, int64_t p)
@@ -91,41 +121,48 @@ __device__ __forceinline__ void screen_point(const ScreenArgs& A, int64_t p)
     const int tag = A.qsess ? A.qsess[p] : -1;
     int c = 0;
     int base = EMIT ? A.off[p] : 0;
-    if (isfinite(x) && isfinite(y) && isfinite(z)) {
-        double u0, u1, u2;
-        if (F32) {
-            u0 = (double)(((float)x - (float)A.g.org[0]) * (float)A.g.inv[0]);
-            u1 = (double)(((float)y - (float)A.g.org[1]) * (float)A.g.inv[1]);
-            u2 = (double)(((float)z - (float)A.g.org[2]) * (float)A.g.inv[2]);
-        } else {
-            u0 = (x - A.g.org[0]) * A.g.inv[0];
-            u1 = (y - A.g.org[1]) * A.g.inv[1];
-            u2 = (z - A.g.org[2]) * A.g.inv[2];
-        }
-        if (u0 >= 0.0 && u1 >= 0.0 && u2 >= 0.0 && u0 <= (double)A.g.dim[0] && u1 <= (double)A.g.dim[1] &&
-            u2 <= (double)A.g.dim[2]) {
-            const int i = min((int)u0, A.g.dim[0] - 1);
-            const int j = min((int)u1, A.g.dim[1] - 1);
-            const int k = min((int)u2, A.g.dim[2] - 1);
-            const int64_t cell = i + (int64_t)A.g.dim[0] * (j + (int64_t)A.g.dim[1] * k);
-            const int b = __ldg(A.cell_start + cell), en = __ldg(A.cell_start + cell + 1);
-            for (int q = b; q < en; ++q) {
-                const int e = __ldg(A.cell_elems + q);
-                if (tag >= 0 && __ldg(A.sub + e) == tag) continue;
-                if (F32) {
-                    if (!inside_boxes32(A.boxes32 + e, (float)x, (float)y, (float)z)) continue;
-                } else if (!inside_boxes(A.boxes + e, x, y, z)) {
-                    continue;
-                }
-                if (EMIT && base + c < A.cap) {
-                    A.pair_elem[base + c] = A.elem_base + e;
+    uint32_t m = 0;
+    if (EMIT && A.mask) m = A.mask[p];
+    if (EMIT && A.mask && !(m & kMaskOverflow)) {
+        // the count pass found these entries of the point's cell list
+        if (m) {
+            const int b = __ldg(A.cell_start + hash_cell<F32>(A.g, x, y, z));
+            while (m) {
+                const int bit = __ffs(m) - 1;
+                m &= m - 1;
+                if (base + c < A.cap) {
+                    A.pair_elem[base + c] = A.elem_base + __ldg(A.cell_elems + b + bit);
                     A.pair_pt[base + c] = A.pt_base + (int32_t)p;
                 }
                 ++c;
             }
         }
+        return;
     }
-    if (!EMIT) A.cnt[p] = c;
+    const int64_t cell = hash_cell<F32>(A.g, x, y, z);
+    if (cell >= 0) {
+        const int b = __ldg(A.cell_start + cell), en = __ldg(A.cell_start + cell + 1);
+        if (!EMIT && en - b > 31) m = kMaskOverflow;
+        for (int q = b; q < en; ++q) {
+            const int e = __ldg(A.cell_elems + q);
+            if (tag >= 0 && __ldg(A.sub + e) == tag) continue;
+            if (F32) {
+                if (!inside_boxes32(A.boxes32 + e, (float)x, (float)y, (float)z)) continue;
+            } else if (!inside_boxes(A.boxes + e, x, y, z)) {
+                continue;
+            }
+            if (EMIT && base + c < A.cap) {
+                A.pair_elem[base + c] = A.elem_base + e;
+                A.pair_pt[base + c] = A.pt_base + (int32_t)p;
+            }
+            if (!EMIT && !(m & kMaskOverflow)) m |= 1u << (q - b);
+            ++c;
+        }
+    }
+    if (!EMIT) {
+        A.cnt[p] = c;
+        if (A.mask) A.mask[p] = m;
+    }
 }
 
 template <bool EMIT, bool F32>
@@ -169,6 +206,7 @@ __global__ void __launch_bounds__(256) k_bscreen(BScreenArgs B)
     A.stride = B.P;
     A.pt_base = 0;
     A.elem_base = I.ebase;
+    A.mask = nullptr;
     screen_point<EMIT, F32>(A, p);
 }
 
@@ -1180,6 +1218,7 @@ static ScreenArgs screen_args(const FindArgs& a)
     s.stride = a.pts_stride;
     s.pt_base = a.pt_base;
     s.elem_base = a.elem_base;
+    s.mask = a.smask;
     return s;
 }
 

@@ -42,6 +42,7 @@ struct fp_handle {
     // find workspace
     int64_t cap_pts = 0, cap_pairs = 0;
     int32_t* cnt = nullptr;
+    uint32_t* smask = nullptr;     // [cap_pts] screen: count-pass candidate masks
     int32_t* off = nullptr;
     int32_t* scan_tmp = nullptr;
     int32_t* pair_elem = nullptr;

@@ -191,7 +191,7 @@ void release(fp_handle* h)
     dfree(h->band);
     dfree(h->coords); dfree(h->coords32); dfree(h->coords32lo); dfree(h->sub); dfree(h->dist); dfree(h->boxes); dfree(h->boxes32);
     dfree(h->cell_start); dfree(h->cell_elems); dfree(h->ecount); dfree(h->estart); dfree(h->escan_tmp);
-    dfree(h->cnt); dfree(h->off); dfree(h->scan_tmp); dfree(h->pair_elem); dfree(h->pair_pt);
+    dfree(h->cnt); dfree(h->smask); dfree(h->off); dfree(h->scan_tmp); dfree(h->pair_elem); dfree(h->pair_pt);
     dfree(h->order); dfree(h->pres); dfree(h->prst); dfree(h->pstate); dfree(h->inv);
     dfree(h->binv); dfree(h->nodebox); dfree(h->red); dfree(h->hcnt); dfree(h->htmp); dfree(h->flag);
     if (h->h_total) cudaFreeHost(h->h_total);
@@ -203,9 +203,9 @@ fp_status grow_points(fp_handle* h, int64_t P)
     if (P <= h->cap_pts) return FP_OK;
     int64_t cap = std::max<int64_t>(P, 1024);
     cudaDeviceSynchronize();
-    dfree(h->cnt); dfree(h->off); dfree(h->scan_tmp);
+    dfree(h->cnt); dfree(h->smask); dfree(h->off); dfree(h->scan_tmp);
     cudaError_t e;
-    if ((e = dalloc(&h->cnt, cap)) != cudaSuccess ||
+    if ((e = dalloc(&h->cnt, cap)) != cudaSuccess || (e = dalloc(&h->smask, cap)) != cudaSuccess ||
         (e = dalloc(&h->off, cap + 1)) != cudaSuccess ||
         (e = dalloc(&h->scan_tmp, std::max(scan_tmp_elems(cap), scan_tmp_elems(h->E)))) != cudaSuccess) {
         h->cap_pts = 0;
@@ -586,6 +586,7 @@ static fp_status find_impl(fp_handle* h, int64_t P, const double* pts, const int
     a.boxes = h->boxes; a.boxes32 = h->boxes32; a.grid = &h->grid;
     a.cell_start = h->cell_start; a.cell_elems = h->cell_elems;
     a.cnt = h->cnt; a.off = h->off; a.ecount = h->ecount; a.estart = h->estart; a.scan_tmp = h->scan_tmp;
+    a.smask = h->dim == 3 ? h->smask : nullptr;
     a.code = code; a.osub = sub; a.oelem = elem; a.rst = rst; a.dist2 = dist2;
     a.eval = ev;
     a.stats = h->prof ? h->stats : nullptr;
@@ -757,6 +758,7 @@ struct fp_workspace {
     int persistent_blocks = 0;
     int64_t grid_pairs = 0;     // without a persistent grid: pairs the launches cover (0: max_pairs)
     int32_t *cnt = nullptr, *off = nullptr, *scan_tmp = nullptr;
+    uint32_t* smask = nullptr;
     int32_t *pair_elem = nullptr, *pair_pt = nullptr, *order = nullptr;
     int32_t *ecount = nullptr, *estart = nullptr;
     double *pres = nullptr, *prst = nullptr;
@@ -766,7 +768,7 @@ struct fp_workspace {
 
 static void ws_release(fp_workspace* w)
 {
-    dfree(w->cnt); dfree(w->off); dfree(w->scan_tmp); dfree(w->pair_elem); dfree(w->pair_pt);
+    dfree(w->cnt); dfree(w->smask); dfree(w->off); dfree(w->scan_tmp); dfree(w->pair_elem); dfree(w->pair_pt);
     dfree(w->order); dfree(w->ecount); dfree(w->estart); dfree(w->pres); dfree(w->prst); dfree(w->pstate);
     dfree(w->inv);
 }
@@ -789,7 +791,8 @@ fp_status fp_workspace_create(const fp_handle* h, int64_t max_points, int64_t ma
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     w->persistent_blocks = 4 * nsm;
     cudaError_t e;
-    if ((e = dalloc(&w->cnt, max_points)) != cudaSuccess || (e = dalloc(&w->off, max_points + 1)) != cudaSuccess ||
+    if ((e = dalloc(&w->cnt, max_points)) != cudaSuccess || (e = dalloc(&w->smask, max_points)) != cudaSuccess ||
+        (e = dalloc(&w->off, max_points + 1)) != cudaSuccess ||
         (e = dalloc(&w->scan_tmp, std::max(scan_tmp_elems(max_points), scan_tmp_elems(h->E)))) != cudaSuccess ||
         (e = dalloc(&w->pair_elem, max_pairs)) != cudaSuccess || (e = dalloc(&w->pair_pt, max_pairs)) != cudaSuccess ||
         (e = dalloc(&w->order, max_pairs)) != cudaSuccess || (e = dalloc(&w->ecount, h->E)) != cudaSuccess ||
@@ -810,7 +813,7 @@ fp_status fp_workspace_bytes(const fp_handle* h, int64_t max_points, int64_t max
     if (!bytes || max_points < 1 || max_points >= (int64_t(1) << 31)) return FP_ERR_INVALID_ARG;
     if (max_pairs <= 0) max_pairs = 2 * max_points;
     if (max_pairs >= (int64_t(1) << 31)) return FP_ERR_INVALID_ARG;
-    *bytes = 4 * max_points + 4 * (max_points + 1) + 4 * std::max(scan_tmp_elems(max_points), scan_tmp_elems(h->E)) +
+    *bytes = 4 * max_points + 4 * max_points + 4 * (max_points + 1) + 4 * std::max(scan_tmp_elems(max_points), scan_tmp_elems(h->E)) +
              max_pairs * (4 + 4 + 4 + 4 + 8 + 24 + (h->opts.precision == FP_PREC_FP64 ? 16 : 0)) + 4 * h->E +
              4 * (h->E + 1);
     return FP_OK;
@@ -883,6 +886,7 @@ static fp_status find_ws_impl(fp_handle* h, fp_workspace* w, int64_t P, const do
     a.boxes = h->boxes; a.boxes32 = h->boxes32; a.grid = &h->grid;
     a.cell_start = h->cell_start; a.cell_elems = h->cell_elems;
     a.cnt = w->cnt; a.off = w->off; a.scan_tmp = w->scan_tmp; a.ecount = w->ecount; a.estart = w->estart;
+    a.smask = w->smask;
     a.pair_elem = w->pair_elem; a.pair_pt = w->pair_pt; a.order = w->order; a.pres = w->pres; a.prst = w->prst;
     a.pstate = w->pstate;
     a.inv = w->inv;
@@ -1169,7 +1173,7 @@ fp_status fp_memory(const fp_handle* h, int64_t* resident, int64_t* workspace)
         *resident = b;
     }
     if (workspace)
-        *workspace = 4 * h->cap_pts + 4 * (h->cap_pts + 1) +
+        *workspace = 4 * h->cap_pts + 4 * h->cap_pts + 4 * (h->cap_pts + 1) +
                      4 * (h->cap_pts > 0 ? std::max(scan_tmp_elems(h->cap_pts), scan_tmp_elems(h->E)) : 0) +
                      h->cap_pairs * (4 + 4 + 4 + 8 + 24 + (h->pstate ? 16 : 0) + (h->inv ? 4 : 0));
     return FP_OK;

@@ -111,6 +111,8 @@ struct FindArgs {
     int32_t* oelem;
     double* rst;
     double* dist2;
+    uint32_t* smask = nullptr;    // [P] screen: candidates that passed the count pass, by bit of the
+                                  //   cell list (bit 31: list too long, test again); null = test again
 };
 cudaError_t find_count(const FindArgs& a, const BasisTab& tab, const FindParams& fp, cudaStream_t s);
 cudaError_t find_screen_count(const FindArgs& a, cudaStream_t s);   // counts only, no scan
