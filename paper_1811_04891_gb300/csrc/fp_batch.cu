@@ -229,6 +229,7 @@ struct fp_batch {
     double* he_all = nullptr;
     int32_t* sub_all = nullptr;
     int32_t *cnt = nullptr, *off = nullptr, *scan_tmp = nullptr;
+    uint32_t* smask = nullptr;
     int32_t *pair_elem = nullptr, *pair_pt = nullptr, *order = nullptr, *ecount = nullptr, *estart = nullptr;
     int32_t* fb_list = nullptr;
     int32_t* gcount = nullptr;    // [2 * groups]: Newton work-queue counter, fallback counter
@@ -256,7 +257,7 @@ static void batch_release(fp_batch* b)
 {
     for (auto& g : b->groups) release_group(g);
     release(b->d_inst); release(b->d_p0); release(b->d_rinst); release(b->d_rgrp); release(b->he_all);
-    release(b->sub_all); release(b->cnt); release(b->off); release(b->scan_tmp); release(b->pair_elem);
+    release(b->sub_all); release(b->cnt); release(b->smask); release(b->off); release(b->scan_tmp); release(b->pair_elem);
     release(b->pair_pt); release(b->order); release(b->ecount); release(b->estart); release(b->fb_list);
     release(b->gcount); release(b->pres); release(b->prst); release(b->pstate); release(b->inv); release(b->band);
     if (b->fork) cudaEventDestroy(b->fork);
@@ -445,6 +446,7 @@ extern "C" fp_status fp_batch_create(fp_batch** out, int ninst, fp_handle* const
         }
         const int64_t P = b->Ptot, ng = (int64_t)b->groups.size();
         if (e == cudaSuccess) e = alloc(&b->cnt, P);
+        if (e == cudaSuccess) e = alloc(&b->smask, P);
         if (e == cudaSuccess) e = alloc(&b->off, P + 1);
         if (e == cudaSuccess) e = alloc(&b->scan_tmp, std::max(scan_tmp_elems(P), scan_tmp_elems(b->Etot)));
         if (e == cudaSuccess) e = alloc(&b->pair_elem, b->cap);
@@ -536,6 +538,7 @@ static cudaError_t batch_run(fp_batch* b, const double* pts, int32_t* code, int3
     sa.P = P;
     sa.pts = pts;
     sa.cnt = b->cnt;
+    sa.mask = b->smask;
     sa.off = b->off;
     sa.pair_elem = b->pair_elem;
     sa.pair_pt = b->pair_pt;

@@ -76,6 +76,7 @@ struct BScreenArgs {
     int32_t* pair_elem;
     int32_t* pair_pt;
     int64_t cap;
+    uint32_t* mask;      // [P] count-pass candidate masks (see ScreenArgs::mask)
 };
 
 // A pair that lost its point's classification is marked by storing ~p

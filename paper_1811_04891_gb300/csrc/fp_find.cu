@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(256) k_bscreen(BScreenArgs B)
     A.stride = B.P;
     A.pt_base = 0;
     A.elem_base = I.ebase;
-    A.mask = nullptr;
+    A.mask = B.mask;
     screen_point<EMIT, F32>(A, p);
 }
 
