@@ -490,6 +490,7 @@ static FindArgs group_args(const fp_batch* b, const Group& g, const double* pts)
 {
     FindArgs a;
     memset(&a, 0, sizeof(a));
+    a.batch = 1;
     a.n = g.n;
     a.E = g.E;
     a.P = b->Ptot;

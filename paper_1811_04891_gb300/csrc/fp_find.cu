@@ -701,6 +701,7 @@ struct NewtonArgs {
     double reject32;      // mixed: reject after FP32 when residual > reject32 * h_e
     int max_newton;
     int refine;           // mixed: compensated residuals per pair before the FP64 fallback
+    int first_pass;       // FP64 form with pstate: iterations of the first pass
     unsigned long long* stats;  // optional path counters (profiling): [0] rejected after FP32,
                                 // [1] FP32 not converged, [2] FP64 step converged, [3] sent to the fallback
     const int32_t* warm_elem;   // optional [P]: each point's element at the previous mesh position
@@ -778,11 +779,13 @@ __device__ __forceinline__ bool warm_seed(const NewtonArgs& A, int64_t p, int e,
 }
 
 // FP64 form: nearest-node (or warm) start, full FP64 trust-region Newton;
-// with A.pstate, the first pass stops a solve after kFirstPass iterations
+// with A.pstate, the first pass stops a solve after A.first_pass iterations
 // and lists it (fbl, capacity fbc) for the second.  Measured on the 32^3
 // N=7 workload: budgets 1 / 2 / 3 / 4 / 5 / 6 gave 387 / 300 / 311 / 319 /
-// 323 / 326 ms for the two passes together.
+// 323 / 326 ms for the two passes together; the batch's per-order groups
+// measured faster with 4 (82 / 88 ms for N = 5 / 7 against 105 / 104 with 2).
 constexpr int kFirstPass = 2;
+constexpr int kFirstPassBatch = 4;
 
 template <int n>
 __device__ __forceinline__ void solve_pair(const NewtonArgs& A, const BasisTab& tab, int64_t s, int32_t* fbl,
@@ -800,7 +803,7 @@ __device__ __forceinline__ void solve_pair(const NewtonArgs& A, const BasisTab& 
     bool conv64;
     NewtonState st{1.0, 0, 0, false};
     const double res = newton<n, double, true>(el64, tab, xs, r, J, A.max_newton, conv64, A.pstate ? &st : nullptr,
-                                               kFirstPass);
+                                               A.first_pass);
     const int64_t w = result_slot(A, s, q);
     A.prst[w] = r[0];
     A.prst[A.cap + w] = r[1];
@@ -1292,6 +1295,7 @@ static cudaError_t newton_n(const FindArgs& a, int64_t npairs, const BasisTab& t
     na.reject32 = 1e-4;
     na.max_newton = fp.max_newton;
     na.refine = fp.refine;
+    na.first_pass = a.batch ? kFirstPassBatch : kFirstPass;
     na.stats = a.stats;
     na.warm_elem = a.warm_elem;
     na.warm_rst = a.warm_rst;

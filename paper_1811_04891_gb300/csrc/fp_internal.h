@@ -113,6 +113,7 @@ struct FindArgs {
     double* dist2;
     uint32_t* smask = nullptr;    // [P] screen: candidates that passed the count pass, by bit of the
                                   //   cell list (bit 31: list too long, test again); null = test again
+    int batch = 0;                // 1: a batch group (its own FP64 first-pass budget)
 };
 cudaError_t find_count(const FindArgs& a, const BasisTab& tab, const FindParams& fp, cudaStream_t s);
 cudaError_t find_screen_count(const FindArgs& a, cudaStream_t s);   // counts only, no scan
