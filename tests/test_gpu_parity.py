@@ -210,14 +210,23 @@ def test_spiral_element_N15(prec):
     assert (g["code"] == 0).all()
 
 
-def test_invariance_hash_and_block():
+@pytest.mark.parametrize("prec", PRECS)
+def test_invariance_hash_and_block(prec):
+    """Hash size and block size change nothing.  0.02 cells per element
+    makes cell lists longer than the screen's 31-entry candidate mask, so
+    the emit pass tests those points again instead of reading the mask."""
     mesh, q = synth.deformed_cube(ne=6, P_uniform=20000, P_face=2000)
-    base = gpu_find(mesh, q.pts, prec=0)
-    for kw in ({"hash_cells_per_elem": 0.2}, {"hash_cells_per_elem": 4.0}, {"points_per_block": 64},
-               {"points_per_block": 256}):
-        g = gpu_find(mesh, q.pts, prec=0, **kw)
+    base = gpu_find(mesh, q.pts, prec=prec)
+    for kw in ({"hash_cells_per_elem": 0.2}, {"hash_cells_per_elem": 4.0}, {"hash_cells_per_elem": 0.02},
+               {"points_per_block": 64}, {"points_per_block": 256}):
+        g = gpu_find(mesh, q.pts, prec=prec, **kw)
         for k in ("code", "sub", "elem", "rst", "dist2"):
             np.testing.assert_array_equal(g[k], base[k], err_msg=str(kw))
+    # the coarse grid does give lists longer than 31 entries
+    import paper_1811_04891_gb300 as fg
+    g = gpu_find(mesh, q.pts[:, :10], prec=prec, hash_cells_per_elem=0.02)
+    cs = fg.fp_debug_boxes(g["handle"])[2].cpu().numpy()
+    assert np.diff(cs).max() > 31
 
 
 def test_hull_and_hash_contain_elements():
