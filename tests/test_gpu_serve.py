@@ -38,7 +38,8 @@ def test_served_results_same_alone_and_in_mix():
     stats = serve.latency_stats(done)
     assert stats["p99_ms"] >= stats["p50_ms"] > 0
     by_id = {r.rid: r for r in done}
-    alone = serve.Server(h, fd, chunk_points=8192, streams=1)
+    # alone: one stream, results copied by the dispatcher itself (no copier threads)
+    alone = serve.Server(h, fd, chunk_points=8192, streams=1, copy_threads=0)
     for r in make():
         alone.submit(r)
         while alone.step(0.0):
