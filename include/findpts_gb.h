@@ -67,8 +67,11 @@ typedef struct {
     int max_newton;             /* Newton iteration cap per candidate (40)               */
     double hash_cells_per_elem; /* hash-grid cells per element (1.0); result-invariant   */
     double tie_band;            /* owner and border ties within tie_band*L (1e-10)       */
-    int points_per_block;       /* threads per block of the Newton kernel: 0 (= 128) or a
-                                   multiple of 32 up to 256; result-invariant          */
+    int points_per_block;       /* threads per block of the Newton kernel: 0 (= 64 for
+                                   fp_find / fp_find_eval on hexahedra, 128 for
+                                   quadrilaterals and for the workspace and
+                                   allocation-free calls) or a multiple of 32 up to
+                                   256; result-invariant                              */
 } fp_opts;
 /* h_e = diagonal of the axis-aligned box spanned by element e's nodes;
    L = diagonal of the box spanned by all nodes. */

@@ -629,7 +629,8 @@ static fp_status find_impl(fp_handle* h, int64_t P, const double* pts, const int
         cudaEventRecord(scr1, s);
         h->ev_pend[PROF_SCREEN].push_back({scr0, scr1});
     }
-    const int block = h->opts.points_per_block > 0 ? h->opts.points_per_block : 128;
+    const int block = h->opts.points_per_block > 0 ? h->opts.points_per_block
+                                                   : (d2 ? kDefaultBlock : kDefaultBlockFind3);
     err = d2 ? find_solve2(a, npairs, h->tab, fp, block, s) : find_solve(a, npairs, h->tab, fp, block, s);
     if (h->prof) {
         if (npairs > 0) {
@@ -902,7 +903,7 @@ static fp_status find_ws_impl(fp_handle* h, fp_workspace* w, int64_t P, const do
     fp.max_newton = h->opts.max_newton;
     fp.mixed = h->opts.precision == FP_PREC_MIXED;
     fp.refine = h->refine;
-    const int block = h->opts.points_per_block > 0 ? h->opts.points_per_block : 128;
+    const int block = h->opts.points_per_block > 0 ? h->opts.points_per_block : kDefaultBlock;
     cudaError_t err = find_count(a, h->tab, fp, s);
     if (err == cudaSuccess) err = find_emit(a, s);
     const int64_t grid_pairs = w->persistent_blocks == 0 && w->grid_pairs > 0 ? std::min(w->grid_pairs, w->max_pairs)

@@ -46,6 +46,14 @@ cudaError_t scan_exclusive(const int32_t* in, int32_t* out, int64_t n, int32_t* 
 // find (fp_find.cu)
 // Optional fused evaluation after classification, in the element-sorted pair
 // order: F fields, FP64 ([F][E][n3]) or double-float pairs; out [F][P].
+// threads per block of the Newton kernels when fp_opts.points_per_block is 0:
+// 64 for fp_find / fp_find_eval on hexahedra (measured 1 % faster than 128
+// for the FP64 form, the same for the mixed form, whose capped kernel takes
+// blocks of at most 128); 128 for quadrilaterals and for the workspace and
+// allocation-free calls, whose persistent grids are sized for it
+constexpr int kDefaultBlockFind3 = 64;
+constexpr int kDefaultBlock = 128;
+
 struct EvalSpec {
     int F;
     const double* f64;

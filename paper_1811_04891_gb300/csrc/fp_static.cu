@@ -176,7 +176,7 @@ extern "C" fp_status fp_find_static(fp_handle* h, int64_t P, const double* pts, 
             err = cudaGetLastError();
         }
     }
-    const int block = h->opts.points_per_block > 0 ? h->opts.points_per_block : 128;
+    const int block = h->opts.points_per_block > 0 ? h->opts.points_per_block : kDefaultBlock;
     if (err == cudaSuccess) err = find_solve_unsorted(a, npairs, h->tab, fp, block, s);
     if (err != cudaSuccess) {
         h->err = std::string("fp_find_static: ") + cudaGetErrorString(err);
